@@ -1,0 +1,334 @@
+"""Benchmark: exact stabilizer-term sums on GB300.
+
+One step = one full exact amplitude of the medium workload (n = 20 qubits,
+600 gates with 40 T gates, seeded random output bitstring): the sum of all
+2^k terms of its compiled parametric scalar on the GPU, result on the device
+(value) or on the host through the public API (e2e).  The circuit is reduced
+to the scalar once, before timing.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank sums its own
+copy of the workload: independent amplitudes, no collective on the data path
+(weak scaling); the timed region is bracketed by barriers and the slowest
+rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exact stabilizer terms/sec and amplitudes/sec (fraction of INT roofline)"
+SM_COUNT_GB300 = 152
+ISSUE_LANES_PER_SM_CLK = 4 * 32       # 4 schedulers x 1 warp-instruction x 32 lanes
+
+
+def alg_ops_per_term(node_words: int, other_words: int, n_pairs: int) -> int:
+    """Integer operations one term needs ('Roofline'):
+    Gray step (ctz, flip XORs, quadratic bit), node count, linear phase
+    planes, zero test, table fetch and the four 64-bit adds."""
+    nw = node_words + other_words
+    ops = 2 + nw + 4                 # ctz + loop, flip XORs, quadratic update
+    ops += 2 * node_words            # popc + add per node word
+    ops += 4 * other_words           # (and + popc) x 2 linear planes
+    ops += nw + 1                    # plane 2: and-xor per word, popc
+    ops += other_words               # zero test
+    ops += 4 + 3 + 8                 # J, table address + load, 4 x 64-bit add
+    ops += 40 * n_pairs              # 16 64-bit multiply-adds per phase-pair
+    return ops
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (clocks, throttle reasons)."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if "Active" in r[4 + i]
+                          and "Not" not in r[4 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def traffic_from_profile(kernel_src_sha: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "sum_kernel_medium.txt")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip()
+    if fields.get("kernel_source_sha256") != kernel_src_sha:
+        return None
+    try:
+        return float(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(blob: bytes, k: int, seconds: float = 10.0):
+    import oracle
+    cores = os.cpu_count() or 1
+    n = 1 << 14
+    t = time.perf_counter()
+    oracle.ps_sum(blob, 0, min(n, 1 << k), nthreads=cores)
+    dt = max(time.perf_counter() - t, 1e-6)
+    target = int(n * seconds / dt)
+    n = 1 << max(10, min(k, target.bit_length() - 1))
+    t = time.perf_counter()
+    oracle.ps_sum(blob, 0, n, nthreads=cores)
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": "terms/s", "cores": cores, "kind": "oracle",
+            "sample": f"Gray-index range [0, 2^{n.bit_length() - 1}) of the same scalar, "
+                      f"{dt:.1f} s on {cores} host threads"}
+
+
+def setup_dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    """The oracle on the host cores, bounded sample per step."""
+    if rank != 0:
+        return
+    import oracle
+    import paper_2403_06777_gb300 as Z
+    import zxp_inputs as zi
+    w = zi.workload_medium(args.seed)
+    s = Z.zxp_compile(w.gates, w.n, w.out_bits)
+    blob = Z.zxp_scalar_to_tables(s)
+    k = Z.zxp_scalar_info(s)["k"]
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    oracle.ps_sum(blob, 0, 1 << 12, nthreads=cores)
+    per_term = (time.perf_counter() - t) / (1 << 12)
+    total_budget = 150.0
+    n = 1 << max(8, min(k, int(total_budget / max(1, args.steps + args.warmup) / per_term).bit_length() - 1))
+    for i in range(args.warmup):
+        oracle.ps_sum(blob, 0, n, nthreads=cores)
+    t = time.perf_counter()
+    for i in range(args.steps):
+        first = (i * n) % ((1 << k) - n + 1)
+        oracle.ps_sum(blob, first, n, nthreads=cores)
+    dt = time.perf_counter() - t
+    v = n * args.steps / dt
+    sample = f"{n} terms (2^{n.bit_length() - 1}) of the 2^{k}-term scalar per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "terms/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int128",
+        "data": "synthetic",
+        "config": {"workload": w.name + f" seed={args.seed} (k={k})", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "terms/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world, rank, local = setup_dist()
+
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    import paper_2403_06777_gb300 as Z
+    import zxp_inputs as zi
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    stream = torch.cuda.current_stream()
+    ctx = Z.zxp_ctx_create(local, stream.cuda_stream)
+
+    w = zi.workload_medium(args.seed)
+    t0 = time.perf_counter()
+    s = Z.zxp_compile(w.gates, w.n, w.out_bits)
+    compile_ms = (time.perf_counter() - t0) * 1e3
+    info = Z.zxp_scalar_info(s)
+    k = info["k"]
+    terms = 1 << k
+    blob = Z.zxp_scalar_to_tables(s)
+
+    out = torch.zeros(5, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+
+    for _ in range(args.warmup):
+        Z.zxp_eval_device(ctx, s, 0, terms, out.data_ptr())
+    torch.cuda.synchronize()
+    ref = Z.zxp_amplitude(ctx, s)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()                           # L2 flushed between timed steps
+            starts[i].record(stream)
+            Z.zxp_eval_device(ctx, s, 0, terms, out.data_ptr())
+            stops[i].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    kernel_ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops))
+    # the device result of the last step must be the exact amplitude
+    r = out.tolist()
+    got = Z.zxp_zomega_canon((r[0], r[1], r[2], r[3], r[4] & 0xFFFFFFFF))
+    assert got == ref, (got, ref)
+    t_rank = torch.tensor([kernel_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
+    kernel_ms = float(t_rank.item())
+    sec = kernel_ms / 1e3
+    value = terms * args.steps * world / sec
+    amps = args.steps * world / sec
+    per_launch_s = sec / args.steps
+
+    # e2e: public host API each step: tables -> scalar (host plan, H2D of the
+    # tables on first use), full sum, D2H of the 40-byte result
+    e2e_steps = max(10, min(args.steps, 50))
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        s2 = Z.zxp_scalar_from_tables(blob)
+        Z.zxp_amplitude(ctx, s2)
+        s2.free()
+    e2e_sec = (time.perf_counter() - t) / e2e_steps
+    table_bytes = 8 * 32 * (info["n_node"] + 1) + 4 * 32 * info["n_pair"] + 5 * 1024
+
+    # large scalar: k = 36 synthetic tables with compiled statistics (the
+    # compiled n = 50 / t = 80 circuit needs k ~ 50, out of reach)
+    large = None
+    if rank == 0 and not os.environ.get("ZXP_BENCH_SKIP_LARGE"):
+        ps36 = zi.synthetic_ps(36, 36, n_lin=45, n_quad=30, n_node=20, odd_nodes_only=True,
+                               density=0.12)
+        s36 = Z.zxp_scalar_from_tables(ps36.pack())
+        i36 = Z.zxp_scalar_info(s36)
+        Z.zxp_eval_device(ctx, s36, 0, 1 << 30, out.data_ptr())
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        Z.zxp_eval_device(ctx, s36, 0, 1 << 36, out.data_ptr())
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms36 = a.elapsed_time(b)
+        large = {"workload": "synthetic k=36 (45 linear, 30 quadratic, 20 odd-node rows)",
+                 "terms": 1 << 36, "ms": ms36, "terms_per_s": (1 << 36) / (ms36 / 1e3),
+                 "node_words": i36["node_words"], "other_words": i36["other_words"]}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    clocks = clk.summary()
+    ops = alg_ops_per_term(info["node_words"], info["other_words"], info["n_pair"])
+    f_hz = 2070e6
+    peak = SM_COUNT_GB300 * ISSUE_LANES_PER_SM_CLK * f_hz / 1e9          # Gop/s
+    achieved = ops * terms / per_launch_s / 1e9
+    src = open(os.path.join(ROOT, "paper_2403_06777_gb300", "csrc", "kernel.cu"), "rb").read()
+    sha = hashlib.sha256(src).hexdigest()
+    traffic = traffic_from_profile(sha)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": kernel_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": f"{w.name} seed={args.seed}: one exact amplitude per step",
+                   "k": k, "terms_per_step": terms, "t_count": info["t_count"],
+                   "compile_ms": compile_ms, "l2": "flushed (256 MB write) between timed steps",
+                   "parallelism": f"replicas x{world}"},
+        "amplitudes_per_s": amps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "ops_per_term": ops,
+                     "peak_basis": "issue: 152 SM x 4 warp-instr/clk x 32 lanes x 2070 MHz"},
+        "e2e": {"value": terms / e2e_sec, "unit": "terms/s", "amplitudes_per_s": 1 / e2e_sec,
+                "h2d_bytes_per_step": table_bytes, "d2h_bytes_per_step": 40},
+        "clocks": clocks,
+        "gpu_launches": args.steps,
+        "wall_s_timed_region": wall,
+    }
+    if large:
+        line["large"] = large
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(blob, k)
+    print(json.dumps(line))
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * zxp.h -- C ABI of libzxp: exact parametric-ZX stabilizer sums on GB300.
+ *
+ * Method: Sutcliffe & Kissinger, "Fast Classical Simulation of Quantum
+ * Circuits via Parametric Rewriting in the ZX-Calculus" (QPL 2024).  A
+ * Clifford+T amplitude (Sec. 2.2) is reduced once, on the host, to a
+ * parametric scalar (Eq. 2) whose parameters are k Boolean decomposition
+ * bits; the library then sums that scalar over all 2^k assignments on the
+ * GPU, exactly, in the ring Z[w]/sqrt2^e (w = e^{i pi/4}).
+ *
+ * Conventions.
+ *   - Scalars are (c0 + c1 w + c2 w^2 + c3 w^3) / sqrt2^e with c_j int64.
+ *   - Qubit q <-> bit q of a basis index; out_bits[q] is qubit q's value.
+ *   - Gates: H = (1/sqrt2)[[1,1],[1,-1]], S = diag(1,i), T = diag(1,w),
+ *     CNOT(q0 = control, q1 = target), CZ(q0, q1); Sdg, Tdg their inverses.
+ *   - The term of Gray-code index t in [0, 2^k) is the assignment
+ *     x = t ^ (t >> 1); a range [first, first+count) sums those terms.
+ *
+ * Ownership.  Callers own every array they pass (copied during the call).
+ * The library owns zxp_scalar and zxp_ctx objects (free with the matching
+ * *_free / *_destroy).  Device memory is allocated by the library.
+ *
+ * Errors.  Every int-returning function returns ZXP_OK (0) or a negative
+ * zxp_status; zxp_strerror() names it.  No function aborts the process.
+ *
+ * Threads.  A zxp_ctx may be used from one thread at a time; distinct
+ * contexts (on one or several devices) are independent.  zxp_scalar objects
+ * are read-only after creation and may be shared.
+ */
+#ifndef ZXP_C_API_H
+#define ZXP_C_API_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ZXP_OK = 0,
+    ZXP_EINVAL = -1,     /* bad argument: qubit, opcode, range beyond 2^k, blob */
+    ZXP_ENOMEM = -2,     /* host or device allocation failed */
+    ZXP_ETOOBIG = -3,    /* k > 62 or a table exceeds the kernel's limits */
+    ZXP_EOVERFLOW = -4,  /* exponent e too large for exact 64-bit numerators */
+    ZXP_ECUDA = -5,      /* a CUDA runtime error (no device, launch failure) */
+    ZXP_ETIMEDOUT = -6,  /* a wait budget expired */
+    ZXP_EAGAIN = -7,     /* zxp_poll: not finished yet */
+    ZXP_ENOTFOUND = -8   /* zxp_poll: unknown ticket */
+} zxp_status;
+
+/* Exact scalar (c0 + c1 w + c2 w^2 + c3 w^3) / sqrt2^e.  `flags` bit 0 is
+ * set on a raw (not yet canonical) range partial. */
+typedef struct zxp_zomega {
+    int64_t c[4];
+    int32_t e;
+    int32_t flags;
+} zxp_zomega;
+
+typedef enum {
+    ZXP_H = 0, ZXP_S = 1, ZXP_T = 2, ZXP_CNOT = 3, ZXP_SDG = 4, ZXP_TDG = 5,
+    ZXP_X = 6, ZXP_Z = 7, ZXP_CZ = 8
+} zxp_op;
+
+/* 8-byte gate record: op (zxp_op), q0 (qubit or control), q1 (target). */
+typedef struct zxp_gate {
+    uint8_t op;
+    uint8_t reserved0;
+    uint16_t q0, q1;
+    uint16_t reserved1;
+} zxp_gate;
+
+typedef enum { ZXP_AMPLITUDE = 0, ZXP_MARGINAL_DOUBLED = 1 } zxp_kind;
+
+typedef struct zxp_scalar zxp_scalar;  /* compiled parametric scalar */
+typedef struct zxp_ctx zxp_ctx;        /* device + stream + workspaces */
+
+/* Statistics of a compiled scalar. */
+typedef struct {
+    uint32_t k;          /* Boolean parameters: the sum has 2^k terms */
+    uint32_t n_lin;      /* linear phase rows (pi-pair rows with fixed Psi) */
+    uint32_t n_quad;     /* quadratic rows (pi-pair rows, two parametric phases) */
+    uint32_t n_node;     /* node rows (1 + e^{i Psi}) */
+    uint32_t n_pair;     /* phase-pair rows (Eq. 3) */
+    int32_t e0;          /* sqrt2 exponent of the denominator */
+    uint32_t acc_bits;   /* 64: int64 numerators are provably exact */
+    uint32_t form_bits;  /* parity forms the kernel tracks per term */
+    uint32_t t_count;    /* T-like gates in the input (0 for tables) */
+    uint32_t node_words; /* 32-bit words of odd-node form bits per term */
+    uint32_t other_words;/* 32-bit words of linear / zero / pair form bits */
+    uint32_t reserved[5];
+} zxp_scalar_info_t;
+
+/* ---- context --------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (e.g. a torch stream handle) or NULL for a stream the context creates.
+ * Returns ZXP_ECUDA when no usable device is present. */
+int zxp_ctx_create(int device, void *cuda_stream, zxp_ctx **out);
+void zxp_ctx_destroy(zxp_ctx *ctx);
+
+/* ---- compile (host only, Sec. 3.1-3.2) -------------------------------- */
+
+/* Reduce a circuit to a parametric scalar.
+ *   kind = ZXP_AMPLITUDE:          value = <out_bits| C |in_bits>
+ *   kind = ZXP_MARGINAL_DOUBLED:   value = <in| C^dag (|b><b|_mask (x) I) C |in>,
+ *        the probability that every qubit q in marg_mask reads out_bits[q]
+ *        (the doubled diagram of Sec. 2.2; n_qubits <= 64).
+ * in_bits may be NULL (all zero).  Arrays have n_qubits entries (0 or 1).
+ * Errors: ZXP_EINVAL (qubit out of range, opcode, CNOT with q0 == q1),
+ * ZXP_ETOOBIG (the reduction leaves more than 62 parameters). */
+int zxp_compile(const zxp_gate *gates, size_t n_gates, int n_qubits,
+                const uint8_t *in_bits, const uint8_t *out_bits,
+                uint64_t marg_mask, int kind, zxp_scalar **out);
+
+/* Build a scalar from the table layout (little endian):
+ *   header  u32 magic 'ZXPS' (0x5350585A), u32 version 1, u32 k, u32 n_lin,
+ *           u32 n_quad, u32 n_node, u32 n_pair, i32 e0, i64 G[4]
+ *   n_lin  x {u64 mask, u32 c, u32 0}        -> w^(c * l(x))
+ *   n_quad x {u64 maskA, u64 maskB}          -> w^(4 lA(x) lB(x))
+ *   n_node x {u64 mask, u32 g, u32 0}        -> 1 + w^(g + 4 l(x))
+ *   n_pair x {u64 maskA, u64 maskB, u32 a, u32 b}
+ *            -> 1 + w^(a+4lA) + w^(b+4lB) - w^(a+b+4(lA^lB))      (Eq. 3)
+ * with l(x) = parity(mask & x); value = G / sqrt2^e0 * sum over x of the
+ * product of all rows (Eq. 2).  Masks may not use bits >= k; k <= 62. */
+int zxp_scalar_from_tables(const void *blob, size_t nbytes, zxp_scalar **out);
+/* Write the table layout; *nbytes in: capacity, out: size needed.  With
+ * buf == NULL only the size is returned. */
+int zxp_scalar_to_tables(const zxp_scalar *s, void *buf, size_t *nbytes);
+int zxp_scalar_info(const zxp_scalar *s, zxp_scalar_info_t *info);
+void zxp_scalar_free(zxp_scalar *s);
+
+/* ---- evaluate (GPU, Sec. 3.3) ------------------------------------------ */
+
+/* Sum the terms with Gray-code index in [first, first + count), multiplied
+ * by G, into *out as a raw partial over sqrt2^e0 (flags bit 0 set).  The
+ * call blocks until the result is on the host.  Partials of disjoint
+ * ranges combine with zxp_zomega_add; the total over [0, 2^k) gives the
+ * scalar after zxp_zomega_canon.  Errors: ZXP_EINVAL (range beyond 2^k),
+ * ZXP_ECUDA. */
+int zxp_eval(zxp_ctx *ctx, const zxp_scalar *s, uint64_t first, uint64_t count,
+             zxp_zomega *out);
+
+/* Device-side form of zxp_eval: queue the range on the context's stream
+ * and write the raw partial (the 40-byte zxp_zomega layout, flags bit 0
+ * set) to `dev_out`, a device pointer aligned to 8 bytes.  Returns without
+ * waiting; the value is ready when the context's stream reaches this point
+ * (synchronise that stream, or order work after it).  The call reuses the
+ * context's workspace, so calls on one context must not overlap in time on
+ * different streams.  Errors: ZXP_EINVAL (range, null or unaligned
+ * pointer), ZXP_ECUDA. */
+int zxp_eval_device(zxp_ctx *ctx, const zxp_scalar *s, uint64_t first, uint64_t count,
+                    zxp_zomega *dev_out);
+
+/* The whole sum over [0, 2^k), canonical.  Errors as zxp_eval, plus
+ * ZXP_EOVERFLOW when e0 > 124 (64-bit numerators not provably exact). */
+int zxp_amplitude(zxp_ctx *ctx, const zxp_scalar *s, zxp_zomega *out);
+
+/* Asynchronous form of zxp_eval: queue the range on the context's stream
+ * and return a ticket.  The scalar must stay alive until the ticket is
+ * polled to completion. */
+int zxp_submit(zxp_ctx *ctx, const zxp_scalar *s, uint64_t first, uint64_t count,
+               uint64_t *ticket);
+/* Wait up to timeout_us (0: do not wait, < 0: wait without limit) for a
+ * ticket.  ZXP_OK: *out holds the raw partial and the ticket is released.
+ * ZXP_EAGAIN: not finished.  ZXP_ENOTFOUND: unknown ticket. */
+int zxp_poll(zxp_ctx *ctx, uint64_t ticket, int64_t timeout_us, zxp_zomega *out);
+
+/* ---- exact scalar helpers (host) ---------------------------------------- */
+
+/* a + b, after bringing both to the larger exponent (x sqrt2 per step). */
+int zxp_zomega_add(const zxp_zomega *a, const zxp_zomega *b, zxp_zomega *out);
+/* Canonical form: divide by sqrt2 while e > 0 and the numerator allows;
+ * zero is (0,0,0,0; e = 0). */
+int zxp_zomega_canon(const zxp_zomega *in, zxp_zomega *out);
+void zxp_zomega_to_complex(const zxp_zomega *z, double *re, double *im);
+
+const char *zxp_strerror(int status);
+/* "zxp <version> sm_103a" */
+const char *zxp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZXP_C_API_H */

@@ -1,0 +1,281 @@
+"""Python binding of libzxp (argument marshalling only).
+
+Every function keeps the C name of include/zxp.h.  The library must have
+been built (``paper_2403_06777_gb300._build.build()`` or
+``__graft_entry__.build()``); importing the package does not build it, and
+every call fails with an error when the shared object is missing.  There is
+no CPU fallback: GPU entry points raise ``ZxpError`` (ZXP_ECUDA) without a
+device.
+
+Scalars are returned as tuples ``(c0, c1, c2, c3, e)`` meaning
+(c0 + c1 w + c2 w^2 + c3 w^3) / sqrt2^e with w = exp(i pi/4).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Iterable, Sequence, Tuple
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libzxp.so")
+
+ZXP_OK, ZXP_EINVAL, ZXP_ENOMEM, ZXP_ETOOBIG, ZXP_EOVERFLOW = 0, -1, -2, -3, -4
+ZXP_ECUDA, ZXP_ETIMEDOUT, ZXP_EAGAIN, ZXP_ENOTFOUND = -5, -6, -7, -8
+ZXP_AMPLITUDE, ZXP_MARGINAL_DOUBLED = 0, 1
+
+
+class ZxpError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {zxp_strerror(code)} ({code})" if what else zxp_strerror(code))
+
+
+class zxp_zomega(C.Structure):
+    _fields_ = [("c", C.c_int64 * 4), ("e", C.c_int32), ("flags", C.c_int32)]
+
+    def tup(self) -> Tuple[int, int, int, int, int]:
+        return (self.c[0], self.c[1], self.c[2], self.c[3], self.e)
+
+
+class zxp_scalar_info_t(C.Structure):
+    _fields_ = [("k", C.c_uint32), ("n_lin", C.c_uint32), ("n_quad", C.c_uint32),
+                ("n_node", C.c_uint32), ("n_pair", C.c_uint32), ("e0", C.c_int32),
+                ("acc_bits", C.c_uint32), ("form_bits", C.c_uint32), ("t_count", C.c_uint32),
+                ("node_words", C.c_uint32), ("other_words", C.c_uint32),
+                ("reserved", C.c_uint32 * 5)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libzxp (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libzxp.so is not built ({LIB_PATH}); run "
+                              "paper_2403_06777_gb300._build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, u64, i64, sz = C.c_void_p, C.c_uint64, C.c_int64, C.c_size_t
+        zp = C.POINTER(zxp_zomega)
+        L.zxp_strerror.argtypes, L.zxp_strerror.restype = [C.c_int], C.c_char_p
+        L.zxp_version.argtypes, L.zxp_version.restype = [], C.c_char_p
+        L.zxp_ctx_create.argtypes = [C.c_int, vp, C.POINTER(vp)]
+        L.zxp_ctx_destroy.argtypes, L.zxp_ctx_destroy.restype = [vp], None
+        L.zxp_compile.argtypes = [C.c_char_p, sz, C.c_int, C.c_char_p, C.c_char_p, u64, C.c_int,
+                                  C.POINTER(vp)]
+        L.zxp_scalar_from_tables.argtypes = [C.c_char_p, sz, C.POINTER(vp)]
+        L.zxp_scalar_to_tables.argtypes = [vp, vp, C.POINTER(sz)]
+        L.zxp_scalar_info.argtypes = [vp, C.POINTER(zxp_scalar_info_t)]
+        L.zxp_scalar_free.argtypes, L.zxp_scalar_free.restype = [vp], None
+        L.zxp_eval.argtypes = [vp, vp, u64, u64, zp]
+        L.zxp_amplitude.argtypes = [vp, vp, zp]
+        L.zxp_eval_device.argtypes = [vp, vp, u64, u64, vp]
+        L.zxp_submit.argtypes = [vp, vp, u64, u64, C.POINTER(u64)]
+        L.zxp_poll.argtypes = [vp, u64, i64, zp]
+        L.zxp_zomega_add.argtypes = [zp, zp, zp]
+        L.zxp_zomega_canon.argtypes = [zp, zp]
+        L.zxp_zomega_to_complex.argtypes = [zp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.zxp_zomega_to_complex.restype = None
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != ZXP_OK:
+        raise ZxpError(rc, what)
+
+
+def _z(v) -> zxp_zomega:
+    z = zxp_zomega()
+    for i in range(4):
+        x = int(v[i]) & ((1 << 64) - 1)
+        z.c[i] = x - (1 << 64) if x >> 63 else x
+    z.e = int(v[4]) if len(v) > 4 else 0
+    return z
+
+
+def zxp_strerror(code: int) -> str:
+    try:
+        return lib().zxp_strerror(code).decode()
+    except ImportError:
+        return f"status {code}"
+
+
+def zxp_version() -> str:
+    return lib().zxp_version().decode()
+
+
+class Ctx:
+    """A zxp_ctx: device, stream and workspaces (zxp_ctx_destroy on close)."""
+
+    def __init__(self, handle: int, device: int):
+        self.handle = C.c_void_p(handle)
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            lib().zxp_ctx_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Scalar:
+    """A compiled parametric scalar (zxp_scalar_free on deletion)."""
+
+    def __init__(self, handle: int):
+        self.handle = C.c_void_p(handle)
+
+    def free(self):
+        if self.handle:
+            lib().zxp_scalar_free(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def info(self) -> dict:
+        return zxp_scalar_info(self)
+
+
+def zxp_ctx_create(device: int = 0, cuda_stream: int | None = None) -> Ctx:
+    """cuda_stream: a cudaStream_t as an integer (torch: stream.cuda_stream)."""
+    h = C.c_void_p()
+    _check(lib().zxp_ctx_create(device, C.c_void_p(cuda_stream) if cuda_stream else None,
+                                C.byref(h)), "zxp_ctx_create")
+    return Ctx(h.value, device)
+
+
+def zxp_ctx_destroy(ctx: Ctx):
+    ctx.close()
+
+
+def _gate_bytes(gates) -> bytes:
+    if isinstance(gates, (bytes, bytearray)):
+        return bytes(gates)
+    import struct
+    st = struct.Struct("<BBHHH")
+    return b"".join(st.pack(op, 0, q0, q1, 0) for op, q0, q1 in gates)
+
+
+def zxp_compile(gates, n_qubits: int, out_bits: Sequence[int],
+                in_bits: Sequence[int] | None = None, marg_mask: int = 0,
+                kind: int = ZXP_AMPLITUDE) -> Scalar:
+    gb = _gate_bytes(gates)
+    h = C.c_void_p()
+    ib = bytes(int(b) & 1 for b in in_bits) if in_bits is not None else None
+    ob = bytes(int(b) & 1 for b in out_bits)
+    if len(ob) != n_qubits or (ib is not None and len(ib) != n_qubits):
+        raise ZxpError(ZXP_EINVAL, "zxp_compile: bit arrays must have n_qubits entries")
+    _check(lib().zxp_compile(gb, len(gb) // 8, n_qubits, ib, ob, marg_mask, kind, C.byref(h)),
+           "zxp_compile")
+    return Scalar(h.value)
+
+
+def zxp_scalar_from_tables(blob: bytes) -> Scalar:
+    h = C.c_void_p()
+    _check(lib().zxp_scalar_from_tables(blob, len(blob), C.byref(h)), "zxp_scalar_from_tables")
+    return Scalar(h.value)
+
+
+def zxp_scalar_to_tables(s: Scalar) -> bytes:
+    n = C.c_size_t(0)
+    _check(lib().zxp_scalar_to_tables(s.handle, None, C.byref(n)), "zxp_scalar_to_tables")
+    buf = C.create_string_buffer(n.value)
+    _check(lib().zxp_scalar_to_tables(s.handle, buf, C.byref(n)), "zxp_scalar_to_tables")
+    return buf.raw[:n.value]
+
+
+def zxp_scalar_info(s: Scalar) -> dict:
+    info = zxp_scalar_info_t()
+    _check(lib().zxp_scalar_info(s.handle, C.byref(info)), "zxp_scalar_info")
+    return {f: getattr(info, f) for f, _ in zxp_scalar_info_t._fields_ if f != "reserved"}
+
+
+def zxp_scalar_free(s: Scalar):
+    s.free()
+
+
+def zxp_eval(ctx: Ctx, s: Scalar, first: int = 0, count: int | None = None):
+    """Raw partial (c0, c1, c2, c3, e0) of the Gray-index range (default: all)."""
+    if count is None:
+        count = (1 << zxp_scalar_info(s)["k"]) - first
+    out = zxp_zomega()
+    _check(lib().zxp_eval(ctx.handle, s.handle, first, count, C.byref(out)), "zxp_eval")
+    return out.tup()
+
+
+def zxp_eval_device(ctx: Ctx, s: Scalar, first: int, count: int, dev_out_ptr: int):
+    """Queue the range; the raw partial (40-byte zxp_zomega) lands at the
+    device address dev_out_ptr (e.g. tensor.data_ptr() of 5 int64) when the
+    context's stream reaches it.  Does not wait."""
+    _check(lib().zxp_eval_device(ctx.handle, s.handle, first, count, C.c_void_p(dev_out_ptr)),
+           "zxp_eval_device")
+
+
+def zxp_amplitude(ctx: Ctx, s: Scalar):
+    """The whole sum, canonical (c0, c1, c2, c3, e)."""
+    out = zxp_zomega()
+    _check(lib().zxp_amplitude(ctx.handle, s.handle, C.byref(out)), "zxp_amplitude")
+    return out.tup()
+
+
+def zxp_submit(ctx: Ctx, s: Scalar, first: int = 0, count: int | None = None) -> int:
+    if count is None:
+        count = (1 << zxp_scalar_info(s)["k"]) - first
+    t = C.c_uint64()
+    _check(lib().zxp_submit(ctx.handle, s.handle, first, count, C.byref(t)), "zxp_submit")
+    return t.value
+
+
+def zxp_poll(ctx: Ctx, ticket: int, timeout_us: int = -1):
+    """Raw partial of a ticket, or None while it is not finished."""
+    out = zxp_zomega()
+    rc = lib().zxp_poll(ctx.handle, ticket, timeout_us, C.byref(out))
+    if rc == ZXP_EAGAIN:
+        return None
+    _check(rc, "zxp_poll")
+    return out.tup()
+
+
+def zxp_zomega_add(a, b):
+    out = zxp_zomega()
+    za, zb = _z(a), _z(b)
+    _check(lib().zxp_zomega_add(C.byref(za), C.byref(zb), C.byref(out)), "zxp_zomega_add")
+    return out.tup()
+
+
+def zxp_zomega_canon(a):
+    out = zxp_zomega()
+    za = _z(a)
+    _check(lib().zxp_zomega_canon(C.byref(za), C.byref(out)), "zxp_zomega_canon")
+    return out.tup()
+
+
+def zxp_zomega_to_complex(a) -> complex:
+    re, im = C.c_double(), C.c_double()
+    za = _z(a)
+    lib().zxp_zomega_to_complex(C.byref(za), C.byref(re), C.byref(im))
+    return complex(re.value, im.value)
+
+
+EXPORTED = ["zxp_ctx_create", "zxp_ctx_destroy", "zxp_compile", "zxp_scalar_from_tables",
+            "zxp_scalar_to_tables", "zxp_scalar_info", "zxp_scalar_free", "zxp_eval",
+            "zxp_eval_device",
+            "zxp_amplitude", "zxp_submit", "zxp_poll", "zxp_zomega_add", "zxp_zomega_canon",
+            "zxp_zomega_to_complex", "zxp_strerror", "zxp_version"]

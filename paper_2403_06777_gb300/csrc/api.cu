@@ -1,0 +1,426 @@
+// api.cu -- the C ABI of libzxp (include/zxp.h).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <chrono>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "../../include/zxp.h"
+#include "compile.h"
+#include "kernel.h"
+#include "plan.h"
+#include "ps.h"
+#include "zring.h"
+
+using namespace zxp;
+
+static_assert(sizeof(DevResult) == sizeof(zxp_zomega), "result record layout");
+
+namespace {
+
+struct DevTables {
+    zw64* table = nullptr;
+    zw64* pv = nullptr;
+};
+
+}  // namespace
+
+struct zxp_scalar {
+    PS ps;
+    Plan plan;
+    int plan_status = ZXP_OK;
+    mutable std::mutex mu;
+    mutable std::map<int, DevTables> dev;   // per-device copies of the tables
+
+    ~zxp_scalar() {
+        int prev = -1;
+        cudaGetDevice(&prev);
+        for (auto& e : dev) {
+            cudaSetDevice(e.first);
+            cudaFree(e.second.table);
+            cudaFree(e.second.pv);
+        }
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+namespace {
+
+struct Ticket {
+    DevResult* dres = nullptr;   // device result slot
+    DevResult* hres = nullptr;   // pinned host slot
+    cudaEvent_t ev = nullptr;
+    int32_t e0 = 0;
+    bool trivial = false;        // no launch: the value is zero
+};
+
+}  // namespace
+
+struct zxp_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sm_count = 0;
+    int max_grid = 0;
+    zw64* partials = nullptr;
+    unsigned int* counter = nullptr;
+    DevResult* dres = nullptr;
+    DevResult* hres = nullptr;
+    uint64_t next_ticket = 1;
+    std::map<uint64_t, Ticket> tickets;
+    std::vector<Ticket> free_slots;
+};
+
+namespace {
+
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
+        if (prev_ != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev_ >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev_) cudaSetDevice(prev_);
+    }
+
+  private:
+    int prev_ = -1;
+};
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? ZXP_OK : ZXP_ECUDA; }
+
+zw64 to_zw(const zxp_zomega& z) {
+    return zw_make((uint64_t)z.c[0], (uint64_t)z.c[1], (uint64_t)z.c[2], (uint64_t)z.c[3]);
+}
+void from_zw(const zw64& v, int32_t e, int32_t flags, zxp_zomega* out) {
+    for (int i = 0; i < 4; i++) out->c[i] = (int64_t)v.c[i];
+    out->e = e;
+    out->flags = flags;
+}
+
+int ensure_device_tables(const zxp_scalar* s, int device, DevTables* out) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->dev.find(device);
+    if (it != s->dev.end()) { *out = it->second; return ZXP_OK; }
+    DevTables d;
+    const Plan& pl = s->plan;
+    size_t tb = pl.table.size() * sizeof(zw64), pb = pl.pv.size() * sizeof(zw64);
+    if (cudaMalloc(&d.table, tb ? tb : sizeof(zw64)) != cudaSuccess) return ZXP_ENOMEM;
+    if (cudaMalloc(&d.pv, pb ? pb : sizeof(zw64)) != cudaSuccess) { cudaFree(d.table); return ZXP_ENOMEM; }
+    if (tb && cudaMemcpy(d.table, pl.table.data(), tb, cudaMemcpyHostToDevice) != cudaSuccess) return ZXP_ECUDA;
+    if (pb && cudaMemcpy(d.pv, pl.pv.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess) return ZXP_ECUDA;
+    s->dev[device] = d;
+    *out = d;
+    return ZXP_OK;
+}
+
+uint64_t next_pow2(uint64_t v) {
+    uint64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// Slice length and grid for `count` terms.
+void launch_shape(const zxp_ctx* ctx, const Plan& pl, uint64_t count, uint64_t* span, int* grid) {
+    int bps = 1;
+    if (sum_occupancy(pl, &bps) != cudaSuccess || bps < 1) bps = 1;
+    int max_grid = ctx->sm_count * bps;
+    if (max_grid > ctx->max_grid) max_grid = ctx->max_grid;
+    const uint64_t threads = (uint64_t)max_grid * (uint64_t)sum_threads();
+    uint64_t sp = next_pow2((count + threads * 4 - 1) / (threads * 4));
+    if (sp < 64) sp = 64;
+    if (sp > (1ull << 20)) sp = 1ull << 20;
+    const uint64_t nslices = (count + sp - 1) / sp;
+    uint64_t g = (nslices + (uint64_t)sum_threads() - 1) / (uint64_t)sum_threads();
+    if (g > (uint64_t)max_grid) g = (uint64_t)max_grid;
+    if (g < 1) g = 1;
+    *span = sp;
+    *grid = (int)g;
+}
+
+int check_range(const zxp_scalar* s, uint64_t first, uint64_t count) {
+    const uint64_t total = 1ull << s->ps.k;
+    if (first > total || count > total - first) return ZXP_EINVAL;
+    return ZXP_OK;
+}
+
+// Queue one range on ctx->stream: the raw partial into dres.
+int enqueue(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, DevResult* dres) {
+    DevTables d;
+    int st = ensure_device_tables(s, ctx->device, &d);
+    if (st != ZXP_OK) return st;
+    uint64_t span;
+    int grid;
+    launch_shape(ctx, s->plan, count, &span, &grid);
+    return cuda_status(sum_launch(s->plan, d.table, d.pv, first, count, span, grid, ctx->partials,
+                                  ctx->counter, dres, ctx->stream));
+}
+
+// canonical form of an exact numerator (int64 coefficients) over sqrt2^e
+void canon_i128(__int128 c[4], int32_t* e) {
+    if (!c[0] && !c[1] && !c[2] && !c[3]) { *e = 0; return; }
+    while (*e > 0 && ((c[0] - c[2]) & 1) == 0 && ((c[1] - c[3]) & 1) == 0) {
+        __int128 n0 = c[1] - c[3], n1 = c[0] + c[2], n2 = c[1] + c[3], n3 = c[2] - c[0];
+        c[0] = n0 / 2; c[1] = n1 / 2; c[2] = n2 / 2; c[3] = n3 / 2;
+        *e -= 1;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* zxp_strerror(int status) {
+    switch (status) {
+    case ZXP_OK: return "ok";
+    case ZXP_EINVAL: return "invalid argument";
+    case ZXP_ENOMEM: return "out of memory";
+    case ZXP_ETOOBIG: return "problem exceeds the kernel's limits (k > 62 or too many forms)";
+    case ZXP_EOVERFLOW: return "sqrt2 exponent too large for exact 64-bit numerators";
+    case ZXP_ECUDA: return "CUDA error";
+    case ZXP_ETIMEDOUT: return "timed out";
+    case ZXP_EAGAIN: return "not finished";
+    case ZXP_ENOTFOUND: return "unknown ticket";
+    default: return "unknown status";
+    }
+}
+
+const char* zxp_version(void) { return "zxp 0.1 sm_103a"; }
+
+int zxp_ctx_create(int device, void* cuda_stream, zxp_ctx** out) {
+    if (!out) return ZXP_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return ZXP_ECUDA;
+    if (device < 0 || device >= ndev) return ZXP_EINVAL;
+    DeviceGuard g(device);
+    std::unique_ptr<zxp_ctx> c(new (std::nothrow) zxp_ctx());
+    if (!c) return ZXP_ENOMEM;
+    c->device = device;
+    if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return ZXP_ECUDA;
+    c->max_grid = c->sm_count * 16;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return ZXP_ECUDA;
+        c->own_stream = true;
+    }
+    if (cudaMalloc(&c->partials, sizeof(zw64) * (size_t)c->max_grid) != cudaSuccess) return ZXP_ENOMEM;
+    if (cudaMalloc(&c->counter, sizeof(unsigned int)) != cudaSuccess) return ZXP_ENOMEM;
+    if (cudaMemset(c->counter, 0, sizeof(unsigned int)) != cudaSuccess) return ZXP_ECUDA;
+    if (cudaMalloc(&c->dres, sizeof(DevResult)) != cudaSuccess) return ZXP_ENOMEM;
+    if (cudaMallocHost(&c->hres, sizeof(DevResult)) != cudaSuccess) return ZXP_ENOMEM;
+    *out = c.release();
+    return ZXP_OK;
+}
+
+void zxp_ctx_destroy(zxp_ctx* c) {
+    if (!c) return;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto& e : c->tickets) c->free_slots.push_back(e.second);
+    for (auto& t : c->free_slots) {
+        cudaFree(t.dres);
+        cudaFreeHost(t.hres);
+        if (t.ev) cudaEventDestroy(t.ev);
+    }
+    cudaFree(c->partials);
+    cudaFree(c->counter);
+    cudaFree(c->dres);
+    cudaFreeHost(c->hres);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+static int finish_scalar(PS&& ps, zxp_scalar** out) {
+    std::unique_ptr<zxp_scalar> s(new (std::nothrow) zxp_scalar());
+    if (!s) return ZXP_ENOMEM;
+    s->ps = std::move(ps);
+    s->plan_status = build_plan(s->ps, &s->plan);
+    if (s->plan_status != ZXP_OK) return s->plan_status;
+    *out = s.release();
+    return ZXP_OK;
+}
+
+int zxp_compile(const zxp_gate* gates, size_t n_gates, int n_qubits, const uint8_t* in_bits,
+                const uint8_t* out_bits, uint64_t marg_mask, int kind, zxp_scalar** out) {
+    if (!out) return ZXP_EINVAL;
+    *out = nullptr;
+    PS ps;
+    CompileOptions opt;
+    int st = compile_circuit(gates, n_gates, n_qubits, in_bits, out_bits, marg_mask, kind, opt, &ps);
+    if (st != ZXP_OK) return st;
+    return finish_scalar(std::move(ps), out);
+}
+
+int zxp_scalar_from_tables(const void* blob, size_t nbytes, zxp_scalar** out) {
+    if (!out) return ZXP_EINVAL;
+    *out = nullptr;
+    PS ps;
+    int st = ps_from_blob(blob, nbytes, &ps);
+    if (st != ZXP_OK) return st;
+    return finish_scalar(std::move(ps), out);
+}
+
+int zxp_scalar_to_tables(const zxp_scalar* s, void* buf, size_t* nbytes) {
+    if (!s || !nbytes) return ZXP_EINVAL;
+    size_t need = ps_blob_size(s->ps);
+    if (!buf) { *nbytes = need; return ZXP_OK; }
+    if (*nbytes < need) { *nbytes = need; return ZXP_EINVAL; }
+    ps_to_blob(s->ps, buf);
+    *nbytes = need;
+    return ZXP_OK;
+}
+
+int zxp_scalar_info(const zxp_scalar* s, zxp_scalar_info_t* info) {
+    if (!s || !info) return ZXP_EINVAL;
+    memset(info, 0, sizeof *info);
+    info->k = s->ps.k;
+    info->n_lin = (uint32_t)s->ps.lin.size();
+    info->n_quad = (uint32_t)s->ps.quad.size();
+    info->n_node = (uint32_t)s->ps.node.size();
+    info->n_pair = (uint32_t)s->ps.pair.size();
+    info->e0 = s->ps.e0;
+    info->acc_bits = s->ps.e0 <= 124 ? 64 : 128;
+    info->form_bits = s->plan.kp.nbits;
+    info->t_count = s->ps.t_count;
+    info->node_words = (uint32_t)s->plan.nwn;
+    info->other_words = (uint32_t)(s->plan.nwl < 1 ? 1 : s->plan.nwl);
+    return ZXP_OK;
+}
+
+void zxp_scalar_free(zxp_scalar* s) { delete s; }
+
+int zxp_eval(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, zxp_zomega* out) {
+    if (!ctx || !s || !out) return ZXP_EINVAL;
+    int st = check_range(s, first, count);
+    if (st != ZXP_OK) return st;
+    if (count == 0 || s->plan.zero) { from_zw(zw_zero(), s->ps.e0, 1, out); return ZXP_OK; }
+    DeviceGuard g(ctx->device);
+    st = enqueue(ctx, s, first, count, ctx->dres);
+    if (st != ZXP_OK) return st;
+    if (cudaMemcpyAsync(ctx->hres, ctx->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+        return ZXP_ECUDA;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return ZXP_ECUDA;
+    memcpy(out, ctx->hres, sizeof *out);
+    return ZXP_OK;
+}
+
+int zxp_eval_device(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count,
+                    zxp_zomega* dev_out) {
+    if (!ctx || !s || !dev_out || ((uintptr_t)dev_out & 7)) return ZXP_EINVAL;
+    int st = check_range(s, first, count);
+    if (st != ZXP_OK) return st;
+    DeviceGuard g(ctx->device);
+    return enqueue(ctx, s, first, count, reinterpret_cast<DevResult*>(dev_out));
+}
+
+int zxp_zomega_canon(const zxp_zomega* in, zxp_zomega* out) {
+    if (!in || !out) return ZXP_EINVAL;
+    __int128 c[4] = {in->c[0], in->c[1], in->c[2], in->c[3]};
+    int32_t e = in->e;
+    canon_i128(c, &e);
+    for (int i = 0; i < 4; i++) out->c[i] = (int64_t)c[i];
+    out->e = e;
+    out->flags = 0;
+    return ZXP_OK;
+}
+
+int zxp_amplitude(zxp_ctx* ctx, const zxp_scalar* s, zxp_zomega* out) {
+    if (!s) return ZXP_EINVAL;
+    zxp_zomega raw;
+    int st = zxp_eval(ctx, s, 0, 1ull << s->ps.k, &raw);
+    if (st != ZXP_OK) return st;
+    zxp_zomega_canon(&raw, out);
+    return s->ps.e0 > 124 ? ZXP_EOVERFLOW : ZXP_OK;
+}
+
+int zxp_submit(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, uint64_t* ticket) {
+    if (!ctx || !s || !ticket) return ZXP_EINVAL;
+    int st = check_range(s, first, count);
+    if (st != ZXP_OK) return st;
+    Ticket t;
+    t.e0 = s->ps.e0;
+    if (count == 0 || s->plan.zero) {
+        t.trivial = true;
+    } else {
+        DeviceGuard g(ctx->device);
+        if (!ctx->free_slots.empty()) {
+            t.dres = ctx->free_slots.back().dres;
+            t.hres = ctx->free_slots.back().hres;
+            t.ev = ctx->free_slots.back().ev;
+            ctx->free_slots.pop_back();
+        } else {
+            if (cudaMalloc(&t.dres, sizeof(DevResult)) != cudaSuccess) return ZXP_ENOMEM;
+            if (cudaMallocHost(&t.hres, sizeof(DevResult)) != cudaSuccess) { cudaFree(t.dres); return ZXP_ENOMEM; }
+            if (cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming) != cudaSuccess) return ZXP_ECUDA;
+        }
+        st = enqueue(ctx, s, first, count, t.dres);
+        if (st == ZXP_OK && cudaMemcpyAsync(t.hres, t.dres, sizeof(DevResult), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+            st = ZXP_ECUDA;
+        if (st == ZXP_OK && cudaEventRecord(t.ev, ctx->stream) != cudaSuccess) st = ZXP_ECUDA;
+        if (st != ZXP_OK) { ctx->free_slots.push_back(t); return st; }
+    }
+    *ticket = ctx->next_ticket++;
+    ctx->tickets[*ticket] = t;
+    return ZXP_OK;
+}
+
+int zxp_poll(zxp_ctx* ctx, uint64_t ticket, int64_t timeout_us, zxp_zomega* out) {
+    if (!ctx || !out) return ZXP_EINVAL;
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) return ZXP_ENOTFOUND;
+    Ticket& t = it->second;
+    if (!t.trivial) {
+        DeviceGuard g(ctx->device);
+        auto t0 = std::chrono::steady_clock::now();
+        for (;;) {
+            cudaError_t e = cudaEventQuery(t.ev);
+            if (e == cudaSuccess) break;
+            if (e != cudaErrorNotReady) return ZXP_ECUDA;
+            if (timeout_us == 0) return ZXP_EAGAIN;
+            auto el = std::chrono::duration_cast<std::chrono::microseconds>(
+                          std::chrono::steady_clock::now() - t0).count();
+            if (timeout_us > 0 && el >= timeout_us) return ZXP_EAGAIN;
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+        memcpy(out, t.hres, sizeof *out);
+    } else {
+        from_zw(zw_zero(), t.e0, 1, out);
+    }
+    if (!t.trivial) ctx->free_slots.push_back(t);
+    ctx->tickets.erase(it);
+    return ZXP_OK;
+}
+
+int zxp_zomega_add(const zxp_zomega* a, const zxp_zomega* b, zxp_zomega* out) {
+    if (!a || !b || !out) return ZXP_EINVAL;
+    zw64 x = to_zw(*a), y = to_zw(*b);
+    int32_t ea = a->e, eb = b->e;
+    while (ea < eb) { x = zw_mul_sqrt2(x); ea++; }
+    while (eb < ea) { y = zw_mul_sqrt2(y); eb++; }
+    from_zw(zw_add(x, y), ea, (a->flags | b->flags) & 1, out);
+    return ZXP_OK;
+}
+
+void zxp_zomega_to_complex(const zxp_zomega* z, double* re, double* im) {
+    if (!z) return;
+    const double h = 0.70710678118654752440;
+    double c0 = (double)z->c[0], c1 = (double)z->c[1], c2 = (double)z->c[2], c3 = (double)z->c[3];
+    double r = c0 + h * c1 - h * c3, i = h * c1 + c2 + h * c3;
+    double s = 1.0;
+    for (int k = 0; k < z->e; k++) s *= h;
+    for (int k = 0; k < -z->e; k++) s *= 1.41421356237309504880;
+    if (re) *re = r * s;
+    if (im) *im = i * s;
+}
+
+}  // extern "C"

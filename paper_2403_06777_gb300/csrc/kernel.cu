@@ -1,0 +1,216 @@
+// kernel.cu -- exact exponential sum of a parametric scalar on sm_103a.
+//
+// Each thread walks contiguous Gray-code slices [t0, t0 + span) of the
+// assignment space (x = t ^ (t >> 1)); consecutive assignments differ in the
+// bit ctz(t), so a step XORs that variable's flip mask into the form bits
+// (the AND / XOR-reduce steps of Sec. 3.3 done incrementally) and updates
+// the quadratic phase with one bit of A x.  A term is then one table entry
+// K * w^(J + 2M) (1 + sqrt2)^M (see plan.h), multiplied by any phase-pair
+// values, and accumulated in four int64 coefficients modulo 2^64.
+// Threads reduce by warp shuffles, then per block in shared memory, then the
+// last block to finish adds the per-block partials (App. E's pairwise sum,
+// done as a shuffle tree).  Integer adds make the result bit-exact and
+// independent of the reduction order.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernel.h"
+#include "plan.h"
+
+namespace zxp {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <int NW>
+__device__ __forceinline__ uint32_t bit_at(const uint32_t (&L)[NW], uint32_t pos) {
+    uint32_t wsel = pos >> 5, v = 0;
+#pragma unroll
+    for (int q = 0; q < NW; q++) v = (wsel == (uint32_t)q) ? L[q] : v;
+    return (v >> (pos & 31)) & 1u;
+}
+
+__device__ __forceinline__ zw64 lds_zw(const zw64* p) {
+    const ulonglong2* q = reinterpret_cast<const ulonglong2*>(p);
+    ulonglong2 a = q[0], b = q[1];
+    return zw_make(a.x, a.y, b.x, b.y);
+}
+
+__device__ __forceinline__ zw64 shfl_xor_zw(zw64 v, int off) {
+    zw64 r;
+#pragma unroll
+    for (int c = 0; c < 4; c++) r.c[c] = __shfl_xor_sync(0xffffffffu, v.c[c], off);
+    return r;
+}
+
+__device__ __forceinline__ zw64 block_reduce(zw64 v, zw64* sred) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = zw_add(v, shfl_xor_zw(v, off));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sred[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = (lane < (int)(blockDim.x >> 5)) ? sred[lane] : zw_zero();
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v = zw_add(v, shfl_xor_zw(v, off));
+    }
+    return v;   // valid in thread 0
+}
+
+template <int NWN, int NWL>
+__global__ void __launch_bounds__(kThreads)
+sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtable,
+           const zw64* __restrict__ gpv, uint64_t first, uint64_t count, uint64_t span,
+           uint64_t nslices, zw64* __restrict__ partials, unsigned int* __restrict__ counter,
+           const zw64 K, const int32_t e0, DevResult* __restrict__ result) {
+    constexpr int NW = NWN + NWL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    zw64* sT = reinterpret_cast<zw64*>(smem_raw);
+    const uint32_t ntab = 8u * p.tab_stride;
+    zw64* sPV = sT + ntab;
+    zw64* sred = sPV + 4u * p.npairs;
+    for (uint32_t i = threadIdx.x; i < ntab; i += blockDim.x) sT[i] = gtable[i];
+    for (uint32_t i = threadIdx.x; i < 4u * p.npairs; i += blockDim.x) sPV[i] = gpv[i];
+    __syncthreads();
+
+    zw64 acc = zw_zero();
+    const uint64_t end = first + count;
+    const uint64_t gstride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nslices; s += gstride) {
+        uint64_t t = first + s * span;
+        const uint64_t tend = (end - t < span) ? end : t + span;
+        const uint64_t x = t ^ (t >> 1);
+        // form bits at x: parity(mask & x) xor inversion
+        uint32_t L[NW];
+#pragma unroll
+        for (int w = 0; w < NW; w++) {
+            uint32_t v = p.INV[w];
+            for (int b = 0; b < 32; b++)
+                v ^= (uint32_t)(__popcll(p.FM[32 * w + b] & x) & 1) << b;
+            L[w] = v;
+        }
+        // quadratic part: a = A x, q = x^T (upper A) x
+        uint64_t a = 0;
+        uint32_t q = 0;
+        for (uint32_t i = 0; i < p.k; i++) {
+            if ((x >> i) & 1) {
+                a ^= p.ADJ[i];
+                q ^= (uint32_t)__popcll(p.ADJ[i] & x & ~((2ull << i) - 1)) & 1u;
+            }
+        }
+        for (;;) {
+            uint32_t M = 0, P0 = 0, P1 = 0, X2 = 0, Zb = 0;
+#pragma unroll
+            for (int w = 0; w < NWN; w++) {
+                M += __popc(L[w]);
+                X2 ^= L[w] & p.CB[w];
+            }
+#pragma unroll
+            for (int w = 0; w < NWL; w++) {
+                const uint32_t v = L[NWN + w];
+                P0 += __popc(v & p.C0[w]);
+                P1 += __popc(v & p.C1[w]);
+                X2 ^= v & p.C2[w];
+                Zb |= v & p.Z[w];
+            }
+            if (Zb == 0) {
+                const uint32_t J = (P0 + 2u * P1 + 4u * ((uint32_t)__popc(X2) + q)) & 7u;
+                zw64 v = lds_zw(sT + J * p.tab_stride + M);
+                for (uint32_t j = 0; j < p.npairs; j++) {
+                    const uint32_t b = bit_at<NW>(L, p.PA[j]) | (bit_at<NW>(L, p.PB[j]) << 1);
+                    v = zw_mul(v, lds_zw(sPV + 4 * j + b));
+                }
+                acc = zw_add(acc, v);
+            }
+            if (++t >= tend) break;
+            const int i = __ffsll((long long)t) - 1;   // x(t) = x(t-1) ^ (1 << ctz(t))
+            q ^= (uint32_t)(a >> i) & 1u;
+            a ^= p.ADJ[i];
+#pragma unroll
+            for (int w = 0; w < NW; w++) L[w] ^= p.F[i][w];
+        }
+    }
+
+    // reduction: warp shuffles, block, then the last block over the partials
+    __shared__ unsigned int s_last;
+    acc = block_reduce(acc, sred);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = acc;
+        __threadfence();
+        const unsigned int done = atomicAdd(counter, 1u);
+        s_last = (done == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        zw64 v = zw_zero();
+        for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+            const ulonglong2* q2 = reinterpret_cast<const ulonglong2*>(partials + b);
+            ulonglong2 lo = __ldcg(q2), hi = __ldcg(q2 + 1);
+            v = zw_add(v, zw_make(lo.x, lo.y, hi.x, hi.y));
+        }
+        v = block_reduce(v, sred);
+        if (threadIdx.x == 0) {
+            const zw64 r = zw_mul(K, v);
+            for (int c = 0; c < 4; c++) result->c[c] = (int64_t)r.c[c];
+            result->e = e0;
+            result->flags = 1;
+            *counter = 0u;       // ready for the next launch on this workspace
+        }
+    }
+}
+
+using KernelFn = void (*)(const KernelParams, const zw64*, const zw64*, uint64_t, uint64_t,
+                          uint64_t, uint64_t, zw64*, unsigned int*, const zw64, const int32_t,
+                          DevResult*);
+
+template <int NWN, int NWL>
+constexpr KernelFn kfn() { return &sum_kernel<NWN, NWL>; }
+
+// [nwn][nwl - 1]
+const KernelFn kTable[kMaxWordsNode + 1][kMaxWordsOther] = {
+    {kfn<0, 1>(), kfn<0, 2>(), kfn<0, 3>(), kfn<0, 4>()},
+    {kfn<1, 1>(), kfn<1, 2>(), kfn<1, 3>(), kfn<1, 4>()},
+    {kfn<2, 1>(), kfn<2, 2>(), kfn<2, 3>(), kfn<2, 4>()},
+    {kfn<3, 1>(), kfn<3, 2>(), kfn<3, 3>(), kfn<3, 4>()},
+    {kfn<4, 1>(), kfn<4, 2>(), kfn<4, 3>(), kfn<4, 4>()},
+};
+
+}  // namespace
+
+size_t sum_smem_bytes(const Plan& pl) {
+    return sizeof(zw64) * (8u * pl.kp.tab_stride + 4u * pl.kp.npairs + kThreads / 32);
+}
+
+int sum_threads() { return kThreads; }
+
+cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, uint64_t first,
+                       uint64_t count, uint64_t span, int grid, zw64* partials,
+                       unsigned int* counter, DevResult* result, cudaStream_t stream) {
+    const int nwl = pl.nwl < 1 ? 1 : pl.nwl;
+    KernelFn fn = kTable[pl.nwn][nwl - 1];
+    const size_t smem = sum_smem_bytes(pl);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const uint64_t nslices = (count + span - 1) / span;
+    fn<<<grid, kThreads, smem, stream>>>(pl.kp, dtable, dpv, first, count, span, nslices, partials,
+                                         counter, pl.K, pl.e0, result);
+    return cudaGetLastError();
+}
+
+cudaError_t sum_occupancy(const Plan& pl, int* blocks_per_sm) {
+    const int nwl = pl.nwl < 1 ? 1 : pl.nwl;
+    KernelFn fn = kTable[pl.nwn][nwl - 1];
+    const size_t smem = sum_smem_bytes(pl);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kThreads, smem);
+}
+
+}  // namespace zxp

@@ -1,0 +1,32 @@
+// kernel.h -- launch interface of the sum kernel (kernel.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "plan.h"
+
+namespace zxp {
+
+// Dynamic shared memory of one block: the w^(J+2M)(1+sqrt2)^M table, the
+// phase-pair values and the reduction scratch.
+size_t sum_smem_bytes(const Plan& pl);
+int sum_threads();
+cudaError_t sum_occupancy(const Plan& pl, int* blocks_per_sm);
+
+// Device copy of the public result record (same layout as zxp_zomega).
+struct DevResult {
+    int64_t c[4];
+    int32_t e;
+    int32_t flags;
+};
+
+// Sum Gray-code indices [first, first + count) in slices of `span` terms
+// over `grid` blocks.  partials holds >= grid entries; *counter must be 0
+// on entry and is 0 again when the kernel ends; *result receives
+// K * (sum of the table terms) over sqrt2^e0, flagged raw.
+cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, uint64_t first,
+                       uint64_t count, uint64_t span, int grid, zw64* partials,
+                       unsigned int* counter, DevResult* result, cudaStream_t stream);
+
+}  // namespace zxp

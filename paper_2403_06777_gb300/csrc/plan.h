@@ -1,0 +1,62 @@
+// plan.h -- a parametric scalar rewritten for the sum kernel.
+//
+// The kernel tracks, per assignment x, one bit per "form" (a parity of x,
+// optionally inverted) in NW = NWN + NWL 32-bit words:
+//   node words  [0, NWN):        one bit per odd-constant node, set when the
+//                                node takes the larger of its two magnitudes
+//                                (effective exponent 1 or 7)
+//   other words [NWN, NWN+NWL):  linear forms (coefficient bit-planes C0, C1,
+//                                C2), zero forms (Z: a set bit zeroes the
+//                                term) and phase-pair forms.
+// With M = number of set node bits and
+//   J = sum_lin c l + 4 (quadratic part) + 4 (set class-B node bits)  mod 8,
+// every term equals  K * w^(J + 2M) (1 + sqrt2)^M * prod_pairs PV  where K is
+// one constant for the whole sum, because every odd node satisfies
+//   1 + w^e = (1 - w) w^j_e (1 + sqrt2)^beta_e,
+//   (j, beta) = (2,1), (3,0), (0,0), (1,1) for e = 1, 3, 5, 7.
+#pragma once
+#include <stdint.h>
+
+#include <vector>
+
+#include "ps.h"
+#include "zring.h"
+
+namespace zxp {
+
+constexpr int kMaxK = 62;
+constexpr int kMaxWordsNode = 4;
+constexpr int kMaxWordsOther = 4;
+constexpr int kMaxNW = kMaxWordsNode + kMaxWordsOther;
+constexpr int kMaxPairs = 32;
+
+// Passed by value as the kernel parameter block (kept in the constant bank).
+struct KernelParams {
+    uint32_t k;
+    uint32_t nbits;          // 32 * (NWN + NWL) form bits (unused bits stay 0)
+    uint32_t npairs;
+    uint32_t tab_stride;     // m_odd + 1
+    uint32_t CB[kMaxWordsNode];                       // class-B node bits
+    uint32_t C0[kMaxWordsOther], C1[kMaxWordsOther], C2[kMaxWordsOther], Z[kMaxWordsOther];
+    uint32_t INV[kMaxNW];    // initial inversion of each form bit
+    uint32_t F[kMaxK][kMaxNW];                        // forms holding variable i
+    uint64_t ADJ[kMaxK];     // quadratic part: 4 * sum_{i<j} A_ij x_i x_j
+    uint64_t FM[32 * kMaxNW];                         // variable mask of each form bit
+    uint16_t PA[kMaxPairs], PB[kMaxPairs];            // bit positions of pair forms
+};
+
+struct Plan {
+    int nwn = 0, nwl = 0;           // node / other words
+    uint32_t m_odd = 0;
+    KernelParams kp;
+    std::vector<zw64> table;        // 8 x (m_odd + 1): w^(J + 2M) (1 + sqrt2)^M
+    std::vector<zw64> pv;           // 4 per pair: value at (lA, lB) = (b & 1, b >> 1)
+    zw64 K;                         // constant factor, G included
+    int32_t e0 = 0;
+    bool zero = false;              // the scalar is identically zero
+};
+
+// Returns 0 or ZXP_ETOOBIG (more forms / pairs than the kernel supports).
+int build_plan(const PS& ps, Plan* out);
+
+}  // namespace zxp

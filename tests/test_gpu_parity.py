@@ -1,0 +1,183 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Every comparison is exact: raw partial sums agree modulo 2^64 (the ring the
+kernel computes in), canonical amplitudes agree as integers."""
+import os
+import random
+
+import pytest
+
+import oracle
+import paper_2403_06777_gb300 as Z
+import zxp_inputs as zi
+
+pytestmark = pytest.mark.gpu
+M64 = (1 << 64) - 1
+NCPU = os.cpu_count() or 4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available(), "these tests need a GPU"
+    c = Z.zxp_ctx_create(0)
+    yield c
+    c.close()
+
+
+def same_raw(gpu, orc):
+    assert gpu[4] == orc[4]
+    return all((gpu[i] - orc[i]) & M64 == 0 for i in range(4))
+
+
+def check_ranges(ctx, ps, ranges):
+    blob = ps.pack()
+    s = Z.zxp_scalar_from_tables(blob)
+    for first, count in ranges:
+        g = Z.zxp_eval(ctx, s, first, count)
+        o = oracle.ps_sum(blob, first, count, nthreads=NCPU)
+        assert same_raw(g, o), (ps.k, first, count, g, o)
+
+
+def std_ranges(k, rng):
+    N = 1 << k
+    r = [(0, N), (0, 0), (N, 0), (N - 1, 1), (0, 1)]
+    if N > 8:
+        r += [(1, N - 3), (N // 3, N // 2)]
+        a = rng.randrange(N)
+        r.append((a, rng.randrange(N - a + 1)))
+    return r
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_synthetic_tables_all_row_kinds(ctx, seed):
+    rng = random.Random(seed)
+    k = rng.choice([0, 1, 3, 6, 9, 12, 14, 16])
+    ps = zi.synthetic_ps(seed, k, n_lin=rng.randint(0, 12), n_quad=rng.randint(0, 6),
+                         n_node=rng.randint(0, 24), n_pair=rng.randint(0, 4),
+                         density=rng.choice([0.1, 0.3, 0.6]), e0=rng.randint(0, 9),
+                         G=(rng.randint(-9, 9), rng.randint(-9, 9), rng.randint(-9, 9), 1))
+    check_ranges(ctx, ps, std_ranges(k, rng))
+
+
+@pytest.mark.parametrize("n_node,n_lin", [(31, 1), (32, 31), (33, 33), (64, 64), (65, 10),
+                                          (100, 100), (128, 120), (5, 127)])
+def test_synthetic_form_word_layouts(ctx, n_node, n_lin):
+    # node words 1..4 and other words 1..4; odd nodes only (the common case)
+    ps = zi.synthetic_ps(n_node * 1000 + n_lin, 11, n_lin=n_lin, n_quad=3, n_node=n_node,
+                         odd_nodes_only=True, density=0.35)
+    check_ranges(ctx, ps, std_ranges(11, random.Random(n_node)))
+
+
+def test_synthetic_pairs_and_zero_nodes(ctx):
+    ps = zi.synthetic_ps(99, 13, n_lin=6, n_quad=5, n_node=20, n_pair=12, density=0.3)
+    ps.node += [(0b101, 0), (0b1100000, 4), (0b11, 2), (0b110, 6), (0, 3), (0, 1)]
+    ps.pair += [(0, 3, 0, 5), (0b1, 2, 0, 6)]
+    check_ranges(ctx, ps, std_ranges(13, random.Random(5)))
+
+
+def test_largest_slices_and_ragged_tails(ctx):
+    ps = zi.synthetic_ps(3, 22, n_lin=10, n_quad=6, n_node=30, odd_nodes_only=True, density=0.3)
+    N = 1 << 22
+    check_ranges(ctx, ps, [(0, N), (12345, N - 2 * 12345), (N - 777, 777), ((1 << 20) + 1, 3)])
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_compiled_small_amplitudes_exact(ctx, seed):
+    n = 2 + seed % 6
+    gates = zi.circuit_iid(seed + 4000, n, 30 + seed)
+    out = zi.random_bits(seed, n)
+    s = Z.zxp_compile(gates, n, out)
+    assert Z.zxp_amplitude(ctx, s) == oracle.amp(gates, n, out)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_compiled_small_marginals_exact(ctx, seed):
+    n = 3 + seed % 4
+    gates = zi.circuit_iid(seed + 8000, n, 40)
+    bits = zi.random_bits(seed, n)
+    mask = 1 << (seed % n)
+    s = Z.zxp_compile(gates, n, bits, marg_mask=mask, kind=Z.ZXP_MARGINAL_DOUBLED)
+    assert Z.zxp_amplitude(ctx, s) == oracle.marginal(gates, n, mask, bits)
+
+
+def test_small_workload_every_output(ctx):
+    w = zi.workload_small(0)
+    want = oracle.amps_all(w.gates, w.n)
+    for x in range(1 << w.n):
+        bits = [(x >> q) & 1 for q in range(w.n)]
+        assert Z.zxp_amplitude(ctx, Z.zxp_compile(w.gates, w.n, bits)) == want[x]
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_medium_workload_amplitude_exact(ctx, seed):
+    # n = 20, 600 gates, t = 40: the full 2^k sum on the GPU (the benchmark's
+    # workload and launch shape) against the exact 2^20-entry state vector
+    w = zi.workload_medium(seed)
+    s = Z.zxp_compile(w.gates, w.n, w.out_bits)
+    assert Z.zxp_amplitude(ctx, s) == oracle.amp(w.gates, w.n, w.out_bits)
+
+
+def test_large_workload_subranges_exact(ctx):
+    # n = 50, 2000 gates, t = 80: seeded 2^20-term sub-ranges of the compiled
+    # scalar against the oracle
+    w = zi.workload_large(0)
+    s = Z.zxp_compile(w.gates, w.n, w.out_bits)
+    blob = Z.zxp_scalar_to_tables(s)
+    k = Z.zxp_scalar_info(s)["k"]
+    rng = zi.SplitMix64(2024)
+    for _ in range(3):
+        first = rng.below((1 << k) - (1 << 20))
+        g = Z.zxp_eval(ctx, s, first, 1 << 20)
+        o = oracle.ps_sum(blob, first, 1 << 20, nthreads=NCPU)
+        assert same_raw(g, o)
+
+
+def test_split_invariance_large_synthetic(ctx):
+    # k = 30 synthetic scalar with compiled-like statistics: any chunking of
+    # the range gives the same bits
+    ps = zi.synthetic_ps(36, 30, n_lin=40, n_quad=20, n_node=50, odd_nodes_only=True, density=0.15)
+    s = Z.zxp_scalar_from_tables(ps.pack())
+    N = 1 << 30
+    whole = Z.zxp_eval(ctx, s)
+    cuts = sorted(random.Random(1).sample(range(1, N), 5))
+    acc = None
+    for a, b in zip([0] + cuts, cuts + [N]):
+        part = Z.zxp_eval(ctx, s, a, b - a)
+        acc = part if acc is None else Z.zxp_zomega_add(acc, part)
+    assert acc == whole
+    o = oracle.ps_sum(ps.pack(), 777777, 1 << 18, nthreads=NCPU)
+    assert same_raw(Z.zxp_eval(ctx, s, 777777, 1 << 18), o)
+
+
+def test_submit_poll_matches_eval(ctx):
+    scalars = []
+    for seed in range(6):
+        ps = zi.synthetic_ps(seed, 14 + seed % 3, n_lin=8, n_node=12, n_pair=seed % 3)
+        scalars.append(Z.zxp_scalar_from_tables(ps.pack()))
+    tickets = [Z.zxp_submit(ctx, s) for s in scalars]
+    tickets.append(Z.zxp_submit(ctx, scalars[0], 5, 0))
+    got = [Z.zxp_poll(ctx, t, -1) for t in tickets]
+    for s, g in zip(scalars, got):
+        assert g == Z.zxp_eval(ctx, s)
+    assert got[-1][:4] == (0, 0, 0, 0)
+    with pytest.raises(Z.ZxpError):
+        Z.zxp_poll(ctx, tickets[0], 0)        # already released
+
+
+def test_context_on_a_torch_stream():
+    import torch
+    st = torch.cuda.Stream()
+    c = Z.zxp_ctx_create(0, st.cuda_stream)
+    ps = zi.synthetic_ps(1, 12, n_node=10)
+    s = Z.zxp_scalar_from_tables(ps.pack())
+    assert same_raw(Z.zxp_eval(c, s), oracle.ps_sum(ps.pack()))
+    c.close()
+
+
+def test_range_errors(ctx):
+    s = Z.zxp_scalar_from_tables(zi.synthetic_ps(1, 5).pack())
+    with pytest.raises(Z.ZxpError):
+        Z.zxp_eval(ctx, s, 30, 3)
+    with pytest.raises(Z.ZxpError):
+        Z.zxp_eval(ctx, s, 33, 0)

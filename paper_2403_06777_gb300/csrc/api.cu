@@ -121,22 +121,20 @@ int ensure_device_tables(const zxp_scalar* s, int device, DevTables* out) {
     return ZXP_OK;
 }
 
-uint64_t next_pow2(uint64_t v) {
-    uint64_t p = 1;
-    while (p < v) p <<= 1;
-    return p;
-}
-
-// Slice length and grid for `count` terms.
+// Slice length and grid for `count` terms: one slice per thread of a full
+// resident grid, slices a multiple of 64 terms so that the lanes of a warp
+// flip the same variable at the same step (their start indices agree
+// modulo 64).
 void launch_shape(const zxp_ctx* ctx, const Plan& pl, uint64_t count, uint64_t* span, int* grid) {
     int bps = 1;
     if (sum_occupancy(pl, &bps) != cudaSuccess || bps < 1) bps = 1;
     int max_grid = ctx->sm_count * bps;
     if (max_grid > ctx->max_grid) max_grid = ctx->max_grid;
     const uint64_t threads = (uint64_t)max_grid * (uint64_t)sum_threads();
-    uint64_t sp = next_pow2((count + threads * 4 - 1) / (threads * 4));
+    uint64_t sp = (count + threads - 1) / threads;
+    sp = (sp + 63) & ~63ull;
     if (sp < 64) sp = 64;
-    if (sp > (1ull << 20)) sp = 1ull << 20;
+    if (sp > (1ull << 18)) sp = 1ull << 18;   // longer ranges: several slices per thread
     const uint64_t nslices = (count + sp - 1) / sp;
     uint64_t g = (nslices + (uint64_t)sum_threads() - 1) / (uint64_t)sum_threads();
     if (g > (uint64_t)max_grid) g = (uint64_t)max_grid;

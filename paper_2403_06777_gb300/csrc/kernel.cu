@@ -22,6 +22,7 @@ namespace zxp {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr uint32_t kHistMaxOdd = 5;   // 8 * 6 counters per lane: 48 KB per block
 
 template <int NW>
 __device__ __forceinline__ uint32_t bit_at(const uint32_t (&L)[NW], uint32_t pos) {
@@ -59,7 +60,7 @@ __device__ __forceinline__ zw64 block_reduce(zw64 v, zw64* sred) {
     return v;   // valid in thread 0
 }
 
-template <int NWN, int NWL>
+template <int NWN, int NWL, bool GENERAL, bool HIST>
 __global__ void __launch_bounds__(kThreads)
 sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtable,
            const zw64* __restrict__ gpv, uint64_t first, uint64_t count, uint64_t span,
@@ -71,36 +72,70 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
     const uint32_t ntab = 8u * p.tab_stride;
     zw64* sPV = sT + ntab;
     zw64* sred = sPV + 4u * p.npairs;
+    uint64_t* sADJ = reinterpret_cast<uint64_t*>(sred + kThreads / 32);
+    uint32_t* sF = reinterpret_cast<uint32_t*>(sADJ + kMaxK);
+    // HIST: per-lane counters of the table index J * stride + M, laid out
+    // [warp][index][lane] so that every lane owns one bank
+    uint32_t* sH = sF + kMaxK * NW;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    if (HIST) {
+        for (uint32_t i = threadIdx.x; i < ntab * (kThreads / 32) * 32u; i += blockDim.x) sH[i] = 0;
+    }
     for (uint32_t i = threadIdx.x; i < ntab; i += blockDim.x) sT[i] = gtable[i];
-    for (uint32_t i = threadIdx.x; i < 4u * p.npairs; i += blockDim.x) sPV[i] = gpv[i];
+    if (GENERAL)
+        for (uint32_t i = threadIdx.x; i < 4u * p.npairs; i += blockDim.x) sPV[i] = gpv[i];
+    for (uint32_t i = threadIdx.x; i < p.k; i += blockDim.x) {
+        sADJ[i] = p.ADJ[i];
+#pragma unroll
+        for (int w = 0; w < NW; w++) sF[i * NW + w] = p.F[i][w];
+    }
     __syncthreads();
+
+    // flip rows and adjacency of the three lowest variables, in registers:
+    // inside an aligned block of 8 Gray steps they are the only ones flipped
+    uint32_t f0[NW], f1[NW], f2[NW];
+#pragma unroll
+    for (int w = 0; w < NW; w++) { f0[w] = p.F[0][w]; f1[w] = p.F[1][w]; f2[w] = p.F[2][w]; }
+    const uint64_t adj0 = p.ADJ[0], adj1 = p.ADJ[1], adj2 = p.ADJ[2];
 
     zw64 acc = zw_zero();
     const uint64_t end = first + count;
     const uint64_t gstride = (uint64_t)gridDim.x * blockDim.x;
+    // HIST: acc += sum_idx count(idx) * T[idx] (mod 2^64), counters reset
+    auto fold = [&]() {
+        for (uint32_t i = 0; i < ntab; i++) {
+            uint32_t* h = sH + ((warp * ntab + i) << 5) + lane;
+            const uint64_t c = *h;
+            if (c) { acc = zw_add(acc, zw_scale(lds_zw(sT + i), c)); *h = 0; }
+        }
+    };
+    // a thread with several slices (ranges beyond threads * 2^30 terms)
+    // folds after each one, so no 32-bit counter can overflow
+    const bool fold_each = nslices > gstride;
     for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nslices; s += gstride) {
         uint64_t t = first + s * span;
         const uint64_t tend = (end - t < span) ? end : t + span;
         const uint64_t x = t ^ (t >> 1);
-        // form bits at x: parity(mask & x) xor inversion
+        // state at x: the form bits are the XOR of the flip rows of x's set
+        // bits (plus the inversions); a = A x; q = x^T (upper A) x, as half
+        // of sum_{j in x} |A_j & x|
         uint32_t L[NW];
 #pragma unroll
-        for (int w = 0; w < NW; w++) {
-            uint32_t v = p.INV[w];
-            for (int b = 0; b < 32; b++)
-                v ^= (uint32_t)(__popcll(p.FM[32 * w + b] & x) & 1) << b;
-            L[w] = v;
-        }
-        // quadratic part: a = A x, q = x^T (upper A) x
+        for (int w = 0; w < NW; w++) L[w] = p.INV[w];
         uint64_t a = 0;
-        uint32_t q = 0;
-        for (uint32_t i = 0; i < p.k; i++) {
-            if ((x >> i) & 1) {
-                a ^= p.ADJ[i];
-                q ^= (uint32_t)__popcll(p.ADJ[i] & x & ~((2ull << i) - 1)) & 1u;
-            }
+        uint32_t qs = 0;
+        for (uint64_t y = x; y; y &= y - 1) {
+            const int j = __ffsll((long long)y) - 1;
+#pragma unroll
+            for (int w = 0; w < NW; w++) L[w] ^= sF[j * NW + w];
+            const uint64_t aj = sADJ[j];
+            a ^= aj;
+            qs += (uint32_t)__popcll(aj & x);
         }
-        for (;;) {
+        uint32_t q = (qs >> 1) & 1u;
+
+        // one term at the current state
+        auto term = [&]() {
             uint32_t M = 0, P0 = 0, P1 = 0, X2 = 0, Zb = 0;
 #pragma unroll
             for (int w = 0; w < NWN; w++) {
@@ -113,25 +148,58 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
                 P0 += __popc(v & p.C0[w]);
                 P1 += __popc(v & p.C1[w]);
                 X2 ^= v & p.C2[w];
-                Zb |= v & p.Z[w];
+                if (GENERAL) Zb |= v & p.Z[w];
             }
-            if (Zb == 0) {
+            if (HIST) {
+                const uint32_t J = (P0 + 2u * P1 + 4u * ((uint32_t)__popc(X2) + q)) & 7u;
+                atomicAdd(sH + ((warp * ntab + J * p.tab_stride + M) << 5) + lane, 1u);
+            } else if (!GENERAL || Zb == 0) {
                 const uint32_t J = (P0 + 2u * P1 + 4u * ((uint32_t)__popc(X2) + q)) & 7u;
                 zw64 v = lds_zw(sT + J * p.tab_stride + M);
-                for (uint32_t j = 0; j < p.npairs; j++) {
-                    const uint32_t b = bit_at<NW>(L, p.PA[j]) | (bit_at<NW>(L, p.PB[j]) << 1);
-                    v = zw_mul(v, lds_zw(sPV + 4 * j + b));
+                if (GENERAL) {
+                    for (uint32_t j = 0; j < p.npairs; j++) {
+                        const uint32_t b = bit_at<NW>(L, p.PA[j]) | (bit_at<NW>(L, p.PB[j]) << 1);
+                        v = zw_mul(v, lds_zw(sPV + 4 * j + b));
+                    }
                 }
                 acc = zw_add(acc, v);
             }
-            if (++t >= tend) break;
-            const int i = __ffsll((long long)t) - 1;   // x(t) = x(t-1) ^ (1 << ctz(t))
+        };
+        // flip of a variable known at compile time (0, 1 or 2)
+        auto flip = [&](const uint32_t (&f)[NW], uint64_t adj, int i) {
             q ^= (uint32_t)(a >> i) & 1u;
-            a ^= p.ADJ[i];
+            a ^= adj;
 #pragma unroll
-            for (int w = 0; w < NW; w++) L[w] ^= p.F[i][w];
+            for (int w = 0; w < NW; w++) L[w] ^= f[w];
+        };
+
+        for (;;) {
+            if ((t & 7u) == 0 && tend - t >= 8) {
+                // Gray steps inside t .. t+7 flip variables 0,1,0,2,0,1,0
+                term(); flip(f0, adj0, 0);
+                term(); flip(f1, adj1, 1);
+                term(); flip(f0, adj0, 0);
+                term(); flip(f2, adj2, 2);
+                term(); flip(f0, adj0, 0);
+                term(); flip(f1, adj1, 1);
+                term(); flip(f0, adj0, 0);
+                term();
+                t += 7;
+            } else {
+                term();
+            }
+            if (++t >= tend) break;
+            // x(t) = x(t-1) ^ (1 << ctz(t))
+            const uint32_t tl = (uint32_t)t;
+            const int i = tl ? __ffs(tl) - 1 : 31 + __ffs((uint32_t)(t >> 32));
+            q ^= (uint32_t)(a >> i) & 1u;
+            a ^= sADJ[i];
+#pragma unroll
+            for (int w = 0; w < NW; w++) L[w] ^= sF[i * NW + w];
         }
+        if (HIST && fold_each) fold();
     }
+    if (HIST) fold();
 
     // reduction: warp shuffles, block, then the last block over the partials
     __shared__ unsigned int s_last;
@@ -166,22 +234,41 @@ using KernelFn = void (*)(const KernelParams, const zw64*, const zw64*, uint64_t
                           uint64_t, uint64_t, zw64*, unsigned int*, const zw64, const int32_t,
                           DevResult*);
 
-template <int NWN, int NWL>
-constexpr KernelFn kfn() { return &sum_kernel<NWN, NWL>; }
+template <int NWN, int NWL, bool G, bool H>
+constexpr KernelFn kfn() { return &sum_kernel<NWN, NWL, G, H>; }
 
-// [nwn][nwl - 1]
-const KernelFn kTable[kMaxWordsNode + 1][kMaxWordsOther] = {
-    {kfn<0, 1>(), kfn<0, 2>(), kfn<0, 3>(), kfn<0, 4>()},
-    {kfn<1, 1>(), kfn<1, 2>(), kfn<1, 3>(), kfn<1, 4>()},
-    {kfn<2, 1>(), kfn<2, 2>(), kfn<2, 3>(), kfn<2, 4>()},
-    {kfn<3, 1>(), kfn<3, 2>(), kfn<3, 3>(), kfn<3, 4>()},
-    {kfn<4, 1>(), kfn<4, 2>(), kfn<4, 3>(), kfn<4, 4>()},
+#define ZXP_ROW(N, G) {kfn<N, 1, G, false>(), kfn<N, 2, G, false>(), kfn<N, 3, G, false>(), kfn<N, 4, G, false>()}
+// [general][nwn][nwl - 1]
+const KernelFn kTable[2][kMaxWordsNode + 1][kMaxWordsOther] = {
+    {ZXP_ROW(0, false), ZXP_ROW(1, false), ZXP_ROW(2, false), ZXP_ROW(3, false), ZXP_ROW(4, false)},
+    {ZXP_ROW(0, true), ZXP_ROW(1, true), ZXP_ROW(2, true), ZXP_ROW(3, true), ZXP_ROW(4, true)},
 };
+#undef ZXP_ROW
+// counting variant: at most kHistMaxOdd odd nodes (so nwn <= 1), no pairs or zero forms
+const KernelFn kHist[2][kMaxWordsOther] = {
+    {kfn<0, 1, false, true>(), kfn<0, 2, false, true>(), kfn<0, 3, false, true>(), kfn<0, 4, false, true>()},
+    {kfn<1, 1, false, true>(), kfn<1, 2, false, true>(), kfn<1, 3, false, true>(), kfn<1, 4, false, true>()},
+};
+
+bool use_hist(const Plan& pl) {
+    return pl.kp.npairs == 0 && !pl.has_zero && pl.m_odd <= kHistMaxOdd;
+}
+
+KernelFn pick(const Plan& pl) {
+    const int nwl = pl.nwl < 1 ? 1 : pl.nwl;
+    if (use_hist(pl)) return kHist[pl.nwn][nwl - 1];
+    const bool general = pl.kp.npairs > 0 || pl.has_zero;
+    return kTable[general ? 1 : 0][pl.nwn][nwl - 1];
+}
 
 }  // namespace
 
 size_t sum_smem_bytes(const Plan& pl) {
-    return sizeof(zw64) * (8u * pl.kp.tab_stride + 4u * pl.kp.npairs + kThreads / 32);
+    const size_t nw = (size_t)pl.nwn + (size_t)(pl.nwl < 1 ? 1 : pl.nwl);
+    const size_t ntab = 8u * (size_t)pl.kp.tab_stride;
+    return sizeof(zw64) * (ntab + 4u * pl.kp.npairs + kThreads / 32) + sizeof(uint64_t) * kMaxK +
+           sizeof(uint32_t) * kMaxK * nw +
+           (use_hist(pl) ? sizeof(uint32_t) * ntab * (size_t)kThreads : 0);
 }
 
 int sum_threads() { return kThreads; }
@@ -189,8 +276,7 @@ int sum_threads() { return kThreads; }
 cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, uint64_t first,
                        uint64_t count, uint64_t span, int grid, zw64* partials,
                        unsigned int* counter, DevResult* result, cudaStream_t stream) {
-    const int nwl = pl.nwl < 1 ? 1 : pl.nwl;
-    KernelFn fn = kTable[pl.nwn][nwl - 1];
+    KernelFn fn = pick(pl);
     const size_t smem = sum_smem_bytes(pl);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -203,8 +289,7 @@ cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, uint
 }
 
 cudaError_t sum_occupancy(const Plan& pl, int* blocks_per_sm) {
-    const int nwl = pl.nwl < 1 ? 1 : pl.nwl;
-    KernelFn fn = kTable[pl.nwn][nwl - 1];
+    KernelFn fn = pick(pl);
     const size_t smem = sum_smem_bytes(pl);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -149,6 +149,7 @@ int build_plan(const PS& ps, Plan* out) {
     pl.K = K;
     pl.e0 = ps.e0;
     pl.zero = exact_zero;
+    pl.has_zero = !zero.empty();
     *out = std::move(pl);
     return ZXP_OK;
 }

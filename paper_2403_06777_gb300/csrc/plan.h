@@ -54,6 +54,7 @@ struct Plan {
     zw64 K;                         // constant factor, G included
     int32_t e0 = 0;
     bool zero = false;              // the scalar is identically zero
+    bool has_zero = false;          // some term can vanish (zero forms present)
 };
 
 // Returns 0 or ZXP_ETOOBIG (more forms / pairs than the kernel supports).

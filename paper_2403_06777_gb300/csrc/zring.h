@@ -60,6 +60,11 @@ ZXP_HD zw64 zw_mul(zw64 a, zw64 b) {
     return r;
 }
 
+// a * n for an integer count n
+ZXP_HD zw64 zw_scale(zw64 a, uint64_t n) {
+    return zw_make(a.c[0] * n, a.c[1] * n, a.c[2] * n, a.c[3] * n);
+}
+
 // a * sqrt2, sqrt2 = w - w^3
 ZXP_HD zw64 zw_mul_sqrt2(zw64 a) {
     return zw_make(a.c[1] - a.c[3], a.c[0] + a.c[2], a.c[1] + a.c[3], a.c[2] - a.c[0]);

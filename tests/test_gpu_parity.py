@@ -150,6 +150,22 @@ def test_split_invariance_large_synthetic(ctx):
     assert same_raw(Z.zxp_eval(ctx, s, 777777, 1 << 18), o)
 
 
+def test_k36_counting_path_split_invariance(ctx):
+    # k = 36 with few odd nodes: the counting (histogram) kernel, with several
+    # slices per thread on the full range and one slice per thread on each
+    # quarter; both must give the same bits, and a sub-range matches the oracle
+    ps = zi.synthetic_ps(7, 36, n_lin=40, n_quad=25, n_node=4, odd_nodes_only=True, density=0.12)
+    s = Z.zxp_scalar_from_tables(ps.pack())
+    whole = Z.zxp_eval(ctx, s)
+    q = 1 << 34
+    acc = Z.zxp_eval(ctx, s, 0, q)
+    for i in range(1, 4):
+        acc = Z.zxp_zomega_add(acc, Z.zxp_eval(ctx, s, i * q, q))
+    assert acc == whole
+    o = oracle.ps_sum(ps.pack(), 123456789, 1 << 18, nthreads=NCPU)
+    assert same_raw(Z.zxp_eval(ctx, s, 123456789, 1 << 18), o)
+
+
 def test_submit_poll_matches_eval(ctx):
     scalars = []
     for seed in range(6):

@@ -11,7 +11,7 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/zxp.h"
+#include "zxp.h"
 #include "compile.h"
 #include "kernel.h"
 #include "plan.h"
@@ -27,6 +27,8 @@ namespace {
 struct DevTables {
     zw64* table = nullptr;
     zw64* pv = nullptr;
+    uint32_t* frows = nullptr;
+    uint64_t* adj = nullptr;
 };
 
 }  // namespace
@@ -43,8 +45,7 @@ struct zxp_scalar {
         cudaGetDevice(&prev);
         for (auto& e : dev) {
             cudaSetDevice(e.first);
-            cudaFree(e.second.table);
-            cudaFree(e.second.pv);
+            cudaFree(e.second.table);   // one allocation holds every table
         }
         if (prev >= 0) cudaSetDevice(prev);
     }
@@ -111,20 +112,35 @@ int ensure_device_tables(const zxp_scalar* s, int device, DevTables* out) {
     if (it != s->dev.end()) { *out = it->second; return ZXP_OK; }
     DevTables d;
     const Plan& pl = s->plan;
-    size_t tb = pl.table.size() * sizeof(zw64), pb = pl.pv.size() * sizeof(zw64);
-    if (cudaMalloc(&d.table, tb ? tb : sizeof(zw64)) != cudaSuccess) return ZXP_ENOMEM;
-    if (cudaMalloc(&d.pv, pb ? pb : sizeof(zw64)) != cudaSuccess) { cudaFree(d.table); return ZXP_ENOMEM; }
-    if (tb && cudaMemcpy(d.table, pl.table.data(), tb, cudaMemcpyHostToDevice) != cudaSuccess) return ZXP_ECUDA;
-    if (pb && cudaMemcpy(d.pv, pl.pv.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess) return ZXP_ECUDA;
+    // one allocation: table | phase-pair values | flip rows | adjacency
+    const size_t tb = pl.table.size() * sizeof(zw64), pb = pl.pv.size() * sizeof(zw64);
+    const size_t fb = pl.frows.size() * sizeof(uint32_t), ab = pl.adj.size() * sizeof(uint64_t);
+    const size_t o_pv = tb, o_f = o_pv + pb, o_adj = (o_f + fb + 7) & ~(size_t)7;
+    const size_t total = o_adj + ab + 8;
+    std::vector<unsigned char> host(total, 0);
+    if (tb) memcpy(host.data(), pl.table.data(), tb);
+    if (pb) memcpy(host.data() + o_pv, pl.pv.data(), pb);
+    if (fb) memcpy(host.data() + o_f, pl.frows.data(), fb);
+    if (ab) memcpy(host.data() + o_adj, pl.adj.data(), ab);
+    unsigned char* base = nullptr;
+    if (cudaMalloc(&base, total) != cudaSuccess) return ZXP_ENOMEM;
+    if (cudaMemcpy(base, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(base);
+        return ZXP_ECUDA;
+    }
+    d.table = reinterpret_cast<zw64*>(base);
+    d.pv = reinterpret_cast<zw64*>(base + o_pv);
+    d.frows = reinterpret_cast<uint32_t*>(base + o_f);
+    d.adj = reinterpret_cast<uint64_t*>(base + o_adj);
     s->dev[device] = d;
     *out = d;
     return ZXP_OK;
 }
 
 // Slice length and grid for `count` terms: one slice per thread of a full
-// resident grid, slices a multiple of 64 terms so that the lanes of a warp
-// flip the same variable at the same step (their start indices agree
-// modulo 64).
+// resident grid, slices a multiple of 8 terms so that the lanes of a warp
+// run the unrolled 8-step blocks in step (their start indices agree
+// modulo 8).
 void launch_shape(const zxp_ctx* ctx, const Plan& pl, uint64_t count, uint64_t* span, int* grid) {
     int bps = 1;
     if (sum_occupancy(pl, &bps) != cudaSuccess || bps < 1) bps = 1;
@@ -132,9 +148,9 @@ void launch_shape(const zxp_ctx* ctx, const Plan& pl, uint64_t count, uint64_t* 
     if (max_grid > ctx->max_grid) max_grid = ctx->max_grid;
     const uint64_t threads = (uint64_t)max_grid * (uint64_t)sum_threads();
     uint64_t sp = (count + threads - 1) / threads;
-    sp = (sp + 63) & ~63ull;
+    sp = (sp + 7) & ~7ull;
     if (sp < 64) sp = 64;
-    if (sp > (1ull << 18)) sp = 1ull << 18;   // longer ranges: several slices per thread
+    if (sp > sum_max_span(pl)) sp = sum_max_span(pl);   // longer ranges: several slices per thread
     const uint64_t nslices = (count + sp - 1) / sp;
     uint64_t g = (nslices + (uint64_t)sum_threads() - 1) / (uint64_t)sum_threads();
     if (g > (uint64_t)max_grid) g = (uint64_t)max_grid;
@@ -157,8 +173,8 @@ int enqueue(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, D
     uint64_t span;
     int grid;
     launch_shape(ctx, s->plan, count, &span, &grid);
-    return cuda_status(sum_launch(s->plan, d.table, d.pv, first, count, span, grid, ctx->partials,
-                                  ctx->counter, dres, ctx->stream));
+    return cuda_status(sum_launch(s->plan, d.table, d.pv, d.frows, d.adj, first, count, span, grid,
+                                  ctx->partials, ctx->counter, dres, ctx->stream));
 }
 
 // canonical form of an exact numerator (int64 coefficients) over sqrt2^e

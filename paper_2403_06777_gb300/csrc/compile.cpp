@@ -29,14 +29,12 @@
 #include "compile.h"
 
 #include <string.h>
-#include <stdio.h>
-#include <stdlib.h>
 
 #include <algorithm>
 #include <unordered_set>
 #include <vector>
 
-#include "../../include/zxp.h"
+#include "zxp.h"
 #include "zring.h"
 
 namespace zxp {
@@ -541,17 +539,6 @@ class PathSum {
                 continue;
             }
             // 3. every live variable is locked: decompose the T-form that frees most
-#ifdef ZXP_COMPILE_DEBUG
-            {
-                int nl = 0, hist[8] = {0}, sz = 0;
-                for (int v = 0; v < nvars; v++) if (live[(size_t)v]) { nl++; hist[std::min(7, locks[(size_t)v])]++; }
-                for (auto& f : tf) sz += f.count();
-                fprintf(stderr, "stuck: live=%d tf=%zu (avg size %.1f) nodes=%zu pairs=%zu locks:", nl, tf.size(),
-                        tf.empty() ? 0.0 : (double)sz / tf.size(), nodes.size(), pairs.size());
-                for (int i = 0; i < 8; i++) fprintf(stderr, " %d", hist[i]);
-                fprintf(stderr, "\n");
-            }
-#endif
             if (tf.empty()) {
                 if (compact()) continue;
                 break;
@@ -743,9 +730,6 @@ int compile_circuit(const zxp_gate* gates, size_t n_gates, int n, const uint8_t*
             {2, 3, 2, true}, {0, 1, 1, true}, {1, 1, 0, true}, {1000, 1000, 1, false},
         };
         PathSum::Strategy strat = kStrategies[t % 8];
-#ifdef ZXP_COMPILE_DEBUG
-        if (getenv("ZXP_STRAT")) sscanf(getenv("ZXP_STRAT"), "%d,%d,%d", &strat.node_damage_max, &strat.pair_damage_max, &strat.tform_gain_min);
-#endif
         Result r = run_once(gates, n_gates, n, in_bits, out_bits, marg_mask, kind,
                             mix64(seed), strat, opt.allow_pairs);
         if (r.status != ZXP_OK) continue;

@@ -22,7 +22,12 @@ namespace zxp {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr uint32_t kHistMaxOdd = 5;   // 8 * 6 counters per lane: 48 KB per block
+// counting variants: 32-bit counters for at most 5 odd nodes (48 counters per
+// lane, 48 KB per block), 16-bit counters packed two per word for at most 15
+// (128 counters per lane, 64 KB per block; slices shorter than 2^16 terms)
+constexpr uint32_t kHistMaxOdd32 = 5;
+constexpr uint32_t kHistMaxOdd16 = 15;
+constexpr uint64_t kSpan16 = 65528;   // largest multiple of 8 below 2^16
 
 template <int NW>
 __device__ __forceinline__ uint32_t bit_at(const uint32_t (&L)[NW], uint32_t pos) {
@@ -60,10 +65,11 @@ __device__ __forceinline__ zw64 block_reduce(zw64 v, zw64* sred) {
     return v;   // valid in thread 0
 }
 
-template <int NWN, int NWL, bool GENERAL, bool HIST>
+template <int NWN, int NWL, bool GENERAL, int HIST>
 __global__ void __launch_bounds__(kThreads)
 sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtable,
-           const zw64* __restrict__ gpv, uint64_t first, uint64_t count, uint64_t span,
+           const zw64* __restrict__ gpv, const uint32_t* __restrict__ gF,
+           const uint64_t* __restrict__ gADJ, uint64_t first, uint64_t count, uint64_t span,
            uint64_t nslices, zw64* __restrict__ partials, unsigned int* __restrict__ counter,
            const zw64 K, const int32_t e0, DevResult* __restrict__ result) {
     constexpr int NW = NWN + NWL;
@@ -74,45 +80,68 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
     zw64* sred = sPV + 4u * p.npairs;
     uint64_t* sADJ = reinterpret_cast<uint64_t*>(sred + kThreads / 32);
     uint32_t* sF = reinterpret_cast<uint32_t*>(sADJ + kMaxK);
-    // HIST: per-lane counters of the table index J * stride + M, laid out
-    // [warp][index][lane] so that every lane owns one bank
+    // HIST (1: 32-bit, 2: 16-bit counters): per-lane counters of the table
+    // index J * stride + M, laid out [warp][word][lane] so that every lane
+    // owns one bank; HIST == 2 packs indices 2w and 2w + 1 into word w
     uint32_t* sH = sF + kMaxK * NW;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t nwords = HIST == 2 ? (ntab + 1) / 2 : ntab;
     if (HIST) {
-        for (uint32_t i = threadIdx.x; i < ntab * (kThreads / 32) * 32u; i += blockDim.x) sH[i] = 0;
+        for (uint32_t i = threadIdx.x; i < nwords * kThreads; i += blockDim.x) sH[i] = 0;
     }
     for (uint32_t i = threadIdx.x; i < ntab; i += blockDim.x) sT[i] = gtable[i];
     if (GENERAL)
         for (uint32_t i = threadIdx.x; i < 4u * p.npairs; i += blockDim.x) sPV[i] = gpv[i];
-    for (uint32_t i = threadIdx.x; i < p.k; i += blockDim.x) {
-        sADJ[i] = p.ADJ[i];
-#pragma unroll
-        for (int w = 0; w < NW; w++) sF[i * NW + w] = p.F[i][w];
-    }
+    for (uint32_t i = threadIdx.x; i < p.k; i += blockDim.x) sADJ[i] = gADJ[i];
+    for (uint32_t i = threadIdx.x; i < p.k * NW; i += blockDim.x) sF[i] = gF[i];
+    for (uint32_t i = p.k + threadIdx.x; i < 3; i += blockDim.x) sADJ[i] = 0;
+    for (uint32_t i = p.k * NW + threadIdx.x; i < 3 * NW; i += blockDim.x) sF[i] = 0;
     __syncthreads();
 
     // flip rows and adjacency of the three lowest variables, in registers:
     // inside an aligned block of 8 Gray steps they are the only ones flipped
     uint32_t f0[NW], f1[NW], f2[NW];
 #pragma unroll
-    for (int w = 0; w < NW; w++) { f0[w] = p.F[0][w]; f1[w] = p.F[1][w]; f2[w] = p.F[2][w]; }
-    const uint64_t adj0 = p.ADJ[0], adj1 = p.ADJ[1], adj2 = p.ADJ[2];
+    for (int w = 0; w < NW; w++) { f0[w] = sF[w]; f1[w] = sF[NW + w]; f2[w] = sF[2 * NW + w]; }
+    const uint64_t adj0 = sADJ[0], adj1 = sADJ[1], adj2 = sADJ[2];
 
     zw64 acc = zw_zero();
     const uint64_t end = first + count;
     const uint64_t gstride = (uint64_t)gridDim.x * blockDim.x;
     // HIST: acc += sum_idx count(idx) * T[idx] (mod 2^64), counters reset
+    // The warp first adds each counter word over its 32 lanes (one redux);
+    // lane (i mod 32) then owns word i's multiply-adds.
     auto fold = [&]() {
-        for (uint32_t i = 0; i < ntab; i++) {
-            uint32_t* h = sH + ((warp * ntab + i) << 5) + lane;
-            const uint64_t c = *h;
-            if (c) { acc = zw_add(acc, zw_scale(lds_zw(sT + i), c)); *h = 0; }
+        __syncwarp();
+        for (uint32_t i = 0; i < nwords; i++) {
+            uint32_t* h = sH + ((warp * nwords + i) << 5) + lane;
+            const uint32_t c = *h;
+            *h = 0;
+            if (HIST == 2) {
+                const uint32_t lo = __reduce_add_sync(0xffffffffu, c & 0xFFFFu);
+                const uint32_t hi = __reduce_add_sync(0xffffffffu, c >> 16);
+                if ((i & 31u) == lane) {
+                    if (lo) acc = zw_madd32(acc, lds_zw(sT + 2 * i), lo);
+                    if (hi) acc = zw_madd32(acc, lds_zw(sT + 2 * i + 1), hi);
+                }
+            } else {
+                // a lane counts at most one slice (<= 2^18 terms) between
+                // folds, so the 32-lane sum fits in 32 bits
+                const uint32_t n = __reduce_add_sync(0xffffffffu, c);
+                if ((i & 31u) == lane && n) acc = zw_madd32(acc, lds_zw(sT + i), n);
+            }
         }
     };
-    // a thread with several slices (ranges beyond threads * 2^30 terms)
-    // folds after each one, so no 32-bit counter can overflow
-    const bool fold_each = nslices > gstride;
-    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nslices; s += gstride) {
+    // a thread with several slices folds after each one, so no counter can
+    // overflow (16-bit counters: every slice is shorter than 2^16 terms)
+    const bool fold_each = HIST == 2 || nslices > gstride;
+    // warp-uniform slice loop: every lane of a warp runs the same number of
+    // iterations (lanes past the end skip the work), so fold() can use
+    // full-warp reductions
+    for (uint64_t s0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); s0 < nslices;
+         s0 += gstride) {
+        const uint64_t s = s0 + lane;
+        if (s < nslices) {
         uint64_t t = first + s * span;
         const uint64_t tend = (end - t < span) ? end : t + span;
         const uint64_t x = t ^ (t >> 1);
@@ -152,7 +181,11 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
             }
             if (HIST) {
                 const uint32_t J = (P0 + 2u * P1 + 4u * ((uint32_t)__popc(X2) + q)) & 7u;
-                atomicAdd(sH + ((warp * ntab + J * p.tab_stride + M) << 5) + lane, 1u);
+                const uint32_t idx = J * p.tab_stride + M;
+                if (HIST == 2)
+                    atomicAdd(sH + ((warp * nwords + (idx >> 1)) << 5) + lane, 1u << ((idx & 1u) << 4));
+                else
+                    atomicAdd(sH + ((warp * nwords + idx) << 5) + lane, 1u);
             } else if (!GENERAL || Zb == 0) {
                 const uint32_t J = (P0 + 2u * P1 + 4u * ((uint32_t)__popc(X2) + q)) & 7u;
                 zw64 v = lds_zw(sT + J * p.tab_stride + M);
@@ -197,6 +230,7 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
 #pragma unroll
             for (int w = 0; w < NW; w++) L[w] ^= sF[i * NW + w];
         }
+        }   // s < nslices
         if (HIST && fold_each) fold();
     }
     if (HIST) fold();
@@ -230,33 +264,42 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
     }
 }
 
-using KernelFn = void (*)(const KernelParams, const zw64*, const zw64*, uint64_t, uint64_t,
+using KernelFn = void (*)(const KernelParams, const zw64*, const zw64*, const uint32_t*,
+                          const uint64_t*, uint64_t, uint64_t,
                           uint64_t, uint64_t, zw64*, unsigned int*, const zw64, const int32_t,
                           DevResult*);
 
-template <int NWN, int NWL, bool G, bool H>
+template <int NWN, int NWL, bool G, int H>
 constexpr KernelFn kfn() { return &sum_kernel<NWN, NWL, G, H>; }
 
-#define ZXP_ROW(N, G) {kfn<N, 1, G, false>(), kfn<N, 2, G, false>(), kfn<N, 3, G, false>(), kfn<N, 4, G, false>()}
+#define ZXP_ROW(N, G) {kfn<N, 1, G, 0>(), kfn<N, 2, G, 0>(), kfn<N, 3, G, 0>(), kfn<N, 4, G, 0>()}
 // [general][nwn][nwl - 1]
 const KernelFn kTable[2][kMaxWordsNode + 1][kMaxWordsOther] = {
     {ZXP_ROW(0, false), ZXP_ROW(1, false), ZXP_ROW(2, false), ZXP_ROW(3, false), ZXP_ROW(4, false)},
     {ZXP_ROW(0, true), ZXP_ROW(1, true), ZXP_ROW(2, true), ZXP_ROW(3, true), ZXP_ROW(4, true)},
 };
 #undef ZXP_ROW
-// counting variant: at most kHistMaxOdd odd nodes (so nwn <= 1), no pairs or zero forms
-const KernelFn kHist[2][kMaxWordsOther] = {
-    {kfn<0, 1, false, true>(), kfn<0, 2, false, true>(), kfn<0, 3, false, true>(), kfn<0, 4, false, true>()},
-    {kfn<1, 1, false, true>(), kfn<1, 2, false, true>(), kfn<1, 3, false, true>(), kfn<1, 4, false, true>()},
+#define ZXP_ROW(N, H) {kfn<N, 1, false, H>(), kfn<N, 2, false, H>(), kfn<N, 3, false, H>(), kfn<N, 4, false, H>()}
+// counting variants (no pairs or zero forms; at most 11 odd nodes, so nwn <= 1):
+// [16-bit counters][nwn][nwl - 1]
+const KernelFn kHist[2][2][kMaxWordsOther] = {
+    {ZXP_ROW(0, 1), ZXP_ROW(1, 1)},
+    {ZXP_ROW(0, 2), ZXP_ROW(1, 2)},
 };
+#undef ZXP_ROW
 
-bool use_hist(const Plan& pl) {
-    return pl.kp.npairs == 0 && !pl.has_zero && pl.m_odd <= kHistMaxOdd;
+// 0: table path, 1: 32-bit counters, 2: 16-bit counters
+int hist_mode(const Plan& pl) {
+    if (pl.kp.npairs > 0 || pl.has_zero) return 0;
+    if (pl.m_odd <= kHistMaxOdd32) return 1;
+    if (pl.m_odd <= kHistMaxOdd16) return 2;
+    return 0;
 }
 
 KernelFn pick(const Plan& pl) {
     const int nwl = pl.nwl < 1 ? 1 : pl.nwl;
-    if (use_hist(pl)) return kHist[pl.nwn][nwl - 1];
+    const int h = hist_mode(pl);
+    if (h) return kHist[h - 1][pl.nwn][nwl - 1];
     const bool general = pl.kp.npairs > 0 || pl.has_zero;
     return kTable[general ? 1 : 0][pl.nwn][nwl - 1];
 }
@@ -266,15 +309,19 @@ KernelFn pick(const Plan& pl) {
 size_t sum_smem_bytes(const Plan& pl) {
     const size_t nw = (size_t)pl.nwn + (size_t)(pl.nwl < 1 ? 1 : pl.nwl);
     const size_t ntab = 8u * (size_t)pl.kp.tab_stride;
+    const int h = hist_mode(pl);
+    const size_t hwords = h == 2 ? (ntab + 1) / 2 : (h == 1 ? ntab : 0);
     return sizeof(zw64) * (ntab + 4u * pl.kp.npairs + kThreads / 32) + sizeof(uint64_t) * kMaxK +
-           sizeof(uint32_t) * kMaxK * nw +
-           (use_hist(pl) ? sizeof(uint32_t) * ntab * (size_t)kThreads : 0);
+           sizeof(uint32_t) * kMaxK * nw + sizeof(uint32_t) * hwords * (size_t)kThreads;
 }
+
+uint64_t sum_max_span(const Plan& pl) { return hist_mode(pl) == 2 ? kSpan16 : (1ull << 18); }
 
 int sum_threads() { return kThreads; }
 
-cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, uint64_t first,
-                       uint64_t count, uint64_t span, int grid, zw64* partials,
+cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, const uint32_t* dF,
+                       const uint64_t* dADJ, uint64_t first, uint64_t count, uint64_t span,
+                       int grid, zw64* partials,
                        unsigned int* counter, DevResult* result, cudaStream_t stream) {
     KernelFn fn = pick(pl);
     const size_t smem = sum_smem_bytes(pl);
@@ -283,8 +330,8 @@ cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, uint
         if (e != cudaSuccess) return e;
     }
     const uint64_t nslices = (count + span - 1) / span;
-    fn<<<grid, kThreads, smem, stream>>>(pl.kp, dtable, dpv, first, count, span, nslices, partials,
-                                         counter, pl.K, pl.e0, result);
+    fn<<<grid, kThreads, smem, stream>>>(pl.kp, dtable, dpv, dF, dADJ, first, count, span, nslices,
+                                         partials, counter, pl.K, pl.e0, result);
     return cudaGetLastError();
 }
 

@@ -12,6 +12,8 @@ namespace zxp {
 // phase-pair values and the reduction scratch.
 size_t sum_smem_bytes(const Plan& pl);
 int sum_threads();
+// Longest slice one thread may take (a multiple of 8).
+uint64_t sum_max_span(const Plan& pl);
 cudaError_t sum_occupancy(const Plan& pl, int* blocks_per_sm);
 
 // Device copy of the public result record (same layout as zxp_zomega).
@@ -25,8 +27,9 @@ struct DevResult {
 // over `grid` blocks.  partials holds >= grid entries; *counter must be 0
 // on entry and is 0 again when the kernel ends; *result receives
 // K * (sum of the table terms) over sqrt2^e0, flagged raw.
-cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, uint64_t first,
-                       uint64_t count, uint64_t span, int grid, zw64* partials,
-                       unsigned int* counter, DevResult* result, cudaStream_t stream);
+cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, const uint32_t* dF,
+                       const uint64_t* dADJ, uint64_t first, uint64_t count, uint64_t span,
+                       int grid, zw64* partials, unsigned int* counter, DevResult* result,
+                       cudaStream_t stream);
 
 }  // namespace zxp

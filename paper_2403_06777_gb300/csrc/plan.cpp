@@ -6,7 +6,7 @@
 #include <map>
 #include <vector>
 
-#include "../../include/zxp.h"
+#include "zxp.h"
 
 namespace zxp {
 
@@ -106,11 +106,12 @@ int build_plan(const PS& ps, Plan* out) {
     pl.nwl = (int)((n_other + 31) / 32);
     if (pl.nwn > kMaxWordsNode || pl.nwl > kMaxWordsOther) return ZXP_ETOOBIG;
     kp.nbits = 32u * (uint32_t)(pl.nwn + pl.nwl);
+    const uint32_t nw = (uint32_t)(pl.nwn + (pl.nwl < 1 ? 1 : pl.nwl));   // kernel words
+    pl.frows.assign((size_t)k * nw, 0u);
     auto put = [&](uint32_t bit, uint64_t mask, uint32_t inv) {
-        kp.FM[bit] = mask;
         if (inv) kp.INV[bit >> 5] |= 1u << (bit & 31);
         for (uint32_t i = 0; i < k; i++)
-            if ((mask >> i) & 1) kp.F[i][bit >> 5] |= 1u << (bit & 31);
+            if ((mask >> i) & 1) pl.frows[(size_t)i * nw + (bit >> 5)] |= 1u << (bit & 31);
     };
     for (size_t j = 0; j < odd.size(); j++) {
         uint32_t bit = (uint32_t)j;
@@ -136,7 +137,7 @@ int build_plan(const PS& ps, Plan* out) {
         put(bit, pair_masks[j], 0);
         if (j & 1) kp.PB[j / 2] = (uint16_t)bit; else kp.PA[j / 2] = (uint16_t)bit;
     }
-    for (uint32_t i = 0; i < k; i++) kp.ADJ[i] = adj[i];
+    pl.adj.assign(adj, adj + k);
 
     // T[J][M] = w^(J + 2M) (1 + sqrt2)^M
     kp.tab_stride = pl.m_odd + 1;

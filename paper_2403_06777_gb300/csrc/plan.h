@@ -39,9 +39,6 @@ struct KernelParams {
     uint32_t CB[kMaxWordsNode];                       // class-B node bits
     uint32_t C0[kMaxWordsOther], C1[kMaxWordsOther], C2[kMaxWordsOther], Z[kMaxWordsOther];
     uint32_t INV[kMaxNW];    // initial inversion of each form bit
-    uint32_t F[kMaxK][kMaxNW];                        // forms holding variable i
-    uint64_t ADJ[kMaxK];     // quadratic part: 4 * sum_{i<j} A_ij x_i x_j
-    uint64_t FM[32 * kMaxNW];                         // variable mask of each form bit
     uint16_t PA[kMaxPairs], PB[kMaxPairs];            // bit positions of pair forms
 };
 
@@ -49,6 +46,8 @@ struct Plan {
     int nwn = 0, nwl = 0;           // node / other words
     uint32_t m_odd = 0;
     KernelParams kp;
+    std::vector<uint32_t> frows;    // k x NW: form bits holding variable i (flip rows)
+    std::vector<uint64_t> adj;      // k: quadratic part 4 sum_{i<j} A_ij x_i x_j, row i
     std::vector<zw64> table;        // 8 x (m_odd + 1): w^(J + 2M) (1 + sqrt2)^M
     std::vector<zw64> pv;           // 4 per pair: value at (lA, lB) = (b & 1, b >> 1)
     zw64 K;                         // constant factor, G included

@@ -7,7 +7,7 @@
 
 #include <string.h>
 
-#include "../../include/zxp.h"
+#include "zxp.h"
 
 namespace zxp {
 

@@ -65,6 +65,16 @@ ZXP_HD zw64 zw_scale(zw64 a, uint64_t n) {
     return zw_make(a.c[0] * n, a.c[1] * n, a.c[2] * n, a.c[3] * n);
 }
 
+// acc + a * n for a 32-bit count n (one wide multiply-add per coefficient)
+ZXP_HD zw64 zw_madd32(zw64 acc, zw64 a, uint32_t n) {
+    zw64 r;
+    for (int i = 0; i < 4; i++) {
+        const uint64_t lo = (uint64_t)(uint32_t)a.c[i] * n + acc.c[i];
+        r.c[i] = lo + ((uint64_t)((uint32_t)(a.c[i] >> 32) * n) << 32);
+    }
+    return r;
+}
+
 // a * sqrt2, sqrt2 = w - w^3
 ZXP_HD zw64 zw_mul_sqrt2(zw64 a) {
     return zw_make(a.c[1] - a.c[3], a.c[0] + a.c[2], a.c[1] + a.c[3], a.c[2] - a.c[0]);

@@ -166,6 +166,30 @@ def test_k36_counting_path_split_invariance(ctx):
     assert same_raw(Z.zxp_eval(ctx, s, 123456789, 1 << 18), o)
 
 
+@pytest.mark.parametrize("n_node", [5, 6, 8, 11, 12])
+def test_counting_paths_by_node_count(ctx, n_node):
+    # 32-bit counters up to 5 odd nodes, packed 16-bit counters up to 11,
+    # the table path beyond: identical results on ragged ranges
+    ps = zi.synthetic_ps(n_node, 17, n_lin=30, n_quad=12, n_node=n_node, odd_nodes_only=True,
+                         density=0.2)
+    check_ranges(ctx, ps, std_ranges(17, random.Random(n_node)))
+
+
+def test_k34_packed_counters_many_slices(ctx):
+    # 8 odd nodes at k = 34: every thread takes several slices shorter than
+    # 2^16 terms; chunking and the oracle agree
+    ps = zi.synthetic_ps(8, 34, n_lin=40, n_quad=25, n_node=8, odd_nodes_only=True, density=0.12)
+    s = Z.zxp_scalar_from_tables(ps.pack())
+    whole = Z.zxp_eval(ctx, s)
+    q = 1 << 32
+    acc = Z.zxp_eval(ctx, s, 0, q)
+    for i in range(1, 4):
+        acc = Z.zxp_zomega_add(acc, Z.zxp_eval(ctx, s, i * q, q))
+    assert acc == whole
+    o = oracle.ps_sum(ps.pack(), 987654321, 1 << 18, nthreads=NCPU)
+    assert same_raw(Z.zxp_eval(ctx, s, 987654321, 1 << 18), o)
+
+
 def test_submit_poll_matches_eval(ctx):
     scalars = []
     for seed in range(6):

@@ -152,6 +152,28 @@ int zxp_eval(zxp_ctx *ctx, const zxp_scalar *s, uint64_t first, uint64_t count,
 int zxp_eval_device(zxp_ctx *ctx, const zxp_scalar *s, uint64_t first, uint64_t count,
                     zxp_zomega *dev_out);
 
+/* zxp_eval_device without any allocation (the paper has no counterpart).
+ * For callers that cannot allocate device memory through the CUDA runtime:
+ * code under a memory manager that owns the whole device (a framework's
+ * caching allocator, a serving runtime's fixed arena) and latency-critical
+ * loops, where cudaMalloc / cudaFree would synchronise the device.  It needs
+ * no zxp_ctx.  The tables of `s` are staged, and the kernel's scratch (block
+ * partials, completion counter) kept, in one file-scope device array of
+ * 256 KB (at most 2048 blocks of partials), held on every GPU that loads the
+ * library until the process exits.  The range is queued on `cuda_stream`
+ * (NULL: the legacy default stream) of the current device, and the raw
+ * partial (40-byte zxp_zomega layout, flags bit 0 set) lands at `dev_out`, a
+ * caller-owned device pointer aligned to 8 bytes, when the stream reaches it.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the array and it keeps the
+ * last call's contents (the counter is cleared at each call): calls that
+ * overlap on the GPU, e.g. on two streams, race.  Errors: ZXP_EINVAL (range,
+ * null or unaligned pointer), ZXP_ETOOBIG (tables larger than the array),
+ * ZXP_ECUDA. */
+int zxp_eval_noalloc(const zxp_scalar *s, uint64_t first, uint64_t count,
+                     zxp_zomega *dev_out, void *cuda_stream);
+
 /* The whole sum over [0, 2^k), canonical.  Errors as zxp_eval, plus
  * ZXP_EOVERFLOW when e0 > 124 (64-bit numerators not provably exact). */
 int zxp_amplitude(zxp_ctx *ctx, const zxp_scalar *s, zxp_zomega *out);

@@ -71,6 +71,7 @@ def lib():
         L.zxp_eval.argtypes = [vp, vp, u64, u64, zp]
         L.zxp_amplitude.argtypes = [vp, vp, zp]
         L.zxp_eval_device.argtypes = [vp, vp, u64, u64, vp]
+        L.zxp_eval_noalloc.argtypes = [vp, u64, u64, vp, vp]
         L.zxp_submit.argtypes = [vp, vp, u64, u64, C.POINTER(u64)]
         L.zxp_poll.argtypes = [vp, u64, i64, zp]
         L.zxp_zomega_add.argtypes = [zp, zp, zp]
@@ -228,6 +229,17 @@ def zxp_eval_device(ctx: Ctx, s: Scalar, first: int, count: int, dev_out_ptr: in
            "zxp_eval_device")
 
 
+def zxp_eval_noalloc(s: Scalar, first: int, count: int, dev_out_ptr: int, cuda_stream: int = 0):
+    """zxp_eval_device for callers that cannot allocate: no context, no
+    allocation; the library's fixed static device scratch is used and the
+    raw partial lands at the caller's device address dev_out_ptr when
+    cuda_stream (0: legacy default stream) reaches it.  Calls that overlap
+    on the GPU race (they share the scratch)."""
+    _check(lib().zxp_eval_noalloc(s.handle, first, count, C.c_void_p(dev_out_ptr),
+                                  C.c_void_p(cuda_stream) if cuda_stream else None),
+           "zxp_eval_noalloc")
+
+
 def zxp_amplitude(ctx: Ctx, s: Scalar):
     """The whole sum, canonical (c0, c1, c2, c3, e)."""
     out = zxp_zomega()
@@ -276,6 +288,6 @@ def zxp_zomega_to_complex(a) -> complex:
 
 EXPORTED = ["zxp_ctx_create", "zxp_ctx_destroy", "zxp_compile", "zxp_scalar_from_tables",
             "zxp_scalar_to_tables", "zxp_scalar_info", "zxp_scalar_free", "zxp_eval",
-            "zxp_eval_device",
+            "zxp_eval_device", "zxp_eval_noalloc",
             "zxp_amplitude", "zxp_submit", "zxp_poll", "zxp_zomega_add", "zxp_zomega_canon",
             "zxp_zomega_to_complex", "zxp_strerror", "zxp_version"]

@@ -438,3 +438,108 @@ void zxp_zomega_to_complex(const zxp_zomega* z, double* re, double* im) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Evaluation without any allocation.
+//
+// Some callers cannot allocate device memory through the CUDA runtime: code
+// that runs under a memory manager owning the whole device (a framework's
+// caching allocator or a serving runtime's fixed arena, where a foreign
+// cudaMalloc breaks the accounting or fails), and latency-critical loops,
+// where cudaMalloc / cudaFree synchronise the device.  zxp_eval_noalloc
+// serves them: it stages the scalar's tables and keeps the kernel's scratch
+// (per-block partial sums and the completion counter) in one file-scope
+// device array of fixed size, and writes the result to a buffer the caller
+// owns.  It calls no allocating routine, host or device.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Layout of the static scratch: [counter, 256 B] [partials] [tables].
+constexpr size_t kNoAllocBytes = 256 * 1024;
+constexpr int kNoAllocMaxBlocks = 2048;
+constexpr size_t kNoAllocPartialsOff = 256;
+constexpr size_t kNoAllocTablesOff = kNoAllocPartialsOff + sizeof(zw64) * kNoAllocMaxBlocks;
+constexpr int kNoAllocMaxDevices = 64;
+
+struct NoAllocDevice {
+    bool ready = false;
+    unsigned char* base = nullptr;   // device address of the scratch array
+    int sm_count = 0;
+};
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+
+}  // namespace
+
+// Every GPU that loads the library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+extern "C" int zxp_eval_noalloc(const zxp_scalar* s, uint64_t first, uint64_t count,
+                                zxp_zomega* dev_out, void* cuda_stream) {
+    if (!s || !dev_out || ((uintptr_t)dev_out & 7)) return ZXP_EINVAL;
+    int st = check_range(s, first, count);
+    if (st != ZXP_OK) return st;
+    const Plan& pl = s->plan;
+    const size_t tb = pl.table.size() * sizeof(zw64), pb = pl.pv.size() * sizeof(zw64);
+    const size_t fb = pl.frows.size() * sizeof(uint32_t), ab = pl.adj.size() * sizeof(uint64_t);
+    const size_t o_pv = kNoAllocTablesOff + tb, o_f = o_pv + pb;
+    const size_t o_adj = (o_f + fb + 7) & ~(size_t)7;
+    if (o_adj + ab > kNoAllocBytes) return ZXP_ETOOBIG;   // tables exceed the static scratch
+
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return ZXP_ECUDA;
+    NoAllocDevice d;
+    {
+        // first call on this device: look up the array's device address with
+        // the device current (the host-side symbol is not a device address)
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        NoAllocDevice& e = g_noalloc_dev[dev];
+        if (!e.ready) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return ZXP_ECUDA;
+            if (cudaDeviceGetAttribute(&e.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                return ZXP_ECUDA;
+            e.base = static_cast<unsigned char*>(p);
+            e.ready = true;
+        }
+        d = e;
+    }
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+
+    // launch shape: one slice per thread of a resident grid, at most
+    // kNoAllocMaxBlocks blocks (the partials the array holds)
+    int bps = 1;
+    if (sum_occupancy(pl, &bps) != cudaSuccess || bps < 1) bps = 1;
+    int max_grid = d.sm_count * bps;
+    if (max_grid > kNoAllocMaxBlocks) max_grid = kNoAllocMaxBlocks;
+    const uint64_t threads = (uint64_t)max_grid * (uint64_t)sum_threads();
+    uint64_t sp = (count + threads - 1) / threads;
+    sp = (sp + 7) & ~7ull;
+    if (sp < 64) sp = 64;
+    if (sp > sum_max_span(pl)) sp = sum_max_span(pl);
+    const uint64_t nslices = (count + sp - 1) / sp;
+    uint64_t g = (nslices + (uint64_t)sum_threads() - 1) / (uint64_t)sum_threads();
+    if (g > (uint64_t)max_grid) g = (uint64_t)max_grid;
+    if (g < 1) g = 1;
+
+    // stage the tables (each call: the array keeps the last call's contents)
+    // and clear the completion counter, which must start at zero
+    unsigned char* base = d.base;
+    if (tb && cudaMemcpyAsync(base + kNoAllocTablesOff, pl.table.data(), tb, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+        return ZXP_ECUDA;
+    if (pb && cudaMemcpyAsync(base + o_pv, pl.pv.data(), pb, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+        return ZXP_ECUDA;
+    if (fb && cudaMemcpyAsync(base + o_f, pl.frows.data(), fb, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+        return ZXP_ECUDA;
+    if (ab && cudaMemcpyAsync(base + o_adj, pl.adj.data(), ab, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+        return ZXP_ECUDA;
+    if (cudaMemsetAsync(base, 0, sizeof(unsigned int), stream) != cudaSuccess) return ZXP_ECUDA;
+    return cuda_status(sum_launch(pl, reinterpret_cast<const zw64*>(base + kNoAllocTablesOff),
+                                  reinterpret_cast<const zw64*>(base + o_pv),
+                                  reinterpret_cast<const uint32_t*>(base + o_f),
+                                  reinterpret_cast<const uint64_t*>(base + o_adj), first, count, sp,
+                                  (int)g, reinterpret_cast<zw64*>(base + kNoAllocPartialsOff),
+                                  reinterpret_cast<unsigned int*>(base),
+                                  reinterpret_cast<DevResult*>(dev_out), stream));
+}

@@ -275,8 +275,10 @@ def main():
     # compiled n = 50 / t = 80 circuit needs k ~ 50, out of reach)
     large = None
     if rank == 0 and not os.environ.get("ZXP_BENCH_SKIP_LARGE"):
-        ps36 = zi.synthetic_ps(36, 36, n_lin=45, n_quad=30, n_node=20, odd_nodes_only=True,
-                               density=0.12)
+        # row counts of the compiled n = 50 / t = 80 circuit (seed 0: 59 linear,
+        # 47 quadratic, 13 odd-node and 1 phase-pair rows at k = 50), at k = 36
+        ps36 = zi.synthetic_ps(36, 36, n_lin=59, n_quad=36, n_node=13, n_pair=1,
+                               odd_nodes_only=True, density=0.12)
         s36 = Z.zxp_scalar_from_tables(ps36.pack())
         i36 = Z.zxp_scalar_info(s36)
         Z.zxp_eval_device(ctx, s36, 0, 1 << 30, out.data_ptr())
@@ -286,9 +288,56 @@ def main():
         b.record(stream)
         torch.cuda.synchronize()
         ms36 = a.elapsed_time(b)
-        large = {"workload": "synthetic k=36 (45 linear, 30 quadratic, 20 odd-node rows)",
+        large = {"workload": "synthetic k=36 (59 linear, 36 quadratic, 13 odd-node, 1 phase-pair rows)",
                  "terms": 1 << 36, "ms": ms36, "terms_per_s": (1 << 36) / (ms36 / 1e3),
                  "node_words": i36["node_words"], "other_words": i36["other_words"]}
+
+    # batched workload: 512 circuits (n ~ U[10,40], T ~ U[20,60]), one
+    # amplitude each: one launch per scalar vs one tuned, graph-captured batch
+    batch = None
+    if rank == 0 and not os.environ.get("ZXP_BENCH_SKIP_BATCH"):
+        items = [zi.workload_batch_item(i) for i in range(512)]
+        scal = [Z.zxp_compile(it.gates, it.n, it.out_bits) for it in items]
+        ks = [Z.zxp_scalar_info(x)["k"] for x in scal]
+        outs = torch.zeros(len(scal), 5, dtype=torch.int64, device="cuda")
+
+        def plain():
+            for j, x in enumerate(scal):
+                Z.zxp_eval_device(ctx, x, 0, 1 << ks[j], outs[j].data_ptr())
+
+        plain()
+        a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        a.record(stream)
+        for _ in range(reps):
+            plain()
+        b2.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = a.elapsed_time(b2) / reps
+        t0b = time.perf_counter()
+        bt = Z.zxp_batch_create(ctx, scal)
+        create_ms = (time.perf_counter() - t0b) * 1e3
+        res = Z.zxp_batch_run(bt)
+        want = [tuple(v[:4]) + (v[4] & 0xFFFFFFFF,) for v in outs.tolist()]
+        assert [tuple(r) for r in res] == want
+        a.record(stream)
+        for _ in range(reps):
+            Z.zxp_batch_run(bt)
+        b2.record(stream)
+        torch.cuda.synchronize()
+        batch_ms = a.elapsed_time(b2) / reps
+        binfo = Z.zxp_batch_info(bt)
+        batch = {"workload": "512 circuits, seeds 0-511, n~U[10,40], T~U[20,60], one amplitude each",
+                 "k_min": min(ks), "k_max": max(ks), "total_terms": sum(1 << x for x in ks),
+                 "plain_ms": plain_ms, "batch_ms": batch_ms,
+                 "plain_amplitudes_per_s": len(scal) / (plain_ms / 1e3),
+                 "batch_amplitudes_per_s": len(scal) / (batch_ms / 1e3),
+                 "batch_terms_per_s": sum(1 << x for x in ks) / (batch_ms / 1e3),
+                 "batch_create_ms": create_ms,
+                 "tuned": {"threads": binfo["threads"], "chunk_log2": binfo["chunk_log2"],
+                           "groups": binfo["n_groups"], "chunks": binfo["n_chunks"],
+                           "candidates": binfo["candidates"]}}
+        bt.close()
 
     if rank != 0:
         if dist:
@@ -326,6 +375,8 @@ def main():
     }
     if large:
         line["large"] = large
+    if batch:
+        line["batch"] = batch
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(blob, k)
     print(json.dumps(line))

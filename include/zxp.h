@@ -188,6 +188,40 @@ int zxp_submit(zxp_ctx *ctx, const zxp_scalar *s, uint64_t first, uint64_t count
  * ZXP_EAGAIN: not finished.  ZXP_ENOTFOUND: unknown ticket. */
 int zxp_poll(zxp_ctx *ctx, uint64_t ticket, int64_t timeout_us, zxp_zomega *out);
 
+/* ---- batches: many scalars, one persistent launch per kernel variant ------ */
+
+/* A batch evaluates the full sums of n scalars of uneven k together: every
+ * scalar's range is cut into chunks that resident blocks take from one
+ * work-stealing queue (App. E's reduction becomes 64-bit atomic adds into each
+ * scalar's result).  zxp_batch_create uploads the descriptors, times a few
+ * launch shapes (chunk size 2^12..2^20 terms, 128 or 256 threads per block)
+ * on the actual batch, keeps the fastest, and captures the whole evaluation
+ * (clears, launches, result copy) as a CUDA graph on the context's stream;
+ * zxp_batch_run replays it.  The scalars must outlive the batch; the context
+ * must not be used from another thread during create or run. */
+typedef struct zxp_batch zxp_batch;
+
+typedef struct {
+    uint32_t n_scalars;
+    uint32_t n_groups;           /* launches per run (one per kernel variant) */
+    uint32_t n_chunks;
+    uint32_t threads;            /* threads per block chosen by the tuner */
+    uint32_t chunk_log2;         /* chunk length 2^chunk_log2 terms chosen by the tuner */
+    uint32_t candidates;         /* launch shapes timed */
+    double tuned_us;             /* device time of the chosen shape */
+    double total_terms;          /* sum of 2^k */
+    uint32_t reserved[6];
+} zxp_batch_info_t;
+
+/* Errors: ZXP_EINVAL (n == 0, null scalar), ZXP_ENOMEM, ZXP_ECUDA. */
+int zxp_batch_create(zxp_ctx *ctx, const zxp_scalar *const *scalars, size_t n,
+                     zxp_batch **out);
+/* Run the batch and wait: out[i] receives scalar i's full raw sum (as
+ * zxp_eval over [0, 2^k); canonicalise with zxp_zomega_canon). */
+int zxp_batch_run(zxp_batch *b, zxp_zomega *out);
+int zxp_batch_info(const zxp_batch *b, zxp_batch_info_t *info);
+void zxp_batch_destroy(zxp_batch *b);
+
 /* ---- exact scalar helpers (host) ---------------------------------------- */
 
 /* a + b, after bringing both to the larger exponent (x sqrt2 per step). */

@@ -45,6 +45,13 @@ class zxp_scalar_info_t(C.Structure):
                 ("reserved", C.c_uint32 * 5)]
 
 
+class zxp_batch_info_t(C.Structure):
+    _fields_ = [("n_scalars", C.c_uint32), ("n_groups", C.c_uint32), ("n_chunks", C.c_uint32),
+                ("threads", C.c_uint32), ("chunk_log2", C.c_uint32), ("candidates", C.c_uint32),
+                ("tuned_us", C.c_double), ("total_terms", C.c_double),
+                ("reserved", C.c_uint32 * 6)]
+
+
 _lib = None
 
 
@@ -74,6 +81,10 @@ def lib():
         L.zxp_eval_noalloc.argtypes = [vp, u64, u64, vp, vp]
         L.zxp_submit.argtypes = [vp, vp, u64, u64, C.POINTER(u64)]
         L.zxp_poll.argtypes = [vp, u64, i64, zp]
+        L.zxp_batch_create.argtypes = [vp, C.POINTER(vp), sz, C.POINTER(vp)]
+        L.zxp_batch_run.argtypes = [vp, zp]
+        L.zxp_batch_info.argtypes = [vp, C.POINTER(zxp_batch_info_t)]
+        L.zxp_batch_destroy.argtypes, L.zxp_batch_destroy.restype = [vp], None
         L.zxp_zomega_add.argtypes = [zp, zp, zp]
         L.zxp_zomega_canon.argtypes = [zp, zp]
         L.zxp_zomega_to_complex.argtypes = [zp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -265,6 +276,50 @@ def zxp_poll(ctx: Ctx, ticket: int, timeout_us: int = -1):
     return out.tup()
 
 
+class Batch:
+    """A zxp_batch (zxp_batch_destroy on close); keeps its scalars alive."""
+
+    def __init__(self, handle: int, scalars):
+        self.handle = C.c_void_p(handle)
+        self.scalars = list(scalars)
+
+    def close(self):
+        if self.handle:
+            lib().zxp_batch_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def zxp_batch_create(ctx: Ctx, scalars) -> Batch:
+    """Tune and capture one batched evaluation of the full sums of `scalars`."""
+    arr = (C.c_void_p * len(scalars))(*[s.handle.value for s in scalars])
+    h = C.c_void_p()
+    _check(lib().zxp_batch_create(ctx.handle, arr, len(scalars), C.byref(h)), "zxp_batch_create")
+    return Batch(h.value, scalars)
+
+
+def zxp_batch_run(b: Batch):
+    """Raw full sums, one (c0, c1, c2, c3, e0) per scalar, in order."""
+    out = (zxp_zomega * len(b.scalars))()
+    _check(lib().zxp_batch_run(b.handle, out), "zxp_batch_run")
+    return [z.tup() for z in out]
+
+
+def zxp_batch_info(b: Batch) -> dict:
+    info = zxp_batch_info_t()
+    _check(lib().zxp_batch_info(b.handle, C.byref(info)), "zxp_batch_info")
+    return {f: getattr(info, f) for f, _ in zxp_batch_info_t._fields_ if f != "reserved"}
+
+
+def zxp_batch_destroy(b: Batch):
+    b.close()
+
+
 def zxp_zomega_add(a, b):
     out = zxp_zomega()
     za, zb = _z(a), _z(b)
@@ -288,6 +343,7 @@ def zxp_zomega_to_complex(a) -> complex:
 
 EXPORTED = ["zxp_ctx_create", "zxp_ctx_destroy", "zxp_compile", "zxp_scalar_from_tables",
             "zxp_scalar_to_tables", "zxp_scalar_info", "zxp_scalar_free", "zxp_eval",
-            "zxp_eval_device", "zxp_eval_noalloc",
+            "zxp_eval_device", "zxp_eval_noalloc", "zxp_batch_create", "zxp_batch_run",
+            "zxp_batch_info", "zxp_batch_destroy",
             "zxp_amplitude", "zxp_submit", "zxp_poll", "zxp_zomega_add", "zxp_zomega_canon",
             "zxp_zomega_to_complex", "zxp_strerror", "zxp_version"]

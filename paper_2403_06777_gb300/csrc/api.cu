@@ -3,7 +3,9 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -29,6 +31,7 @@ struct DevTables {
     zw64* pv = nullptr;
     uint32_t* frows = nullptr;
     uint64_t* adj = nullptr;
+    uint32_t* seek = nullptr;
 };
 
 }  // namespace
@@ -112,16 +115,19 @@ int ensure_device_tables(const zxp_scalar* s, int device, DevTables* out) {
     if (it != s->dev.end()) { *out = it->second; return ZXP_OK; }
     DevTables d;
     const Plan& pl = s->plan;
-    // one allocation: table | phase-pair values | flip rows | adjacency
+    // one allocation: table | phase-pair values | flip rows | adjacency | seek tables
     const size_t tb = pl.table.size() * sizeof(zw64), pb = pl.pv.size() * sizeof(zw64);
     const size_t fb = pl.frows.size() * sizeof(uint32_t), ab = pl.adj.size() * sizeof(uint64_t);
+    const size_t sb = pl.seek.size() * sizeof(uint32_t);
     const size_t o_pv = tb, o_f = o_pv + pb, o_adj = (o_f + fb + 7) & ~(size_t)7;
-    const size_t total = o_adj + ab + 8;
+    const size_t o_seek = (o_adj + ab + 15) & ~(size_t)15;
+    const size_t total = o_seek + sb + 16;
     std::vector<unsigned char> host(total, 0);
     if (tb) memcpy(host.data(), pl.table.data(), tb);
     if (pb) memcpy(host.data() + o_pv, pl.pv.data(), pb);
     if (fb) memcpy(host.data() + o_f, pl.frows.data(), fb);
     if (ab) memcpy(host.data() + o_adj, pl.adj.data(), ab);
+    if (sb) memcpy(host.data() + o_seek, pl.seek.data(), sb);
     unsigned char* base = nullptr;
     if (cudaMalloc(&base, total) != cudaSuccess) return ZXP_ENOMEM;
     if (cudaMemcpy(base, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -132,6 +138,7 @@ int ensure_device_tables(const zxp_scalar* s, int device, DevTables* out) {
     d.pv = reinterpret_cast<zw64*>(base + o_pv);
     d.frows = reinterpret_cast<uint32_t*>(base + o_f);
     d.adj = reinterpret_cast<uint64_t*>(base + o_adj);
+    d.seek = reinterpret_cast<uint32_t*>(base + o_seek);
     s->dev[device] = d;
     *out = d;
     return ZXP_OK;
@@ -173,8 +180,8 @@ int enqueue(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, D
     uint64_t span;
     int grid;
     launch_shape(ctx, s->plan, count, &span, &grid);
-    return cuda_status(sum_launch(s->plan, d.table, d.pv, d.frows, d.adj, first, count, span, grid,
-                                  ctx->partials, ctx->counter, dres, ctx->stream));
+    return cuda_status(sum_launch(s->plan, d.table, d.pv, d.frows, d.adj, d.seek, first, count, span,
+                                  grid, ctx->partials, ctx->counter, dres, ctx->stream));
 }
 
 // canonical form of an exact numerator (int64 coefficients) over sqrt2^e
@@ -440,6 +447,247 @@ void zxp_zomega_to_complex(const zxp_zomega* z, double* re, double* im) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+
+struct zxp_batch {
+    zxp_ctx* ctx = nullptr;
+    size_t n = 0;
+    struct Group {
+        int key;
+        uint32_t ntab_cap, npairs_cap;
+        std::vector<uint32_t> members;
+        uint32_t off = 0, count = 0;   // chunk range of this group
+        int grid = 1;
+    };
+    std::vector<Group> groups;
+    BatchScalar* d_scalars = nullptr;
+    BatchChunk* d_chunks = nullptr;
+    size_t chunk_cap = 0;
+    unsigned int* d_queue = nullptr;
+    DevResult* d_results = nullptr;
+    DevResult* h_results = nullptr;
+    int threads = 256;
+    uint32_t chunk_log2 = 16;
+    uint32_t candidates = 0;
+    double tuned_us = 0, total_terms = 0;
+    std::vector<uint32_t> k;   // per scalar
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+
+    ~zxp_batch() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaFree(d_scalars);
+        cudaFree(d_chunks);
+        cudaFree(d_queue);
+        cudaFree(d_results);
+        cudaFreeHost(h_results);
+    }
+};
+
+namespace {
+
+// Chunk list for chunk length 2^clog: groups contiguous, a scalar's chunks
+// in index order.
+std::vector<BatchChunk> batch_chunks(zxp_batch* b, uint32_t clog) {
+    std::vector<BatchChunk> out;
+    for (auto& g : b->groups) {
+        g.off = (uint32_t)out.size();
+        for (uint32_t m : g.members) {
+            const uint64_t total = 1ull << b->k[m];
+            const uint64_t len = 1ull << clog;
+            for (uint64_t f = 0; f < total; f += len)
+                out.push_back(BatchChunk{m, 0, f, (total - f < len) ? total - f : len});
+        }
+        g.count = (uint32_t)out.size() - g.off;
+    }
+    return out;
+}
+
+int batch_upload_chunks(zxp_batch* b, const std::vector<BatchChunk>& ch) {
+    if (ch.size() > b->chunk_cap) {
+        cudaFree(b->d_chunks);
+        b->d_chunks = nullptr;
+        b->chunk_cap = 0;
+        if (cudaMalloc(&b->d_chunks, ch.size() * sizeof(BatchChunk)) != cudaSuccess) return ZXP_ENOMEM;
+        b->chunk_cap = ch.size();
+    }
+    if (cudaMemcpy(b->d_chunks, ch.data(), ch.size() * sizeof(BatchChunk), cudaMemcpyHostToDevice) != cudaSuccess)
+        return ZXP_ECUDA;
+    return ZXP_OK;
+}
+
+int batch_shape(zxp_batch* b, int threads) {
+    for (auto& g : b->groups) {
+        int bps = 0;
+        if (batch_occupancy(g.key, g.ntab_cap, g.npairs_cap, threads, &bps) != cudaSuccess || bps < 1)
+            return ZXP_ECUDA;
+        int grid = b->ctx->sm_count * bps;
+        if ((uint32_t)grid > g.count) grid = (int)g.count;
+        g.grid = grid < 1 ? 1 : grid;
+    }
+    return ZXP_OK;
+}
+
+// clears, one launch per group, and the result copy, all on the stream
+int batch_enqueue(zxp_batch* b, bool copy_out) {
+    cudaStream_t st = b->ctx->stream;
+    if (cudaMemsetAsync(b->d_results, 0, b->n * sizeof(DevResult), st) != cudaSuccess) return ZXP_ECUDA;
+    if (cudaMemsetAsync(b->d_queue, 0, b->groups.size() * sizeof(unsigned int), st) != cudaSuccess) return ZXP_ECUDA;
+    for (size_t i = 0; i < b->groups.size(); i++) {
+        const auto& g = b->groups[i];
+        if (!g.count) continue;
+        if (batch_launch(g.key, b->d_scalars, b->d_chunks + g.off, g.count, b->d_queue + i,
+                         b->d_results, g.ntab_cap, g.npairs_cap, b->threads, g.grid, 1, st) != cudaSuccess)
+            return ZXP_ECUDA;
+    }
+    if (copy_out && cudaMemcpyAsync(b->h_results, b->d_results, b->n * sizeof(DevResult),
+                                    cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return ZXP_ECUDA;
+    return ZXP_OK;
+}
+
+}  // namespace
+
+extern "C" int zxp_batch_create(zxp_ctx* ctx, const zxp_scalar* const* scalars, size_t n,
+                                zxp_batch** out) {
+    if (!ctx || !scalars || !out || n == 0 || n > 0xFFFFFFFFu) return ZXP_EINVAL;
+    *out = nullptr;
+    DeviceGuard dg(ctx->device);
+    std::unique_ptr<zxp_batch> b(new (std::nothrow) zxp_batch());
+    if (!b) return ZXP_ENOMEM;
+    b->ctx = ctx;
+    b->n = n;
+    std::vector<BatchScalar> hs(n);
+    std::map<int, size_t> gidx;
+    for (size_t i = 0; i < n; i++) {
+        const zxp_scalar* s = scalars[i];
+        if (!s) return ZXP_EINVAL;
+        DevTables d;
+        int st = ensure_device_tables(s, ctx->device, &d);
+        if (st != ZXP_OK) return st;
+        const Plan& pl = s->plan;
+        BatchScalar& bs = hs[i];
+        bs.kp = pl.kp;
+        bs.table = d.table;
+        bs.pv = d.pv;
+        bs.frows = d.frows;
+        bs.adj = d.adj;
+        bs.seek = d.seek;
+        bs.K = pl.K;
+        bs.e0 = pl.e0;
+        bs.key = batch_key(pl);
+        b->k.push_back(s->ps.k);
+        b->total_terms += std::ldexp(1.0, (int)s->ps.k);
+        auto it = gidx.find(bs.key);
+        if (it == gidx.end()) {
+            it = gidx.emplace(bs.key, b->groups.size()).first;
+            b->groups.push_back(zxp_batch::Group{bs.key, 0, 0, {}, 0, 0, 1});
+        }
+        auto& g = b->groups[it->second];
+        g.members.push_back((uint32_t)i);
+        g.ntab_cap = std::max(g.ntab_cap, pl.kp.tab_size);
+        g.npairs_cap = std::max(g.npairs_cap, pl.kp.npairs);
+    }
+    if (cudaMalloc(&b->d_scalars, n * sizeof(BatchScalar)) != cudaSuccess) return ZXP_ENOMEM;
+    if (cudaMemcpy(b->d_scalars, hs.data(), n * sizeof(BatchScalar), cudaMemcpyHostToDevice) != cudaSuccess)
+        return ZXP_ECUDA;
+    if (cudaMalloc(&b->d_queue, b->groups.size() * sizeof(unsigned int)) != cudaSuccess) return ZXP_ENOMEM;
+    if (cudaMalloc(&b->d_results, n * sizeof(DevResult)) != cudaSuccess) return ZXP_ENOMEM;
+    if (cudaMallocHost(&b->h_results, n * sizeof(DevResult)) != cudaSuccess) return ZXP_ENOMEM;
+
+    // tuner: time every (chunk length, block size) candidate on this batch
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return ZXP_ECUDA;
+    double best = -1;
+    uint32_t best_clog = 16;
+    int best_threads = 256;
+    int st = ZXP_OK;
+    for (uint32_t clog = 12; clog <= 20 && st == ZXP_OK; clog += 2) {
+        std::vector<BatchChunk> ch = batch_chunks(b.get(), clog);
+        if (ch.size() > (1u << 22)) continue;
+        if ((st = batch_upload_chunks(b.get(), ch)) != ZXP_OK) break;
+        for (int threads : {128, 256}) {
+            b->threads = threads;
+            if ((st = batch_shape(b.get(), threads)) != ZXP_OK) break;
+            if ((st = batch_enqueue(b.get(), false)) != ZXP_OK) break;   // warm-up
+            double t_min = -1;
+            for (int rep = 0; rep < 2; rep++) {
+                cudaEventRecord(e0, ctx->stream);
+                if ((st = batch_enqueue(b.get(), false)) != ZXP_OK) break;
+                cudaEventRecord(e1, ctx->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) { st = ZXP_ECUDA; break; }
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (t_min < 0 || ms < t_min) t_min = ms;
+            }
+            b->candidates++;
+            if (st == ZXP_OK && (best < 0 || t_min < best)) {
+                best = t_min;
+                best_clog = clog;
+                best_threads = threads;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != ZXP_OK) return st;
+    b->chunk_log2 = best_clog;
+    b->threads = best_threads;
+    b->tuned_us = best * 1e3;
+    if ((st = batch_upload_chunks(b.get(), batch_chunks(b.get(), best_clog))) != ZXP_OK) return st;
+    if ((st = batch_shape(b.get(), best_threads)) != ZXP_OK) return st;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return ZXP_ECUDA;
+
+    // capture the evaluation as a graph on the context's stream
+    if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return ZXP_ECUDA;
+    st = batch_enqueue(b.get(), true);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+    if (st != ZXP_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return st != ZXP_OK ? st : ZXP_ECUDA;
+    }
+    b->graph = graph;
+    if (cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) return ZXP_ECUDA;
+    *out = b.release();
+    return ZXP_OK;
+}
+
+extern "C" int zxp_batch_run(zxp_batch* b, zxp_zomega* out) {
+    if (!b || !out) return ZXP_EINVAL;
+    DeviceGuard dg(b->ctx->device);
+    if (cudaGraphLaunch(b->exec, b->ctx->stream) != cudaSuccess) return ZXP_ECUDA;
+    if (cudaStreamSynchronize(b->ctx->stream) != cudaSuccess) return ZXP_ECUDA;
+    memcpy(out, b->h_results, b->n * sizeof(zxp_zomega));
+    return ZXP_OK;
+}
+
+extern "C" int zxp_batch_info(const zxp_batch* b, zxp_batch_info_t* info) {
+    if (!b || !info) return ZXP_EINVAL;
+    memset(info, 0, sizeof *info);
+    info->n_scalars = (uint32_t)b->n;
+    info->n_groups = (uint32_t)b->groups.size();
+    uint32_t nch = 0;
+    for (auto& g : b->groups) nch += g.count;
+    info->n_chunks = nch;
+    info->threads = (uint32_t)b->threads;
+    info->chunk_log2 = b->chunk_log2;
+    info->candidates = b->candidates;
+    info->tuned_us = b->tuned_us;
+    info->total_terms = b->total_terms;
+    return ZXP_OK;
+}
+
+extern "C" void zxp_batch_destroy(zxp_batch* b) {
+    if (!b) return;
+    DeviceGuard dg(b->ctx->device);
+    cudaStreamSynchronize(b->ctx->stream);
+    delete b;
+}
+
+// ---------------------------------------------------------------------------
 // Evaluation without any allocation.
 //
 // Some callers cannot allocate device memory through the CUDA runtime: code
@@ -485,7 +733,9 @@ extern "C" int zxp_eval_noalloc(const zxp_scalar* s, uint64_t first, uint64_t co
     const size_t fb = pl.frows.size() * sizeof(uint32_t), ab = pl.adj.size() * sizeof(uint64_t);
     const size_t o_pv = kNoAllocTablesOff + tb, o_f = o_pv + pb;
     const size_t o_adj = (o_f + fb + 7) & ~(size_t)7;
-    if (o_adj + ab > kNoAllocBytes) return ZXP_ETOOBIG;   // tables exceed the static scratch
+    const size_t sb = pl.seek.size() * sizeof(uint32_t);
+    const size_t o_seek = (o_adj + ab + 15) & ~(size_t)15;
+    if (o_seek + sb > kNoAllocBytes) return ZXP_ETOOBIG;   // tables exceed the static scratch
 
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return ZXP_ECUDA;
@@ -534,11 +784,14 @@ extern "C" int zxp_eval_noalloc(const zxp_scalar* s, uint64_t first, uint64_t co
         return ZXP_ECUDA;
     if (ab && cudaMemcpyAsync(base + o_adj, pl.adj.data(), ab, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return ZXP_ECUDA;
+    if (sb && cudaMemcpyAsync(base + o_seek, pl.seek.data(), sb, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+        return ZXP_ECUDA;
     if (cudaMemsetAsync(base, 0, sizeof(unsigned int), stream) != cudaSuccess) return ZXP_ECUDA;
     return cuda_status(sum_launch(pl, reinterpret_cast<const zw64*>(base + kNoAllocTablesOff),
                                   reinterpret_cast<const zw64*>(base + o_pv),
                                   reinterpret_cast<const uint32_t*>(base + o_f),
-                                  reinterpret_cast<const uint64_t*>(base + o_adj), first, count, sp,
+                                  reinterpret_cast<const uint64_t*>(base + o_adj),
+                                  reinterpret_cast<const uint32_t*>(base + o_seek), first, count, sp,
                                   (int)g, reinterpret_cast<zw64*>(base + kNoAllocPartialsOff),
                                   reinterpret_cast<unsigned int*>(base),
                                   reinterpret_cast<DevResult*>(dev_out), stream));

@@ -515,7 +515,9 @@ class PathSum {
                     if (nkey < 0 || key < nkey) { nkey = key; nu = v; ndam = d; }
                     long key_w = (long)d * 64 + r;      // most damaging: decompose it
                     if (wkey < 0 || key_w > wkey) { wkey = key_w; wu = v; }
-                    if (!allow_pairs) return;
+                    // at most kFoldPairs phase-pairs: the kernel folds that many into
+                    // its term table; more would need a Z[w] product per pair and term
+                    if (!allow_pairs || pairs.size() >= 2) return;
                     adj[(size_t)v].each([&](int w) {
                         if (w <= v || !freev.get(w)) return;
                         Bits un = adj[(size_t)v];

@@ -28,8 +28,43 @@ struct DevResult {
 // on entry and is 0 again when the kernel ends; *result receives
 // K * (sum of the table terms) over sqrt2^e0, flagged raw.
 cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, const uint32_t* dF,
-                       const uint64_t* dADJ, uint64_t first, uint64_t count, uint64_t span,
-                       int grid, zw64* partials, unsigned int* counter, DevResult* result,
-                       cudaStream_t stream);
+                       const uint64_t* dADJ, const uint32_t* dS, uint64_t first, uint64_t count,
+                       uint64_t span, int grid, zw64* partials, unsigned int* counter,
+                       DevResult* result, cudaStream_t stream);
+
+// ---- batches (batch.cu) -----------------------------------------------------
+
+// One scalar of a batch, as the batch kernel reads it (device memory).
+struct BatchScalar {
+    KernelParams kp;
+    const zw64* table;
+    const zw64* pv;
+    const uint32_t* frows;
+    const uint64_t* adj;
+    const uint32_t* seek;
+    zw64 K;
+    int32_t e0;
+    int32_t key;
+};
+
+// A range [first, first + count) of one scalar; first is a multiple of 8.
+struct BatchChunk {
+    uint32_t scalar;
+    uint32_t reserved;
+    uint64_t first;
+    uint64_t count;
+};
+
+// Kernel variant of a scalar: scalars with equal keys share a launch.
+int batch_key(const Plan& pl);
+size_t batch_smem_bytes(int key, uint32_t ntab_cap, uint32_t npairs_cap, int threads);
+cudaError_t batch_occupancy(int key, uint32_t ntab_cap, uint32_t npairs_cap, int threads,
+                            int* blocks_per_sm);
+// Persistent launch over chunks[0, nchunks) (one variant); *queue must be 0
+// and results[] zero for the scalars it touches.
+cudaError_t batch_launch(int key, const BatchScalar* scalars, const BatchChunk* chunks,
+                         uint32_t nchunks, unsigned int* queue, DevResult* results,
+                         uint32_t ntab_cap, uint32_t npairs_cap, int threads, int grid,
+                         uint32_t slices_per_thread, cudaStream_t stream);
 
 }  // namespace zxp

@@ -1,0 +1,343 @@
+// kernel_core.cuh -- device code shared by the single-scalar and the batched
+// sum kernels: shared-memory layout of one scalar's tables, the per-thread
+// Gray-code walk over slices, and the block reduction.
+//
+// Each thread walks contiguous Gray-code slices [t0, t0 + span) of the
+// assignment space (x = t ^ (t >> 1)); consecutive assignments differ in the
+// bit ctz(t), so a step XORs that variable's flip row into the form bits
+// (the AND / XOR-reduce steps of Sec. 3.3 done incrementally) and updates the
+// quadratic phase with one bit of A x.  A term is then one table entry
+// K * w^(J + 2M) (1 + sqrt2)^M (see plan.h), multiplied by any phase-pair
+// values, accumulated in four int64 coefficients modulo 2^64 -- or, in the
+// counting variants, the pair (J, M) is counted and the counts are folded
+// into Z[w] at the end of each slice batch.  Integer adds make the result
+// bit-exact and independent of the reduction order.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernel.h"
+#include "plan.h"
+
+namespace zxp {
+namespace core {
+
+constexpr int kMaxThreads = 256;
+constexpr int kMaxWarps = kMaxThreads / 32;
+// counting variants: 32-bit counters for tables of at most 48 entries (48 KB
+// per 256-thread block), 16-bit counters packed two per word for at most 128
+// (64 KB per block; slices shorter than 2^16 terms)
+constexpr uint64_t kSpan16 = 65528;        // largest multiple of 8 below 2^16
+constexpr uint64_t kSpan32 = 1ull << 18;   // longest slice of the other variants
+
+template <int NW>
+__device__ __forceinline__ uint32_t bit_at(const uint32_t (&L)[NW], uint32_t pos) {
+    uint32_t wsel = pos >> 5, v = 0;
+#pragma unroll
+    for (int q = 0; q < NW; q++) v = (wsel == (uint32_t)q) ? L[q] : v;
+    return (v >> (pos & 31)) & 1u;
+}
+
+__device__ __forceinline__ zw64 lds_zw(const zw64* p) {
+    const ulonglong2* q = reinterpret_cast<const ulonglong2*>(p);
+    ulonglong2 a = q[0], b = q[1];
+    return zw_make(a.x, a.y, b.x, b.y);
+}
+
+__device__ __forceinline__ zw64 shfl_xor_zw(zw64 v, int off) {
+    zw64 r;
+#pragma unroll
+    for (int c = 0; c < 4; c++) r.c[c] = __shfl_xor_sync(0xffffffffu, v.c[c], off);
+    return r;
+}
+
+// warp shuffles, then one value per warp through shared memory; the block
+// total is valid in thread 0
+__device__ __forceinline__ zw64 block_reduce(zw64 v, zw64* sred) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = zw_add(v, shfl_xor_zw(v, off));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sred[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = (lane < (int)(blockDim.x >> 5)) ? sred[lane] : zw_zero();
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v = zw_add(v, shfl_xor_zw(v, off));
+    }
+    return v;
+}
+
+// 0: table path, 1: 32-bit counters, 2: 16-bit counters (by the number of
+// distinct term values the table holds)
+constexpr uint32_t kHistMaxEntries32 = 48;
+constexpr uint32_t kHistMaxEntries16 = 128;
+inline int hist_mode(const Plan& pl) {
+    if (pl.general) return 0;
+    if (pl.kp.tab_size <= kHistMaxEntries32) return 1;
+    if (pl.kp.tab_size <= kHistMaxEntries16) return 2;
+    return 0;
+}
+inline int kernel_words(const Plan& pl) { return pl.nwn + (pl.nwl < 1 ? 1 : pl.nwl); }
+// kernel variant: 0 table, 1 table + extra index bits, 2 general (phase-pair
+// products), 3/4 32-bit counters (+ extra bits), 5/6 16-bit counters (+ extra)
+inline int variant(const Plan& pl) {
+    if (pl.general) return 2;
+    const int x = pl.kp.xshift ? 1 : 0;
+    const int h = hist_mode(pl);
+    return h == 0 ? x : (h == 1 ? 3 + x : 5 + x);
+}
+__host__ __device__ constexpr bool var_general(int v) { return v == 2; }
+__host__ __device__ constexpr int var_hist(int v) { return v >= 5 ? 2 : (v >= 3 ? 1 : 0); }
+__host__ __device__ constexpr bool var_xtra(int v) { return v == 1 || v == 4 || v == 6; }
+inline uint32_t hist_words(int h, uint32_t ntab) {
+    return h == 2 ? (ntab + 1) / 2 : (h == 1 ? ntab : 0);
+}
+inline uint64_t max_span(int h) { return h == 2 ? kSpan16 : kSpan32; }
+
+// Shared memory of one block: [table][pair values][reduction][adjacency]
+// [flip rows][counters], sized for the largest scalar the block may hold.
+struct Smem {
+    zw64* sT;
+    zw64* sPV;
+    zw64* sred;
+    uint64_t* sADJ;
+    uint32_t* sS;   // seek tables
+    uint32_t* sF;
+    uint32_t* sH;
+};
+
+// words of one seek-table entry (flip words, adjacency, quadratic bit)
+__host__ __device__ constexpr uint32_t seek_stride(int nw) { return ((uint32_t)nw + 3u + 3u) & ~3u; }
+__host__ __device__ constexpr uint32_t seek_words(int nw) {
+    return ((kMaxK + 3) / 4) * 16u * seek_stride(nw);
+}
+
+__host__ __device__ inline size_t smem_bytes(uint32_t ntab_cap, uint32_t npairs_cap, int nw, int h,
+                                             int threads) {
+    return sizeof(zw64) * (ntab_cap + 4u * npairs_cap + kMaxWarps) + sizeof(uint64_t) * kMaxK +
+           sizeof(uint32_t) * seek_words(nw) + sizeof(uint32_t) * (size_t)kMaxK * nw +
+           sizeof(uint32_t) * (h == 2 ? (ntab_cap + 1) / 2 : (h == 1 ? ntab_cap : 0)) * (size_t)threads;
+}
+
+template <int NW, int HIST>
+__device__ __forceinline__ Smem carve(unsigned char* raw, uint32_t ntab_cap, uint32_t npairs_cap) {
+    const uint32_t hist_words =
+        (HIST == 2 ? (ntab_cap + 1) / 2 : (HIST == 1 ? ntab_cap : 0u)) * blockDim.x;
+    Smem s;
+    s.sT = reinterpret_cast<zw64*>(raw);
+    s.sPV = s.sT + ntab_cap;
+    s.sred = s.sPV + 4u * npairs_cap;
+    // 16-byte aligned first (vector loads and stores): seek tables, counters
+    s.sS = reinterpret_cast<uint32_t*>(s.sred + kMaxWarps);
+    s.sH = s.sS + seek_words(NW);
+    s.sADJ = reinterpret_cast<uint64_t*>(s.sH + hist_words);
+    s.sF = reinterpret_cast<uint32_t*>(s.sADJ + kMaxK);
+    return s;
+}
+
+// Cooperative copy of one scalar's tables into shared memory (the three
+// lowest variables padded with zero rows when k < 3).
+template <int NW, bool GENERAL>
+__device__ __forceinline__ void load_tables(const KernelParams& p, const Smem& sm,
+                                            const zw64* __restrict__ gtable,
+                                            const zw64* __restrict__ gpv,
+                                            const uint32_t* __restrict__ gF,
+                                            const uint64_t* __restrict__ gADJ,
+                                            const uint32_t* __restrict__ gS) {
+    const uint32_t ntab = p.tab_size;
+    for (uint32_t i = threadIdx.x; i < ntab; i += blockDim.x) sm.sT[i] = gtable[i];
+    const uint32_t ns = ((p.k + 3) / 4) * 16u * seek_stride(NW);
+    for (uint32_t i = threadIdx.x; i < ns; i += blockDim.x) sm.sS[i] = gS[i];
+    if (GENERAL)
+        for (uint32_t i = threadIdx.x; i < 4u * p.npairs; i += blockDim.x) sm.sPV[i] = gpv[i];
+    for (uint32_t i = threadIdx.x; i < p.k; i += blockDim.x) sm.sADJ[i] = gADJ[i];
+    for (uint32_t i = threadIdx.x; i < p.k * NW; i += blockDim.x) sm.sF[i] = gF[i];
+    for (uint32_t i = p.k + threadIdx.x; i < 3; i += blockDim.x) sm.sADJ[i] = 0;
+    for (uint32_t i = p.k * NW + threadIdx.x; i < 3 * NW; i += blockDim.x) sm.sF[i] = 0;
+}
+
+// Walk the slices s = s_begin + lane, s_begin + stride + lane, ... (< nslices)
+// of [first, first + count) and add the terms into acc.  s_begin must be
+// the same for the 32 lanes of a warp (the loop is warp-uniform, lanes past
+// the end skip the work) so that the counter fold can use full-warp
+// reductions.  The counters (HIST) are zero on entry, and on exit when
+// fold_each or clear_on_exit is set.
+template <int NWN, int NWL, bool GENERAL, int HIST, bool XTRA>
+__device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint64_t first,
+                                     uint64_t count, uint64_t span, uint64_t nslices,
+                                     uint64_t s_begin, uint64_t stride, bool fold_each,
+                                     bool clear_on_exit, zw64& acc) {
+    constexpr int NW = NWN + NWL;
+    const zw64* __restrict__ sT = sm.sT;
+    const zw64* __restrict__ sPV = sm.sPV;
+    const uint64_t* __restrict__ sADJ = sm.sADJ;
+    const uint32_t* __restrict__ sF = sm.sF;
+    uint32_t* __restrict__ sH = sm.sH;
+    const uint32_t* __restrict__ sS = sm.sS;
+    constexpr uint32_t SW = seek_stride(NW);
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t ntab = p.tab_size;
+    const uint32_t nwords = HIST == 2 ? (ntab + 1) / 2 : ntab;
+
+    // flip rows and adjacency of the three lowest variables, in registers:
+    // inside an aligned block of 8 Gray steps they are the only ones flipped
+    uint32_t f0[NW], f1[NW], f2[NW];
+#pragma unroll
+    for (int w = 0; w < NW; w++) { f0[w] = sF[w]; f1[w] = sF[NW + w]; f2[w] = sF[2 * NW + w]; }
+    const uint64_t adj0 = sADJ[0], adj1 = sADJ[1], adj2 = sADJ[2];
+
+    // HIST: acc += sum_idx count(idx) * T[idx] (mod 2^64).  Lane l adds up
+    // counter word i = l (+32, ...) over the warp's 32 lanes, reading them in
+    // lane-rotated order so that the 32 reads of a step hit 32 banks; the
+    // owning lane then does that word's multiply-add.  clear: reset the
+    // counters for further counting.
+    auto fold = [&](bool clear) {
+        __syncwarp();
+        uint32_t* wbase = sH + warp * nwords * 32u;
+        for (uint32_t i0 = 0; i0 < nwords; i0 += 32) {
+            const uint32_t i = i0 + lane;
+            uint32_t lo = 0, hi = 0;
+            if (i < nwords) {
+                const uint32_t* row = wbase + i * 32u;
+#pragma unroll 8
+                for (uint32_t j = 0; j < 32; j++) {
+                    const uint32_t c = row[(j + lane) & 31u];
+                    if (HIST == 2) { lo += c & 0xFFFFu; hi += c >> 16; } else lo += c;
+                }
+                // HIST == 1: a lane counts at most one slice (<= 2^18 terms)
+                // between folds, so the 32-lane sum fits in 32 bits
+                if (HIST == 2) {
+                    if (lo) acc = zw_madd32(acc, lds_zw(sT + 2 * i), lo);
+                    if (hi) acc = zw_madd32(acc, lds_zw(sT + 2 * i + 1), hi);
+                } else if (lo) {
+                    acc = zw_madd32(acc, lds_zw(sT + i), lo);
+                }
+            }
+        }
+        if (clear) {
+            __syncwarp();
+            for (uint32_t i = 0; i < nwords; i++) wbase[i * 32u + lane] = 0;
+            __syncwarp();
+        }
+    };
+
+    const uint64_t end = first + count;
+    for (uint64_t s0 = s_begin; s0 < nslices; s0 += stride) {
+        const uint64_t s = s0 + lane;
+        if (s < nslices) {
+            uint64_t t = first + s * span;
+            const uint64_t tend = (end - t < span) ? end : t + span;
+            const uint64_t x = t ^ (t >> 1);
+            // state at x: the form bits are the XOR of the flip rows of x's set
+            // bits (plus the inversions); a = A x; q = x^T (upper A) x, as half
+            // of sum_{j in x} |A_j & x|
+            // (4-bit groups: the quadratic cross terms of group b with the
+            // lower groups are the bits of v_b against the running A x)
+            uint32_t L[NW];
+#pragma unroll
+            for (int w = 0; w < NW; w++) L[w] = p.INV[w];
+            uint64_t a = 0;
+            uint32_t q = 0;
+            const uint32_t nnib = (p.k + 3) >> 2;
+            for (uint32_t b = 0; b < nnib; b++) {
+                const uint32_t v = (uint32_t)(x >> (4 * b)) & 15u;
+                const uint32_t* e = sS + (b * 16u + v) * SW;
+                uint32_t ev[SW];
+#pragma unroll
+                for (uint32_t w4 = 0; w4 < SW; w4 += 4) {
+                    const uint4 t4 = *reinterpret_cast<const uint4*>(e + w4);
+                    ev[w4] = t4.x; ev[w4 + 1] = t4.y; ev[w4 + 2] = t4.z; ev[w4 + 3] = t4.w;
+                }
+                q ^= ev[NW + 2] ^ ((uint32_t)__popc(v & (uint32_t)(a >> (4 * b))) & 1u);
+                a ^= ((uint64_t)ev[NW + 1] << 32) | ev[NW];
+#pragma unroll
+                for (int w = 0; w < NW; w++) L[w] ^= ev[w];
+            }
+
+            // one term at the current state
+            auto term = [&]() {
+                uint32_t M = 0, P0 = 0, P1 = 0, X2 = 0, Zb = 0;
+#pragma unroll
+                for (int w = 0; w < NWN; w++) {
+                    M += __popc(L[w]);
+                    X2 ^= L[w] & p.CB[w];
+                }
+#pragma unroll
+                for (int w = 0; w < NWL; w++) {
+                    const uint32_t v = L[NWN + w];
+                    P0 += __popc(v & p.C0[w]);
+                    P1 += __popc(v & p.C1[w]);
+                    X2 ^= v & p.C2[w];
+                    if (GENERAL) Zb |= v & p.Z[w];
+                }
+                if (!GENERAL) {
+                    // term value = table[(J, M, pair bits, zero bit)]
+                    const uint32_t J = (P0 + 2u * P1 + 4u * ((uint32_t)__popc(X2) + q)) & 7u;
+                    uint32_t idx = J * p.tab_stride + M;
+                    if (XTRA) {   // phase-pair or zero forms present
+                        uint32_t z = 0;
+#pragma unroll
+                        for (int w = 0; w < NWL; w++) z |= L[NWN + w] & p.Z[w];
+                        idx = (idx << p.xshift) | (L[NWN] & p.pmask) | ((z != 0 ? 1u : 0u) << p.zshift);
+                    }
+                    if (HIST == 2)
+                        atomicAdd(sH + ((warp * nwords + (idx >> 1)) << 5) + lane, 1u << ((idx & 1u) << 4));
+                    else if (HIST == 1)
+                        atomicAdd(sH + ((warp * nwords + idx) << 5) + lane, 1u);
+                    else
+                        acc = zw_add(acc, lds_zw(sT + idx));
+                } else if (Zb == 0) {
+                    const uint32_t J = (P0 + 2u * P1 + 4u * ((uint32_t)__popc(X2) + q)) & 7u;
+                    zw64 v = lds_zw(sT + J * p.tab_stride + M);
+                    if (GENERAL) {
+                        for (uint32_t j = 0; j < p.npairs; j++) {
+                            const uint32_t b = bit_at<NW>(L, p.PA[j]) | (bit_at<NW>(L, p.PB[j]) << 1);
+                            v = zw_mul(v, lds_zw(sPV + 4 * j + b));
+                        }
+                    }
+                    acc = zw_add(acc, v);
+                }
+            };
+            // flip of a variable known at compile time (0, 1 or 2)
+            auto flip = [&](const uint32_t (&f)[NW], uint64_t adj, int i) {
+                q ^= (uint32_t)(a >> i) & 1u;
+                a ^= adj;
+#pragma unroll
+                for (int w = 0; w < NW; w++) L[w] ^= f[w];
+            };
+
+            for (;;) {
+                if ((t & 7u) == 0 && tend - t >= 8) {
+                    // Gray steps inside t .. t+7 flip variables 0,1,0,2,0,1,0
+                    term(); flip(f0, adj0, 0);
+                    term(); flip(f1, adj1, 1);
+                    term(); flip(f0, adj0, 0);
+                    term(); flip(f2, adj2, 2);
+                    term(); flip(f0, adj0, 0);
+                    term(); flip(f1, adj1, 1);
+                    term(); flip(f0, adj0, 0);
+                    term();
+                    t += 7;
+                } else {
+                    term();
+                }
+                if (++t >= tend) break;
+                // x(t) = x(t-1) ^ (1 << ctz(t))
+                const uint32_t tl = (uint32_t)t;
+                const int i = tl ? __ffs(tl) - 1 : 31 + __ffs((uint32_t)(t >> 32));
+                q ^= (uint32_t)(a >> i) & 1u;
+                a ^= sADJ[i];
+#pragma unroll
+                for (int w = 0; w < NW; w++) L[w] ^= sF[i * NW + w];
+            }
+        }
+        // a thread with several slices folds after each one, so no counter
+        // can overflow (16-bit counters: every slice is shorter than 2^16)
+        if (HIST && fold_each) fold(true);
+    }
+    if (HIST && !fold_each) fold(clear_on_exit);
+}
+
+}  // namespace core
+}  // namespace zxp

@@ -119,6 +119,13 @@ int build_plan(const PS& ps, Plan* out) {
         if (odd_b[j]) kp.CB[bit >> 5] |= 1u << (bit & 31);
     }
     uint32_t base = 32u * (uint32_t)pl.nwn, pos = 0;
+    // phase-pair forms first (bits 0.. of the first other word), so that up
+    // to kFoldPairs of them index the term table directly
+    for (size_t j = 0; j < pair_masks.size(); j++) {
+        uint32_t bit = base + pos++;
+        put(bit, pair_masks[j], 0);
+        if (j & 1) kp.PB[j / 2] = (uint16_t)bit; else kp.PA[j / 2] = (uint16_t)bit;
+    }
     for (auto& e : lins) {
         uint32_t bit = base + pos++;
         put(bit, e.first, 0);
@@ -132,19 +139,52 @@ int build_plan(const PS& ps, Plan* out) {
         put(bit, z.mask, z.inv);
         kp.Z[(bit - base) >> 5] |= 1u << (bit & 31);
     }
-    for (size_t j = 0; j < pair_masks.size(); j++) {
-        uint32_t bit = base + pos++;
-        put(bit, pair_masks[j], 0);
-        if (j & 1) kp.PB[j / 2] = (uint16_t)bit; else kp.PA[j / 2] = (uint16_t)bit;
-    }
     pl.adj.assign(adj, adj + k);
+    // seek tables (stride padded to a multiple of 4 words for vector loads)
+    pl.seek_stride = (nw + 3 + 3) & ~3u;
+    const uint32_t nnib = (k + 3) / 4;
+    pl.seek.assign((size_t)nnib * 16 * pl.seek_stride, 0u);
+    for (uint32_t b = 0; b < nnib; b++)
+        for (uint32_t v = 0; v < 16; v++) {
+            uint32_t* e = &pl.seek[((size_t)b * 16 + v) * pl.seek_stride];
+            uint64_t a = 0;
+            uint32_t q = 0;
+            for (uint32_t i = 0; i < 4; i++) {
+                const uint32_t var = 4 * b + i;
+                if (!((v >> i) & 1) || var >= k) continue;
+                for (uint32_t w = 0; w < nw; w++) e[w] ^= pl.frows[(size_t)var * nw + w];
+                for (uint32_t j = 0; j < i; j++)     // pairs inside the group
+                    if (((v >> j) & 1) && ((adj[var] >> (4 * b + j)) & 1)) q ^= 1u;
+                a ^= adj[var];
+            }
+            e[nw] = (uint32_t)a;
+            e[nw + 1] = (uint32_t)(a >> 32);
+            e[nw + 2] = q;
+        }
 
-    // T[J][M] = w^(J + 2M) (1 + sqrt2)^M
+    // T[J][M][pair bits][zero] = w^(J + 2M) (1 + sqrt2)^M * prod_j PV_j(bits_j) * [not zero]
+    const uint32_t np = kp.npairs;
+    pl.general = np > (uint32_t)kFoldPairs;
+    const uint32_t pbits = pl.general ? 0 : 2 * np;
+    const uint32_t zbit = (!pl.general && !zero.empty()) ? 1 : 0;
+    kp.has_zero = zero.empty() ? 0 : 1;
+    kp.xshift = pbits + zbit;
+    kp.pmask = (1u << pbits) - 1;
+    kp.zshift = pbits;
     kp.tab_stride = pl.m_odd + 1;
-    pl.table.assign(8 * (size_t)kp.tab_stride, zw_zero());
+    kp.tab_size = (8u * kp.tab_stride) << kp.xshift;
+    pl.table.assign(kp.tab_size, zw_zero());
     zw64 s = zw_one();
     for (uint32_t M = 0; M <= pl.m_odd; M++) {
-        for (unsigned J = 0; J < 8; J++) pl.table[J * kp.tab_stride + M] = zw_rot(s, J + 2 * M);
+        for (unsigned J = 0; J < 8; J++) {
+            const zw64 base_v = zw_rot(s, J + 2 * M);
+            for (uint32_t x = 0; x < (1u << kp.xshift); x++) {
+                zw64 v = base_v;
+                if (zbit && ((x >> pbits) & 1)) v = zw_zero();
+                for (uint32_t j = 0; j < pbits / 2; j++) v = zw_mul(v, pl.pv[4 * j + ((x >> (2 * j)) & 3)]);
+                pl.table[((J * kp.tab_stride + M) << kp.xshift) | x] = v;
+            }
+        }
         s = zw_mul(s, zw_silver());
     }
     pl.K = K;

@@ -29,6 +29,7 @@ constexpr int kMaxWordsNode = 4;
 constexpr int kMaxWordsOther = 4;
 constexpr int kMaxNW = kMaxWordsNode + kMaxWordsOther;
 constexpr int kMaxPairs = 32;
+constexpr int kFoldPairs = 2;        // phase-pairs folded into the term table
 
 // Passed by value as the kernel parameter block (kept in the constant bank).
 struct KernelParams {
@@ -36,6 +37,12 @@ struct KernelParams {
     uint32_t nbits;          // 32 * (NWN + NWL) form bits (unused bits stay 0)
     uint32_t npairs;
     uint32_t tab_stride;     // m_odd + 1
+    uint32_t tab_size;       // table entries: 8 * tab_stride << xshift
+    // Extra table index bits below (J, M): the bits of up to kFoldPairs
+    // phase-pair forms (first other word, bits 0 .. 2 np - 1) and one bit
+    // for "some zero form is set" (bit zshift).  idx =
+    //   ((J * tab_stride + M) << xshift) | (L[NWN] & pmask) | (zero << zshift)
+    uint32_t xshift, pmask, zshift, has_zero;
     uint32_t CB[kMaxWordsNode];                       // class-B node bits
     uint32_t C0[kMaxWordsOther], C1[kMaxWordsOther], C2[kMaxWordsOther], Z[kMaxWordsOther];
     uint32_t INV[kMaxNW];    // initial inversion of each form bit
@@ -48,12 +55,18 @@ struct Plan {
     KernelParams kp;
     std::vector<uint32_t> frows;    // k x NW: form bits holding variable i (flip rows)
     std::vector<uint64_t> adj;      // k: quadratic part 4 sum_{i<j} A_ij x_i x_j, row i
-    std::vector<zw64> table;        // 8 x (m_odd + 1): w^(J + 2M) (1 + sqrt2)^M
+    // Seek tables, per 4-bit group b of x and value v (ceil(k/4) x 16 entries
+    // of seek_stride words): XOR of the flip rows of v's bits, XOR of their
+    // adjacency rows (two words), and the quadratic bit of v inside the group.
+    std::vector<uint32_t> seek;
+    uint32_t seek_stride = 0;
+    std::vector<zw64> table;        // w^(J + 2M) (1 + sqrt2)^M x pair values x (1 - zero)
     std::vector<zw64> pv;           // 4 per pair: value at (lA, lB) = (b & 1, b >> 1)
     zw64 K;                         // constant factor, G included
     int32_t e0 = 0;
     bool zero = false;              // the scalar is identically zero
     bool has_zero = false;          // some term can vanish (zero forms present)
+    bool general = false;           // more phase-pairs than fold into the table
 };
 
 // Returns 0 or ZXP_ETOOBIG (more forms / pairs than the kernel supports).

@@ -98,6 +98,17 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
+KERNEL_SOURCES = ("kernel.cu", "kernel_core.cuh", "zring.h", "plan.cpp")
+
+
+def kernel_source_sha() -> str:
+    """Hash of the sources that decide the sum kernel's code and tables."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2403_06777_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def traffic_from_profile(kernel_src_sha: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source."""
@@ -349,8 +360,7 @@ def main():
     f_hz = 2070e6
     peak = SM_COUNT_GB300 * ISSUE_LANES_PER_SM_CLK * f_hz / 1e9          # Gop/s
     achieved = ops * terms / per_launch_s / 1e9
-    src = open(os.path.join(ROOT, "paper_2403_06777_gb300", "csrc", "kernel.cu"), "rb").read()
-    sha = hashlib.sha256(src).hexdigest()
+    sha = kernel_source_sha()
     traffic = traffic_from_profile(sha)
 
     line = {

@@ -145,6 +145,63 @@ def cpu_baseline(blob: bytes, k: int, seconds: float = 10.0):
                       f"{dt:.1f} s on {cores} host threads"}
 
 
+SERVE_MAX_K = 38
+
+
+def serve_run(Z, ctx, reqs, policy, max_k):
+    """Replay the arrivals against one server; per-request latency is the
+    library's own submit-to-value time."""
+    srv = Z.zxp_server_create(ctx, policy=policy, max_k=max_k)
+    warm = [Z.zxp_server_submit(srv, r["gb"], r["n"], r["bits"], marg_mask=r["mask"],
+                                kind=r["kind"]) for r in reqs[:16]]
+    for t in warm:
+        Z.zxp_server_poll(srv, t, -1)
+    tickets = []
+    t0 = time.perf_counter()
+    for r in reqs:
+        target = t0 + r["t"]
+        while True:
+            now = time.perf_counter()
+            if now >= target:
+                break
+            if target - now > 6e-4:
+                time.sleep(target - now - 5e-4)
+        tickets.append(Z.zxp_server_submit(srv, r["gb"], r["n"], r["bits"],
+                                           marg_mask=r["mask"], kind=r["kind"]))
+    res = [Z.zxp_server_poll(srv, t, -1) for t in tickets]
+    st = Z.zxp_server_stats(srv)
+    srv.close()
+    ok = [(v, tm) for rc, v, tm in res if rc == Z.ZXP_OK]
+    lat = sorted((tm["done_us"] - tm["submit_us"]) / 1e3 for _, tm in ok)
+    span_s = (max(tm["done_us"] for _, tm in ok) - min(tm["submit_us"] for _, tm in ok)) / 1e6
+
+    def pct(q):
+        return lat[min(len(lat) - 1, int(q * len(lat)))]
+
+    out = {"p50_ms": pct(0.50), "p90_ms": pct(0.90), "p99_ms": pct(0.99), "max_ms": lat[-1],
+           "amplitudes_per_s": len(ok) / span_s, "completed": len(ok),
+           "rejected_k": sum(1 for rc, _, _ in res if rc == Z.ZXP_ETOOBIG),
+           "other_errors": sum(1 for rc, _, _ in res if rc not in (Z.ZXP_OK, Z.ZXP_ETOOBIG)),
+           "steps": st["steps"], "launches": st["launches"],
+           "terms": st["terms"], "device_busy_ms": st["device_busy_us"] / 1e3,
+           "peak_active": st["peak_active"]}
+    return out, [v for rc, v, _ in res]
+
+
+def serve_bench(Z, ctx, zi, n_req: int, rate_hz: float, max_k: int):
+    reqs = zi.serve_requests(0, n_req, rate_hz)
+    for r in reqs:
+        r["gb"] = zi.pack_gates(r["gates"])
+    batched, vb = serve_run(Z, ctx, reqs, Z.ZXP_SERVE_BATCHED, max_k)
+    plain, vp = serve_run(Z, ctx, reqs, Z.ZXP_SERVE_PLAIN, max_k)
+    assert vb == vp, "served values differ between policies"
+    return {"workload": f"{n_req} requests, Poisson {rate_hz:.0f}/s, seed 0: amplitude and "
+                        "single-qubit doubled-marginal, n~U[10,50], T~U[10,70]",
+            "admission_max_k": max_k, "batched": batched,
+            "plain_one_scalar_per_launch": plain,
+            "p99_plain_over_batched": plain["p99_ms"] / batched["p99_ms"]}
+
+
 def setup_dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -350,6 +407,13 @@ def main():
                            "candidates": binfo["candidates"]}}
         bt.close()
 
+    # serving: Poisson arrivals (2000 req/s) of amplitude and doubled-marginal
+    # requests; the server with continuous batching vs the same server
+    # evaluating one scalar per launch in arrival order
+    serving = None
+    if rank == 0 and not os.environ.get("ZXP_BENCH_SKIP_SERVE"):
+        serving = serve_bench(Z, ctx, zi, n_req=2000, rate_hz=2000.0, max_k=SERVE_MAX_K)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -387,6 +451,8 @@ def main():
         line["large"] = large
     if batch:
         line["batch"] = batch
+    if serving:
+        line["serving"] = serving
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(blob, k)
     print(json.dumps(line))

@@ -88,7 +88,8 @@ typedef struct {
     uint32_t t_count;    /* T-like gates in the input (0 for tables) */
     uint32_t node_words; /* 32-bit words of odd-node form bits per term */
     uint32_t other_words;/* 32-bit words of linear / zero / pair form bits */
-    uint32_t reserved[5];
+    uint32_t device_bytes;       /* bytes of the tables a device evaluation keeps resident */
+    uint32_t reserved[4];
 } zxp_scalar_info_t;
 
 /* ---- context --------------------------------------------------------- */
@@ -221,6 +222,97 @@ int zxp_batch_create(zxp_ctx *ctx, const zxp_scalar *const *scalars, size_t n,
 int zxp_batch_run(zxp_batch *b, zxp_zomega *out);
 int zxp_batch_info(const zxp_batch *b, zxp_batch_info_t *info);
 void zxp_batch_destroy(zxp_batch *b);
+
+/* ---- request server: continuous batching ---------------------------------- */
+
+/* A server owns a request loop on one context.  Requests (a circuit plus
+ * output bits and kind, as for zxp_compile, or an already compiled scalar)
+ * are accepted at any time from any thread.  Host worker threads compile
+ * them; a scheduler thread admits compiled scalars to the device while the
+ * device arena has room for their tables and a result slot is free, keeps
+ * their tables and partial sums resident there, and runs steps: each step
+ * gives every resident request a share of a term budget (small requests
+ * whole, shortest first; what is left to the large ones, oldest first, so a
+ * 2^40-term request proceeds in resumable chunks while small ones pass it)
+ * and evaluates all shares together in one persistent launch per kernel
+ * variant (the batch kernel).  Requests that arrive while steps are on the
+ * device join the next step; finished values are copied back per step.
+ * Two steps are in flight at a time.  The arithmetic is that of zxp_eval:
+ * each value is exactly the one zxp_amplitude returns for the same scalar.
+ *
+ * policy ZXP_SERVE_PLAIN runs the same loop one request at a time, one
+ * launch over its whole range (the one-scalar-per-launch baseline).
+ *
+ * The server is not part of the paper (its evaluation is offline); it is
+ * the serving form of the sum in Sec. 4. */
+typedef struct zxp_server zxp_server;
+
+typedef enum { ZXP_SERVE_BATCHED = 0, ZXP_SERVE_PLAIN = 1 } zxp_serve_policy;
+
+typedef struct {
+    uint32_t policy;             /* zxp_serve_policy */
+    uint32_t max_k;              /* admission: larger k completes with ZXP_ETOOBIG (0: 44) */
+    uint32_t compile_threads;    /* host compile workers (0: hardware threads, at most 16) */
+    uint32_t max_active;         /* requests resident on the device (0: 4096) */
+    uint64_t arena_bytes;        /* device memory for resident tables (0: 64 MiB) */
+    uint64_t step_terms;         /* term budget of one step (0: 2^28) */
+    uint64_t small_terms;        /* requests with at most this many terms left run whole (0: 2^22) */
+    uint32_t chunk_log2;         /* chunk length 2^chunk_log2 terms (0: 16) */
+    uint32_t threads;            /* threads per block of the batch kernel (0: 256) */
+    uint32_t reserved[8];
+} zxp_server_opts;
+
+typedef struct {
+    const zxp_gate *gates;
+    size_t n_gates;
+    int32_t n_qubits;
+    int32_t kind;                /* zxp_kind */
+    const uint8_t *in_bits;      /* NULL: all zero */
+    const uint8_t *out_bits;     /* n_qubits entries */
+    uint64_t marg_mask;
+} zxp_request;
+
+/* Per-request record, times in microseconds since the server started. */
+typedef struct {
+    double submit_us;
+    double compiled_us;          /* compile finished (submit time for scalars) */
+    double admitted_us;          /* tables resident on the device */
+    double done_us;              /* value back on the host */
+    uint32_t k;
+    uint32_t steps;              /* steps that carried part of its range */
+    int32_t status;              /* ZXP_OK, or the error that ended it */
+    uint32_t reserved;
+} zxp_request_timing;
+
+typedef struct {
+    uint64_t submitted, completed, rejected;   /* rejected: ZXP_ETOOBIG at admission */
+    uint64_t steps, launches;
+    double terms;                /* terms evaluated */
+    double device_busy_us;       /* sum of step device times */
+    uint32_t active, peak_active;
+    uint64_t arena_bytes, arena_peak;
+    uint32_t reserved[8];
+} zxp_server_stats_t;
+
+/* opts may be NULL (all defaults).  Errors: ZXP_EINVAL, ZXP_ENOMEM, ZXP_ECUDA.
+ * The context must outlive the server and is used only by its scheduler. */
+int zxp_server_create(zxp_ctx *ctx, const zxp_server_opts *opts, zxp_server **out);
+/* Copy the request and queue it; *ticket identifies it.  ZXP_EINVAL for a
+ * malformed request (checked again, fully, by the compiler). */
+int zxp_server_submit(zxp_server *srv, const zxp_request *req, uint64_t *ticket);
+/* Queue a compiled scalar (borrowed: it must stay alive until its ticket
+ * has been polled to completion). */
+int zxp_server_submit_scalar(zxp_server *srv, const zxp_scalar *s, uint64_t *ticket);
+/* Wait up to timeout_us (0: do not wait, < 0: without limit).  Returns
+ * ZXP_EAGAIN while the request runs, ZXP_ENOTFOUND for an unknown ticket;
+ * otherwise the request's own status (ZXP_OK: *out holds the canonical
+ * value; ZXP_EOVERFLOW: as zxp_amplitude), and the ticket is released.
+ * out and timing may be NULL. */
+int zxp_server_poll(zxp_server *srv, uint64_t ticket, int64_t timeout_us, zxp_zomega *out,
+                    zxp_request_timing *timing);
+int zxp_server_stats(zxp_server *srv, zxp_server_stats_t *stats);
+/* Finish every queued request, then stop the threads and free everything. */
+void zxp_server_destroy(zxp_server *srv);
 
 /* ---- exact scalar helpers (host) ---------------------------------------- */
 

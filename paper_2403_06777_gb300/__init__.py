@@ -42,7 +42,7 @@ class zxp_scalar_info_t(C.Structure):
                 ("n_node", C.c_uint32), ("n_pair", C.c_uint32), ("e0", C.c_int32),
                 ("acc_bits", C.c_uint32), ("form_bits", C.c_uint32), ("t_count", C.c_uint32),
                 ("node_words", C.c_uint32), ("other_words", C.c_uint32),
-                ("reserved", C.c_uint32 * 5)]
+                ("device_bytes", C.c_uint32), ("reserved", C.c_uint32 * 4)]
 
 
 class zxp_batch_info_t(C.Structure):
@@ -51,6 +51,35 @@ class zxp_batch_info_t(C.Structure):
                 ("tuned_us", C.c_double), ("total_terms", C.c_double),
                 ("reserved", C.c_uint32 * 6)]
 
+
+class zxp_server_opts(C.Structure):
+    _fields_ = [("policy", C.c_uint32), ("max_k", C.c_uint32), ("compile_threads", C.c_uint32),
+                ("max_active", C.c_uint32), ("arena_bytes", C.c_uint64), ("step_terms", C.c_uint64),
+                ("small_terms", C.c_uint64), ("chunk_log2", C.c_uint32), ("threads", C.c_uint32),
+                ("reserved", C.c_uint32 * 8)]
+
+
+class zxp_request(C.Structure):
+    _fields_ = [("gates", C.c_char_p), ("n_gates", C.c_size_t), ("n_qubits", C.c_int32),
+                ("kind", C.c_int32), ("in_bits", C.c_char_p), ("out_bits", C.c_char_p),
+                ("marg_mask", C.c_uint64)]
+
+
+class zxp_request_timing(C.Structure):
+    _fields_ = [("submit_us", C.c_double), ("compiled_us", C.c_double),
+                ("admitted_us", C.c_double), ("done_us", C.c_double), ("k", C.c_uint32),
+                ("steps", C.c_uint32), ("status", C.c_int32), ("reserved", C.c_uint32)]
+
+
+class zxp_server_stats_t(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("rejected", C.c_uint64),
+                ("steps", C.c_uint64), ("launches", C.c_uint64), ("terms", C.c_double),
+                ("device_busy_us", C.c_double), ("active", C.c_uint32),
+                ("peak_active", C.c_uint32), ("arena_bytes", C.c_uint64),
+                ("arena_peak", C.c_uint64), ("reserved", C.c_uint32 * 8)]
+
+
+ZXP_SERVE_BATCHED, ZXP_SERVE_PLAIN = 0, 1
 
 _lib = None
 
@@ -85,6 +114,12 @@ def lib():
         L.zxp_batch_run.argtypes = [vp, zp]
         L.zxp_batch_info.argtypes = [vp, C.POINTER(zxp_batch_info_t)]
         L.zxp_batch_destroy.argtypes, L.zxp_batch_destroy.restype = [vp], None
+        L.zxp_server_create.argtypes = [vp, C.POINTER(zxp_server_opts), C.POINTER(vp)]
+        L.zxp_server_submit.argtypes = [vp, C.POINTER(zxp_request), C.POINTER(u64)]
+        L.zxp_server_submit_scalar.argtypes = [vp, vp, C.POINTER(u64)]
+        L.zxp_server_poll.argtypes = [vp, u64, i64, zp, C.POINTER(zxp_request_timing)]
+        L.zxp_server_stats.argtypes = [vp, C.POINTER(zxp_server_stats_t)]
+        L.zxp_server_destroy.argtypes, L.zxp_server_destroy.restype = [vp], None
         L.zxp_zomega_add.argtypes = [zp, zp, zp]
         L.zxp_zomega_canon.argtypes = [zp, zp]
         L.zxp_zomega_to_complex.argtypes = [zp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -320,6 +355,97 @@ def zxp_batch_destroy(b: Batch):
     b.close()
 
 
+class Server:
+    """A zxp_server (zxp_server_destroy on close: queued requests finish
+    first); keeps borrowed scalars alive until their tickets are polled."""
+
+    def __init__(self, handle: int, ctx: Ctx):
+        self.handle = C.c_void_p(handle)
+        self.ctx = ctx
+        self.borrowed = {}
+
+    def close(self):
+        if self.handle:
+            lib().zxp_server_destroy(self.handle)
+            self.handle = C.c_void_p()
+            self.borrowed.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def zxp_server_create(ctx: Ctx, **opts) -> Server:
+    """opts: the fields of zxp_server_opts (policy, max_k, compile_threads,
+    max_active, arena_bytes, step_terms, small_terms, chunk_log2, threads);
+    0 or absent means the default."""
+    o = zxp_server_opts()
+    for k, v in opts.items():
+        if k not in dict(zxp_server_opts._fields_) or k == "reserved":
+            raise ZxpError(ZXP_EINVAL, f"zxp_server_create: unknown option {k}")
+        setattr(o, k, int(v))
+    h = C.c_void_p()
+    _check(lib().zxp_server_create(ctx.handle, C.byref(o), C.byref(h)), "zxp_server_create")
+    return Server(h.value, ctx)
+
+
+def zxp_server_submit(srv: Server, gates, n_qubits: int, out_bits: Sequence[int],
+                      in_bits: Sequence[int] | None = None, marg_mask: int = 0,
+                      kind: int = ZXP_AMPLITUDE) -> int:
+    """Queue a circuit request (copied); returns its ticket."""
+    gb = _gate_bytes(gates)
+    ob = bytes(int(b) & 1 for b in out_bits)
+    ib = bytes(int(b) & 1 for b in in_bits) if in_bits is not None else None
+    if len(ob) != n_qubits or (ib is not None and len(ib) != n_qubits):
+        raise ZxpError(ZXP_EINVAL, "zxp_server_submit: bit arrays must have n_qubits entries")
+    r = zxp_request(gb, len(gb) // 8, n_qubits, kind, ib, ob, marg_mask)
+    t = C.c_uint64()
+    _check(lib().zxp_server_submit(srv.handle, C.byref(r), C.byref(t)), "zxp_server_submit")
+    return t.value
+
+
+def zxp_server_submit_scalar(srv: Server, s: Scalar) -> int:
+    t = C.c_uint64()
+    _check(lib().zxp_server_submit_scalar(srv.handle, s.handle, C.byref(t)),
+           "zxp_server_submit_scalar")
+    srv.borrowed[t.value] = s
+    return t.value
+
+
+def zxp_server_poll(srv: Server, ticket: int, timeout_us: int = -1):
+    """None while the request runs; else (status, value, timing): value the
+    canonical (c0, c1, c2, c3, e) when status is ZXP_OK or ZXP_EOVERFLOW,
+    timing a dict of zxp_request_timing."""
+    out = zxp_zomega()
+    tm = zxp_request_timing()
+    rc = lib().zxp_server_poll(srv.handle, ticket, timeout_us, C.byref(out), C.byref(tm))
+    if rc == ZXP_EAGAIN:
+        return None
+    if rc == ZXP_ENOTFOUND or rc == ZXP_EINVAL:
+        raise ZxpError(rc, "zxp_server_poll")
+    srv.borrowed.pop(ticket, None)
+    timing = {f: getattr(tm, f) for f, _ in zxp_request_timing._fields_ if f != "reserved"}
+    return rc, (out.tup() if rc in (ZXP_OK, ZXP_EOVERFLOW) else None), timing
+
+
+def zxp_server_stats(srv: Server) -> dict:
+    st = zxp_server_stats_t()
+    _check(lib().zxp_server_stats(srv.handle, C.byref(st)), "zxp_server_stats")
+    return {f: getattr(st, f) for f, _ in zxp_server_stats_t._fields_ if f != "reserved"}
+
+
+def zxp_server_destroy(srv: Server):
+    srv.close()
+
+
 def zxp_zomega_add(a, b):
     out = zxp_zomega()
     za, zb = _z(a), _z(b)
@@ -344,6 +470,7 @@ def zxp_zomega_to_complex(a) -> complex:
 EXPORTED = ["zxp_ctx_create", "zxp_ctx_destroy", "zxp_compile", "zxp_scalar_from_tables",
             "zxp_scalar_to_tables", "zxp_scalar_info", "zxp_scalar_free", "zxp_eval",
             "zxp_eval_device", "zxp_eval_noalloc", "zxp_batch_create", "zxp_batch_run",
-            "zxp_batch_info", "zxp_batch_destroy",
+            "zxp_batch_info", "zxp_batch_destroy", "zxp_server_create", "zxp_server_submit",
+            "zxp_server_submit_scalar", "zxp_server_poll", "zxp_server_stats", "zxp_server_destroy",
             "zxp_amplitude", "zxp_submit", "zxp_poll", "zxp_zomega_add", "zxp_zomega_canon",
             "zxp_zomega_to_complex", "zxp_strerror", "zxp_version"]

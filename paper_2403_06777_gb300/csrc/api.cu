@@ -16,129 +16,29 @@
 #include "zxp.h"
 #include "compile.h"
 #include "kernel.h"
+#include "objects.h"
 #include "plan.h"
 #include "ps.h"
 #include "zring.h"
 
 using namespace zxp;
 
-static_assert(sizeof(DevResult) == sizeof(zxp_zomega), "result record layout");
-
 namespace {
-
-struct DevTables {
-    zw64* table = nullptr;
-    zw64* pv = nullptr;
-    uint32_t* frows = nullptr;
-    uint64_t* adj = nullptr;
-    uint32_t* seek = nullptr;
-};
-
-}  // namespace
-
-struct zxp_scalar {
-    PS ps;
-    Plan plan;
-    int plan_status = ZXP_OK;
-    mutable std::mutex mu;
-    mutable std::map<int, DevTables> dev;   // per-device copies of the tables
-
-    ~zxp_scalar() {
-        int prev = -1;
-        cudaGetDevice(&prev);
-        for (auto& e : dev) {
-            cudaSetDevice(e.first);
-            cudaFree(e.second.table);   // one allocation holds every table
-        }
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
-
-namespace {
-
-struct Ticket {
-    DevResult* dres = nullptr;   // device result slot
-    DevResult* hres = nullptr;   // pinned host slot
-    cudaEvent_t ev = nullptr;
-    int32_t e0 = 0;
-    bool trivial = false;        // no launch: the value is zero
-};
-
-}  // namespace
-
-struct zxp_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    int sm_count = 0;
-    int max_grid = 0;
-    zw64* partials = nullptr;
-    unsigned int* counter = nullptr;
-    DevResult* dres = nullptr;
-    DevResult* hres = nullptr;
-    uint64_t next_ticket = 1;
-    std::map<uint64_t, Ticket> tickets;
-    std::vector<Ticket> free_slots;
-};
-
-namespace {
-
-class DeviceGuard {
-  public:
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
-        if (prev_ != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev_ >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev_) cudaSetDevice(prev_);
-    }
-
-  private:
-    int prev_ = -1;
-};
-
-int cuda_status(cudaError_t e) { return e == cudaSuccess ? ZXP_OK : ZXP_ECUDA; }
-
-zw64 to_zw(const zxp_zomega& z) {
-    return zw_make((uint64_t)z.c[0], (uint64_t)z.c[1], (uint64_t)z.c[2], (uint64_t)z.c[3]);
-}
-void from_zw(const zw64& v, int32_t e, int32_t flags, zxp_zomega* out) {
-    for (int i = 0; i < 4; i++) out->c[i] = (int64_t)v.c[i];
-    out->e = e;
-    out->flags = flags;
-}
 
 int ensure_device_tables(const zxp_scalar* s, int device, DevTables* out) {
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->dev.find(device);
     if (it != s->dev.end()) { *out = it->second; return ZXP_OK; }
-    DevTables d;
-    const Plan& pl = s->plan;
-    // one allocation: table | phase-pair values | flip rows | adjacency | seek tables
-    const size_t tb = pl.table.size() * sizeof(zw64), pb = pl.pv.size() * sizeof(zw64);
-    const size_t fb = pl.frows.size() * sizeof(uint32_t), ab = pl.adj.size() * sizeof(uint64_t);
-    const size_t sb = pl.seek.size() * sizeof(uint32_t);
-    const size_t o_pv = tb, o_f = o_pv + pb, o_adj = (o_f + fb + 7) & ~(size_t)7;
-    const size_t o_seek = (o_adj + ab + 15) & ~(size_t)15;
-    const size_t total = o_seek + sb + 16;
-    std::vector<unsigned char> host(total, 0);
-    if (tb) memcpy(host.data(), pl.table.data(), tb);
-    if (pb) memcpy(host.data() + o_pv, pl.pv.data(), pb);
-    if (fb) memcpy(host.data() + o_f, pl.frows.data(), fb);
-    if (ab) memcpy(host.data() + o_adj, pl.adj.data(), ab);
-    if (sb) memcpy(host.data() + o_seek, pl.seek.data(), sb);
+    const TableLayout L = table_layout(s->plan);
+    std::vector<unsigned char> host(L.total, 0);
+    pack_tables(s->plan, L, host.data());
     unsigned char* base = nullptr;
-    if (cudaMalloc(&base, total) != cudaSuccess) return ZXP_ENOMEM;
-    if (cudaMemcpy(base, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (cudaMalloc(&base, L.total) != cudaSuccess) return ZXP_ENOMEM;
+    if (cudaMemcpy(base, host.data(), L.total, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(base);
         return ZXP_ECUDA;
     }
-    d.table = reinterpret_cast<zw64*>(base);
-    d.pv = reinterpret_cast<zw64*>(base + o_pv);
-    d.frows = reinterpret_cast<uint32_t*>(base + o_f);
-    d.adj = reinterpret_cast<uint64_t*>(base + o_adj);
-    d.seek = reinterpret_cast<uint32_t*>(base + o_seek);
+    const DevTables d = device_tables(L, base);
     s->dev[device] = d;
     *out = d;
     return ZXP_OK;
@@ -184,17 +84,17 @@ int enqueue(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, D
                                   grid, ctx->partials, ctx->counter, dres, ctx->stream));
 }
 
-// canonical form of an exact numerator (int64 coefficients) over sqrt2^e
-void canon_i128(__int128 c[4], int32_t* e) {
-    if (!c[0] && !c[1] && !c[2] && !c[3]) { *e = 0; return; }
-    while (*e > 0 && ((c[0] - c[2]) & 1) == 0 && ((c[1] - c[3]) & 1) == 0) {
-        __int128 n0 = c[1] - c[3], n1 = c[0] + c[2], n2 = c[1] + c[3], n3 = c[2] - c[0];
-        c[0] = n0 / 2; c[1] = n1 / 2; c[2] = n2 / 2; c[3] = n3 / 2;
-        *e -= 1;
-    }
-}
-
 }  // namespace
+
+int zxp::make_scalar(PS&& ps, zxp_scalar** out) {
+    std::unique_ptr<zxp_scalar> s(new (std::nothrow) zxp_scalar());
+    if (!s) return ZXP_ENOMEM;
+    s->ps = std::move(ps);
+    s->plan_status = build_plan(s->ps, &s->plan);
+    if (s->plan_status != ZXP_OK) return s->plan_status;
+    *out = s.release();
+    return ZXP_OK;
+}
 
 extern "C" {
 
@@ -261,15 +161,6 @@ void zxp_ctx_destroy(zxp_ctx* c) {
     delete c;
 }
 
-static int finish_scalar(PS&& ps, zxp_scalar** out) {
-    std::unique_ptr<zxp_scalar> s(new (std::nothrow) zxp_scalar());
-    if (!s) return ZXP_ENOMEM;
-    s->ps = std::move(ps);
-    s->plan_status = build_plan(s->ps, &s->plan);
-    if (s->plan_status != ZXP_OK) return s->plan_status;
-    *out = s.release();
-    return ZXP_OK;
-}
 
 int zxp_compile(const zxp_gate* gates, size_t n_gates, int n_qubits, const uint8_t* in_bits,
                 const uint8_t* out_bits, uint64_t marg_mask, int kind, zxp_scalar** out) {
@@ -279,7 +170,7 @@ int zxp_compile(const zxp_gate* gates, size_t n_gates, int n_qubits, const uint8
     CompileOptions opt;
     int st = compile_circuit(gates, n_gates, n_qubits, in_bits, out_bits, marg_mask, kind, opt, &ps);
     if (st != ZXP_OK) return st;
-    return finish_scalar(std::move(ps), out);
+    return make_scalar(std::move(ps), out);
 }
 
 int zxp_scalar_from_tables(const void* blob, size_t nbytes, zxp_scalar** out) {
@@ -288,7 +179,7 @@ int zxp_scalar_from_tables(const void* blob, size_t nbytes, zxp_scalar** out) {
     PS ps;
     int st = ps_from_blob(blob, nbytes, &ps);
     if (st != ZXP_OK) return st;
-    return finish_scalar(std::move(ps), out);
+    return make_scalar(std::move(ps), out);
 }
 
 int zxp_scalar_to_tables(const zxp_scalar* s, void* buf, size_t* nbytes) {
@@ -315,6 +206,7 @@ int zxp_scalar_info(const zxp_scalar* s, zxp_scalar_info_t* info) {
     info->t_count = s->ps.t_count;
     info->node_words = (uint32_t)s->plan.nwn;
     info->other_words = (uint32_t)(s->plan.nwl < 1 ? 1 : s->plan.nwl);
+    info->device_bytes = (uint32_t)table_layout(s->plan).total;
     return ZXP_OK;
 }
 
@@ -461,7 +353,7 @@ struct zxp_batch {
         int grid = 1;
     };
     std::vector<Group> groups;
-    BatchScalar* d_scalars = nullptr;
+    unsigned char* d_scalars = nullptr;   // n descriptors, kBatchScalarBytes apart
     BatchChunk* d_chunks = nullptr;
     size_t chunk_cap = 0;
     unsigned int* d_queue = nullptr;
@@ -498,7 +390,7 @@ std::vector<BatchChunk> batch_chunks(zxp_batch* b, uint32_t clog) {
             const uint64_t total = 1ull << b->k[m];
             const uint64_t len = 1ull << clog;
             for (uint64_t f = 0; f < total; f += len)
-                out.push_back(BatchChunk{m, 0, f, (total - f < len) ? total - f : len});
+                out.push_back(BatchChunk{m, m, f, (total - f < len) ? total - f : len});
         }
         g.count = (uint32_t)out.size() - g.off;
     }
@@ -559,7 +451,7 @@ extern "C" int zxp_batch_create(zxp_ctx* ctx, const zxp_scalar* const* scalars, 
     if (!b) return ZXP_ENOMEM;
     b->ctx = ctx;
     b->n = n;
-    std::vector<BatchScalar> hs(n);
+    std::vector<unsigned char> hs(n * kBatchScalarBytes, 0);
     std::map<int, size_t> gidx;
     for (size_t i = 0; i < n; i++) {
         const zxp_scalar* s = scalars[i];
@@ -568,16 +460,8 @@ extern "C" int zxp_batch_create(zxp_ctx* ctx, const zxp_scalar* const* scalars, 
         int st = ensure_device_tables(s, ctx->device, &d);
         if (st != ZXP_OK) return st;
         const Plan& pl = s->plan;
-        BatchScalar& bs = hs[i];
-        bs.kp = pl.kp;
-        bs.table = d.table;
-        bs.pv = d.pv;
-        bs.frows = d.frows;
-        bs.adj = d.adj;
-        bs.seek = d.seek;
-        bs.K = pl.K;
-        bs.e0 = pl.e0;
-        bs.key = batch_key(pl);
+        BatchScalar& bs = *reinterpret_cast<BatchScalar*>(hs.data() + i * kBatchScalarBytes);
+        bs = batch_descriptor(pl, d);
         b->k.push_back(s->ps.k);
         b->total_terms += std::ldexp(1.0, (int)s->ps.k);
         auto it = gidx.find(bs.key);
@@ -590,8 +474,8 @@ extern "C" int zxp_batch_create(zxp_ctx* ctx, const zxp_scalar* const* scalars, 
         g.ntab_cap = std::max(g.ntab_cap, pl.kp.tab_size);
         g.npairs_cap = std::max(g.npairs_cap, pl.kp.npairs);
     }
-    if (cudaMalloc(&b->d_scalars, n * sizeof(BatchScalar)) != cudaSuccess) return ZXP_ENOMEM;
-    if (cudaMemcpy(b->d_scalars, hs.data(), n * sizeof(BatchScalar), cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMalloc(&b->d_scalars, hs.size()) != cudaSuccess) return ZXP_ENOMEM;
+    if (cudaMemcpy(b->d_scalars, hs.data(), hs.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return ZXP_ECUDA;
     if (cudaMalloc(&b->d_queue, b->groups.size() * sizeof(unsigned int)) != cudaSuccess) return ZXP_ENOMEM;
     if (cudaMalloc(&b->d_results, n * sizeof(DevResult)) != cudaSuccess) return ZXP_ENOMEM;

@@ -24,7 +24,7 @@ using namespace core;
 
 template <int NWN, int NWL, int VAR>
 __global__ void __launch_bounds__(kMaxThreads)
-batch_kernel(const BatchScalar* __restrict__ scalars, const BatchChunk* __restrict__ chunks,
+batch_kernel(const unsigned char* __restrict__ scalars, const BatchChunk* __restrict__ chunks,
              uint32_t nchunks, unsigned int* __restrict__ queue, DevResult* __restrict__ results,
              uint32_t ntab_cap, uint32_t npairs_cap, uint32_t slices_per_thread) {
     constexpr int NW = NWN + NWL;
@@ -48,12 +48,13 @@ batch_kernel(const BatchScalar* __restrict__ scalars, const BatchChunk* __restri
         const uint32_t c = s_chunk;
         if (c >= nchunks) break;
         const BatchChunk ch = chunks[c];
+        const BatchScalar& bs =
+            *reinterpret_cast<const BatchScalar*>(scalars + (size_t)ch.scalar * kBatchScalarBytes);
         if (ch.scalar != s_loaded) {
-            const uint32_t* src = reinterpret_cast<const uint32_t*>(&scalars[ch.scalar].kp);
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(&bs.kp);
             uint32_t* dst = reinterpret_cast<uint32_t*>(&sp);
             for (uint32_t i = threadIdx.x; i < sizeof(KernelParams) / 4; i += blockDim.x) dst[i] = src[i];
             __syncthreads();
-            const BatchScalar& bs = scalars[ch.scalar];
             load_tables<NW, GENERAL>(sp, sm, bs.table, bs.pv, bs.frows, bs.adj, bs.seek);
             if (threadIdx.x == 0) s_loaded = ch.scalar;
             __syncthreads();
@@ -70,18 +71,18 @@ batch_kernel(const BatchScalar* __restrict__ scalars, const BatchChunk* __restri
                                                      HIST == 2 || nslices > blockDim.x, true, acc);
         acc = block_reduce(acc, sm.sred);
         if (threadIdx.x == 0) {
-            const zw64 r = zw_mul(scalars[ch.scalar].K, acc);
-            DevResult* out = results + ch.scalar;
+            const zw64 r = zw_mul(bs.K, acc);
+            DevResult* out = results + ch.slot;
             for (int i = 0; i < 4; i++)
                 atomicAdd(reinterpret_cast<unsigned long long*>(&out->c[i]), (unsigned long long)r.c[i]);
-            out->e = scalars[ch.scalar].e0;
+            out->e = bs.e0;
             out->flags = 1;
         }
         __syncthreads();   // s_chunk and the reduction scratch are reused
     }
 }
 
-using BatchFn = void (*)(const BatchScalar*, const BatchChunk*, uint32_t, unsigned int*, DevResult*,
+using BatchFn = void (*)(const unsigned char*, const BatchChunk*, uint32_t, unsigned int*, DevResult*,
                          uint32_t, uint32_t, uint32_t);
 
 template <int NWN, int NWL, int V>
@@ -104,7 +105,24 @@ BatchFn pick(int key) {
     return kTable[v][nwn][nwl - 1];
 }
 
+__global__ void __launch_bounds__(256)
+gather_kernel(DevResult* __restrict__ results, const uint32_t* __restrict__ slots, uint32_t n,
+              DevResult* __restrict__ out) {
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        DevResult* r = results + slots[i];
+        out[i] = *r;
+        *r = DevResult{{0, 0, 0, 0}, 0, 0};
+    }
+}
+
 }  // namespace
+
+cudaError_t gather_results(DevResult* results, const uint32_t* slots, uint32_t n, DevResult* out,
+                           cudaStream_t stream) {
+    if (!n) return cudaSuccess;
+    gather_kernel<<<1, 256, 0, stream>>>(results, slots, n, out);
+    return cudaGetLastError();
+}
 
 int batch_key(const Plan& pl) {
     const int nwl = pl.nwl < 1 ? 1 : pl.nwl;
@@ -120,17 +138,19 @@ cudaError_t batch_occupancy(int key, uint32_t ntab_cap, uint32_t npairs_cap, int
                             int* blocks_per_sm) {
     BatchFn fn = pick(key);
     const size_t smem = batch_smem_bytes(key, ntab_cap, npairs_cap, threads);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(fn), smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);
 }
 
-cudaError_t batch_launch(int key, const BatchScalar* scalars, const BatchChunk* chunks,
+cudaError_t batch_launch(int key, const unsigned char* scalars, const BatchChunk* chunks,
                          uint32_t nchunks, unsigned int* queue, DevResult* results,
                          uint32_t ntab_cap, uint32_t npairs_cap, int threads, int grid,
                          uint32_t slices_per_thread, cudaStream_t stream) {
     BatchFn fn = pick(key);
     const size_t smem = batch_smem_bytes(key, ntab_cap, npairs_cap, threads);
+    const cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(fn), smem);
+    if (e != cudaSuccess) return e;
     fn<<<grid, threads, smem, stream>>>(scalars, chunks, nchunks, queue, results, ntab_cap,
                                         npairs_cap, slices_per_thread);
     return cudaGetLastError();

@@ -8,6 +8,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "kernel.h"
 #include "kernel_core.cuh"
 #include "plan.h"
@@ -106,6 +110,21 @@ KernelFn pick(const Plan& pl) {
 
 }  // namespace
 
+cudaError_t ensure_dynamic_smem(const void* fn, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> set;   // (device, kernel) -> limit
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& cur = set[std::make_pair(dev, fn)];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
 size_t sum_smem_bytes(const Plan& pl) {
     return smem_bytes(pl.kp.tab_size, pl.kp.npairs, kernel_words(pl), hist_mode(pl), kThreads);
 }
@@ -121,10 +140,8 @@ cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, cons
                        unsigned int* counter, DevResult* result, cudaStream_t stream) {
     KernelFn fn = pick(pl);
     const size_t smem = sum_smem_bytes(pl);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(fn), smem);
+    if (e != cudaSuccess) return e;
     const uint64_t nslices = (count + span - 1) / span;
     fn<<<grid, kThreads, smem, stream>>>(pl.kp, dtable, dpv, dF, dADJ, dS, first, count, span, nslices,
                                          partials, counter, pl.K, pl.e0, result);
@@ -134,10 +151,8 @@ cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, cons
 cudaError_t sum_occupancy(const Plan& pl, int* blocks_per_sm) {
     KernelFn fn = pick(pl);
     const size_t smem = sum_smem_bytes(pl);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(fn), smem);
+    if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kThreads, smem);
 }
 

@@ -8,6 +8,11 @@
 
 namespace zxp {
 
+// Raise a kernel's dynamic shared memory limit on the current device to at
+// least `bytes` (never lowers it: launches of the same kernel with larger
+// tables may be in flight from other threads).
+cudaError_t ensure_dynamic_smem(const void* fn, size_t bytes);
+
 // Dynamic shared memory of one block: the w^(J+2M)(1+sqrt2)^M table, the
 // phase-pair values and the reduction scratch.
 size_t sum_smem_bytes(const Plan& pl);
@@ -47,10 +52,17 @@ struct BatchScalar {
     int32_t key;
 };
 
+// Scalar descriptors sit at multiples of this many bytes from a base
+// address (an array of them, or blocks of a device arena).
+constexpr size_t kBatchScalarBytes = 512;
+static_assert(sizeof(BatchScalar) <= kBatchScalarBytes, "scalar descriptor too large");
+
 // A range [first, first + count) of one scalar; first is a multiple of 8.
+// The descriptor is at base + scalar * kBatchScalarBytes; the range's sum
+// times K is added into results[slot].
 struct BatchChunk {
     uint32_t scalar;
-    uint32_t reserved;
+    uint32_t slot;
     uint64_t first;
     uint64_t count;
 };
@@ -61,10 +73,14 @@ size_t batch_smem_bytes(int key, uint32_t ntab_cap, uint32_t npairs_cap, int thr
 cudaError_t batch_occupancy(int key, uint32_t ntab_cap, uint32_t npairs_cap, int threads,
                             int* blocks_per_sm);
 // Persistent launch over chunks[0, nchunks) (one variant); *queue must be 0
-// and results[] zero for the scalars it touches.
-cudaError_t batch_launch(int key, const BatchScalar* scalars, const BatchChunk* chunks,
+// and results[] zero for the slots it touches.
+cudaError_t batch_launch(int key, const unsigned char* scalars, const BatchChunk* chunks,
                          uint32_t nchunks, unsigned int* queue, DevResult* results,
                          uint32_t ntab_cap, uint32_t npairs_cap, int threads, int grid,
                          uint32_t slices_per_thread, cudaStream_t stream);
+
+// Copy results[slots[i]] to out[i] and zero the slots (i < n), one block.
+cudaError_t gather_results(DevResult* results, const uint32_t* slots, uint32_t n, DevResult* out,
+                           cudaStream_t stream);
 
 }  // namespace zxp

@@ -1,0 +1,179 @@
+// objects.h -- the library's opaque objects (zxp_scalar, zxp_ctx) and the
+// small helpers that the C ABI's translation units share.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "zxp.h"
+#include "kernel.h"
+#include "plan.h"
+#include "ps.h"
+#include "zring.h"
+
+static_assert(sizeof(zxp::DevResult) == sizeof(zxp_zomega), "result record layout");
+
+namespace zxp {
+
+// Device addresses of one scalar's tables.
+struct DevTables {
+    zw64* table = nullptr;
+    zw64* pv = nullptr;
+    uint32_t* frows = nullptr;
+    uint64_t* adj = nullptr;
+    uint32_t* seek = nullptr;
+};
+
+// Byte offsets of the tables in one contiguous block:
+// term table | phase-pair values | flip rows | adjacency | seek tables.
+struct TableLayout {
+    size_t o_pv = 0, o_f = 0, o_adj = 0, o_seek = 0, total = 0;
+};
+
+inline TableLayout table_layout(const Plan& pl) {
+    TableLayout L;
+    const size_t tb = pl.table.size() * sizeof(zw64), pb = pl.pv.size() * sizeof(zw64);
+    const size_t fb = pl.frows.size() * sizeof(uint32_t), ab = pl.adj.size() * sizeof(uint64_t);
+    const size_t sb = pl.seek.size() * sizeof(uint32_t);
+    L.o_pv = tb;
+    L.o_f = L.o_pv + pb;
+    L.o_adj = (L.o_f + fb + 7) & ~(size_t)7;
+    L.o_seek = (L.o_adj + ab + 15) & ~(size_t)15;
+    L.total = L.o_seek + sb + 16;
+    return L;
+}
+
+// Fill dst (L.total bytes, zeroed by the caller) with the tables.
+inline void pack_tables(const Plan& pl, const TableLayout& L, unsigned char* dst) {
+    if (!pl.table.empty()) memcpy(dst, pl.table.data(), pl.table.size() * sizeof(zw64));
+    if (!pl.pv.empty()) memcpy(dst + L.o_pv, pl.pv.data(), pl.pv.size() * sizeof(zw64));
+    if (!pl.frows.empty()) memcpy(dst + L.o_f, pl.frows.data(), pl.frows.size() * sizeof(uint32_t));
+    if (!pl.adj.empty()) memcpy(dst + L.o_adj, pl.adj.data(), pl.adj.size() * sizeof(uint64_t));
+    if (!pl.seek.empty()) memcpy(dst + L.o_seek, pl.seek.data(), pl.seek.size() * sizeof(uint32_t));
+}
+
+inline DevTables device_tables(const TableLayout& L, unsigned char* base) {
+    DevTables d;
+    d.table = reinterpret_cast<zw64*>(base);
+    d.pv = reinterpret_cast<zw64*>(base + L.o_pv);
+    d.frows = reinterpret_cast<uint32_t*>(base + L.o_f);
+    d.adj = reinterpret_cast<uint64_t*>(base + L.o_adj);
+    d.seek = reinterpret_cast<uint32_t*>(base + L.o_seek);
+    return d;
+}
+
+// Descriptor the batch kernel reads for a scalar whose tables are at d.
+inline BatchScalar batch_descriptor(const Plan& pl, const DevTables& d) {
+    BatchScalar bs;
+    memset(&bs, 0, sizeof bs);
+    bs.kp = pl.kp;
+    bs.table = d.table;
+    bs.pv = d.pv;
+    bs.frows = d.frows;
+    bs.adj = d.adj;
+    bs.seek = d.seek;
+    bs.K = pl.K;
+    bs.e0 = pl.e0;
+    bs.key = batch_key(pl);
+    return bs;
+}
+
+// A pending zxp_submit: device and pinned result slots and its event.
+struct Ticket {
+    DevResult* dres = nullptr;
+    DevResult* hres = nullptr;
+    cudaEvent_t ev = nullptr;
+    int32_t e0 = 0;
+    bool trivial = false;        // no launch: the value is zero
+};
+
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
+        if (prev_ != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev_ >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev_) cudaSetDevice(prev_);
+    }
+
+  private:
+    int prev_ = -1;
+};
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? ZXP_OK : ZXP_ECUDA; }
+
+inline zw64 to_zw(const zxp_zomega& z) {
+    return zw_make((uint64_t)z.c[0], (uint64_t)z.c[1], (uint64_t)z.c[2], (uint64_t)z.c[3]);
+}
+inline void from_zw(const zw64& v, int32_t e, int32_t flags, zxp_zomega* out) {
+    for (int i = 0; i < 4; i++) out->c[i] = (int64_t)v.c[i];
+    out->e = e;
+    out->flags = flags;
+}
+
+// Canonical form of an exact numerator (int64 coefficients) over sqrt2^e:
+// divide by sqrt2 (x / sqrt2 = x (w - w^3) / 2) while e > 0 and the
+// coefficients allow it; zero becomes e = 0.
+inline void canon_i128(__int128 c[4], int32_t* e) {
+    if (!c[0] && !c[1] && !c[2] && !c[3]) { *e = 0; return; }
+    while (*e > 0 && ((c[0] - c[2]) & 1) == 0 && ((c[1] - c[3]) & 1) == 0) {
+        __int128 n0 = c[1] - c[3], n1 = c[0] + c[2], n2 = c[1] + c[3], n3 = c[2] - c[0];
+        c[0] = n0 / 2; c[1] = n1 / 2; c[2] = n2 / 2; c[3] = n3 / 2;
+        *e -= 1;
+    }
+}
+
+inline void canon_result(const DevResult& r, zxp_zomega* out) {
+    __int128 c[4] = {r.c[0], r.c[1], r.c[2], r.c[3]};
+    int32_t e = r.e;
+    canon_i128(c, &e);
+    for (int i = 0; i < 4; i++) out->c[i] = (int64_t)c[i];
+    out->e = e;
+    out->flags = 0;
+}
+
+}  // namespace zxp
+
+struct zxp_scalar {
+    zxp::PS ps;
+    zxp::Plan plan;
+    int plan_status = ZXP_OK;
+    mutable std::mutex mu;
+    mutable std::map<int, zxp::DevTables> dev;   // per-device copies of the tables
+
+    ~zxp_scalar() {
+        int prev = -1;
+        cudaGetDevice(&prev);
+        for (auto& e : dev) {
+            cudaSetDevice(e.first);
+            cudaFree(e.second.table);   // one allocation holds every table
+        }
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+struct zxp_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sm_count = 0;
+    int max_grid = 0;
+    zxp::zw64* partials = nullptr;
+    unsigned int* counter = nullptr;
+    zxp::DevResult* dres = nullptr;
+    zxp::DevResult* hres = nullptr;
+    uint64_t next_ticket = 1;
+    std::map<uint64_t, zxp::Ticket> tickets;
+    std::vector<zxp::Ticket> free_slots;
+};
+
+namespace zxp {
+// Compile a circuit or decode tables into a new scalar (api.cu).
+int make_scalar(PS&& ps, zxp_scalar** out);
+}  // namespace zxp

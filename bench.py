@@ -34,9 +34,11 @@ ISSUE_LANES_PER_SM_CLK = 4 * 32       # 4 schedulers x 1 warp-instruction x 32 l
 
 
 def alg_ops_per_term(node_words: int, other_words: int, n_pairs: int) -> int:
-    """Integer operations one term needs ('Roofline'):
-    Gray step (ctz, flip XORs, quadratic bit), node count, linear phase
-    planes, zero test, table fetch and the four 64-bit adds."""
+    """Integer operations the method needs per term, counted from the steps
+    of one term: Gray step (ctz, flip XORs, quadratic bit), node count, linear
+    phase planes, zero test, table fetch and the four 64-bit adds.  Up to
+    two phase-pair factors are folded into the table index (2 operations);
+    beyond that each is a Z[w] product (16 64-bit multiply-adds)."""
     nw = node_words + other_words
     ops = 2 + nw + 4                 # ctz + loop, flip XORs, quadratic update
     ops += 2 * node_words            # popc + add per node word
@@ -44,7 +46,7 @@ def alg_ops_per_term(node_words: int, other_words: int, n_pairs: int) -> int:
     ops += nw + 1                    # plane 2: and-xor per word, popc
     ops += other_words               # zero test
     ops += 4 + 3 + 8                 # J, table address + load, 4 x 64-bit add
-    ops += 40 * n_pairs              # 16 64-bit multiply-adds per phase-pair
+    ops += 40 * n_pairs if n_pairs > 2 else (2 if n_pairs else 0)
     return ops
 
 
@@ -98,7 +100,8 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-KERNEL_SOURCES = ("kernel.cu", "kernel_core.cuh", "zring.h", "plan.cpp")
+KERNEL_SOURCES = ("sum_kernel.cuh", "kernel_core.cuh", "kernel.cu", "kernel_count.cu", "zring.h",
+                  "plan.cpp")
 
 
 def kernel_source_sha() -> str:
@@ -351,14 +354,22 @@ def main():
         i36 = Z.zxp_scalar_info(s36)
         Z.zxp_eval_device(ctx, s36, 0, 1 << 30, out.data_ptr())
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        Z.zxp_eval_device(ctx, s36, 0, 1 << 36, out.data_ptr())
-        b.record(stream)
         torch.cuda.synchronize()
+        with ClockSampler(local) as clk36:
+            a.record(stream)
+            Z.zxp_eval_device(ctx, s36, 0, 1 << 36, out.data_ptr())
+            b.record(stream)
+            torch.cuda.synchronize()
         ms36 = a.elapsed_time(b)
+        ops36 = alg_ops_per_term(i36["node_words"], i36["other_words"], i36["n_pair"])
+        ach36 = ops36 * (1 << 36) / (ms36 / 1e3) / 1e9
+        peak = SM_COUNT_GB300 * ISSUE_LANES_PER_SM_CLK * 2070e6 / 1e9
         large = {"workload": "synthetic k=36 (59 linear, 36 quadratic, 13 odd-node, 1 phase-pair rows)",
                  "terms": 1 << 36, "ms": ms36, "terms_per_s": (1 << 36) / (ms36 / 1e3),
-                 "node_words": i36["node_words"], "other_words": i36["other_words"]}
+                 "node_words": i36["node_words"], "other_words": i36["other_words"],
+                 "roofline": {"bound": "alu", "achieved": ach36, "peak": peak, "unit": "Gop/s",
+                              "frac": ach36 / peak, "ops_per_term": ops36},
+                 "clocks": clk36.summary()}
 
     # batched workload: 512 circuits (n ~ U[10,40], T ~ U[20,60]), one
     # amplitude each: one launch per scalar vs one tuned, graph-captured batch

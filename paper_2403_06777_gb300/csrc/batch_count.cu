@@ -1,0 +1,15 @@
+// batch_count.cu -- the counting variants of the batch kernel
+// (batch_kernel.cuh).
+#include "batch_kernel.cuh"
+
+namespace zxp {
+namespace batchk {
+
+extern const BatchFn kHist[4][2][kMaxWordsOther] = {
+    {ZXP_BATCH_ROW(0, 3), ZXP_BATCH_ROW(1, 3)}, {ZXP_BATCH_ROW(0, 4), ZXP_BATCH_ROW(1, 4)},
+    {ZXP_BATCH_ROW(0, 5), ZXP_BATCH_ROW(1, 5)}, {ZXP_BATCH_ROW(0, 6), ZXP_BATCH_ROW(1, 6)},
+};
+extern const BatchFn kShared[2][kMaxWordsNode + 1][kMaxWordsOther] = {ZXP_BATCH_ALL(7), ZXP_BATCH_ALL(8)};
+
+}  // namespace batchk
+}  // namespace zxp

@@ -68,30 +68,36 @@ __device__ __forceinline__ zw64 block_reduce(zw64 v, zw64* sred) {
     return v;
 }
 
-// 0: table path, 1: 32-bit counters, 2: 16-bit counters (by the number of
-// distinct term values the table holds)
+// 0: table path, 1: lane-private 32-bit counters, 2: lane-private 16-bit
+// counters, 3: warp-shared 32-bit counters (by the number of distinct term
+// values the table holds)
 constexpr uint32_t kHistMaxEntries32 = 48;
 constexpr uint32_t kHistMaxEntries16 = 128;
+constexpr uint32_t kHistMaxEntriesShared = 2048;
 inline int hist_mode(const Plan& pl) {
     if (pl.general) return 0;
     if (pl.kp.tab_size <= kHistMaxEntries32) return 1;
     if (pl.kp.tab_size <= kHistMaxEntries16) return 2;
+    if (pl.kp.tab_size <= kHistMaxEntriesShared) return 3;
     return 0;
 }
 inline int kernel_words(const Plan& pl) { return pl.nwn + (pl.nwl < 1 ? 1 : pl.nwl); }
 // kernel variant: 0 table, 1 table + extra index bits, 2 general (phase-pair
-// products), 3/4 32-bit counters (+ extra bits), 5/6 16-bit counters (+ extra)
+// products), 3/4 lane-private 32-bit counters (+ extra bits), 5/6
+// lane-private 16-bit counters (+ extra), 7/8 warp-shared counters (+ extra)
 inline int variant(const Plan& pl) {
     if (pl.general) return 2;
     const int x = pl.kp.xshift ? 1 : 0;
     const int h = hist_mode(pl);
-    return h == 0 ? x : (h == 1 ? 3 + x : 5 + x);
+    return h == 0 ? x : 1 + 2 * h + x;
 }
 __host__ __device__ constexpr bool var_general(int v) { return v == 2; }
-__host__ __device__ constexpr int var_hist(int v) { return v >= 5 ? 2 : (v >= 3 ? 1 : 0); }
-__host__ __device__ constexpr bool var_xtra(int v) { return v == 1 || v == 4 || v == 6; }
-inline uint32_t hist_words(int h, uint32_t ntab) {
-    return h == 2 ? (ntab + 1) / 2 : (h == 1 ? ntab : 0);
+__host__ __device__ constexpr int var_hist(int v) { return v >= 3 ? (v - 1) / 2 : 0; }
+__host__ __device__ constexpr bool var_xtra(int v) { return v == 1 || (v >= 3 && (v & 1) == 0); }
+// 32-bit counter words of one block
+__host__ __device__ constexpr uint32_t counter_words(int h, uint32_t ntab, uint32_t threads) {
+    return h == 1 ? ntab * threads
+                  : (h == 2 ? (ntab + 1) / 2 * threads : (h == 3 ? ntab * (threads / 32) : 0u));
 }
 inline uint64_t max_span(int h) { return h == 2 ? kSpan16 : kSpan32; }
 
@@ -117,13 +123,12 @@ __host__ __device__ inline size_t smem_bytes(uint32_t ntab_cap, uint32_t npairs_
                                              int threads) {
     return sizeof(zw64) * (ntab_cap + 4u * npairs_cap + kMaxWarps) + sizeof(uint64_t) * kMaxK +
            sizeof(uint32_t) * seek_words(nw) + sizeof(uint32_t) * (size_t)kMaxK * nw +
-           sizeof(uint32_t) * (h == 2 ? (ntab_cap + 1) / 2 : (h == 1 ? ntab_cap : 0)) * (size_t)threads;
+           sizeof(uint32_t) * (size_t)counter_words(h, ntab_cap, (uint32_t)threads);
 }
 
 template <int NW, int HIST>
 __device__ __forceinline__ Smem carve(unsigned char* raw, uint32_t ntab_cap, uint32_t npairs_cap) {
-    const uint32_t hist_words =
-        (HIST == 2 ? (ntab_cap + 1) / 2 : (HIST == 1 ? ntab_cap : 0u)) * blockDim.x;
+    const uint32_t hist_words = counter_words(HIST, ntab_cap, blockDim.x);
     Smem s;
     s.sT = reinterpret_cast<zw64*>(raw);
     s.sPV = s.sT + ntab_cap;
@@ -179,6 +184,7 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t ntab = p.tab_size;
     const uint32_t nwords = HIST == 2 ? (ntab + 1) / 2 : ntab;
+    uint32_t* const wshared = sH + warp * ntab;   // HIST 3: this warp's counters
 
     // flip rows and adjacency of the three lowest variables, in registers:
     // inside an aligned block of 8 Gray steps they are the only ones flipped
@@ -194,6 +200,19 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
     // counters for further counting.
     auto fold = [&](bool clear) {
         __syncwarp();
+        if (HIST == 3) {
+            // one counter per index for the whole warp: at most 32 lanes x one
+            // slice (<= 2^18 terms) between folds, so it fits in 32 bits
+            for (uint32_t i = lane; i < ntab; i += 32) {
+                const uint32_t c = wshared[i];
+                if (c) {
+                    acc = zw_madd32(acc, lds_zw(sT + i), c);
+                    if (clear) wshared[i] = 0;
+                }
+            }
+            __syncwarp();
+            return;
+        }
         uint32_t* wbase = sH + warp * nwords * 32u;
         for (uint32_t i0 = 0; i0 < nwords; i0 += 32) {
             const uint32_t i = i0 + lane;
@@ -281,7 +300,9 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                         for (int w = 0; w < NWL; w++) z |= L[NWN + w] & p.Z[w];
                         idx = (idx << p.xshift) | (L[NWN] & p.pmask) | ((z != 0 ? 1u : 0u) << p.zshift);
                     }
-                    if (HIST == 2)
+                    if (HIST == 3)
+                        atomicAdd(wshared + idx, 1u);
+                    else if (HIST == 2)
                         atomicAdd(sH + ((warp * nwords + (idx >> 1)) << 5) + lane, 1u << ((idx & 1u) << 4));
                     else if (HIST == 1)
                         atomicAdd(sH + ((warp * nwords + idx) << 5) + lane, 1u);

@@ -1,0 +1,104 @@
+// sum_kernel.cuh -- the single-scalar sum kernel template.  Its variants
+// are instantiated in two translation units (kernel.cu: table and general
+// variants; kernel_count.cu: counting variants) so that they compile in
+// parallel; kernel.cu picks one per scalar.
+//
+// One thread per Gray-code slice of a resident grid (the walk itself is in
+// kernel_core.cuh).  Threads reduce by warp shuffles, then per block in
+// shared memory, then the last block to finish adds the per-block partials
+// (App. E's pairwise sum, done as a shuffle tree) and multiplies by the
+// scalar's constant K once.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernel.h"
+#include "kernel_core.cuh"
+#include "plan.h"
+
+namespace zxp {
+namespace sumk {
+
+using namespace core;
+constexpr int kThreads = kMaxThreads;
+
+using KernelFn = void (*)(const KernelParams, const zw64*, const zw64*, const uint32_t*,
+                          const uint64_t*, const uint32_t*, uint64_t, uint64_t,
+                          uint64_t, uint64_t, zw64*, unsigned int*, const zw64, const int32_t,
+                          DevResult*);
+
+
+// variant tables: [variant][nwn][nwl - 1]
+extern const KernelFn kTable[3][kMaxWordsNode + 1][kMaxWordsOther];   // kernel.cu
+extern const KernelFn kHist[4][2][kMaxWordsOther];                    // kernel_count.cu (nwn <= 1)
+extern const KernelFn kShared[2][kMaxWordsNode + 1][kMaxWordsOther];  // kernel_count.cu
+
+namespace {
+
+template <int NWN, int NWL, int VAR>
+__global__ void __launch_bounds__(kThreads)
+sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtable,
+           const zw64* __restrict__ gpv, const uint32_t* __restrict__ gF,
+           const uint64_t* __restrict__ gADJ, const uint32_t* __restrict__ gS, uint64_t first,
+           uint64_t count, uint64_t span,
+           uint64_t nslices, zw64* __restrict__ partials, unsigned int* __restrict__ counter,
+           const zw64 K, const int32_t e0, DevResult* __restrict__ result) {
+    constexpr int NW = NWN + NWL;
+    constexpr bool GENERAL = var_general(VAR);
+    constexpr int HIST = var_hist(VAR);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t ntab = p.tab_size;
+    const Smem sm = carve<NW, HIST>(smem_raw, ntab, p.npairs);
+    if (HIST) {
+        uint4* h4 = reinterpret_cast<uint4*>(sm.sH);
+        for (uint32_t i = threadIdx.x; i < counter_words(HIST, ntab, blockDim.x) / 4; i += blockDim.x)
+            h4[i] = make_uint4(0, 0, 0, 0);
+    }
+    load_tables<NW, GENERAL>(p, sm, gtable, gpv, gF, gADJ, gS);
+    __syncthreads();
+
+    zw64 acc = zw_zero();
+    const uint64_t gstride = (uint64_t)gridDim.x * blockDim.x;
+    walk<NWN, NWL, GENERAL, HIST, var_xtra(VAR)>(p, sm, first, count, span, nslices,
+                                  (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u), gstride,
+                                  HIST == 2 || nslices > gstride, false, acc);
+
+    // reduction: warp shuffles, block, then the last block over the partials
+    __shared__ unsigned int s_last;
+    acc = block_reduce(acc, sm.sred);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = acc;
+        __threadfence();
+        const unsigned int done = atomicAdd(counter, 1u);
+        s_last = (done == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        zw64 v = zw_zero();
+        for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+            const ulonglong2* q2 = reinterpret_cast<const ulonglong2*>(partials + b);
+            ulonglong2 lo = __ldcg(q2), hi = __ldcg(q2 + 1);
+            v = zw_add(v, zw_make(lo.x, lo.y, hi.x, hi.y));
+        }
+        v = block_reduce(v, sm.sred);
+        if (threadIdx.x == 0) {
+            const zw64 r = zw_mul(K, v);
+            for (int c = 0; c < 4; c++) result->c[c] = (int64_t)r.c[c];
+            result->e = e0;
+            result->flags = 1;
+            *counter = 0u;       // ready for the next launch on this workspace
+        }
+    }
+}
+
+template <int NWN, int NWL, int V>
+constexpr KernelFn kfn() { return &sum_kernel<NWN, NWL, V>; }
+
+}  // namespace
+
+}  // namespace sumk
+}  // namespace zxp
+
+#define ZXP_SUM_ROW(N, V) {kfn<N, 1, V>(), kfn<N, 2, V>(), kfn<N, 3, V>(), kfn<N, 4, V>()}
+#define ZXP_SUM_ALL(V) {ZXP_SUM_ROW(0, V), ZXP_SUM_ROW(1, V), ZXP_SUM_ROW(2, V), ZXP_SUM_ROW(3, V), ZXP_SUM_ROW(4, V)}

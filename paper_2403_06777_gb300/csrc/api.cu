@@ -80,7 +80,7 @@ int enqueue(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, D
     uint64_t span;
     int grid;
     launch_shape(ctx, s->plan, count, &span, &grid);
-    return cuda_status(sum_launch(s->plan, d.table, d.pv, d.frows, d.adj, d.seek, first, count, span,
+    return cuda_status(sum_launch(s->plan, d.table, d.pv, d.rows, d.adj, d.seek, first, count, span,
                                   grid, ctx->partials, ctx->counter, dres, ctx->stream));
 }
 
@@ -614,8 +614,8 @@ extern "C" int zxp_eval_noalloc(const zxp_scalar* s, uint64_t first, uint64_t co
     if (st != ZXP_OK) return st;
     const Plan& pl = s->plan;
     const size_t tb = pl.table.size() * sizeof(zw64), pb = pl.pv.size() * sizeof(zw64);
-    const size_t fb = pl.frows.size() * sizeof(uint32_t), ab = pl.adj.size() * sizeof(uint64_t);
-    const size_t o_pv = kNoAllocTablesOff + tb, o_f = o_pv + pb;
+    const size_t fb = pl.rows.size() * sizeof(uint32_t), ab = pl.adj.size() * sizeof(uint64_t);
+    const size_t o_pv = kNoAllocTablesOff + tb, o_f = (o_pv + pb + 15) & ~(size_t)15;
     const size_t o_adj = (o_f + fb + 7) & ~(size_t)7;
     const size_t sb = pl.seek.size() * sizeof(uint32_t);
     const size_t o_seek = (o_adj + ab + 15) & ~(size_t)15;
@@ -664,7 +664,7 @@ extern "C" int zxp_eval_noalloc(const zxp_scalar* s, uint64_t first, uint64_t co
         return ZXP_ECUDA;
     if (pb && cudaMemcpyAsync(base + o_pv, pl.pv.data(), pb, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return ZXP_ECUDA;
-    if (fb && cudaMemcpyAsync(base + o_f, pl.frows.data(), fb, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+    if (fb && cudaMemcpyAsync(base + o_f, pl.rows.data(), fb, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return ZXP_ECUDA;
     if (ab && cudaMemcpyAsync(base + o_adj, pl.adj.data(), ab, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return ZXP_ECUDA;

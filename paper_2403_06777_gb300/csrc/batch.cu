@@ -50,8 +50,8 @@ int batch_key(const Plan& pl) {
 }
 
 size_t batch_smem_bytes(int key, uint32_t ntab_cap, uint32_t npairs_cap, int threads) {
-    const int nw = ((key >> 4) & 7) + (key & 7);
-    return core::smem_bytes(ntab_cap, npairs_cap, nw, core::var_hist((key >> 8) & 15), threads);
+    return core::smem_bytes(ntab_cap, npairs_cap, (key >> 4) & 7, key & 7, core::var_hist((key >> 8) & 15),
+                            threads);
 }
 
 cudaError_t batch_occupancy(int key, uint32_t ntab_cap, uint32_t npairs_cap, int threads,

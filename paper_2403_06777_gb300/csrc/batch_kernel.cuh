@@ -68,7 +68,7 @@ batch_kernel(const unsigned char* __restrict__ scalars, const BatchChunk* __rest
             uint32_t* dst = reinterpret_cast<uint32_t*>(&sp);
             for (uint32_t i = threadIdx.x; i < sizeof(KernelParams) / 4; i += blockDim.x) dst[i] = src[i];
             __syncthreads();
-            load_tables<NW, GENERAL>(sp, sm, bs.table, bs.pv, bs.frows, bs.adj, bs.seek);
+            load_tables<NWN, NWL, GENERAL>(sp, sm, bs.table, bs.pv, bs.rows, bs.adj, bs.seek);
             if (threadIdx.x == 0) s_loaded = ch.scalar;
             __syncthreads();
         }

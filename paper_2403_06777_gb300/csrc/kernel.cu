@@ -48,7 +48,8 @@ cudaError_t ensure_dynamic_smem(const void* fn, size_t bytes) {
 }
 
 size_t sum_smem_bytes(const Plan& pl) {
-    return smem_bytes(pl.kp.tab_size, pl.kp.npairs, kernel_words(pl), hist_mode(pl), kThreads);
+    return smem_bytes(pl.kp.tab_size, pl.kp.npairs, pl.nwn, kernel_words(pl) - pl.nwn, hist_mode(pl),
+                      kThreads);
 }
 
 uint64_t sum_max_span(const Plan& pl) { return max_span(hist_mode(pl)); }

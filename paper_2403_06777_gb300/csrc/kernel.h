@@ -32,7 +32,7 @@ struct DevResult {
 // over `grid` blocks.  partials holds >= grid entries; *counter must be 0
 // on entry and is 0 again when the kernel ends; *result receives
 // K * (sum of the table terms) over sqrt2^e0, flagged raw.
-cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, const uint32_t* dF,
+cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, const uint32_t* drows,
                        const uint64_t* dADJ, const uint32_t* dS, uint64_t first, uint64_t count,
                        uint64_t span, int grid, zw64* partials, unsigned int* counter,
                        DevResult* result, cudaStream_t stream);
@@ -44,7 +44,7 @@ struct BatchScalar {
     KernelParams kp;
     const zw64* table;
     const zw64* pv;
-    const uint32_t* frows;
+    const uint32_t* rows;
     const uint64_t* adj;
     const uint32_t* seek;
     zw64 K;
@@ -54,7 +54,7 @@ struct BatchScalar {
 
 // Scalar descriptors sit at multiples of this many bytes from a base
 // address (an array of them, or blocks of a device arena).
-constexpr size_t kBatchScalarBytes = 512;
+constexpr size_t kBatchScalarBytes = 1024;
 static_assert(sizeof(BatchScalar) <= kBatchScalarBytes, "scalar descriptor too large");
 
 // A range [first, first + count) of one scalar; first is a multiple of 8.

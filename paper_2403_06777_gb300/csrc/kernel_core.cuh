@@ -119,15 +119,17 @@ __host__ __device__ constexpr uint32_t seek_words(int nw) {
     return ((kMaxK + 3) / 4) * 16u * seek_stride(nw);
 }
 
-__host__ __device__ inline size_t smem_bytes(uint32_t ntab_cap, uint32_t npairs_cap, int nw, int h,
-                                             int threads) {
+__host__ __device__ inline size_t smem_bytes(uint32_t ntab_cap, uint32_t npairs_cap, int nwn, int nwl,
+                                             int h, int threads) {
     return sizeof(zw64) * (ntab_cap + 4u * npairs_cap + kMaxWarps) + sizeof(uint64_t) * kMaxK +
-           sizeof(uint32_t) * seek_words(nw) + sizeof(uint32_t) * (size_t)kMaxK * nw +
+           sizeof(uint32_t) * seek_words(nwn + nwl) + sizeof(uint32_t) * (size_t)kMaxK * row_words(nwn, nwl) +
            sizeof(uint32_t) * (size_t)counter_words(h, ntab_cap, (uint32_t)threads);
 }
 
 template <int NW, int HIST>
 __device__ __forceinline__ Smem carve(unsigned char* raw, uint32_t ntab_cap, uint32_t npairs_cap) {
+    // (step rows last: 16-byte aligned after the 8-byte adjacency words, as
+    // kMaxK is even)
     const uint32_t hist_words = counter_words(HIST, ntab_cap, blockDim.x);
     Smem s;
     s.sT = reinterpret_cast<zw64*>(raw);
@@ -143,13 +145,15 @@ __device__ __forceinline__ Smem carve(unsigned char* raw, uint32_t ntab_cap, uin
 
 // Cooperative copy of one scalar's tables into shared memory (the three
 // lowest variables padded with zero rows when k < 3).
-template <int NW, bool GENERAL>
+template <int NWN, int NWL, bool GENERAL>
 __device__ __forceinline__ void load_tables(const KernelParams& p, const Smem& sm,
                                             const zw64* __restrict__ gtable,
                                             const zw64* __restrict__ gpv,
-                                            const uint32_t* __restrict__ gF,
+                                            const uint32_t* __restrict__ gR,
                                             const uint64_t* __restrict__ gADJ,
                                             const uint32_t* __restrict__ gS) {
+    constexpr int NW = NWN + NWL;
+    constexpr uint32_t RW = row_words(NWN, NWL);
     const uint32_t ntab = p.tab_size;
     for (uint32_t i = threadIdx.x; i < ntab; i += blockDim.x) sm.sT[i] = gtable[i];
     const uint32_t ns = ((p.k + 3) / 4) * 16u * seek_stride(NW);
@@ -157,9 +161,11 @@ __device__ __forceinline__ void load_tables(const KernelParams& p, const Smem& s
     if (GENERAL)
         for (uint32_t i = threadIdx.x; i < 4u * p.npairs; i += blockDim.x) sm.sPV[i] = gpv[i];
     for (uint32_t i = threadIdx.x; i < p.k; i += blockDim.x) sm.sADJ[i] = gADJ[i];
-    for (uint32_t i = threadIdx.x; i < p.k * NW; i += blockDim.x) sm.sF[i] = gF[i];
+    // step rows (see plan.h), 16-byte vectors
+    const uint4* g4 = reinterpret_cast<const uint4*>(gR);
+    uint4* s4 = reinterpret_cast<uint4*>(sm.sF);
+    for (uint32_t i = threadIdx.x; i < p.k * RW / 4; i += blockDim.x) s4[i] = g4[i];
     for (uint32_t i = p.k + threadIdx.x; i < 3; i += blockDim.x) sm.sADJ[i] = 0;
-    for (uint32_t i = p.k * NW + threadIdx.x; i < 3 * NW; i += blockDim.x) sm.sF[i] = 0;
 }
 
 // Walk the slices s = s_begin + lane, s_begin + stride + lane, ... (< nslices)
@@ -174,6 +180,7 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                                      uint64_t s_begin, uint64_t stride, bool fold_each,
                                      bool clear_on_exit, zw64& acc) {
     constexpr int NW = NWN + NWL;
+    constexpr uint32_t RW = row_words(NWN, NWL);
     const zw64* __restrict__ sT = sm.sT;
     const zw64* __restrict__ sPV = sm.sPV;
     const uint64_t* __restrict__ sADJ = sm.sADJ;
@@ -188,9 +195,8 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
 
     // flip rows and adjacency of the three lowest variables, in registers:
     // inside an aligned block of 8 Gray steps they are the only ones flipped
-    uint32_t f0[NW], f1[NW], f2[NW];
-#pragma unroll
-    for (int w = 0; w < NW; w++) { f0[w] = sF[w]; f1[w] = sF[NW + w]; f2[w] = sF[2 * NW + w]; }
+    // (the step rows of variables 0, 1, 2 are read from the parameters: the
+    // constant bank in the single-scalar kernel)
     const uint64_t adj0 = sADJ[0], adj1 = sADJ[1], adj2 = sADJ[2];
 
     // HIST: acc += sum_idx count(idx) * T[idx] (mod 2^64).  Lane l adds up
@@ -258,6 +264,7 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
             for (int w = 0; w < NW; w++) L[w] = p.INV[w];
             uint64_t a = 0;
             uint32_t q = 0;
+            uint32_t Jl;   // linear and class-B node part of the phase exponent (mod 8)
             const uint32_t nnib = (p.k + 3) >> 2;
             for (uint32_t b = 0; b < nnib; b++) {
                 const uint32_t v = (uint32_t)(x >> (4 * b)) & 15u;
@@ -273,26 +280,32 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
 #pragma unroll
                 for (int w = 0; w < NW; w++) L[w] ^= ev[w];
             }
-
-            // one term at the current state
-            auto term = [&]() {
-                uint32_t M = 0, P0 = 0, P1 = 0, X2 = 0, Zb = 0;
+            {
+                uint32_t P0 = 0, P1 = 0, X2 = 0;
 #pragma unroll
-                for (int w = 0; w < NWN; w++) {
-                    M += __popc(L[w]);
-                    X2 ^= L[w] & p.CB[w];
-                }
+                for (int w = 0; w < NWN; w++) X2 ^= L[w] & p.CB[w];
 #pragma unroll
                 for (int w = 0; w < NWL; w++) {
                     const uint32_t v = L[NWN + w];
                     P0 += __popc(v & p.C0[w]);
                     P1 += __popc(v & p.C1[w]);
                     X2 ^= v & p.C2[w];
-                    if (GENERAL) Zb |= v & p.Z[w];
+                }
+                Jl = P0 + 2u * P1 + 4u * (uint32_t)__popc(X2);
+            }
+
+            // one term at the current state
+            auto term = [&]() {
+                uint32_t M = 0, Zb = 0;
+#pragma unroll
+                for (int w = 0; w < NWN; w++) M += __popc(L[w]);
+                if (GENERAL) {
+#pragma unroll
+                    for (int w = 0; w < NWL; w++) Zb |= L[NWN + w] & p.Z[w];
                 }
                 if (!GENERAL) {
                     // term value = table[(J, M, pair bits, zero bit)]
-                    const uint32_t J = (P0 + 2u * P1 + 4u * ((uint32_t)__popc(X2) + q)) & 7u;
+                    const uint32_t J = (Jl + 4u * q) & 7u;
                     uint32_t idx = J * p.tab_stride + M;
                     if (XTRA) {   // phase-pair or zero forms present
                         uint32_t z = 0;
@@ -309,7 +322,7 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                     else
                         acc = zw_add(acc, lds_zw(sT + idx));
                 } else if (Zb == 0) {
-                    const uint32_t J = (P0 + 2u * P1 + 4u * ((uint32_t)__popc(X2) + q)) & 7u;
+                    const uint32_t J = (Jl + 4u * q) & 7u;
                     zw64 v = lds_zw(sT + J * p.tab_stride + M);
                     if (GENERAL) {
                         for (uint32_t j = 0; j < p.npairs; j++) {
@@ -320,24 +333,36 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                     acc = zw_add(acc, v);
                 }
             };
-            // flip of a variable known at compile time (0, 1 or 2)
-            auto flip = [&](const uint32_t (&f)[NW], uint64_t adj, int i) {
-                q ^= (uint32_t)(a >> i) & 1u;
-                a ^= adj;
+            // flip of variable i with step row f (before the XOR: the phase
+            // change depends on the forms' current bits)
+            auto step = [&](const uint32_t* f) {
+                uint32_t d0 = 0, d1 = 0;
+#pragma unroll
+                for (int w = 0; w < NWL; w++) {
+                    d0 += __popc(L[NWN + w] & f[NW + w]);
+                    d1 += __popc(L[NWN + w] & f[NW + NWL + w]);
+                }
+                Jl += f[NW + 2 * NWL] - 2u * d0 - 4u * d1;
 #pragma unroll
                 for (int w = 0; w < NW; w++) L[w] ^= f[w];
+            };
+            // flip of a variable known at compile time (0, 1 or 2)
+            auto flip = [&](const uint32_t* f, uint64_t adj, int i) {
+                q ^= (uint32_t)(a >> i) & 1u;
+                a ^= adj;
+                step(f);
             };
 
             for (;;) {
                 if ((t & 7u) == 0 && tend - t >= 8) {
                     // Gray steps inside t .. t+7 flip variables 0,1,0,2,0,1,0
-                    term(); flip(f0, adj0, 0);
-                    term(); flip(f1, adj1, 1);
-                    term(); flip(f0, adj0, 0);
-                    term(); flip(f2, adj2, 2);
-                    term(); flip(f0, adj0, 0);
-                    term(); flip(f1, adj1, 1);
-                    term(); flip(f0, adj0, 0);
+                    term(); flip(p.R[0], adj0, 0);
+                    term(); flip(p.R[1], adj1, 1);
+                    term(); flip(p.R[0], adj0, 0);
+                    term(); flip(p.R[2], adj2, 2);
+                    term(); flip(p.R[0], adj0, 0);
+                    term(); flip(p.R[1], adj1, 1);
+                    term(); flip(p.R[0], adj0, 0);
                     term();
                     t += 7;
                 } else {
@@ -349,8 +374,13 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                 const int i = tl ? __ffs(tl) - 1 : 31 + __ffs((uint32_t)(t >> 32));
                 q ^= (uint32_t)(a >> i) & 1u;
                 a ^= sADJ[i];
+                uint32_t fr[RW];
 #pragma unroll
-                for (int w = 0; w < NW; w++) L[w] ^= sF[i * NW + w];
+                for (uint32_t w4 = 0; w4 < RW; w4 += 4) {
+                    const uint4 t4 = *reinterpret_cast<const uint4*>(sF + i * RW + w4);
+                    fr[w4] = t4.x; fr[w4 + 1] = t4.y; fr[w4 + 2] = t4.z; fr[w4 + 3] = t4.w;
+                }
+                step(fr);
             }
         }
         // a thread with several slices folds after each one, so no counter

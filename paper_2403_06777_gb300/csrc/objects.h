@@ -23,13 +23,13 @@ namespace zxp {
 struct DevTables {
     zw64* table = nullptr;
     zw64* pv = nullptr;
-    uint32_t* frows = nullptr;
+    uint32_t* rows = nullptr;
     uint64_t* adj = nullptr;
     uint32_t* seek = nullptr;
 };
 
 // Byte offsets of the tables in one contiguous block:
-// term table | phase-pair values | flip rows | adjacency | seek tables.
+// term table | phase-pair values | step rows | adjacency | seek tables.
 struct TableLayout {
     size_t o_pv = 0, o_f = 0, o_adj = 0, o_seek = 0, total = 0;
 };
@@ -37,10 +37,10 @@ struct TableLayout {
 inline TableLayout table_layout(const Plan& pl) {
     TableLayout L;
     const size_t tb = pl.table.size() * sizeof(zw64), pb = pl.pv.size() * sizeof(zw64);
-    const size_t fb = pl.frows.size() * sizeof(uint32_t), ab = pl.adj.size() * sizeof(uint64_t);
+    const size_t fb = pl.rows.size() * sizeof(uint32_t), ab = pl.adj.size() * sizeof(uint64_t);
     const size_t sb = pl.seek.size() * sizeof(uint32_t);
     L.o_pv = tb;
-    L.o_f = L.o_pv + pb;
+    L.o_f = (L.o_pv + pb + 15) & ~(size_t)15;
     L.o_adj = (L.o_f + fb + 7) & ~(size_t)7;
     L.o_seek = (L.o_adj + ab + 15) & ~(size_t)15;
     L.total = L.o_seek + sb + 16;
@@ -51,7 +51,7 @@ inline TableLayout table_layout(const Plan& pl) {
 inline void pack_tables(const Plan& pl, const TableLayout& L, unsigned char* dst) {
     if (!pl.table.empty()) memcpy(dst, pl.table.data(), pl.table.size() * sizeof(zw64));
     if (!pl.pv.empty()) memcpy(dst + L.o_pv, pl.pv.data(), pl.pv.size() * sizeof(zw64));
-    if (!pl.frows.empty()) memcpy(dst + L.o_f, pl.frows.data(), pl.frows.size() * sizeof(uint32_t));
+    if (!pl.rows.empty()) memcpy(dst + L.o_f, pl.rows.data(), pl.rows.size() * sizeof(uint32_t));
     if (!pl.adj.empty()) memcpy(dst + L.o_adj, pl.adj.data(), pl.adj.size() * sizeof(uint64_t));
     if (!pl.seek.empty()) memcpy(dst + L.o_seek, pl.seek.data(), pl.seek.size() * sizeof(uint32_t));
 }
@@ -60,7 +60,7 @@ inline DevTables device_tables(const TableLayout& L, unsigned char* base) {
     DevTables d;
     d.table = reinterpret_cast<zw64*>(base);
     d.pv = reinterpret_cast<zw64*>(base + L.o_pv);
-    d.frows = reinterpret_cast<uint32_t*>(base + L.o_f);
+    d.rows = reinterpret_cast<uint32_t*>(base + L.o_f);
     d.adj = reinterpret_cast<uint64_t*>(base + L.o_adj);
     d.seek = reinterpret_cast<uint32_t*>(base + L.o_seek);
     return d;
@@ -73,7 +73,7 @@ inline BatchScalar batch_descriptor(const Plan& pl, const DevTables& d) {
     bs.kp = pl.kp;
     bs.table = d.table;
     bs.pv = d.pv;
-    bs.frows = d.frows;
+    bs.rows = d.rows;
     bs.adj = d.adj;
     bs.seek = d.seek;
     bs.K = pl.K;

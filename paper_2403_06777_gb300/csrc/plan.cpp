@@ -162,6 +162,35 @@ int build_plan(const PS& ps, Plan* out) {
             e[nw + 2] = q;
         }
 
+    // step rows (the lowest three also in the kernel parameters, zero rows
+    // for variables beyond k)
+    {
+        const int nwl_k = pl.nwl < 1 ? 1 : pl.nwl;
+        const uint32_t rw = row_words(pl.nwn, nwl_k);
+        pl.row_stride = rw;
+        pl.rows.assign((size_t)k * rw, 0u);
+        for (uint32_t i = 0; i < k; i++) {
+            uint32_t* r = &pl.rows[(size_t)i * rw];
+            uint32_t S = 0;
+            for (uint32_t w = 0; w < nw; w++) {
+                const uint32_t f = pl.frows[(size_t)i * nw + w];
+                r[w] = f;
+                if ((int)w < pl.nwn) {
+                    S += 4u * (uint32_t)__builtin_popcount(f & kp.CB[w]);
+                } else {
+                    const uint32_t o = w - (uint32_t)pl.nwn;
+                    r[nw + o] = f & kp.C0[o];
+                    r[nw + nwl_k + o] = f & kp.C1[o];
+                    S += (uint32_t)__builtin_popcount(f & kp.C0[o]) + 2u * (uint32_t)__builtin_popcount(f & kp.C1[o]) +
+                         4u * (uint32_t)__builtin_popcount(f & kp.C2[o]);
+                }
+            }
+            r[nw + 2 * nwl_k] = S & 7u;
+        }
+        for (uint32_t i = 0; i < 3 && i < k; i++)
+            for (uint32_t w = 0; w < rw; w++) kp.R[i][w] = pl.rows[(size_t)i * rw + w];
+    }
+
     // T[J][M][pair bits][zero] = w^(J + 2M) (1 + sqrt2)^M * prod_j PV_j(bits_j) * [not zero]
     const uint32_t np = kp.npairs;
     pl.general = np > (uint32_t)kFoldPairs;

@@ -31,6 +31,14 @@ constexpr int kMaxNW = kMaxWordsNode + kMaxWordsOther;
 constexpr int kMaxPairs = 32;
 constexpr int kFoldPairs = 2;        // phase-pairs folded into the term table
 
+// Words of one variable's step row: its flip row F_i (NW = nwn + nwl words),
+// F_i & C0 and F_i & C1 on the linear words (2 nwl), and the constant S_i
+// (padded to a multiple of 4 words).
+ZXP_HD constexpr uint32_t row_words(int nwn, int nwl) {
+    return ((uint32_t)(nwn + 3 * nwl + 1) + 3u) & ~3u;
+}
+constexpr int kMaxRowWords = (int)row_words(kMaxWordsNode, kMaxWordsOther);
+
 // Passed by value as the kernel parameter block (kept in the constant bank).
 struct KernelParams {
     uint32_t k;
@@ -47,6 +55,7 @@ struct KernelParams {
     uint32_t C0[kMaxWordsOther], C1[kMaxWordsOther], C2[kMaxWordsOther], Z[kMaxWordsOther];
     uint32_t INV[kMaxNW];    // initial inversion of each form bit
     uint16_t PA[kMaxPairs], PB[kMaxPairs];            // bit positions of pair forms
+    uint32_t R[3][kMaxRowWords];                      // step rows of variables 0, 1, 2
 };
 
 struct Plan {
@@ -54,6 +63,12 @@ struct Plan {
     uint32_t m_odd = 0;
     KernelParams kp;
     std::vector<uint32_t> frows;    // k x NW: form bits holding variable i (flip rows)
+    // k x row_words: step rows.  Flipping variable i changes the phase
+    // exponent J = sum_lin c l + 4 (class-B node bits) by
+    //   S_i - 2 |L & F_i & C0| - 4 |L & F_i & C1|  (mod 8, L before the flip)
+    // with S_i = sum of c over the forms F_i holds + 4 per class-B node it holds.
+    std::vector<uint32_t> rows;
+    uint32_t row_stride = 0;
     std::vector<uint64_t> adj;      // k: quadratic part 4 sum_{i<j} A_ij x_i x_j, row i
     // Seek tables, per 4-bit group b of x and value v (ceil(k/4) x 16 entries
     // of seek_stride words): XOR of the flip rows of v's bits, XOR of their

@@ -405,7 +405,7 @@ struct Scheduler {
             sp = std::min<uint64_t>(std::max<uint64_t>((sp + 7) & ~7ull, 64), sum_max_span(pl));
             const uint64_t nsl = (count + sp - 1) / sp;
             const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((nsl + sum_threads() - 1) / sum_threads(), max_grid));
-            if (sum_launch(pl, d.table, d.pv, d.frows, d.adj, d.seek, planned[0].first, count, sp, grid,
+            if (sum_launch(pl, d.table, d.pv, d.rows, d.adj, d.seek, planned[0].first, count, sp, grid,
                            s->ctx->partials, s->ctx->counter, s->d_results + r->slot, stream) != cudaSuccess)
                 return ZXP_ECUDA;
             launches = 1;

@@ -38,7 +38,7 @@ namespace {
 template <int NWN, int NWL, int VAR>
 __global__ void __launch_bounds__(kThreads)
 sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtable,
-           const zw64* __restrict__ gpv, const uint32_t* __restrict__ gF,
+           const zw64* __restrict__ gpv, const uint32_t* __restrict__ gR,
            const uint64_t* __restrict__ gADJ, const uint32_t* __restrict__ gS, uint64_t first,
            uint64_t count, uint64_t span,
            uint64_t nslices, zw64* __restrict__ partials, unsigned int* __restrict__ counter,
@@ -54,7 +54,7 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
         for (uint32_t i = threadIdx.x; i < counter_words(HIST, ntab, blockDim.x) / 4; i += blockDim.x)
             h4[i] = make_uint4(0, 0, 0, 0);
     }
-    load_tables<NW, GENERAL>(p, sm, gtable, gpv, gF, gADJ, gS);
+    load_tables<NWN, NWL, GENERAL>(p, sm, gtable, gpv, gR, gADJ, gS);
     __syncthreads();
 
     zw64 acc = zw_zero();

@@ -264,7 +264,9 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
             for (int w = 0; w < NW; w++) L[w] = p.INV[w];
             uint64_t a = 0;
             uint32_t q = 0;
-            uint32_t Jl;   // linear and class-B node part of the phase exponent (mod 8)
+            // phase exponent mod 8: linear forms, class-B node bits and 4 x the
+            // quadratic part (updated by 4 x bit i of A x when x_i flips)
+            uint32_t Jl;
             const uint32_t nnib = (p.k + 3) >> 2;
             for (uint32_t b = 0; b < nnib; b++) {
                 const uint32_t v = (uint32_t)(x >> (4 * b)) & 15u;
@@ -291,7 +293,7 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                     P1 += __popc(v & p.C1[w]);
                     X2 ^= v & p.C2[w];
                 }
-                Jl = P0 + 2u * P1 + 4u * (uint32_t)__popc(X2);
+                Jl = P0 + 2u * P1 + 4u * ((uint32_t)__popc(X2) + q);
             }
 
             // one term at the current state
@@ -305,7 +307,7 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                 }
                 if (!GENERAL) {
                     // term value = table[(J, M, pair bits, zero bit)]
-                    const uint32_t J = (Jl + 4u * q) & 7u;
+                    const uint32_t J = Jl & 7u;
                     uint32_t idx = J * p.tab_stride + M;
                     if (XTRA) {   // phase-pair or zero forms present
                         uint32_t z = 0;
@@ -322,7 +324,7 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                     else
                         acc = zw_add(acc, lds_zw(sT + idx));
                 } else if (Zb == 0) {
-                    const uint32_t J = (Jl + 4u * q) & 7u;
+                    const uint32_t J = Jl & 7u;
                     zw64 v = lds_zw(sT + J * p.tab_stride + M);
                     if (GENERAL) {
                         for (uint32_t j = 0; j < p.npairs; j++) {
@@ -348,7 +350,7 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
             };
             // flip of a variable known at compile time (0, 1 or 2)
             auto flip = [&](const uint32_t* f, uint64_t adj, int i) {
-                q ^= (uint32_t)(a >> i) & 1u;
+                Jl += ((uint32_t)a >> i & 1u) << 2;
                 a ^= adj;
                 step(f);
             };
@@ -372,7 +374,7 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                 // x(t) = x(t-1) ^ (1 << ctz(t))
                 const uint32_t tl = (uint32_t)t;
                 const int i = tl ? __ffs(tl) - 1 : 31 + __ffs((uint32_t)(t >> 32));
-                q ^= (uint32_t)(a >> i) & 1u;
+                Jl += ((uint32_t)(a >> i) & 1u) << 2;
                 a ^= sADJ[i];
                 uint32_t fr[RW];
 #pragma unroll

@@ -189,6 +189,41 @@ int zxp_submit(zxp_ctx *ctx, const zxp_scalar *s, uint64_t first, uint64_t count
  * ZXP_EAGAIN: not finished.  ZXP_ENOTFOUND: unknown ticket. */
 int zxp_poll(zxp_ctx *ctx, uint64_t ticket, int64_t timeout_us, zxp_zomega *out);
 
+/* ---- parametric scalars: one reduction for many bitstrings ---------------- */
+
+/* The paper's own use (Sec. 3, Sec. 4): the output bits of the flagged
+ * qubits (kind ZXP_AMPLITUDE), or the projected bits of the flagged qubits
+ * inside marg_mask (kind ZXP_MARGINAL_DOUBLED), stay Boolean parameters
+ * through the whole reduction.  The result is reduced once; zxp_bind then
+ * turns it into an ordinary scalar for any values of the parameters (host
+ * work linear in its size), whose value is exactly that of zxp_compile with
+ * those bits.  Parameter j is the j-th flagged qubit in ascending order.
+ * A parametric reduction can need more decomposition parameters k than a
+ * reduction with fixed bits (fewer simplifications apply, Lemma 1). */
+typedef struct zxp_pscalar zxp_pscalar;
+
+typedef struct {
+    uint32_t k;                  /* summed variables of every bound scalar */
+    uint32_t n_params;
+    uint32_t n_lin, n_quad, n_node, n_pair;
+    int32_t e0;
+    uint32_t t_count;
+    uint32_t reserved[8];
+} zxp_pscalar_info_t;
+
+/* param_qubits: n_qubits entries, nonzero = parameter (at most 64 count);
+ * out_bits gives the bits of the other qubits.  Errors as zxp_compile. */
+int zxp_compile_param(const zxp_gate *gates, size_t n_gates, int n_qubits,
+                      const uint8_t *in_bits, const uint8_t *out_bits,
+                      const uint8_t *param_qubits, uint64_t marg_mask, int kind,
+                      zxp_pscalar **out);
+int zxp_pscalar_info(const zxp_pscalar *ps, zxp_pscalar_info_t *info);
+/* qubits[j] = the qubit of parameter j (n_params entries). */
+int zxp_pscalar_params(const zxp_pscalar *ps, uint32_t *qubits);
+/* The scalar for parameter values `bits` (bit j = parameter j). */
+int zxp_bind(const zxp_pscalar *ps, uint64_t bits, zxp_scalar **out);
+void zxp_pscalar_free(zxp_pscalar *ps);
+
 /* ---- batches: many scalars, one persistent launch per kernel variant ------ */
 
 /* A batch evaluates the full sums of n scalars of uneven k together: every
@@ -303,6 +338,10 @@ int zxp_server_submit(zxp_server *srv, const zxp_request *req, uint64_t *ticket)
 /* Queue a compiled scalar (borrowed: it must stay alive until its ticket
  * has been polled to completion). */
 int zxp_server_submit_scalar(zxp_server *srv, const zxp_scalar *s, uint64_t *ticket);
+/* Queue the binding `bits` of a parametric scalar (borrowed: it must stay
+ * alive until the ticket has been polled); a compile worker binds it. */
+int zxp_server_submit_bind(zxp_server *srv, const zxp_pscalar *ps, uint64_t bits,
+                           uint64_t *ticket);
 /* Wait up to timeout_us (0: do not wait, < 0: without limit).  Returns
  * ZXP_EAGAIN while the request runs, ZXP_ENOTFOUND for an unknown ticket;
  * otherwise the request's own status (ZXP_OK: *out holds the canonical

@@ -81,6 +81,12 @@ class zxp_server_stats_t(C.Structure):
 
 ZXP_SERVE_BATCHED, ZXP_SERVE_PLAIN = 0, 1
 
+
+class zxp_pscalar_info_t(C.Structure):
+    _fields_ = [("k", C.c_uint32), ("n_params", C.c_uint32), ("n_lin", C.c_uint32),
+                ("n_quad", C.c_uint32), ("n_node", C.c_uint32), ("n_pair", C.c_uint32),
+                ("e0", C.c_int32), ("t_count", C.c_uint32), ("reserved", C.c_uint32 * 8)]
+
 _lib = None
 
 
@@ -114,6 +120,13 @@ def lib():
         L.zxp_batch_run.argtypes = [vp, zp]
         L.zxp_batch_info.argtypes = [vp, C.POINTER(zxp_batch_info_t)]
         L.zxp_batch_destroy.argtypes, L.zxp_batch_destroy.restype = [vp], None
+        L.zxp_compile_param.argtypes = [C.c_char_p, sz, C.c_int, C.c_char_p, C.c_char_p,
+                                        C.c_char_p, u64, C.c_int, C.POINTER(vp)]
+        L.zxp_pscalar_info.argtypes = [vp, C.POINTER(zxp_pscalar_info_t)]
+        L.zxp_pscalar_params.argtypes = [vp, C.POINTER(C.c_uint32)]
+        L.zxp_bind.argtypes = [vp, u64, C.POINTER(vp)]
+        L.zxp_pscalar_free.argtypes, L.zxp_pscalar_free.restype = [vp], None
+        L.zxp_server_submit_bind.argtypes = [vp, vp, u64, C.POINTER(u64)]
         L.zxp_server_create.argtypes = [vp, C.POINTER(zxp_server_opts), C.POINTER(vp)]
         L.zxp_server_submit.argtypes = [vp, C.POINTER(zxp_request), C.POINTER(u64)]
         L.zxp_server_submit_scalar.argtypes = [vp, vp, C.POINTER(u64)]
@@ -232,6 +245,70 @@ def zxp_compile(gates, n_qubits: int, out_bits: Sequence[int],
     _check(lib().zxp_compile(gb, len(gb) // 8, n_qubits, ib, ob, marg_mask, kind, C.byref(h)),
            "zxp_compile")
     return Scalar(h.value)
+
+
+class PScalar:
+    """A parametric scalar (zxp_pscalar_free on deletion)."""
+
+    def __init__(self, handle: int):
+        self.handle = C.c_void_p(handle)
+
+    def free(self):
+        if self.handle:
+            lib().zxp_pscalar_free(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def info(self) -> dict:
+        return zxp_pscalar_info(self)
+
+
+def zxp_compile_param(gates, n_qubits: int, out_bits: Sequence[int], param_qubits: Sequence[int],
+                      in_bits: Sequence[int] | None = None, marg_mask: int = 0,
+                      kind: int = ZXP_AMPLITUDE) -> PScalar:
+    """param_qubits: the qubits whose bit is a parameter (parameter j = the
+    j-th of them in ascending order)."""
+    gb = _gate_bytes(gates)
+    ob = bytes(int(b) & 1 for b in out_bits)
+    ib = bytes(int(b) & 1 for b in in_bits) if in_bits is not None else None
+    flags = bytearray(n_qubits)
+    for q in param_qubits:
+        flags[int(q)] = 1
+    if len(ob) != n_qubits or (ib is not None and len(ib) != n_qubits):
+        raise ZxpError(ZXP_EINVAL, "zxp_compile_param: bit arrays must have n_qubits entries")
+    h = C.c_void_p()
+    _check(lib().zxp_compile_param(gb, len(gb) // 8, n_qubits, ib, ob, bytes(flags), marg_mask,
+                                   kind, C.byref(h)), "zxp_compile_param")
+    return PScalar(h.value)
+
+
+def zxp_pscalar_info(ps: PScalar) -> dict:
+    info = zxp_pscalar_info_t()
+    _check(lib().zxp_pscalar_info(ps.handle, C.byref(info)), "zxp_pscalar_info")
+    return {f: getattr(info, f) for f, _ in zxp_pscalar_info_t._fields_ if f != "reserved"}
+
+
+def zxp_pscalar_params(ps: PScalar):
+    n = zxp_pscalar_info(ps)["n_params"]
+    arr = (C.c_uint32 * max(1, n))()
+    _check(lib().zxp_pscalar_params(ps.handle, arr), "zxp_pscalar_params")
+    return list(arr[:n])
+
+
+def zxp_bind(ps: PScalar, bits: int) -> Scalar:
+    h = C.c_void_p()
+    _check(lib().zxp_bind(ps.handle, bits, C.byref(h)), "zxp_bind")
+    return Scalar(h.value)
+
+
+def zxp_pscalar_free(ps: PScalar):
+    ps.free()
 
 
 def zxp_scalar_from_tables(blob: bytes) -> Scalar:
@@ -420,6 +497,15 @@ def zxp_server_submit_scalar(srv: Server, s: Scalar) -> int:
     return t.value
 
 
+def zxp_server_submit_bind(srv: Server, ps: PScalar, bits: int) -> int:
+    """Queue the binding `bits` of a parametric scalar; returns its ticket."""
+    t = C.c_uint64()
+    _check(lib().zxp_server_submit_bind(srv.handle, ps.handle, bits, C.byref(t)),
+           "zxp_server_submit_bind")
+    srv.borrowed[t.value] = ps
+    return t.value
+
+
 def zxp_server_poll(srv: Server, ticket: int, timeout_us: int = -1):
     """None while the request runs; else (status, value, timing): value the
     canonical (c0, c1, c2, c3, e) when status is ZXP_OK or ZXP_EOVERFLOW,
@@ -472,5 +558,7 @@ EXPORTED = ["zxp_ctx_create", "zxp_ctx_destroy", "zxp_compile", "zxp_scalar_from
             "zxp_eval_device", "zxp_eval_noalloc", "zxp_batch_create", "zxp_batch_run",
             "zxp_batch_info", "zxp_batch_destroy", "zxp_server_create", "zxp_server_submit",
             "zxp_server_submit_scalar", "zxp_server_poll", "zxp_server_stats", "zxp_server_destroy",
+            "zxp_compile_param", "zxp_pscalar_info", "zxp_pscalar_params", "zxp_bind",
+            "zxp_pscalar_free", "zxp_server_submit_bind",
             "zxp_amplitude", "zxp_submit", "zxp_poll", "zxp_zomega_add", "zxp_zomega_canon",
             "zxp_zomega_to_complex", "zxp_strerror", "zxp_version"]

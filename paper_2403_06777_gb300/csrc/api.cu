@@ -173,6 +173,53 @@ int zxp_compile(const zxp_gate* gates, size_t n_gates, int n_qubits, const uint8
     return make_scalar(std::move(ps), out);
 }
 
+int zxp_compile_param(const zxp_gate* gates, size_t n_gates, int n_qubits, const uint8_t* in_bits,
+                      const uint8_t* out_bits, const uint8_t* param_qubits, uint64_t marg_mask,
+                      int kind, zxp_pscalar** out) {
+    if (!out || !param_qubits) return ZXP_EINVAL;
+    *out = nullptr;
+    std::unique_ptr<zxp_pscalar> p(new (std::nothrow) zxp_pscalar());
+    if (!p) return ZXP_ENOMEM;
+    CompileOptions opt;
+    int st = compile_circuit_param(gates, n_gates, n_qubits, in_bits, out_bits, param_qubits, marg_mask,
+                                   kind, opt, &p->pps);
+    if (st != ZXP_OK) return st;
+    *out = p.release();
+    return ZXP_OK;
+}
+
+int zxp_pscalar_info(const zxp_pscalar* ps, zxp_pscalar_info_t* info) {
+    if (!ps || !info) return ZXP_EINVAL;
+    memset(info, 0, sizeof *info);
+    const PPS& p = ps->pps;
+    info->k = p.k;
+    info->n_params = p.p;
+    info->n_lin = (uint32_t)p.lin.size();
+    info->n_quad = (uint32_t)p.quad.size();
+    info->n_node = (uint32_t)p.node.size();
+    info->n_pair = (uint32_t)p.pair.size();
+    info->e0 = p.e0;
+    info->t_count = p.t_count;
+    return ZXP_OK;
+}
+
+int zxp_pscalar_params(const zxp_pscalar* ps, uint32_t* qubits) {
+    if (!ps || (!qubits && ps->pps.p)) return ZXP_EINVAL;
+    for (uint32_t j = 0; j < ps->pps.p; j++) qubits[j] = ps->pps.param_qubit[j];
+    return ZXP_OK;
+}
+
+int zxp_bind(const zxp_pscalar* ps, uint64_t bits, zxp_scalar** out) {
+    if (!ps || !out) return ZXP_EINVAL;
+    *out = nullptr;
+    if (ps->pps.p < 64 && (bits >> ps->pps.p)) return ZXP_EINVAL;
+    PS b;
+    bind(ps->pps, bits, &b);
+    return make_scalar(std::move(b), out);
+}
+
+void zxp_pscalar_free(zxp_pscalar* ps) { delete ps; }
+
 int zxp_scalar_from_tables(const void* blob, size_t nbytes, zxp_scalar** out) {
     if (!out) return ZXP_EINVAL;
     *out = nullptr;

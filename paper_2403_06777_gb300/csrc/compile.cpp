@@ -101,6 +101,11 @@ class PathSum {
   public:
     int cap = 0, nw = 0, nvars = 0;
     std::vector<uint8_t> live, sing;     // sing[v]: coefficient of y_v (mod 8)
+    // Parameters: variables that are never summed (output bits left open);
+    // they appear in forms like summed variables, are never pivots, and
+    // remain in the result as the parameter part of each form.
+    std::vector<uint8_t> ext;
+    Bits extm;
     std::vector<Bits> adj;               // 4 y_u y_v terms (symmetric, no loops)
     std::unordered_set<Bits, BitsHash> tf;  // coefficient-1 parity forms, >= 2 vars
     std::vector<NodeF> nodes;
@@ -121,6 +126,8 @@ class PathSum {
         nw = (cap + 63) / 64;
         live.assign((size_t)cap, 0);
         sing.assign((size_t)cap, 0);
+        ext.assign((size_t)cap, 0);
+        extm = Bits(nw);
         adj.assign((size_t)cap, Bits(nw));
         qf.assign((size_t)n_qubits, Bits(nw));
         qc.assign((size_t)n_qubits, 0);
@@ -130,6 +137,8 @@ class PathSum {
         int ncap = cap * 2, nnw = (ncap + 63) / 64;
         live.resize((size_t)ncap, 0);
         sing.resize((size_t)ncap, 0);
+        ext.resize((size_t)ncap, 0);
+        extm.resize(nnw);
         for (auto& b : adj) b.resize(nnw);
         adj.resize((size_t)ncap, Bits(nnw));
         std::vector<Bits> t(tf.begin(), tf.end());
@@ -146,8 +155,17 @@ class PathSum {
         int v = nvars++;
         live[(size_t)v] = 1;
         sing[(size_t)v] = 0;
+        ext[(size_t)v] = 0;
         return v;
     }
+    int new_param() {
+        int v = new_var();
+        ext[(size_t)v] = 1;
+        extm.set(v);
+        return v;
+    }
+    // the summed variables of a form
+    Bits internal(const Bits& f) const { Bits r = f; r.and_not(extm); return r; }
     Bits unit(int v) const { Bits b(nw); b.set(v); return b; }
 
     void toggle_edge(int i, int j) { adj[(size_t)i].flip(j); adj[(size_t)j].flip(i); }
@@ -248,6 +266,7 @@ class PathSum {
         int best = -1;
         long bestkey = 0;
         F.each([&](int i) {
+            if (ext[(size_t)i]) return;
             long key = (long)hard[(size_t)i] * 100000000L + (long)locks[(size_t)i] * 100000L +
                        adj[(size_t)i].count() * 16 + (long)(mix64(rng) & 15);
             if (best < 0 || key < bestkey) { best = i; bestkey = key; }
@@ -258,6 +277,13 @@ class PathSum {
     // require (F xor c) = 0
     void constrain(const Bits& F, int c) {
         if (!F.any()) { if (c) zero = true; return; }
+        if (!internal(F).any()) {
+            // a condition on the parameters alone stays a factor of the result:
+            // [l xor c = 0] = (1 + w^(4c + 4l)) / 2
+            e0 += 2;
+            nodes.push_back(NodeF{c ? 4 : 0, F});
+            return;
+        }
         std::vector<int> locks = lock_counts(), hard = hard_lock_counts();
         int p = pick_pivot(F, locks, hard);
         Bits A = F;
@@ -314,6 +340,13 @@ class PathSum {
                     again = true;
                     break;
                 }
+                if ((g == 0 || g == 4) && !internal(nodes[i].f).any()) {
+                    // a condition on the parameters: kept (see constrain);
+                    // the same condition with the opposite value is zero
+                    for (size_t j = i + 1; j < nodes.size(); j++)
+                        if (nodes[j].f == nodes[i].f && ((nodes[j].g - g) & 7) == 4) zero = true;
+                    continue;
+                }
                 if (g == 0 || g == 4) {
                     Bits f = nodes[i].f;
                     nodes.erase(nodes.begin() + (long)i);
@@ -323,7 +356,7 @@ class PathSum {
                     break;
                 }
                 for (size_t j = i + 1; j < nodes.size(); j++) {
-                    if (nodes[j].f == nodes[i].f && ((nodes[j].g - nodes[i].g) & 7) == 4) {
+                    if ((nodes[i].g & 1) && nodes[j].f == nodes[i].f && ((nodes[j].g - nodes[i].g) & 7) == 4) {
                         int gi = nodes[i].g;
                         nodes.erase(nodes.begin() + (long)j);
                         nodes.erase(nodes.begin() + (long)i);
@@ -447,7 +480,7 @@ class PathSum {
         std::vector<Bits> rows;
         for (auto& f : tf) rows.push_back(f);
         for (int v = 0; v < nvars; v++)
-            if (live[(size_t)v] && (sing[(size_t)v] & 1)) rows.push_back(unit(v));
+            if (live[(size_t)v] && !ext[(size_t)v] && (sing[(size_t)v] & 1)) rows.push_back(unit(v));
         for (auto& n : nodes) rows.push_back(n.f);
         for (auto& p : pairs) { rows.push_back(p.fa); rows.push_back(p.fb); }
         return rows;
@@ -461,7 +494,7 @@ class PathSum {
         std::vector<int> piv;
         std::vector<Bits> basis;
         for (auto& r0 : rows) {
-            Bits r = r0;
+            Bits r = internal(r0);      // parameters are not summed: not pivots
             for (size_t i = 0; i < basis.size(); i++)
                 if (r.get(piv[i])) r.xor_with(basis[i]);
             int p = r.first();
@@ -476,7 +509,7 @@ class PathSum {
         for (int p : piv) is_piv.set(p);
         bool freed = false;
         for (int q = 0; q < nvars; q++) {
-            if (!live[(size_t)q] || is_piv.get(q)) continue;
+            if (!live[(size_t)q] || ext[(size_t)q] || is_piv.get(q)) continue;
             bool inrow = false;
             for (auto& b : basis) if (b.get(q)) { inrow = true; break; }
             if (!inrow) continue;     // already free of factor forms
@@ -500,11 +533,15 @@ class PathSum {
             // 1. Clifford variables
             int cv = -1;
             for (int v = 0; v < nvars; v++)
-                if (live[(size_t)v] && !locks[(size_t)v] && !(sing[(size_t)v] & 1)) { cv = v; break; }
+                if (live[(size_t)v] && !ext[(size_t)v] && !locks[(size_t)v] && !(sing[(size_t)v] & 1)) {
+                    cv = v;
+                    break;
+                }
             if (cv >= 0) { elim_clifford(cv); continue; }
             // 2. free T-like variables: node, pair or decomposition
             Bits freev(nw);
-            for (int v = 0; v < nvars; v++) if (live[(size_t)v] && !locks[(size_t)v]) freev.set(v);
+            for (int v = 0; v < nvars; v++)
+                if (live[(size_t)v] && !ext[(size_t)v] && !locks[(size_t)v]) freev.set(v);
             if (freev.any()) {
                 long nkey = -1, pkey = -1, wkey = -1;
                 int nu = -1, pu = -1, pw = -1, wu = -1, ndam = 0, pdam = 0;
@@ -549,8 +586,9 @@ class PathSum {
             const Bits* best = nullptr;
             int bestgain = 0;
             for (auto& f : tf) {
+                if (!internal(f).any()) continue;   // a phase on the parameters alone
                 int gain = 0;
-                f.each([&](int v) { if (locks[(size_t)v] == 1) gain++; });
+                f.each([&](int v) { if (!ext[(size_t)v] && locks[(size_t)v] == 1) gain++; });
                 long key = (long)gain * 64 + (long)(mix64(rng) & 31);
                 if (key > bestkey) { bestkey = key; best = &f; bestgain = gain; }
             }
@@ -604,21 +642,21 @@ int apply_gate(PathSum& ps, const zxp_gate& g, bool dagger) {
 }
 
 struct Result {
-    PS ps;
+    PPS ps;
     int status = ZXP_OK;
     long score = 0;
 };
 
 // Materialise the global factor w^phase (1+sqrt2)^N (1-w)^v / sqrt2^e0
 // with small integer coefficients.
-void finish_global(PathSum& s, PS& ps) {
+void finish_global(PathSum& s, PPS& ps) {
     int h = s.v1w / 2;                     // (1 - w)^2 = sqrt2 (1+sqrt2)^-1 w^5
     int e0 = s.e0 - h;
     int N = s.unitN - h;
     int ph = (s.phase + 5 * h) & 7;
     // keep |N| small: (1+sqrt2) = (1+w)(1+w^7)/sqrt2, (sqrt2-1) = (1+w^3)(1+w^5)/sqrt2
-    while (N > 24) { ps.node.push_back({0, 1}); ps.node.push_back({0, 7}); e0 += 1; N--; }
-    while (N < -24) { ps.node.push_back({0, 3}); ps.node.push_back({0, 5}); e0 += 1; N++; }
+    while (N > 24) { ps.node.push_back({0, 0, 1}); ps.node.push_back({0, 0, 7}); e0 += 1; N--; }
+    while (N < -24) { ps.node.push_back({0, 0, 3}); ps.node.push_back({0, 0, 5}); e0 += 1; N++; }
     zw64 G = zw_wpow((unsigned)ph);
     if (N > 0) G = zw_mul(G, zw_pow(zw_silver(), (unsigned)N));
     if (N < 0) G = zw_mul(G, zw_pow(zw_silver_inv(), (unsigned)-N));
@@ -628,28 +666,46 @@ void finish_global(PathSum& s, PS& ps) {
     ps.e0 = e0;
 }
 
+// One reduction.  param_q (nullable): qubits whose output bit (kind 0) or
+// projected bit (kind 1, inside marg_mask) is a parameter instead of
+// out_bits[q]; parameter j is the j-th such qubit in ascending order.
 Result run_once(const zxp_gate* gates, size_t n_gates, int n, const uint8_t* in_bits,
-                const uint8_t* out_bits, uint64_t marg_mask, int kind, uint64_t seed,
-                const PathSum::Strategy& strat, bool allow_pairs) {
+                const uint8_t* out_bits, const uint8_t* param_q, uint64_t marg_mask, int kind,
+                uint64_t seed, const PathSum::Strategy& strat, bool allow_pairs) {
     Result res;
     int nh = count_h(gates, n_gates) * (kind == 1 ? 2 : 1);
     PathSum s(n, nh + 64);
     s.rng = seed;
     s.allow_pairs = allow_pairs;
+    std::vector<int> pvar((size_t)n, -1);
+    std::vector<int> params;
+    for (int q = 0; q < n; q++)
+        if (param_q && param_q[q] && (kind == 0 || ((marg_mask >> q) & 1))) {
+            pvar[(size_t)q] = s.new_param();
+            params.push_back(q);
+        }
     for (int q = 0; q < n; q++) s.qc[(size_t)q] = in_bits ? (in_bits[q] & 1) : 0;
     for (size_t i = 0; i < n_gates; i++) apply_gate(s, gates[i], false);
+    // the output constraint of qubit q: its wire equals the bit (or parameter)
+    auto out_form = [&](int q) {
+        Bits f = s.qf[(size_t)q];
+        f.resize(s.nw);
+        if (pvar[(size_t)q] >= 0) f.flip(pvar[(size_t)q]);
+        return f;
+    };
+    auto out_value = [&](int q) { return pvar[(size_t)q] >= 0 ? 0 : (out_bits[q] & 1); };
     if (kind == 0) {
         for (int q = 0; q < n && !s.zero; q++) {
-            Bits f = s.qf[(size_t)q];
-            s.constrain(f, s.qc[(size_t)q] ^ (out_bits[q] & 1));
+            Bits f = out_form(q);
+            s.constrain(f, s.qc[(size_t)q] ^ out_value(q));
         }
     } else {
         for (int q = 0; q < n && !s.zero; q++) {
             if (!((marg_mask >> q) & 1)) continue;
-            Bits f = s.qf[(size_t)q];
-            int b = out_bits[q] & 1;
+            Bits f = out_form(q);
+            int b = out_value(q);
             s.constrain(f, s.qc[(size_t)q] ^ b);
-            s.qf[(size_t)q] = Bits(s.nw);
+            s.qf[(size_t)q] = pvar[(size_t)q] >= 0 ? s.unit(pvar[(size_t)q]) : Bits(s.nw);
             s.qc[(size_t)q] = (uint8_t)b;
         }
         for (size_t i = n_gates; i-- > 0 && !s.zero;) apply_gate(s, gates[i], true);
@@ -662,55 +718,74 @@ Result run_once(const zxp_gate* gates, size_t n_gates, int n, const uint8_t* in_
         s.simplify_nodes();
         s.reduce(strat);
     }
-    PS& ps = res.ps;
+    PPS& ps = res.ps;
+    ps.p = (uint32_t)params.size();
+    for (int q : params) ps.param_qubit.push_back((uint32_t)q);
     if (s.zero) {
         ps.k = 0;
         ps.e0 = 0;
         ps.G[0] = ps.G[1] = ps.G[2] = ps.G[3] = 0;
+        ps.zero = true;
         res.score = 0;
         return res;
     }
-    // order the remaining variables: fewest forms first (the low Gray-code
-    // bits flip most often)
+    // order the remaining summed variables: fewest forms first (the low
+    // Gray-code bits flip most often)
     std::vector<int> locks = s.lock_counts();
     std::vector<int> vars;
-    for (int v = 0; v < s.nvars; v++) if (s.live[(size_t)v]) vars.push_back(v);
+    for (int v = 0; v < s.nvars; v++) if (s.live[(size_t)v] && !s.ext[(size_t)v]) vars.push_back(v);
     if (vars.size() > 62) { res.status = ZXP_ETOOBIG; res.score = 1L << 40; return res; }
     std::stable_sort(vars.begin(), vars.end(), [&](int a, int b) {
         return locks[(size_t)a] < locks[(size_t)b];
     });
-    std::vector<int> idx((size_t)s.nvars, -1);
+    std::vector<int> idx((size_t)s.nvars, -1), pidx((size_t)s.nvars, -1);
     for (size_t i = 0; i < vars.size(); i++) idx[(size_t)vars[i]] = (int)i;
-    auto mask_of = [&](const Bits& b) {
+    for (size_t j = 0; j < params.size(); j++) pidx[(size_t)pvar[(size_t)params[j]]] = (int)j;
+    auto mask_x = [&](const Bits& b) {
         uint64_t m = 0;
-        b.each([&](int v) { m |= 1ull << idx[(size_t)v]; });
+        b.each([&](int v) { if (idx[(size_t)v] >= 0) m |= 1ull << idx[(size_t)v]; });
+        return m;
+    };
+    auto mask_b = [&](const Bits& b) {
+        uint64_t m = 0;
+        b.each([&](int v) { if (pidx[(size_t)v] >= 0) m |= 1ull << pidx[(size_t)v]; });
         return m;
     };
     ps.k = (uint32_t)vars.size();
     for (size_t i = 0; i < vars.size(); i++) {
         int v = vars[i];
-        if (s.sing[(size_t)v]) ps.lin.push_back({1ull << i, s.sing[(size_t)v]});
+        if (s.sing[(size_t)v]) ps.lin.push_back({1ull << i, 0, s.sing[(size_t)v]});
     }
-    for (auto& f : s.tf) ps.lin.push_back({mask_of(f), 1});
+    for (size_t j = 0; j < params.size(); j++) {
+        int v = pvar[(size_t)params[j]];
+        if (s.sing[(size_t)v]) ps.lin.push_back({0, 1ull << j, s.sing[(size_t)v]});
+    }
+    for (auto& f : s.tf) ps.lin.push_back({mask_x(f), mask_b(f), 1});
+    // 4 y_v (sum of its neighbours): summed rows take their later summed
+    // neighbours and all parameter neighbours, parameter rows their later
+    // parameter neighbours
     for (size_t i = 0; i < vars.size(); i++) {
-        uint64_t row = mask_of(s.adj[(size_t)vars[i]]);
-        uint64_t upper = row & ~((2ull << i) - 1);
-        if (upper) ps.quad.push_back({1ull << i, upper});
+        const Bits& row = s.adj[(size_t)vars[i]];
+        uint64_t upper = mask_x(row) & ~((2ull << i) - 1), rb = mask_b(row);
+        if (upper || rb) ps.quad.push_back({1ull << i, 0, upper, rb});
     }
-    for (auto& nd : s.nodes) ps.node.push_back({mask_of(nd.f), (uint32_t)nd.g});
-    for (auto& p : s.pairs) ps.pair.push_back({mask_of(p.fa), mask_of(p.fb), (uint32_t)p.a, (uint32_t)p.b});
-    for (auto& p : s.const_pairs) ps.pair.push_back({0, 0, (uint32_t)p.a, (uint32_t)p.b});
+    for (size_t j = 0; j < params.size(); j++) {
+        uint64_t upper = mask_b(s.adj[(size_t)pvar[(size_t)params[j]]]) & ~((2ull << j) - 1);
+        if (upper) ps.quad.push_back({0, 1ull << j, 0, upper});
+    }
+    for (auto& nd : s.nodes) ps.node.push_back({mask_x(nd.f), mask_b(nd.f), (uint32_t)nd.g});
+    for (auto& p : s.pairs)
+        ps.pair.push_back({mask_x(p.fa), mask_b(p.fa), mask_x(p.fb), mask_b(p.fb), (uint32_t)p.a, (uint32_t)p.b});
+    for (auto& p : s.const_pairs) ps.pair.push_back({0, 0, 0, 0, (uint32_t)p.a, (uint32_t)p.b});
     finish_global(s, ps);
     // score: terms first, then per-term work
     res.score = ((long)ps.k << 20) + (long)ps.pair.size() * 64 + (long)(ps.node.size() + ps.lin.size());
     return res;
 }
 
-}  // namespace
-
-int compile_circuit(const zxp_gate* gates, size_t n_gates, int n, const uint8_t* in_bits,
-                    const uint8_t* out_bits, uint64_t marg_mask, int kind,
-                    const CompileOptions& opt, PS* out) {
+int compile_impl(const zxp_gate* gates, size_t n_gates, int n, const uint8_t* in_bits,
+                 const uint8_t* out_bits, const uint8_t* param_q, uint64_t marg_mask, int kind,
+                 const CompileOptions& opt, PPS* out) {
     if (n < 1 || n > 65535 || (!gates && n_gates) || !out_bits || !out) return ZXP_EINVAL;
     if (kind != 0 && kind != 1) return ZXP_EINVAL;
     if (kind == 1 && n > 64) return ZXP_EINVAL;
@@ -720,6 +795,11 @@ int compile_circuit(const zxp_gate* gates, size_t n_gates, int n, const uint8_t*
         if (g.op > ZXP_CZ || g.q0 >= n) return ZXP_EINVAL;
         if ((g.op == ZXP_CNOT || g.op == ZXP_CZ) && (g.q1 >= n || g.q1 == g.q0)) return ZXP_EINVAL;
         tcount += (g.op == ZXP_T || g.op == ZXP_TDG);
+    }
+    if (param_q) {
+        int np = 0;
+        for (int q = 0; q < n; q++) np += param_q[q] && (kind == 0 || ((marg_mask >> q) & 1));
+        if (np > 64) return ZXP_EINVAL;
     }
     Result best;
     best.status = ZXP_ETOOBIG;
@@ -732,7 +812,7 @@ int compile_circuit(const zxp_gate* gates, size_t n_gates, int n, const uint8_t*
             {2, 3, 2, true}, {0, 1, 1, true}, {1, 1, 0, true}, {1000, 1000, 1, false},
         };
         PathSum::Strategy strat = kStrategies[t % 8];
-        Result r = run_once(gates, n_gates, n, in_bits, out_bits, marg_mask, kind,
+        Result r = run_once(gates, n_gates, n, in_bits, out_bits, param_q, marg_mask, kind,
                             mix64(seed), strat, opt.allow_pairs);
         if (r.status != ZXP_OK) continue;
         if (best.score < 0 || r.score < best.score) best = std::move(r);
@@ -741,6 +821,26 @@ int compile_circuit(const zxp_gate* gates, size_t n_gates, int n, const uint8_t*
     best.ps.t_count = tcount * (kind == 1 ? 2u : 1u);
     *out = std::move(best.ps);
     return ZXP_OK;
+}
+
+}  // namespace
+
+int compile_circuit(const zxp_gate* gates, size_t n_gates, int n, const uint8_t* in_bits,
+                    const uint8_t* out_bits, uint64_t marg_mask, int kind,
+                    const CompileOptions& opt, PS* out) {
+    if (!out) return ZXP_EINVAL;
+    PPS pps;
+    int st = compile_impl(gates, n_gates, n, in_bits, out_bits, nullptr, marg_mask, kind, opt, &pps);
+    if (st != ZXP_OK) return st;
+    bind(pps, 0, out);
+    return ZXP_OK;
+}
+
+int compile_circuit_param(const zxp_gate* gates, size_t n_gates, int n, const uint8_t* in_bits,
+                          const uint8_t* out_bits, const uint8_t* param_qubits, uint64_t marg_mask,
+                          int kind, const CompileOptions& opt, PPS* out) {
+    if (!param_qubits) return ZXP_EINVAL;
+    return compile_impl(gates, n_gates, n, in_bits, out_bits, param_qubits, marg_mask, kind, opt, out);
 }
 
 }  // namespace zxp

@@ -4,6 +4,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "param.h"
 #include "ps.h"
 
 struct zxp_gate;
@@ -25,5 +26,13 @@ struct CompileStats {
 int compile_circuit(const zxp_gate* gates, size_t n_gates, int n_qubits,
                     const uint8_t* in_bits, const uint8_t* out_bits, uint64_t marg_mask,
                     int kind, const CompileOptions& opt, PS* out);
+
+// The same reduction with the bits of the qubits flagged in param_qubits
+// (n_qubits entries; for kind 1 only those inside marg_mask count) left as
+// parameters (at most 64); out_bits gives the other qubits' bits.
+int compile_circuit_param(const zxp_gate* gates, size_t n_gates, int n_qubits,
+                          const uint8_t* in_bits, const uint8_t* out_bits,
+                          const uint8_t* param_qubits, uint64_t marg_mask, int kind,
+                          const CompileOptions& opt, PPS* out);
 
 }  // namespace zxp

@@ -11,6 +11,7 @@
 
 #include "zxp.h"
 #include "kernel.h"
+#include "param.h"
 #include "plan.h"
 #include "ps.h"
 #include "zring.h"
@@ -171,6 +172,10 @@ struct zxp_ctx {
     uint64_t next_ticket = 1;
     std::map<uint64_t, zxp::Ticket> tickets;
     std::vector<zxp::Ticket> free_slots;
+};
+
+struct zxp_pscalar {
+    zxp::PPS pps;
 };
 
 namespace zxp {

@@ -59,7 +59,10 @@ struct Request {
     std::vector<uint8_t> in_bits, out_bits;
     int32_t n_qubits = 0, kind = 0;
     uint64_t mask = 0;
-    // the scalar: compiled here (owned) or the caller's (borrowed)
+    // a binding request: a parametric scalar (borrowed) and parameter values
+    const PPS* pps = nullptr;
+    uint64_t bits = 0;
+    // the scalar: compiled or bound here (owned) or the caller's (borrowed)
     std::unique_ptr<zxp_scalar> owned;
     const zxp_scalar* scalar = nullptr;
     // completion (under the server mutex)
@@ -165,10 +168,15 @@ void compile_worker(zxp_server* s) {
             s->compiling++;
         }
         PS ps;
-        CompileOptions opt;
-        int st = compile_circuit(r->gates.data(), r->gates.size(), r->n_qubits,
+        int st = ZXP_OK;
+        if (r->pps) {
+            bind(*r->pps, r->bits, &ps);
+        } else {
+            CompileOptions opt;
+            st = compile_circuit(r->gates.data(), r->gates.size(), r->n_qubits,
                                  r->in_bits.empty() ? nullptr : r->in_bits.data(), r->out_bits.data(),
                                  r->mask, r->kind, opt, &ps);
+        }
         zxp_scalar* sc = nullptr;
         if (st == ZXP_OK) st = make_scalar(std::move(ps), &sc);
         {
@@ -634,6 +642,15 @@ int zxp_server_submit(zxp_server* s, const zxp_request* req, uint64_t* ticket) {
     r->mask = req->marg_mask;
     r->out_bits.assign(req->out_bits, req->out_bits + req->n_qubits);
     if (req->in_bits) r->in_bits.assign(req->in_bits, req->in_bits + req->n_qubits);
+    return submit_common(s, r, false, ticket);
+}
+
+int zxp_server_submit_bind(zxp_server* s, const zxp_pscalar* ps, uint64_t bits, uint64_t* ticket) {
+    if (!s || !ps || !ticket) return ZXP_EINVAL;
+    if (ps->pps.p < 64 && (bits >> ps->pps.p)) return ZXP_EINVAL;
+    ReqPtr r = std::make_shared<Request>();
+    r->pps = &ps->pps;
+    r->bits = bits;
     return submit_common(s, r, false, ticket);
 }
 

@@ -205,6 +205,74 @@ def serve_bench(Z, ctx, zi, n_req: int, rate_hz: float, max_k: int):
             "p99_plain_over_batched": plain["p99_ms"] / batched["p99_ms"]}
 
 
+def param_bench(Z, ctx, zi, n_values=(1, 4, 16, 64, 256, 1024), seed=0):
+    """The paper's own use: one parametric reduction of the medium circuit
+    (all 20 output bits parameters), N random bitstrings bound and evaluated
+    through the server, against N fixed-bit compiles through the same server.
+    S_N = T_plain(N) / T_param(N); T_param includes the one reduction."""
+    import random
+    w = zi.workload_medium(seed)
+    t0 = time.perf_counter()
+    ps = Z.zxp_compile_param(w.gates, w.n, [0] * w.n, list(range(w.n)))
+    t_reduce = time.perf_counter() - t0
+    gb = zi.pack_gates(w.gates)
+    rng = random.Random(1234)
+    srv = Z.zxp_server_create(ctx)
+    # warm-up: kernels' first launches, worker threads
+    for t in [Z.zxp_server_submit_bind(srv, ps, 0), Z.zxp_server_submit(srv, gb, w.n, [0] * w.n)]:
+        Z.zxp_server_poll(srv, t, -1)
+    rows = []
+    for N in n_values:
+        bs = [rng.getrandbits(w.n) for _ in range(N)]
+        t0 = time.perf_counter()
+        tk = [Z.zxp_server_submit_bind(srv, ps, b) for b in bs]
+        vp = [Z.zxp_server_poll(srv, t, -1)[1] for t in tk]
+        t_param = t_reduce + (time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        tk = [Z.zxp_server_submit(srv, gb, w.n, [(b >> q) & 1 for q in range(w.n)]) for b in bs]
+        vc = [Z.zxp_server_poll(srv, t, -1)[1] for t in tk]
+        t_plain = time.perf_counter() - t0
+        assert vp == vc, "bound and fixed-bit values differ"
+        rows.append({"N": N, "param_s": t_param, "plain_s": t_plain, "S_N": t_plain / t_param})
+    srv.close()
+    # the same plain path with one compile thread (the paper's baseline reduces
+    # each bitstring on one core); the parametric path's binding is cheap
+    # enough that its thread count does not matter
+    srv1 = Z.zxp_server_create(ctx, compile_threads=1)
+    one = []
+    for N in (16, 128):
+        bs = [rng.getrandbits(w.n) for _ in range(N)]
+        t0 = time.perf_counter()
+        tk = [Z.zxp_server_submit(srv1, gb, w.n, [(b >> q) & 1 for q in range(w.n)]) for b in bs]
+        for t in tk:
+            Z.zxp_server_poll(srv1, t, -1)
+        one.append((N, time.perf_counter() - t0))
+    srv1.close()
+    plain1_per_eval = (one[1][1] - one[0][1]) / (one[1][0] - one[0][0])
+    # terminal speedup: ratio of the marginal per-evaluation costs of the two
+    # largest N; inflection: the N where S_N reaches half of it (log interpolation)
+    a, b = rows[-2], rows[-1]
+    s_inf = (b["plain_s"] - a["plain_s"]) / max(1e-9, b["param_s"] - a["param_s"])
+    n_inf = None
+    for r0, r1 in zip(rows, rows[1:]):
+        if r0["S_N"] < s_inf / 2 <= r1["S_N"]:
+            import math
+            f = (s_inf / 2 - r0["S_N"]) / (r1["S_N"] - r0["S_N"])
+            n_inf = math.exp(math.log(r0["N"]) + f * (math.log(r1["N"]) - math.log(r0["N"])))
+    if n_inf is None and rows[0]["S_N"] >= s_inf / 2:
+        n_inf = rows[0]["N"]
+    info = Z.zxp_pscalar_info(ps)
+    return {"workload": f"{w.name} seed={seed}: all {w.n} output bits parameters, random bitstrings",
+            "k_param": info["k"], "k_fixed": Z.zxp_scalar_info(Z.zxp_compile(w.gates, w.n, w.out_bits))["k"],
+            "reduce_ms": t_reduce * 1e3, "rows": rows, "S_inf": s_inf, "N_inflec": n_inf,
+            "param_ms_per_eval": 1e3 * (b["param_s"] - a["param_s"]) / (b["N"] - a["N"]),
+            "plain_ms_per_eval": 1e3 * (b["plain_s"] - a["plain_s"]) / (b["N"] - a["N"]),
+            "plain_1thread_ms_per_eval": plain1_per_eval * 1e3,
+            "S_inf_vs_1thread": plain1_per_eval / ((b["param_s"] - a["param_s"]) / (b["N"] - a["N"])),
+            "plain": "fixed-bit compile of each bitstring on the server's compile workers "
+                     "(all host threads; 1thread: one worker), same GPU path"}
+
+
 def setup_dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -425,6 +493,10 @@ def main():
     if rank == 0 and not os.environ.get("ZXP_BENCH_SKIP_SERVE"):
         serving = serve_bench(Z, ctx, zi, n_req=2000, rate_hz=2000.0, max_k=SERVE_MAX_K)
 
+    param = None
+    if rank == 0 and not os.environ.get("ZXP_BENCH_SKIP_PARAM"):
+        param = param_bench(Z, ctx, zi)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -464,6 +536,8 @@ def main():
         line["batch"] = batch
     if serving:
         line["serving"] = serving
+    if param:
+        line["parametric"] = param
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(blob, k)
     print(json.dumps(line))

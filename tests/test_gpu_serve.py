@@ -195,3 +195,31 @@ def test_destroy_finishes_queued_requests(ctx):
     for s in scalars:
         Z.zxp_server_submit_scalar(srv, s)
     srv.close()   # must return with everything finished, not hang
+
+
+def test_bind_requests_cover_every_output_bitstring(ctx):
+    """One parametric reduction, every output bitstring through the server:
+    each value equals the exact state vector amplitude."""
+    w = zi.workload_small(2)
+    n = w.n
+    ps = Z.zxp_compile_param(w.gates, n, [0] * n, list(range(n)))
+    amps = oracle.amps_all(w.gates, n)
+    with Z.zxp_server_create(ctx) as srv:
+        tickets = [Z.zxp_server_submit_bind(srv, ps, x) for x in range(1 << n)]
+        res = drain(srv, tickets)
+    for x, t in enumerate(tickets):
+        assert res[t][0] == Z.ZXP_OK and res[t][1] == amps[x]
+
+
+def test_bind_requests_equal_fixed_bit_compiles(ctx):
+    w = zi.workload_medium(2)
+    ps = Z.zxp_compile_param(w.gates, w.n, [0] * w.n, list(range(w.n)))
+    rng = random.Random(5)
+    bitstrings = [rng.getrandbits(w.n) for _ in range(6)]
+    with Z.zxp_server_create(ctx) as srv:
+        tickets = [Z.zxp_server_submit_bind(srv, ps, b) for b in bitstrings]
+        res = drain(srv, tickets)
+    for b, t in zip(bitstrings, tickets):
+        bits = [(b >> q) & 1 for q in range(w.n)]
+        s = Z.zxp_compile(w.gates, w.n, bits)
+        assert res[t][0] == Z.ZXP_OK and res[t][1] == Z.zxp_amplitude(ctx, s)

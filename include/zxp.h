@@ -353,6 +353,42 @@ int zxp_server_stats(zxp_server *srv, zxp_server_stats_t *stats);
 /* Finish every queued request, then stop the threads and free everything. */
 void zxp_server_destroy(zxp_server *srv);
 
+/* ---- weak simulation and marginals by summing ----------------------------- */
+
+/* Weak simulation by chained marginals (Sec. 2.2; App. F, Algorithm 2).
+ * zxp_sampler_create reduces the n doubled diagrams P(a_0 .. a_j),
+ * j = 0 .. n-1, once each with the bits a_0 .. a_j as parameters (n <= 64).
+ * zxp_sampler_draw then draws n_samples bitstrings together: for each qubit
+ * j in turn it evaluates P(B_i || 0) for every sample i on the device (one
+ * step of continuous batching for all samples) and sets bit j of sample i to
+ * 0 if u[i*n + j] < P(B_i || 0) / P(B_i), else to 1, where P(B_i) is the
+ * exact probability of the prefix drawn so far.  The uniforms u in [0, 1)
+ * are the caller's.  The comparison uses doubles computed from the exact
+ * values as (c0 + (c1 - c3) / sqrt2) 2^(-e/2) (one more 1/sqrt2 for odd e),
+ * in that order of IEEE operations.  The algorithm as printed compares u
+ * with P(B_i || 0) alone; the ratio, which Sec. 2.2 states, is used.
+ * out_bits: n_samples x n (row-major, bit j of sample i at [i*n + j]);
+ * prob (nullable): the exact probability of each drawn bitstring.
+ * The context must not be used by other threads while a sampler exists. */
+typedef struct zxp_sampler zxp_sampler;
+int zxp_sampler_create(zxp_ctx *ctx, const zxp_gate *gates, size_t n_gates, int n_qubits,
+                       const uint8_t *in_bits, zxp_sampler **out);
+/* k_per_prefix: n entries, the summed variables of each reduced marginal. */
+int zxp_sampler_info(const zxp_sampler *s, uint32_t *k_per_prefix);
+int zxp_sampler_draw(zxp_sampler *s, size_t n_samples, const double *u, uint8_t *out_bits,
+                     zxp_zomega *prob);
+void zxp_sampler_destroy(zxp_sampler *s);
+
+/* The marginal probability that the qubits in mask read bits[q], by the
+ * summing approach of Sec. 2.2: the amplitude is reduced once with the
+ * other output bits as parameters and sum_b |<b|C|in>|^2 is taken exactly
+ * over their 2^(n - |mask|) values (at most 2^30).  bits has n_qubits entries
+ * (those outside mask are ignored).  Same value as zxp_compile with
+ * ZXP_MARGINAL_DOUBLED and zxp_amplitude. */
+int zxp_marginal_by_sum(zxp_ctx *ctx, const zxp_gate *gates, size_t n_gates, int n_qubits,
+                        const uint8_t *in_bits, uint64_t mask, const uint8_t *bits,
+                        zxp_zomega *out);
+
 /* ---- exact scalar helpers (host) ---------------------------------------- */
 
 /* a + b, after bringing both to the larger exponent (x sqrt2 per step). */

@@ -19,6 +19,10 @@ the ZX-Calculus"):
 * ``amps_all``     every amplitude of C|in>.
 * ``marginal``     a marginal probability by the Born rule (Sec. 2.2).
 * ``psum_tree``    App. E Algorithm 1 (pairwise tree sum), pure Python.
+* ``sample``       weak simulation by chained marginals: Sec. 2.2's product
+                   rule, the loop of App. F Algorithm 2 with the conditional
+                   ratio P(B||0) / P(B) (Sec. 2.2) in place of P(B||0).
+* ``marginal_by_sum``  Sec. 2.2's summing approach, sum_b |amp|^2.
 * ``lut``, ``abcd_mul``, ``abcd_add``  single operations, for pinning.
 
 Values come back exact as Python integers: ``(c0, c1, c2, c3, e)`` meaning
@@ -248,3 +252,76 @@ def to_complex(v) -> complex:
     w = cmath.exp(1j * cmath.pi / 4)
     c0, c1, c2, c3, e = v
     return (c0 + c1 * w + c2 * w ** 2 + c3 * w ** 3) / (2 ** 0.5) ** e
+
+
+_INV_SQRT2 = 0.70710678118654752440
+
+
+def real_value(v) -> float:
+    """The real part of an exact value as a double, by one fixed sequence of
+    IEEE operations: (c0 + (c1 - c3) / sqrt2), an extra 1/sqrt2 for odd e,
+    then the power of two 2^(-e/2) (exact)."""
+    import math
+    c0, c1, c2, c3, e = v
+    r = float(c0) + float(c1 - c3) * _INV_SQRT2
+    if e & 1:
+        r *= _INV_SQRT2
+        e -= 1
+    return math.ldexp(r, -(e // 2))
+
+
+def _sub(a, b):
+    """a - b exactly (common sqrt2 exponent), canonical."""
+    def up(v):   # x sqrt2 = (c1 - c3) + (c0 + c2) w + (c1 + c3) w^2 + (c2 - c0) w^3
+        c0, c1, c2, c3, e = v
+        return (c1 - c3, c0 + c2, c1 + c3, c2 - c0, e + 1)
+    while a[4] < b[4]:
+        a = up(a)
+    while b[4] < a[4]:
+        b = up(b)
+    return canon([a[i] - b[i] for i in range(4)], a[4])
+
+
+def sample(gates, n: int, u_rows, in_bits: Sequence[int] | None = None):
+    """Draw one bitstring per row of uniforms: for qubit j = 0 .. n-1, bit j is
+    0 when u[j] < P(B || 0) / P(B) (exact marginals of the state vector, the
+    ratio as doubles by real_value), else 1.  Returns (bitstrings, exact
+    probabilities of the drawn bitstrings)."""
+    out, probs = [], []
+    for u in u_rows:
+        pB = (1, 0, 0, 0, 0)
+        bits = [0] * n
+        for j in range(n):
+            mask = (2 << j) - 1
+            bits[j] = 0
+            p0 = marginal(gates, n, mask, bits, in_bits)
+            if u[j] < real_value(p0) / real_value(pB):
+                pB = p0
+            else:
+                bits[j] = 1
+                pB = _sub(pB, p0)
+        out.append(list(bits))
+        probs.append(pB)
+    return out, probs
+
+
+def marginal_by_sum(gates, n: int, mask: int, bits: Sequence[int],
+                    in_bits: Sequence[int] | None = None):
+    """P(qubits in mask read bits) as sum over the other bits of |amp|^2,
+    exact (Sec. 2.2, summing approach)."""
+    amps = amps_all(gates, n, in_bits)
+    acc = None
+    want = sum((int(bits[q]) & 1) << q for q in range(n) if (mask >> q) & 1)
+    for x, a in enumerate(amps):
+        if (x & mask) != want:
+            continue
+        c0, c1, c2, c3, e = a
+        r = (c0 * c0 + c1 * c1 + c2 * c2 + c3 * c3,
+             c1 * c0 + c2 * c1 + c3 * c2 - c0 * c3,
+             c2 * c0 + c3 * c1 - c0 * c2 - c1 * c3,
+             c3 * c0 - c0 * c1 - c1 * c2 - c2 * c3, 2 * e)
+        if acc is None:
+            acc = r
+        else:
+            acc = _sub(acc, (-r[0], -r[1], -r[2], -r[3], r[4]))
+    return canon(acc[:4], acc[4]) if acc else (0, 0, 0, 0, 0)

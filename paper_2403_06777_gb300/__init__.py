@@ -127,6 +127,11 @@ def lib():
         L.zxp_bind.argtypes = [vp, u64, C.POINTER(vp)]
         L.zxp_pscalar_free.argtypes, L.zxp_pscalar_free.restype = [vp], None
         L.zxp_server_submit_bind.argtypes = [vp, vp, u64, C.POINTER(u64)]
+        L.zxp_sampler_create.argtypes = [vp, C.c_char_p, sz, C.c_int, C.c_char_p, C.POINTER(vp)]
+        L.zxp_sampler_info.argtypes = [vp, C.POINTER(C.c_uint32)]
+        L.zxp_sampler_draw.argtypes = [vp, sz, C.POINTER(C.c_double), C.POINTER(C.c_uint8), zp]
+        L.zxp_sampler_destroy.argtypes, L.zxp_sampler_destroy.restype = [vp], None
+        L.zxp_marginal_by_sum.argtypes = [vp, C.c_char_p, sz, C.c_int, C.c_char_p, u64, C.c_char_p, zp]
         L.zxp_server_create.argtypes = [vp, C.POINTER(zxp_server_opts), C.POINTER(vp)]
         L.zxp_server_submit.argtypes = [vp, C.POINTER(zxp_request), C.POINTER(u64)]
         L.zxp_server_submit_scalar.argtypes = [vp, vp, C.POINTER(u64)]
@@ -532,6 +537,77 @@ def zxp_server_destroy(srv: Server):
     srv.close()
 
 
+class Sampler:
+    """A zxp_sampler (zxp_sampler_destroy on close)."""
+
+    def __init__(self, handle: int, n: int, ctx: Ctx):
+        self.handle = C.c_void_p(handle)
+        self.n = n
+        self.ctx = ctx
+
+    def close(self):
+        if self.handle:
+            lib().zxp_sampler_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def zxp_sampler_create(ctx: Ctx, gates, n_qubits: int, in_bits: Sequence[int] | None = None) -> Sampler:
+    gb = _gate_bytes(gates)
+    ib = bytes(int(b) & 1 for b in in_bits) if in_bits is not None else None
+    h = C.c_void_p()
+    _check(lib().zxp_sampler_create(ctx.handle, gb, len(gb) // 8, n_qubits, ib, C.byref(h)),
+           "zxp_sampler_create")
+    return Sampler(h.value, n_qubits, ctx)
+
+
+def zxp_sampler_info(s: Sampler):
+    arr = (C.c_uint32 * s.n)()
+    _check(lib().zxp_sampler_info(s.handle, arr), "zxp_sampler_info")
+    return list(arr)
+
+
+def zxp_sampler_draw(s: Sampler, u):
+    """u: n_samples rows of n uniforms in [0, 1).  Returns (bitstrings as
+    lists of n bits, exact probabilities (c0, c1, c2, c3, e))."""
+    rows = [list(r) for r in u]
+    ns = len(rows)
+    if any(len(r) != s.n for r in rows):
+        raise ZxpError(ZXP_EINVAL, "zxp_sampler_draw: each row needs n uniforms")
+    flat = (C.c_double * max(1, ns * s.n))(*[float(x) for r in rows for x in r])
+    out = (C.c_uint8 * max(1, ns * s.n))()
+    prob = (zxp_zomega * max(1, ns))()
+    _check(lib().zxp_sampler_draw(s.handle, ns, flat, out, prob), "zxp_sampler_draw")
+    bits = [list(out[i * s.n:(i + 1) * s.n]) for i in range(ns)]
+    return bits, [prob[i].tup() for i in range(ns)]
+
+
+def zxp_sampler_destroy(s: Sampler):
+    s.close()
+
+
+def zxp_marginal_by_sum(ctx: Ctx, gates, n_qubits: int, mask: int, bits: Sequence[int],
+                        in_bits: Sequence[int] | None = None):
+    gb = _gate_bytes(gates)
+    ib = bytes(int(b) & 1 for b in in_bits) if in_bits is not None else None
+    out = zxp_zomega()
+    _check(lib().zxp_marginal_by_sum(ctx.handle, gb, len(gb) // 8, n_qubits, ib, mask,
+                                     bytes(int(b) & 1 for b in bits), C.byref(out)),
+           "zxp_marginal_by_sum")
+    return out.tup()
+
+
 def zxp_zomega_add(a, b):
     out = zxp_zomega()
     za, zb = _z(a), _z(b)
@@ -559,6 +635,7 @@ EXPORTED = ["zxp_ctx_create", "zxp_ctx_destroy", "zxp_compile", "zxp_scalar_from
             "zxp_batch_info", "zxp_batch_destroy", "zxp_server_create", "zxp_server_submit",
             "zxp_server_submit_scalar", "zxp_server_poll", "zxp_server_stats", "zxp_server_destroy",
             "zxp_compile_param", "zxp_pscalar_info", "zxp_pscalar_params", "zxp_bind",
-            "zxp_pscalar_free", "zxp_server_submit_bind",
+            "zxp_pscalar_free", "zxp_server_submit_bind", "zxp_sampler_create", "zxp_sampler_info",
+            "zxp_sampler_draw", "zxp_sampler_destroy", "zxp_marginal_by_sum",
             "zxp_amplitude", "zxp_submit", "zxp_poll", "zxp_zomega_add", "zxp_zomega_canon",
             "zxp_zomega_to_complex", "zxp_strerror", "zxp_version"]

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libzxp.so")
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-HOST_SRC = ["ps.cpp", "compile.cpp", "param.cpp", "plan.cpp"]
+HOST_SRC = ["ps.cpp", "compile.cpp", "param.cpp", "plan.cpp", "sample.cpp"]
 CUDA_SRC = ["kernel.cu", "kernel_count.cu", "batch.cu", "batch_count.cu", "api.cu", "serve.cu"]
 
 
@@ -52,7 +52,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     jobs = []
     for f in HOST_SRC:
         obj = os.path.join(BUILD, f + ".o")
-        jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", "-Wno-unused-function", *inc,
+        jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-ffp-contract=off", "-Wall", "-Wno-unused-function", *inc,
                      "-c", os.path.join(CSRC, f), "-o", obj])
     for f in CUDA_SRC:
         obj = os.path.join(BUILD, f + ".o")

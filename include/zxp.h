@@ -89,7 +89,10 @@ typedef struct {
     uint32_t node_words; /* 32-bit words of odd-node form bits per term */
     uint32_t other_words;/* 32-bit words of linear / zero / pair form bits */
     uint32_t device_bytes;       /* bytes of the tables a device evaluation keeps resident */
-    uint32_t reserved[4];
+    uint32_t kernel_variant;     /* 0 table, 1 table + folded bits, 2 general, 3-8 counting
+                                    (lane-private 32 / 16 bit, warp-shared; odd: no folded
+                                    bits), 9 block lookup */
+    uint32_t reserved[3];
 } zxp_scalar_info_t;
 
 /* ---- context --------------------------------------------------------- */

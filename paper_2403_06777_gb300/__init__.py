@@ -42,7 +42,8 @@ class zxp_scalar_info_t(C.Structure):
                 ("n_node", C.c_uint32), ("n_pair", C.c_uint32), ("e0", C.c_int32),
                 ("acc_bits", C.c_uint32), ("form_bits", C.c_uint32), ("t_count", C.c_uint32),
                 ("node_words", C.c_uint32), ("other_words", C.c_uint32),
-                ("device_bytes", C.c_uint32), ("reserved", C.c_uint32 * 4)]
+                ("device_bytes", C.c_uint32), ("kernel_variant", C.c_uint32),
+                ("reserved", C.c_uint32 * 3)]
 
 
 class zxp_batch_info_t(C.Structure):

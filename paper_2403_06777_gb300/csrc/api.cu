@@ -254,6 +254,7 @@ int zxp_scalar_info(const zxp_scalar* s, zxp_scalar_info_t* info) {
     info->node_words = (uint32_t)s->plan.nwn;
     info->other_words = (uint32_t)(s->plan.nwl < 1 ? 1 : s->plan.nwl);
     info->device_bytes = (uint32_t)table_layout(s->plan).total;
+    info->kernel_variant = (uint32_t)sum_variant(s->plan);
     return ZXP_OK;
 }
 
@@ -664,9 +665,9 @@ extern "C" int zxp_eval_noalloc(const zxp_scalar* s, uint64_t first, uint64_t co
     const size_t fb = pl.rows.size() * sizeof(uint32_t), ab = pl.adj.size() * sizeof(uint64_t);
     const size_t o_pv = kNoAllocTablesOff + tb, o_f = (o_pv + pb + 15) & ~(size_t)15;
     const size_t o_adj = (o_f + fb + 7) & ~(size_t)7;
-    const size_t sb = pl.seek.size() * sizeof(uint32_t);
+    const size_t sb = pl.seek.size() * sizeof(uint32_t), lb = pl.lut.size() * sizeof(uint64_t);
     const size_t o_seek = (o_adj + ab + 15) & ~(size_t)15;
-    if (o_seek + sb > kNoAllocBytes) return ZXP_ETOOBIG;   // tables exceed the static scratch
+    if (o_seek + sb + lb > kNoAllocBytes) return ZXP_ETOOBIG;   // tables exceed the static scratch
 
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return ZXP_ECUDA;
@@ -716,6 +717,8 @@ extern "C" int zxp_eval_noalloc(const zxp_scalar* s, uint64_t first, uint64_t co
     if (ab && cudaMemcpyAsync(base + o_adj, pl.adj.data(), ab, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return ZXP_ECUDA;
     if (sb && cudaMemcpyAsync(base + o_seek, pl.seek.data(), sb, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+        return ZXP_ECUDA;
+    if (lb && cudaMemcpyAsync(base + o_seek + sb, pl.lut.data(), lb, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return ZXP_ECUDA;
     if (cudaMemsetAsync(base, 0, sizeof(unsigned int), stream) != cudaSuccess) return ZXP_ECUDA;
     return cuda_status(sum_launch(pl, reinterpret_cast<const zw64*>(base + kNoAllocTablesOff),

@@ -33,6 +33,7 @@ using BatchFn = void (*)(const unsigned char*, const BatchChunk*, uint32_t, unsi
 extern const BatchFn kTable[3][kMaxWordsNode + 1][kMaxWordsOther];   // batch.cu
 extern const BatchFn kHist[4][2][kMaxWordsOther];                    // batch_count.cu
 extern const BatchFn kShared[2][kMaxWordsNode + 1][kMaxWordsOther];  // batch_count.cu
+extern const BatchFn kLut[2][kMaxWordsOther];                              // block lookup
 
 namespace {
 
@@ -68,7 +69,7 @@ batch_kernel(const unsigned char* __restrict__ scalars, const BatchChunk* __rest
             uint32_t* dst = reinterpret_cast<uint32_t*>(&sp);
             for (uint32_t i = threadIdx.x; i < sizeof(KernelParams) / 4; i += blockDim.x) dst[i] = src[i];
             __syncthreads();
-            load_tables<NWN, NWL, GENERAL>(sp, sm, bs.table, bs.pv, bs.rows, bs.adj, bs.seek);
+            load_tables<NWN, NWL, GENERAL, HIST>(sp, sm, bs.table, bs.pv, bs.rows, bs.adj, bs.seek);
             if (threadIdx.x == 0) s_loaded = ch.scalar;
             __syncthreads();
         }

@@ -25,6 +25,7 @@ using namespace sumk;
 KernelFn pick(const Plan& pl) {
     const int nwl = pl.nwl < 1 ? 1 : pl.nwl;
     const int v = variant(pl);
+    if (v == 9) return kLut[pl.nwn][nwl - 1];
     if (v >= 7) return kShared[v - 7][pl.nwn][nwl - 1];
     if (v >= 3) return kHist[v - 3][pl.nwn][nwl - 1];
     return kTable[v][pl.nwn][nwl - 1];
@@ -55,6 +56,8 @@ size_t sum_smem_bytes(const Plan& pl) {
 uint64_t sum_max_span(const Plan& pl) { return max_span(hist_mode(pl)); }
 
 int sum_threads() { return kThreads; }
+
+int sum_variant(const Plan& pl) { return variant(pl); }
 
 cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, const uint32_t* dF,
                        const uint64_t* dADJ, const uint32_t* dS, uint64_t first, uint64_t count,

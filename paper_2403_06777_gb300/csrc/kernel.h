@@ -17,6 +17,8 @@ cudaError_t ensure_dynamic_smem(const void* fn, size_t bytes);
 // phase-pair values and the reduction scratch.
 size_t sum_smem_bytes(const Plan& pl);
 int sum_threads();
+// Kernel variant chosen for a scalar (see zxp_scalar_info_t).
+int sum_variant(const Plan& pl);
 // Longest slice one thread may take (a multiple of 8).
 uint64_t sum_max_span(const Plan& pl);
 cudaError_t sum_occupancy(const Plan& pl, int* blocks_per_sm);

@@ -70,12 +70,15 @@ __device__ __forceinline__ zw64 block_reduce(zw64 v, zw64* sred) {
 
 // 0: table path, 1: lane-private 32-bit counters, 2: lane-private 16-bit
 // counters, 3: warp-shared 32-bit counters (by the number of distinct term
-// values the table holds)
+// values the table holds), 4: block lookup with warp-shared counters over
+// kLutRows rows of the table (when the plan built the lookup)
 constexpr uint32_t kHistMaxEntries32 = 48;
 constexpr uint32_t kHistMaxEntries16 = 128;
 constexpr uint32_t kHistMaxEntriesShared = 2048;
+constexpr uint32_t kLutEntries = (1u << kLutMaxBits) + 8u;
 inline int hist_mode(const Plan& pl) {
     if (pl.general) return 0;
+    if (pl.lut_ok) return 4;
     if (pl.kp.tab_size <= kHistMaxEntries32) return 1;
     if (pl.kp.tab_size <= kHistMaxEntries16) return 2;
     if (pl.kp.tab_size <= kHistMaxEntriesShared) return 3;
@@ -84,7 +87,8 @@ inline int hist_mode(const Plan& pl) {
 inline int kernel_words(const Plan& pl) { return pl.nwn + (pl.nwl < 1 ? 1 : pl.nwl); }
 // kernel variant: 0 table, 1 table + extra index bits, 2 general (phase-pair
 // products), 3/4 lane-private 32-bit counters (+ extra bits), 5/6
-// lane-private 16-bit counters (+ extra), 7/8 warp-shared counters (+ extra)
+// lane-private 16-bit counters (+ extra), 7/8 warp-shared counters (+ extra),
+// 9 block lookup
 inline int variant(const Plan& pl) {
     if (pl.general) return 2;
     const int x = pl.kp.xshift ? 1 : 0;
@@ -97,7 +101,9 @@ __host__ __device__ constexpr bool var_xtra(int v) { return v == 1 || (v >= 3 &&
 // 32-bit counter words of one block
 __host__ __device__ constexpr uint32_t counter_words(int h, uint32_t ntab, uint32_t threads) {
     return h == 1 ? ntab * threads
-                  : (h == 2 ? (ntab + 1) / 2 * threads : (h == 3 ? ntab * (threads / 32) : 0u));
+                  : (h == 2 ? (ntab + 1) / 2 * threads
+                            : (h == 3 ? ntab * (threads / 32)
+                                      : (h == 4 ? (uint32_t)(kLutRows / 8) * ntab * (threads / 32) : 0u)));
 }
 inline uint64_t max_span(int h) { return h == 2 ? kSpan16 : kSpan32; }
 
@@ -109,6 +115,7 @@ struct Smem {
     zw64* sred;
     uint64_t* sADJ;
     uint32_t* sS;   // seek tables
+    uint64_t* sL;   // block lookup (HIST 4)
     uint32_t* sF;
     uint32_t* sH;
 };
@@ -123,6 +130,7 @@ __host__ __device__ inline size_t smem_bytes(uint32_t ntab_cap, uint32_t npairs_
                                              int h, int threads) {
     return sizeof(zw64) * (ntab_cap + 4u * npairs_cap + kMaxWarps) + sizeof(uint64_t) * kMaxK +
            sizeof(uint32_t) * seek_words(nwn + nwl) + sizeof(uint32_t) * (size_t)kMaxK * row_words(nwn, nwl) +
+           (h == 4 ? sizeof(uint64_t) * kLutEntries : 0) +
            sizeof(uint32_t) * (size_t)counter_words(h, ntab_cap, (uint32_t)threads);
 }
 
@@ -137,7 +145,8 @@ __device__ __forceinline__ Smem carve(unsigned char* raw, uint32_t ntab_cap, uin
     s.sred = s.sPV + 4u * npairs_cap;
     // 16-byte aligned first (vector loads and stores): seek tables, counters
     s.sS = reinterpret_cast<uint32_t*>(s.sred + kMaxWarps);
-    s.sH = s.sS + seek_words(NW);
+    s.sL = reinterpret_cast<uint64_t*>(s.sS + seek_words(NW));
+    s.sH = reinterpret_cast<uint32_t*>(s.sL + (HIST == 4 ? kLutEntries : 0u));
     s.sADJ = reinterpret_cast<uint64_t*>(s.sH + hist_words);
     s.sF = reinterpret_cast<uint32_t*>(s.sADJ + kMaxK);
     return s;
@@ -145,7 +154,7 @@ __device__ __forceinline__ Smem carve(unsigned char* raw, uint32_t ntab_cap, uin
 
 // Cooperative copy of one scalar's tables into shared memory (the three
 // lowest variables padded with zero rows when k < 3).
-template <int NWN, int NWL, bool GENERAL>
+template <int NWN, int NWL, bool GENERAL, int HIST>
 __device__ __forceinline__ void load_tables(const KernelParams& p, const Smem& sm,
                                             const zw64* __restrict__ gtable,
                                             const zw64* __restrict__ gpv,
@@ -158,6 +167,11 @@ __device__ __forceinline__ void load_tables(const KernelParams& p, const Smem& s
     for (uint32_t i = threadIdx.x; i < ntab; i += blockDim.x) sm.sT[i] = gtable[i];
     const uint32_t ns = ((p.k + 3) / 4) * 16u * seek_stride(NW);
     for (uint32_t i = threadIdx.x; i < ns; i += blockDim.x) sm.sS[i] = gS[i];
+    if (HIST == 4) {   // the block lookup follows the seek tables
+        const uint64_t* gL = reinterpret_cast<const uint64_t*>(gS + ns);
+        const uint32_t nl = (1u << (p.lut_no + p.lut_nn)) + 8u;
+        for (uint32_t i = threadIdx.x; i < nl; i += blockDim.x) sm.sL[i] = gL[i];
+    }
     if (GENERAL)
         for (uint32_t i = threadIdx.x; i < 4u * p.npairs; i += blockDim.x) sm.sPV[i] = gpv[i];
     for (uint32_t i = threadIdx.x; i < p.k; i += blockDim.x) sm.sADJ[i] = gADJ[i];
@@ -174,11 +188,169 @@ __device__ __forceinline__ void load_tables(const KernelParams& p, const Smem& s
 // the end skip the work) so that the counter fold can use full-warp
 // reductions.  The counters (HIST) are zero on entry, and on exit when
 // fold_each or clear_on_exit is set.
+// Block-lookup walk (HIST 4, no phase-pair or zero forms).  A term's counter
+// is J * stride + M with J = the phase exponent (rows up to kLutRows: J is not
+// reduced mod 8 inside a block; the fold maps row r to table row r mod 8).
+// An aligned block of 8 Gray steps costs one lookup: the forms holding
+// variables 0, 1, 2 are the lowest node and linear bits, their values at the
+// block's first state index sL, and h = (A x) restricted to variables 0-2
+// indexes the quadratic part; byte s - 1 of the sum is term s's counter
+// offset from the block's base.  Other steps update L, J and h directly.
+template <int NWN, int NWL>
+__device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, uint64_t first,
+                                         uint64_t count, uint64_t span, uint64_t nslices,
+                                         uint64_t s_begin, uint64_t stride, bool fold_each,
+                                         bool clear_on_exit, zw64& acc) {
+    constexpr int NW = NWN + NWL;
+    constexpr uint32_t RW = row_words(NWN, NWL);
+    constexpr uint32_t SW = seek_stride(NW);
+    const zw64* __restrict__ sT = sm.sT;
+    const uint64_t* __restrict__ sADJ = sm.sADJ;
+    const uint32_t* __restrict__ sF = sm.sF;
+    const uint32_t* __restrict__ sS = sm.sS;
+    const uint64_t* __restrict__ sL = sm.sL;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t ts = p.tab_stride;
+    const uint32_t nbins = (uint32_t)kLutRows * ts;
+    uint32_t* const wc = sm.sH + warp * nbins;
+    const uint32_t no = p.lut_no, nn = p.lut_nn;
+    const uint32_t mo = (1u << no) - 1u, mn = (1u << nn) - 1u;
+    const uint64_t* __restrict__ qlut = sL + (1u << (no + nn));
+
+    auto fold = [&](bool clear) {
+        __syncwarp();
+        for (uint32_t i = lane; i < nbins; i += 32) {
+            const uint32_t c = wc[i];
+            if (c) {
+                const uint32_t row = i / ts, m = i - row * ts;
+                acc = zw_madd32(acc, lds_zw(sT + (row & 7u) * ts + m), c);
+                if (clear) wc[i] = 0;
+            }
+        }
+        __syncwarp();
+    };
+
+    const uint64_t end = first + count;
+    for (uint64_t s0 = s_begin; s0 < nslices; s0 += stride) {
+        const uint64_t s = s0 + lane;
+        if (s < nslices) {
+            uint64_t t = first + s * span;
+            const uint64_t tend = (end - t < span) ? end : t + span;
+            const uint64_t x = t ^ (t >> 1);
+            uint32_t L[NW];
+#pragma unroll
+            for (int w = 0; w < NW; w++) L[w] = p.INV[w];
+            uint64_t a = 0;
+            uint32_t q = 0;
+            const uint32_t nnib = (p.k + 3) >> 2;
+            for (uint32_t b = 0; b < nnib; b++) {
+                const uint32_t v = (uint32_t)(x >> (4 * b)) & 15u;
+                const uint32_t* e = sS + (b * 16u + v) * SW;
+                uint32_t ev[SW];
+#pragma unroll
+                for (uint32_t w4 = 0; w4 < SW; w4 += 4) {
+                    const uint4 t4 = *reinterpret_cast<const uint4*>(e + w4);
+                    ev[w4] = t4.x; ev[w4 + 1] = t4.y; ev[w4 + 2] = t4.z; ev[w4 + 3] = t4.w;
+                }
+                q ^= ev[NW + 2] ^ ((uint32_t)__popc(v & (uint32_t)(a >> (4 * b))) & 1u);
+                a ^= ((uint64_t)ev[NW + 1] << 32) | ev[NW];
+#pragma unroll
+                for (int w = 0; w < NW; w++) L[w] ^= ev[w];
+            }
+            uint32_t Jl;
+            {
+                uint32_t P0 = 0, P1 = 0, X2 = 0;
+#pragma unroll
+                for (int w = 0; w < NWN; w++) X2 ^= L[w] & p.CB[w];
+#pragma unroll
+                for (int w = 0; w < NWL; w++) {
+                    const uint32_t v = L[NWN + w];
+                    P0 += __popc(v & p.C0[w]);
+                    P1 += __popc(v & p.C1[w]);
+                    X2 ^= v & p.C2[w];
+                }
+                Jl = P0 + 2u * P1 + 4u * ((uint32_t)__popc(X2) + q);
+            }
+            uint32_t h = (uint32_t)a & 7u;   // (A x) on variables 0, 1, 2
+
+            auto node_count = [&]() {
+                uint32_t M = 0;
+#pragma unroll
+                for (int w = 0; w < NWN; w++) M += __popc(L[w]);
+                return M;
+            };
+            for (;;) {
+                if ((t & 7u) == 0 && tend - t >= 8) {
+                    uint32_t u = L[NWN] & mo;
+                    if (NWN) u |= (L[0] & mn) << no;
+                    const uint64_t e = sL[u] + qlut[h];
+                    const uint32_t lo = (uint32_t)e, hi = (uint32_t)(e >> 32);
+                    const int base = (int)((Jl & 7u) * ts + node_count()) - (int)nn;
+                    uint32_t* const wb = wc + base;
+                    atomicAdd(wb + nn, 1u);
+                    atomicAdd(wb + (lo & 0xFFu), 1u);
+                    atomicAdd(wb + ((lo >> 8) & 0xFFu), 1u);
+                    atomicAdd(wb + ((lo >> 16) & 0xFFu), 1u);
+                    atomicAdd(wb + (lo >> 24), 1u);
+                    atomicAdd(wb + (hi & 0xFFu), 1u);
+                    atomicAdd(wb + ((hi >> 8) & 0xFFu), 1u);
+                    atomicAdd(wb + ((hi >> 16) & 0xFFu), 1u);
+                    // the block ends with variable 2 flipped (Gray 000 -> 100)
+#pragma unroll
+                    for (int w = 0; w < NW; w++) L[w] ^= p.R[2][w];
+                    Jl += (hi >> 24) & 31u;
+                    h = hi >> 29;
+                    t += 7;
+                } else {
+                    atomicAdd(wc + (Jl & 7u) * ts + node_count(), 1u);
+                }
+                if (++t >= tend) break;
+                // flip variable i = ctz(t): 4 (A x)_i for the quadratic part,
+                // the step row for the linear part, h follows A x
+                const uint32_t tl = (uint32_t)t;
+                const int i = tl ? __ffs(tl) - 1 : 31 + __ffs((uint32_t)(t >> 32));
+                const uint64_t adj = sADJ[i];
+                uint32_t ai;
+                if (i < 3) {
+                    ai = (h >> i) & 1u;
+                } else {
+                    const uint64_t xp = (t - 1) ^ ((t - 1) >> 1);
+                    ai = (uint32_t)(__popcll(adj & xp)) & 1u;
+                }
+                Jl += ai << 2;
+                h ^= (uint32_t)adj & 7u;
+                uint32_t fr[RW];
+#pragma unroll
+                for (uint32_t w4 = 0; w4 < RW; w4 += 4) {
+                    const uint4 t4 = *reinterpret_cast<const uint4*>(sF + i * RW + w4);
+                    fr[w4] = t4.x; fr[w4 + 1] = t4.y; fr[w4 + 2] = t4.z; fr[w4 + 3] = t4.w;
+                }
+                uint32_t d0 = 0, d1 = 0;
+#pragma unroll
+                for (int w = 0; w < NWL; w++) {
+                    d0 += __popc(L[NWN + w] & fr[NW + w]);
+                    d1 += __popc(L[NWN + w] & fr[NW + NWL + w]);
+                }
+                Jl += fr[NW + 2 * NWL] - 2u * d0 - 4u * d1;
+#pragma unroll
+                for (int w = 0; w < NW; w++) L[w] ^= fr[w];
+            }
+        }
+        if (fold_each) fold(true);
+    }
+    if (!fold_each) fold(clear_on_exit);
+}
+
 template <int NWN, int NWL, bool GENERAL, int HIST, bool XTRA>
 __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint64_t first,
                                      uint64_t count, uint64_t span, uint64_t nslices,
                                      uint64_t s_begin, uint64_t stride, bool fold_each,
                                      bool clear_on_exit, zw64& acc) {
+    if constexpr (HIST == 4) {
+        walk_lut<NWN, NWL>(p, sm, first, count, span, nslices, s_begin, stride, fold_each,
+                           clear_on_exit, acc);
+        return;
+    }
     constexpr int NW = NWN + NWL;
     constexpr uint32_t RW = row_words(NWN, NWL);
     const zw64* __restrict__ sT = sm.sT;

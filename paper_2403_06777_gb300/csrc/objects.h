@@ -39,7 +39,8 @@ inline TableLayout table_layout(const Plan& pl) {
     TableLayout L;
     const size_t tb = pl.table.size() * sizeof(zw64), pb = pl.pv.size() * sizeof(zw64);
     const size_t fb = pl.rows.size() * sizeof(uint32_t), ab = pl.adj.size() * sizeof(uint64_t);
-    const size_t sb = pl.seek.size() * sizeof(uint32_t);
+    // seek tables, then the block lookup (if any) right after them
+    const size_t sb = pl.seek.size() * sizeof(uint32_t) + pl.lut.size() * sizeof(uint64_t);
     L.o_pv = tb;
     L.o_f = (L.o_pv + pb + 15) & ~(size_t)15;
     L.o_adj = (L.o_f + fb + 7) & ~(size_t)7;
@@ -55,6 +56,8 @@ inline void pack_tables(const Plan& pl, const TableLayout& L, unsigned char* dst
     if (!pl.rows.empty()) memcpy(dst + L.o_f, pl.rows.data(), pl.rows.size() * sizeof(uint32_t));
     if (!pl.adj.empty()) memcpy(dst + L.o_adj, pl.adj.data(), pl.adj.size() * sizeof(uint64_t));
     if (!pl.seek.empty()) memcpy(dst + L.o_seek, pl.seek.data(), pl.seek.size() * sizeof(uint32_t));
+    if (!pl.lut.empty())
+        memcpy(dst + L.o_seek + pl.seek.size() * sizeof(uint32_t), pl.lut.data(), pl.lut.size() * sizeof(uint64_t));
 }
 
 inline DevTables device_tables(const TableLayout& L, unsigned char* base) {

@@ -3,6 +3,7 @@
 
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <vector>
 
@@ -101,6 +102,27 @@ int build_plan(const PS& ps, Plan* out) {
     // layout
     std::vector<std::pair<uint64_t, uint32_t>> lins;
     for (auto& e : lin) if (e.second) lins.push_back(e);
+    // block lookup candidates: no phase-pair or zero forms (their bits would
+    // vary inside a block); forms holding variable 0, 1 or 2 go first
+    const uint64_t low3 = 7;
+    bool lut_try = k >= 3 && pair_masks.empty() && zero.empty();
+    uint32_t lut_nn = 0, lut_no = 0;
+    if (lut_try) {
+        std::vector<Form> o2;
+        std::vector<uint8_t> b2;
+        for (int pass = 0; pass < 2; pass++)
+            for (size_t j = 0; j < odd.size(); j++)
+                if (((odd[j].mask & low3) != 0) == (pass == 0)) { o2.push_back(odd[j]); b2.push_back(odd_b[j]); }
+        odd.swap(o2);
+        odd_b.swap(b2);
+        std::stable_partition(lins.begin(), lins.end(),
+                              [&](const std::pair<uint64_t, uint32_t>& e) { return (e.first & low3) != 0; });
+        for (auto& f : odd) lut_nn += (f.mask & low3) ? 1 : 0;
+        for (auto& e : lins) lut_no += (e.first & low3) ? 1 : 0;
+        const uint32_t stride = (uint32_t)odd.size() + 1;
+        lut_try = lut_nn + lut_no <= (uint32_t)kLutMaxBits && 11 * stride + 2 * lut_nn <= 255 &&
+                  (uint32_t)kLutRows * stride <= 2048;
+    }
     size_t n_other = lins.size() + zero.size() + pair_masks.size();
     pl.nwn = (int)((odd.size() + 31) / 32);
     pl.nwl = (int)((n_other + 31) / 32);
@@ -189,6 +211,56 @@ int build_plan(const PS& ps, Plan* out) {
         }
         for (uint32_t i = 0; i < 3 && i < k; i++)
             for (uint32_t w = 0; w < rw; w++) kp.R[i][w] = pl.rows[(size_t)i * rw + w];
+    }
+
+    // block lookup (see plan.h)
+    if (lut_try) {
+        const uint32_t nU = lut_nn + lut_no, stride = pl.m_odd + 1;
+        const uint32_t mo = (1u << lut_no) - 1, mn = (1u << lut_nn) - 1;
+        const int nwn_k = pl.nwn;
+        uint32_t fo[3], fn[3];
+        for (int i = 0; i < 3; i++) {
+            fo[i] = pl.frows[(size_t)i * nw + (uint32_t)nwn_k] & mo;
+            fn[i] = nwn_k ? (pl.frows[(size_t)i * nw] & mn) : 0u;
+        }
+        static const int seq[7] = {0, 1, 0, 2, 0, 1, 0};
+        pl.lut.assign(((size_t)1 << nU) + 8, 0ull);
+        for (uint32_t u = 0; u < (1u << nU); u++) {
+            uint32_t Lo = u & mo, Ln = u >> lut_no;
+            int dJ = 0, dM = 0;
+            uint64_t e = 0;
+            for (int s = 1; s <= 7; s++) {
+                const int i = seq[s - 1];
+                for (uint32_t r = 0; r < lut_no; r++)
+                    if ((fo[i] >> r) & 1) dJ += (int)lins[r].second * (((Lo >> r) & 1) ? -1 : 1);
+                for (uint32_t r = 0; r < lut_nn; r++)
+                    if ((fn[i] >> r) & 1) {
+                        dM += ((Ln >> r) & 1) ? -1 : 1;
+                        if (odd_b[r]) dJ += 4;
+                    }
+                Lo ^= fo[i];
+                Ln ^= fn[i];
+                const uint32_t j8 = (uint32_t)(((dJ % 8) + 8) % 8);
+                if (s < 7) e |= (uint64_t)(j8 * stride + (uint32_t)(dM + (int)lut_nn)) << (8 * (s - 1));
+                else e |= ((uint64_t)(j8 * stride + (uint32_t)(dM + (int)lut_nn)) << 48) | ((uint64_t)j8 << 56);
+            }
+            pl.lut[u] = e;
+        }
+        for (uint32_t h = 0; h < 8; h++) {
+            uint32_t a = h, Q = 0;
+            uint64_t e = 0;
+            for (int s = 1; s <= 7; s++) {
+                const int i = seq[s - 1];
+                Q ^= (a >> i) & 1u;
+                a ^= (uint32_t)(adj[i] & low3);
+                if (s < 7) e |= (uint64_t)(4 * Q * stride) << (8 * (s - 1));
+                else e |= ((uint64_t)(4 * Q * stride) << 48) | ((uint64_t)((4 * Q) | (a << 5)) << 56);
+            }
+            pl.lut[((size_t)1 << nU) + h] = e;
+        }
+        kp.lut_no = lut_no;
+        kp.lut_nn = lut_nn;
+        pl.lut_ok = true;
     }
 
     // T[J][M][pair bits][zero] = w^(J + 2M) (1 + sqrt2)^M * prod_j PV_j(bits_j) * [not zero]

@@ -38,6 +38,11 @@ ZXP_HD constexpr uint32_t row_words(int nwn, int nwl) {
     return ((uint32_t)(nwn + 3 * nwl + 1) + 3u) & ~3u;
 }
 constexpr int kMaxRowWords = (int)row_words(kMaxWordsNode, kMaxWordsOther);
+// Block lookup (variant 9): at most this many forms may hold one of the
+// variables 0, 1, 2 (the lookup has 2^bits entries of 8 bytes), and the
+// counters span kLutRows rows of the term table.
+constexpr int kLutMaxBits = 10;
+constexpr int kLutRows = 24;
 
 // Passed by value as the kernel parameter block (kept in the constant bank).
 struct KernelParams {
@@ -56,6 +61,9 @@ struct KernelParams {
     uint32_t INV[kMaxNW];    // initial inversion of each form bit
     uint16_t PA[kMaxPairs], PB[kMaxPairs];            // bit positions of pair forms
     uint32_t R[3][kMaxRowWords];                      // step rows of variables 0, 1, 2
+    // block lookup: forms holding variable 0, 1 or 2 are node bits [0, lut_nn)
+    // and linear bits [0, lut_no) of the first other word
+    uint32_t lut_no, lut_nn;
 };
 
 struct Plan {
@@ -82,6 +90,15 @@ struct Plan {
     bool zero = false;              // the scalar is identically zero
     bool has_zero = false;          // some term can vanish (zero forms present)
     bool general = false;           // more phase-pairs than fold into the table
+    // Block lookup for aligned blocks of 8 Gray steps (variables 0,1,0,2,0,1,0
+    // flip): entry u (the block's first-state bits of the forms holding
+    // variables 0-2) holds, in byte s-1 for s = 1..7, the offset of term s's
+    // counter from the block's base, dJ_s * stride + dM_s + lut_nn, and in
+    // byte 7 dJ_7; the 8 entries after them, indexed by the three bits h of
+    // A x for variables 0-2, add the quadratic part 4 Q_s * stride (byte 7:
+    // 4 Q_7, and h at the end of the block in bits 5-7).
+    bool lut_ok = false;
+    std::vector<uint64_t> lut;
 };
 
 // Returns 0 or ZXP_ETOOBIG (more forms / pairs than the kernel supports).

@@ -32,6 +32,7 @@ using KernelFn = void (*)(const KernelParams, const zw64*, const zw64*, const ui
 extern const KernelFn kTable[3][kMaxWordsNode + 1][kMaxWordsOther];   // kernel.cu
 extern const KernelFn kHist[4][2][kMaxWordsOther];                    // kernel_count.cu (nwn <= 1)
 extern const KernelFn kShared[2][kMaxWordsNode + 1][kMaxWordsOther];  // kernel_count.cu
+extern const KernelFn kLut[2][kMaxWordsOther];                              // block lookup
 
 namespace {
 
@@ -54,7 +55,7 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
         for (uint32_t i = threadIdx.x; i < counter_words(HIST, ntab, blockDim.x) / 4; i += blockDim.x)
             h4[i] = make_uint4(0, 0, 0, 0);
     }
-    load_tables<NWN, NWL, GENERAL>(p, sm, gtable, gpv, gR, gADJ, gS);
+    load_tables<NWN, NWL, GENERAL, HIST>(p, sm, gtable, gpv, gR, gADJ, gS);
     __syncthreads();
 
     zw64 acc = zw_zero();

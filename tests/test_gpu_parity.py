@@ -221,3 +221,34 @@ def test_range_errors(ctx):
         Z.zxp_eval(ctx, s, 30, 3)
     with pytest.raises(Z.ZxpError):
         Z.zxp_eval(ctx, s, 33, 0)
+
+
+def test_block_lookup_variant_matches_oracle(ctx):
+    """Scalars whose low variables touch few forms take the block-lookup
+    kernel (variant 9); full sums and ragged ranges equal the oracle."""
+    rng = random.Random(21)
+    seen = 0
+    blobs = []
+    for seed in range(3):
+        w = zi.workload_medium(seed)
+        blobs.append(Z.zxp_scalar_to_tables(Z.zxp_compile(w.gates, w.n, w.out_bits)))
+    for i in range(12):
+        k = rng.choice([3, 5, 8, 11, 14, 17])
+        blobs.append(zi.synthetic_ps(800 + i, k, n_lin=rng.randint(2, 8), n_quad=rng.randint(0, 6),
+                                     n_node=rng.randint(0, 7), odd_nodes_only=True,
+                                     density=rng.choice([0.2, 0.4])).pack())
+    for blob in blobs:
+        s = Z.zxp_scalar_from_tables(blob)
+        if s.info["kernel_variant"] != 9:
+            continue
+        seen += 1
+        k = s.info["k"]
+        N = 1 << k
+        ranges = [(0, N), (5, N - 11), (N // 3, N // 2), (N - 9, 9)] if N >= 32 else [(0, N), (1, N - 2)]
+        if k > 20:
+            ranges = [(0, N), (1 << 20, (1 << 19) + 13)]
+        for first, count in ranges:
+            g = Z.zxp_eval(ctx, s, first, count)
+            o = oracle.ps_sum(blob, first, count, nthreads=NCPU)
+            assert same_raw(g, o), (k, first, count)
+    assert seen >= 5

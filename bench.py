@@ -112,10 +112,10 @@ def kernel_source_sha() -> str:
     return h.hexdigest()
 
 
-def traffic_from_profile(kernel_src_sha: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "sum_kernel_medium.txt")
+def profile_fields(kernel_src_sha: str, name: str = "sum_kernel_medium.txt"):
+    """Fields of a committed ncu summary, if it was taken on the current
+    kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     fields = {}
@@ -125,9 +125,13 @@ def traffic_from_profile(kernel_src_sha: str):
             fields[k.strip()] = v.strip()
     if fields.get("kernel_source_sha256") != kernel_src_sha:
         return None
+    return fields
+
+
+def profile_number(fields, key):
     try:
-        return float(fields["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
+        return float(fields[key].split()[0]) if fields else None
+    except (KeyError, ValueError, IndexError):
         return None
 
 
@@ -439,6 +443,32 @@ def main():
                               "frac": ach36 / peak, "ops_per_term": ops36},
                  "clocks": clk36.summary()}
 
+    # large compiled circuit: n = 50, 2000 gates at T-count 50 (k = 37), the
+    # full exact sum in one launch
+    large_c = None
+    if rank == 0 and not os.environ.get("ZXP_BENCH_SKIP_LARGE"):
+        wl = zi.workload_large_t50(0)
+        sl = Z.zxp_compile(wl.gates, wl.n, wl.out_bits)
+        il = Z.zxp_scalar_info(sl)
+        nl = 1 << il["k"]
+        Z.zxp_eval_device(ctx, sl, 0, min(nl, 1 << 30), out.data_ptr())
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clkl:
+            a.record(stream)
+            Z.zxp_eval_device(ctx, sl, 0, nl, out.data_ptr())
+            b.record(stream)
+            torch.cuda.synchronize()
+        msl = a.elapsed_time(b)
+        opsl = alg_ops_per_term(il["node_words"], il["other_words"], il["n_pair"])
+        achl = opsl * nl / (msl / 1e3) / 1e9
+        peak = SM_COUNT_GB300 * ISSUE_LANES_PER_SM_CLK * 2070e6 / 1e9
+        large_c = {"workload": f"{wl.name} seed=0: one exact amplitude", "k": il["k"], "terms": nl,
+                   "ms": msl, "terms_per_s": nl / (msl / 1e3), "kernel_variant": il["kernel_variant"],
+                   "roofline": {"bound": "alu", "achieved": achl, "peak": peak, "unit": "Gop/s",
+                                "frac": achl / peak, "ops_per_term": opsl},
+                   "clocks": clkl.summary()}
+
     # batched workload: 512 circuits (n ~ U[10,40], T ~ U[20,60]), one
     # amplitude each: one launch per scalar vs one tuned, graph-captured batch
     batch = None
@@ -508,7 +538,9 @@ def main():
     peak = SM_COUNT_GB300 * ISSUE_LANES_PER_SM_CLK * f_hz / 1e9          # Gop/s
     achieved = ops * terms / per_launch_s / 1e9
     sha = kernel_source_sha()
-    traffic = traffic_from_profile(sha)
+    prof = profile_fields(sha)
+    traffic = profile_number(prof, "dram_bytes_per_launch")
+    ipt = profile_number(prof, "instructions_per_term")
 
     line = {
         "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world,
@@ -523,7 +555,14 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "ops_per_term": ops,
-                     "peak_basis": "issue: 152 SM x 4 warp-instr/clk x 32 lanes x 2070 MHz"},
+                     "peak_basis": "issue: 152 SM x 4 warp-instr/clk x 32 lanes x 2070 MHz",
+                     "issue": {"instructions_per_term": ipt,
+                               "achieved": None if ipt is None else ipt * terms / per_launch_s / 1e9,
+                               "frac": None if ipt is None else ipt * terms / per_launch_s / 1e9 / peak,
+                               "source": "thread instructions per term of the committed ncu capture"},
+                     "note": "ops_per_term counts the per-term method (ctz, flips, popcount planes, "
+                             "table fetch, 64-bit adds); the block lookup shares work across 8 terms, "
+                             "so the kernel executes fewer instructions per term (issue)"},
         "e2e": {"value": terms / e2e_sec, "unit": "terms/s", "amplitudes_per_s": 1 / e2e_sec,
                 "h2d_bytes_per_step": table_bytes, "d2h_bytes_per_step": 40},
         "clocks": clocks,
@@ -532,6 +571,8 @@ def main():
     }
     if large:
         line["large"] = large
+    if large_c:
+        line["large_compiled"] = large_c
     if batch:
         line["batch"] = batch
     if serving:

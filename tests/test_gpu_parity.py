@@ -252,3 +252,18 @@ def test_block_lookup_variant_matches_oracle(ctx):
             o = oracle.ps_sum(blob, first, count, nthreads=NCPU)
             assert same_raw(g, o), (k, first, count)
     assert seen >= 5
+
+
+def test_large_compiled_t50_subranges(ctx):
+    """n = 50, 2000 gates, T-count 50 (k = 37): seeded 2^20-term sub-ranges
+    of the full sum equal the oracle."""
+    w = zi.workload_large_t50(0)
+    s = Z.zxp_compile(w.gates, w.n, w.out_bits)
+    blob = Z.zxp_scalar_to_tables(s)
+    k = s.info["k"]
+    rng = random.Random(37)
+    for _ in range(3):
+        first = rng.randrange((1 << k) - (1 << 20))
+        g = Z.zxp_eval(ctx, s, first, 1 << 20)
+        o = oracle.ps_sum(blob, first, 1 << 20, nthreads=NCPU)
+        assert same_raw(g, o), first

@@ -177,6 +177,13 @@ def workload_large(seed: int = 0) -> Workload:
     return Workload("large n=50 G=2000 t=80", 50, g, random_bits(seed, 50), [0] * 50)
 
 
+def workload_large_t50(seed: int = 0) -> Workload:
+    """The large circuit shape (n=50, 2000 gates) at T-count 50: seed 0
+    reduces to k = 37, a full sum of 1.4e11 terms."""
+    g = circuit_fixed_t(seed, 50, 2000, 50)
+    return Workload("large n=50 G=2000 t=50", 50, g, random_bits(seed, 50), [0] * 50)
+
+
 def workload_batch_item(seed: int) -> Workload:
     rng = SplitMix64(seed ^ 0x5EED0BA7C4)
     n = rng.between(10, 40)

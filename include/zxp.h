@@ -50,7 +50,9 @@ typedef enum {
 } zxp_status;
 
 /* Exact scalar (c0 + c1 w + c2 w^2 + c3 w^3) / sqrt2^e.  `flags` bit 0 is
- * set on a raw (not yet canonical) range partial. */
+ * set on a raw (not yet canonical) range partial; bit 1 marks a device
+ * result that is not valid because a block's bounded wait for its table
+ * copies gave up (the host entry points then return ZXP_ETIMEDOUT). */
 typedef struct zxp_zomega {
     int64_t c[4];
     int32_t e;
@@ -141,7 +143,7 @@ void zxp_scalar_free(zxp_scalar *s);
  * call blocks until the result is on the host.  Partials of disjoint
  * ranges combine with zxp_zomega_add; the total over [0, 2^k) gives the
  * scalar after zxp_zomega_canon.  Errors: ZXP_EINVAL (range beyond 2^k),
- * ZXP_ECUDA. */
+ * ZXP_ECUDA, ZXP_ETIMEDOUT (flags bit 1). */
 int zxp_eval(zxp_ctx *ctx, const zxp_scalar *s, uint64_t first, uint64_t count,
              zxp_zomega *out);
 

@@ -81,7 +81,7 @@ int enqueue(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, D
     int grid;
     launch_shape(ctx, s->plan, count, &span, &grid);
     return cuda_status(sum_launch(s->plan, d.table, d.pv, d.rows, d.adj, d.seek, first, count, span,
-                                  grid, ctx->partials, ctx->counter, dres, ctx->stream));
+                                  grid, ctx->acc, ctx->counter, dres, ctx->stream));
 }
 
 }  // namespace
@@ -134,7 +134,9 @@ int zxp_ctx_create(int device, void* cuda_stream, zxp_ctx** out) {
         if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return ZXP_ECUDA;
         c->own_stream = true;
     }
-    if (cudaMalloc(&c->partials, sizeof(zw64) * (size_t)c->max_grid) != cudaSuccess) return ZXP_ENOMEM;
+    // the sum kernel's accumulator starts at zero
+    if (cudaMalloc(&c->acc, sizeof(zw64)) != cudaSuccess) return ZXP_ENOMEM;
+    if (cudaMemset(c->acc, 0, sizeof(zw64)) != cudaSuccess) return ZXP_ECUDA;
     if (cudaMalloc(&c->counter, sizeof(unsigned int)) != cudaSuccess) return ZXP_ENOMEM;
     if (cudaMemset(c->counter, 0, sizeof(unsigned int)) != cudaSuccess) return ZXP_ECUDA;
     if (cudaMalloc(&c->dres, sizeof(DevResult)) != cudaSuccess) return ZXP_ENOMEM;
@@ -153,7 +155,7 @@ void zxp_ctx_destroy(zxp_ctx* c) {
         cudaFreeHost(t.hres);
         if (t.ev) cudaEventDestroy(t.ev);
     }
-    cudaFree(c->partials);
+    cudaFree(c->acc);
     cudaFree(c->counter);
     cudaFree(c->dres);
     cudaFreeHost(c->hres);
@@ -272,7 +274,7 @@ int zxp_eval(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, 
         return ZXP_ECUDA;
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return ZXP_ECUDA;
     memcpy(out, ctx->hres, sizeof *out);
-    return ZXP_OK;
+    return (out->flags & 2) ? ZXP_ETIMEDOUT : ZXP_OK;
 }
 
 int zxp_eval_device(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count,
@@ -354,6 +356,11 @@ int zxp_poll(zxp_ctx* ctx, uint64_t ticket, int64_t timeout_us, zxp_zomega* out)
             std::this_thread::sleep_for(std::chrono::microseconds(20));
         }
         memcpy(out, t.hres, sizeof *out);
+        if (out->flags & 2) {
+            ctx->free_slots.push_back(t);
+            ctx->tickets.erase(it);
+            return ZXP_ETIMEDOUT;
+        }
     } else {
         from_zw(zw_zero(), t.e0, 1, out);
     }
@@ -593,6 +600,8 @@ extern "C" int zxp_batch_run(zxp_batch* b, zxp_zomega* out) {
     if (cudaGraphLaunch(b->exec, b->ctx->stream) != cudaSuccess) return ZXP_ECUDA;
     if (cudaStreamSynchronize(b->ctx->stream) != cudaSuccess) return ZXP_ECUDA;
     memcpy(out, b->h_results, b->n * sizeof(zxp_zomega));
+    for (size_t i = 0; i < b->n; i++)
+        if (out[i].flags & 2) return ZXP_ETIMEDOUT;
     return ZXP_OK;
 }
 
@@ -628,18 +637,19 @@ extern "C" void zxp_batch_destroy(zxp_batch* b) {
 // cudaMalloc breaks the accounting or fails), and latency-critical loops,
 // where cudaMalloc / cudaFree synchronise the device.  zxp_eval_noalloc
 // serves them: it stages the scalar's tables and keeps the kernel's scratch
-// (per-block partial sums and the completion counter) in one file-scope
+// (the 64-bit accumulator and the completion counter) in one file-scope
 // device array of fixed size, and writes the result to a buffer the caller
 // owns.  It calls no allocating routine, host or device.
 // ---------------------------------------------------------------------------
 
 namespace {
 
-// Layout of the static scratch: [counter, 256 B] [partials] [tables].
+// Layout of the static scratch: [counter at 0, accumulator at 64; 256 B]
+// [tables].  Launches use at most kNoAllocMaxBlocks blocks.
 constexpr size_t kNoAllocBytes = 256 * 1024;
 constexpr int kNoAllocMaxBlocks = 2048;
-constexpr size_t kNoAllocPartialsOff = 256;
-constexpr size_t kNoAllocTablesOff = kNoAllocPartialsOff + sizeof(zw64) * kNoAllocMaxBlocks;
+constexpr size_t kNoAllocAccOff = 64;
+constexpr size_t kNoAllocTablesOff = 256;
 constexpr int kNoAllocMaxDevices = 64;
 
 struct NoAllocDevice {
@@ -664,10 +674,10 @@ extern "C" int zxp_eval_noalloc(const zxp_scalar* s, uint64_t first, uint64_t co
     const size_t tb = pl.table.size() * sizeof(zw64), pb = pl.pv.size() * sizeof(zw64);
     const size_t fb = pl.rows.size() * sizeof(uint32_t), ab = pl.adj.size() * sizeof(uint64_t);
     const size_t o_pv = kNoAllocTablesOff + tb, o_f = (o_pv + pb + 15) & ~(size_t)15;
-    const size_t o_adj = (o_f + fb + 7) & ~(size_t)7;
+    const size_t o_adj = (o_f + fb + 15) & ~(size_t)15;
     const size_t sb = pl.seek.size() * sizeof(uint32_t), lb = pl.lut.size() * sizeof(uint64_t);
     const size_t o_seek = (o_adj + ab + 15) & ~(size_t)15;
-    if (o_seek + sb + lb > kNoAllocBytes) return ZXP_ETOOBIG;   // tables exceed the static scratch
+    if (o_seek + sb + lb + 16 > kNoAllocBytes) return ZXP_ETOOBIG;   // tables exceed the static scratch
 
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return ZXP_ECUDA;
@@ -690,7 +700,7 @@ extern "C" int zxp_eval_noalloc(const zxp_scalar* s, uint64_t first, uint64_t co
     cudaStream_t stream = (cudaStream_t)cuda_stream;
 
     // launch shape: one slice per thread of a resident grid, at most
-    // kNoAllocMaxBlocks blocks (the partials the array holds)
+    // kNoAllocMaxBlocks blocks
     int bps = 1;
     if (sum_occupancy(pl, &bps) != cudaSuccess || bps < 1) bps = 1;
     int max_grid = d.sm_count * bps;
@@ -706,7 +716,8 @@ extern "C" int zxp_eval_noalloc(const zxp_scalar* s, uint64_t first, uint64_t co
     if (g < 1) g = 1;
 
     // stage the tables (each call: the array keeps the last call's contents)
-    // and clear the completion counter, which must start at zero
+    // and clear the completion counter and the accumulator, which must start
+    // at zero
     unsigned char* base = d.base;
     if (tb && cudaMemcpyAsync(base + kNoAllocTablesOff, pl.table.data(), tb, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return ZXP_ECUDA;
@@ -720,13 +731,13 @@ extern "C" int zxp_eval_noalloc(const zxp_scalar* s, uint64_t first, uint64_t co
         return ZXP_ECUDA;
     if (lb && cudaMemcpyAsync(base + o_seek + sb, pl.lut.data(), lb, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return ZXP_ECUDA;
-    if (cudaMemsetAsync(base, 0, sizeof(unsigned int), stream) != cudaSuccess) return ZXP_ECUDA;
+    if (cudaMemsetAsync(base, 0, kNoAllocAccOff + sizeof(zw64), stream) != cudaSuccess) return ZXP_ECUDA;
     return cuda_status(sum_launch(pl, reinterpret_cast<const zw64*>(base + kNoAllocTablesOff),
                                   reinterpret_cast<const zw64*>(base + o_pv),
                                   reinterpret_cast<const uint32_t*>(base + o_f),
                                   reinterpret_cast<const uint64_t*>(base + o_adj),
                                   reinterpret_cast<const uint32_t*>(base + o_seek), first, count, sp,
-                                  (int)g, reinterpret_cast<zw64*>(base + kNoAllocPartialsOff),
+                                  (int)g, reinterpret_cast<zw64*>(base + kNoAllocAccOff),
                                   reinterpret_cast<unsigned int*>(base),
                                   reinterpret_cast<DevResult*>(dev_out), stream));
 }

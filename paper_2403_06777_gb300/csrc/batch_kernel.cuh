@@ -48,11 +48,17 @@ batch_kernel(const unsigned char* __restrict__ scalars, const BatchChunk* __rest
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ KernelParams sp;
     __shared__ uint32_t s_chunk, s_loaded;
+    __shared__ __align__(8) uint64_t s_bar;
     const Smem sm = carve<NW, HIST>(smem_raw, ntab_cap, npairs_cap);
     if (HIST)
         for (uint32_t i = threadIdx.x; i < counter_words(HIST, ntab_cap, blockDim.x); i += blockDim.x)
             sm.sH[i] = 0;
-    if (threadIdx.x == 0) s_loaded = 0xFFFFFFFFu;
+    if (threadIdx.x == 0) {
+        s_loaded = 0xFFFFFFFFu;
+        mbar_init(&s_bar);
+    }
+    uint32_t phase = 0;   // bulk loads so far (the barrier's phase parity)
+    bool ok = true;       // the current scalar's tables are loaded
     const uint64_t per = (uint64_t)blockDim.x * slices_per_thread;
     const uint64_t cap = HIST == 2 ? kSpan16 : kSpan32;
 
@@ -69,9 +75,11 @@ batch_kernel(const unsigned char* __restrict__ scalars, const BatchChunk* __rest
             uint32_t* dst = reinterpret_cast<uint32_t*>(&sp);
             for (uint32_t i = threadIdx.x; i < sizeof(KernelParams) / 4; i += blockDim.x) dst[i] = src[i];
             __syncthreads();
-            load_tables<NWN, NWL, GENERAL, HIST>(sp, sm, bs.table, bs.pv, bs.rows, bs.adj, bs.seek);
+            const bool loaded =
+                load_tables<NWN, NWL, GENERAL, HIST>(sp, sm, bs.table, bs.pv, bs.rows, bs.adj, bs.seek,
+                                                     &s_bar, phase);
             if (threadIdx.x == 0) s_loaded = ch.scalar;
-            __syncthreads();
+            ok = __syncthreads_and(loaded) != 0;
         }
         // slices: a multiple of 8 terms (chunk starts are multiples of 8)
         uint64_t span = (ch.count + per - 1) / per;
@@ -80,9 +88,10 @@ batch_kernel(const unsigned char* __restrict__ scalars, const BatchChunk* __rest
         if (span > cap) span = cap;
         const uint64_t nslices = (ch.count + span - 1) / span;
         zw64 acc = zw_zero();
-        walk<NWN, NWL, GENERAL, HIST, var_xtra(VAR)>(sp, sm, ch.first, ch.count, span, nslices,
-                                                     threadIdx.x & ~31u, blockDim.x,
-                                                     HIST == 2 || nslices > blockDim.x, true, acc);
+        if (ok)
+            walk<NWN, NWL, GENERAL, HIST, var_xtra(VAR)>(sp, sm, ch.first, ch.count, span, nslices,
+                                                         threadIdx.x & ~31u, blockDim.x,
+                                                         HIST == 2 || nslices > blockDim.x, true, acc);
         acc = block_reduce(acc, sm.sred);
         if (threadIdx.x == 0) {
             const zw64 r = zw_mul(bs.K, acc);
@@ -90,7 +99,8 @@ batch_kernel(const unsigned char* __restrict__ scalars, const BatchChunk* __rest
             for (int i = 0; i < 4; i++)
                 atomicAdd(reinterpret_cast<unsigned long long*>(&out->c[i]), (unsigned long long)r.c[i]);
             out->e = bs.e0;
-            out->flags = 1;
+            // flag 2: this scalar's tables could not be loaded (not the sum)
+            atomicOr(reinterpret_cast<int*>(&out->flags), ok ? 1 : 3);
         }
         __syncthreads();   // s_chunk and the reduction scratch are reused
     }

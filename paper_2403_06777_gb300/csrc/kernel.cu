@@ -62,7 +62,7 @@ int sum_variant(const Plan& pl) { return variant(pl); }
 cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, const uint32_t* dF,
                        const uint64_t* dADJ, const uint32_t* dS, uint64_t first, uint64_t count,
                        uint64_t span,
-                       int grid, zw64* partials,
+                       int grid, zw64* acc,
                        unsigned int* counter, DevResult* result, cudaStream_t stream) {
     KernelFn fn = pick(pl);
     const size_t smem = sum_smem_bytes(pl);
@@ -70,7 +70,7 @@ cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, cons
     if (e != cudaSuccess) return e;
     const uint64_t nslices = (count + span - 1) / span;
     fn<<<grid, kThreads, smem, stream>>>(pl.kp, dtable, dpv, dF, dADJ, dS, first, count, span, nslices,
-                                         partials, counter, pl.K, pl.e0, result);
+                                         acc, counter, pl.K, pl.e0, result);
     return cudaGetLastError();
 }
 

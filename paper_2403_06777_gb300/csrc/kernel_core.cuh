@@ -152,34 +152,81 @@ __device__ __forceinline__ Smem carve(unsigned char* raw, uint32_t ntab_cap, uin
     return s;
 }
 
-// Cooperative copy of one scalar's tables into shared memory (the three
-// lowest variables padded with zero rows when k < 3).
+// ---- bulk copies into shared memory (TMA, cp.async.bulk) -------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// global -> shared, `bytes` a multiple of 16, both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Each try_wait suspends the thread for a bounded time; this many of them
+// (several seconds in all) end a wait that would otherwise never end.
+constexpr uint32_t kWaitTries = 1u << 22;
+
+__device__ __forceinline__ uint32_t round16(uint32_t b) { return (b + 15u) & ~15u; }
+
+// Copy one scalar's tables into shared memory with bulk copies issued by
+// thread 0 on the mbarrier `bar` (initialised, count 1), then wait for the
+// barrier's phase `phase` (bounded; phase counts the loads so far and is
+// advanced here).  Every thread calls it; the caller
+// synchronises the block before and after.  Returns false if the wait gave
+// up (the tables are then not valid).  Variables 0..2 beyond k get zero
+// adjacency rows.
 template <int NWN, int NWL, bool GENERAL, int HIST>
-__device__ __forceinline__ void load_tables(const KernelParams& p, const Smem& sm,
+__device__ __forceinline__ bool load_tables(const KernelParams& p, const Smem& sm,
                                             const zw64* __restrict__ gtable,
                                             const zw64* __restrict__ gpv,
                                             const uint32_t* __restrict__ gR,
                                             const uint64_t* __restrict__ gADJ,
-                                            const uint32_t* __restrict__ gS) {
+                                            const uint32_t* __restrict__ gS, uint64_t* bar,
+                                            uint32_t& phase) {
     constexpr int NW = NWN + NWL;
     constexpr uint32_t RW = row_words(NWN, NWL);
-    const uint32_t ntab = p.tab_size;
-    for (uint32_t i = threadIdx.x; i < ntab; i += blockDim.x) sm.sT[i] = gtable[i];
     const uint32_t ns = ((p.k + 3) / 4) * 16u * seek_stride(NW);
-    for (uint32_t i = threadIdx.x; i < ns; i += blockDim.x) sm.sS[i] = gS[i];
-    if (HIST == 4) {   // the block lookup follows the seek tables
-        const uint64_t* gL = reinterpret_cast<const uint64_t*>(gS + ns);
-        const uint32_t nl = (1u << (p.lut_no + p.lut_nn)) + 8u;
-        for (uint32_t i = threadIdx.x; i < nl; i += blockDim.x) sm.sL[i] = gL[i];
+    const uint32_t bt = p.tab_size * 32u, bs = ns * 4u, br = p.k * RW * 4u, ba = round16(p.k * 8u);
+    const uint32_t bpv = GENERAL ? 4u * p.npairs * 32u : 0u;
+    const uint32_t bl = HIST == 4 ? round16(((1u << (p.lut_no + p.lut_nn)) + 8u) * 8u) : 0u;
+    if (threadIdx.x == 0) {
+        // order the shared-memory reads of a previous scalar before the
+        // asynchronous writes
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, bt + bs + br + ba + bpv + bl);
+        if (bt) bulk_copy(sm.sT, gtable, bt, bar);
+        if (bs) bulk_copy(sm.sS, gS, bs, bar);
+        if (br) bulk_copy(sm.sF, gR, br, bar);
+        if (ba) bulk_copy(sm.sADJ, gADJ, ba, bar);
+        if (bpv) bulk_copy(sm.sPV, gpv, bpv, bar);
+        if (bl) bulk_copy(sm.sL, gS + ns, bl, bar);   // the block lookup follows the seek tables
     }
-    if (GENERAL)
-        for (uint32_t i = threadIdx.x; i < 4u * p.npairs; i += blockDim.x) sm.sPV[i] = gpv[i];
-    for (uint32_t i = threadIdx.x; i < p.k; i += blockDim.x) sm.sADJ[i] = gADJ[i];
-    // step rows (see plan.h), 16-byte vectors
-    const uint4* g4 = reinterpret_cast<const uint4*>(gR);
-    uint4* s4 = reinterpret_cast<uint4*>(sm.sF);
-    for (uint32_t i = threadIdx.x; i < p.k * RW / 4; i += blockDim.x) s4[i] = g4[i];
-    for (uint32_t i = p.k + threadIdx.x; i < 3; i += blockDim.x) sm.sADJ[i] = 0;
+    bool ok = false;
+    for (uint32_t i = 0; i < kWaitTries; i++)
+        if (mbar_try_wait(bar, phase & 1u)) { ok = true; break; }
+    phase++;
+    if (threadIdx.x < 3 && threadIdx.x >= p.k) sm.sADJ[threadIdx.x] = 0;
+    return ok;
 }
 
 // Walk the slices s = s_begin + lane, s_begin + stride + lane, ... (< nslices)
@@ -217,15 +264,20 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
     const uint32_t mo = (1u << no) - 1u, mn = (1u << nn) - 1u;
     const uint64_t* __restrict__ qlut = sL + (1u << (no + nn));
 
+    // counter i = row * ts + m holds table entry (row mod 8) * ts + m = i mod 8 ts
+    const uint32_t t8 = 8u * ts;
     auto fold = [&](bool clear) {
         __syncwarp();
+        uint32_t ti = lane;
+        while (ti >= t8) ti -= t8;
         for (uint32_t i = lane; i < nbins; i += 32) {
             const uint32_t c = wc[i];
             if (c) {
-                const uint32_t row = i / ts, m = i - row * ts;
-                acc = zw_madd32(acc, lds_zw(sT + (row & 7u) * ts + m), c);
+                acc = zw_madd32(acc, lds_zw(sT + ti), c);
                 if (clear) wc[i] = 0;
             }
+            ti += 32;
+            while (ti >= t8) ti -= t8;
         }
         __syncwarp();
     };

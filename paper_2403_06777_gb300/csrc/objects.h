@@ -43,7 +43,7 @@ inline TableLayout table_layout(const Plan& pl) {
     const size_t sb = pl.seek.size() * sizeof(uint32_t) + pl.lut.size() * sizeof(uint64_t);
     L.o_pv = tb;
     L.o_f = (L.o_pv + pb + 15) & ~(size_t)15;
-    L.o_adj = (L.o_f + fb + 7) & ~(size_t)7;
+    L.o_adj = (L.o_f + fb + 15) & ~(size_t)15;   // every region 16-byte aligned (bulk copies)
     L.o_seek = (L.o_adj + ab + 15) & ~(size_t)15;
     L.total = L.o_seek + sb + 16;
     return L;
@@ -168,7 +168,7 @@ struct zxp_ctx {
     bool own_stream = false;
     int sm_count = 0;
     int max_grid = 0;
-    zxp::zw64* partials = nullptr;
+    zxp::zw64* acc = nullptr;           // the sum kernel's accumulator (zero between launches)
     unsigned int* counter = nullptr;
     zxp::DevResult* dres = nullptr;
     zxp::DevResult* hres = nullptr;

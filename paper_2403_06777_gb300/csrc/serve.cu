@@ -242,7 +242,10 @@ struct Scheduler {
             canon_result(st.h_out[i], &v);
             s->arena.release(r->arena_off);
             s->free_slots.push_back(r->slot);
-            complete(s, r, r->scalar->ps.e0 > 124 ? ZXP_EOVERFLOW : ZXP_OK, &v);
+            if (st.h_out[i].flags & 2)
+                complete(s, r, ZXP_ETIMEDOUT, nullptr);
+            else
+                complete(s, r, r->scalar->ps.e0 > 124 ? ZXP_EOVERFLOW : ZXP_OK, &v);
         }
         {
             std::lock_guard<std::mutex> lk(s->mu);
@@ -414,7 +417,7 @@ struct Scheduler {
             const uint64_t nsl = (count + sp - 1) / sp;
             const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((nsl + sum_threads() - 1) / sum_threads(), max_grid));
             if (sum_launch(pl, d.table, d.pv, d.rows, d.adj, d.seek, planned[0].first, count, sp, grid,
-                           s->ctx->partials, s->ctx->counter, s->d_results + r->slot, stream) != cudaSuccess)
+                           s->ctx->acc, s->ctx->counter, s->d_results + r->slot, stream) != cudaSuccess)
                 return ZXP_ECUDA;
             launches = 1;
         } else {

@@ -42,52 +42,56 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
            const zw64* __restrict__ gpv, const uint32_t* __restrict__ gR,
            const uint64_t* __restrict__ gADJ, const uint32_t* __restrict__ gS, uint64_t first,
            uint64_t count, uint64_t span,
-           uint64_t nslices, zw64* __restrict__ partials, unsigned int* __restrict__ counter,
+           uint64_t nslices, zw64* __restrict__ acc_g, unsigned int* __restrict__ counter,
            const zw64 K, const int32_t e0, DevResult* __restrict__ result) {
     constexpr int NW = NWN + NWL;
     constexpr bool GENERAL = var_general(VAR);
     constexpr int HIST = var_hist(VAR);
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t s_bar;
     const uint32_t ntab = p.tab_size;
     const Smem sm = carve<NW, HIST>(smem_raw, ntab, p.npairs);
+    if (threadIdx.x == 0) mbar_init(&s_bar);
     if (HIST) {
         uint4* h4 = reinterpret_cast<uint4*>(sm.sH);
         for (uint32_t i = threadIdx.x; i < counter_words(HIST, ntab, blockDim.x) / 4; i += blockDim.x)
             h4[i] = make_uint4(0, 0, 0, 0);
     }
-    load_tables<NWN, NWL, GENERAL, HIST>(p, sm, gtable, gpv, gR, gADJ, gS);
     __syncthreads();
+    uint32_t phase = 0;
+    const bool loaded =
+        load_tables<NWN, NWL, GENERAL, HIST>(p, sm, gtable, gpv, gR, gADJ, gS, &s_bar, phase);
+    const bool ok = __syncthreads_and(loaded) != 0;
 
     zw64 acc = zw_zero();
     const uint64_t gstride = (uint64_t)gridDim.x * blockDim.x;
-    walk<NWN, NWL, GENERAL, HIST, var_xtra(VAR)>(p, sm, first, count, span, nslices,
-                                  (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u), gstride,
-                                  HIST == 2 || nslices > gstride, false, acc);
+    if (ok)
+        walk<NWN, NWL, GENERAL, HIST, var_xtra(VAR)>(p, sm, first, count, span, nslices,
+                                      (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u), gstride,
+                                      HIST == 2 || nslices > gstride, false, acc);
 
-    // reduction: warp shuffles, block, then the last block over the partials
-    __shared__ unsigned int s_last;
+    // reduction: warp shuffles, then the block; each block adds K x (its sum)
+    // into the accumulator acc_g with 64-bit atomic adds (exact mod 2^64, any
+    // order), and the last block to finish moves it to the result and clears
+    // it (acc_g and *counter are zero between launches)
+    // (bit 31 of the counter: some block could not load its tables; the
+    // result is then flagged 2 and is not the sum)
     acc = block_reduce(acc, sm.sred);
     if (threadIdx.x == 0) {
-        partials[blockIdx.x] = acc;
+        if (!ok) atomicOr(counter, 0x80000000u);
+        const zw64 r = zw_mul(K, acc);
+        unsigned long long* g = reinterpret_cast<unsigned long long*>(acc_g);
+        for (int c = 0; c < 4; c++) atomicAdd(g + c, (unsigned long long)r.c[c]);
         __threadfence();
         const unsigned int done = atomicAdd(counter, 1u);
-        s_last = (done == gridDim.x - 1) ? 1u : 0u;
-    }
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
-        zw64 v = zw_zero();
-        for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
-            const ulonglong2* q2 = reinterpret_cast<const ulonglong2*>(partials + b);
-            ulonglong2 lo = __ldcg(q2), hi = __ldcg(q2 + 1);
-            v = zw_add(v, zw_make(lo.x, lo.y, hi.x, hi.y));
-        }
-        v = block_reduce(v, sm.sred);
-        if (threadIdx.x == 0) {
-            const zw64 r = zw_mul(K, v);
-            for (int c = 0; c < 4; c++) result->c[c] = (int64_t)r.c[c];
+        if ((done & 0x7FFFFFFFu) == gridDim.x - 1) {
+            __threadfence();
+            for (int c = 0; c < 4; c++) {
+                result->c[c] = (int64_t)__ldcg(g + c);
+                g[c] = 0ull;
+            }
             result->e = e0;
-            result->flags = 1;
+            result->flags = 1 | ((done >> 31) ? 2 : 0);
             *counter = 0u;       // ready for the next launch on this workspace
         }
     }

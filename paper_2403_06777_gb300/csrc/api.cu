@@ -44,26 +44,10 @@ int ensure_device_tables(const zxp_scalar* s, int device, DevTables* out) {
     return ZXP_OK;
 }
 
-// Slice length and grid for `count` terms: one slice per thread of a full
-// resident grid, slices a multiple of 8 terms so that the lanes of a warp
-// run the unrolled 8-step blocks in step (their start indices agree
-// modulo 8).
+// Slice length and grid for `count` terms (slices a multiple of 8 terms so
+// that the lanes of a warp run the unrolled 8-step blocks in step).
 void launch_shape(const zxp_ctx* ctx, const Plan& pl, uint64_t count, uint64_t* span, int* grid) {
-    int bps = 1;
-    if (sum_occupancy(pl, &bps) != cudaSuccess || bps < 1) bps = 1;
-    int max_grid = ctx->sm_count * bps;
-    if (max_grid > ctx->max_grid) max_grid = ctx->max_grid;
-    const uint64_t threads = (uint64_t)max_grid * (uint64_t)sum_threads();
-    uint64_t sp = (count + threads - 1) / threads;
-    sp = (sp + 7) & ~7ull;
-    if (sp < 64) sp = 64;
-    if (sp > sum_max_span(pl)) sp = sum_max_span(pl);   // longer ranges: several slices per thread
-    const uint64_t nslices = (count + sp - 1) / sp;
-    uint64_t g = (nslices + (uint64_t)sum_threads() - 1) / (uint64_t)sum_threads();
-    if (g > (uint64_t)max_grid) g = (uint64_t)max_grid;
-    if (g < 1) g = 1;
-    *span = sp;
-    *grid = (int)g;
+    sum_shape(pl, ctx->sm_count, ctx->max_grid, count, span, grid);
 }
 
 int check_range(const zxp_scalar* s, uint64_t first, uint64_t count) {
@@ -699,21 +683,11 @@ extern "C" int zxp_eval_noalloc(const zxp_scalar* s, uint64_t first, uint64_t co
     }
     cudaStream_t stream = (cudaStream_t)cuda_stream;
 
-    // launch shape: one slice per thread of a resident grid, at most
-    // kNoAllocMaxBlocks blocks
-    int bps = 1;
-    if (sum_occupancy(pl, &bps) != cudaSuccess || bps < 1) bps = 1;
-    int max_grid = d.sm_count * bps;
-    if (max_grid > kNoAllocMaxBlocks) max_grid = kNoAllocMaxBlocks;
-    const uint64_t threads = (uint64_t)max_grid * (uint64_t)sum_threads();
-    uint64_t sp = (count + threads - 1) / threads;
-    sp = (sp + 7) & ~7ull;
-    if (sp < 64) sp = 64;
-    if (sp > sum_max_span(pl)) sp = sum_max_span(pl);
-    const uint64_t nslices = (count + sp - 1) / sp;
-    uint64_t g = (nslices + (uint64_t)sum_threads() - 1) / (uint64_t)sum_threads();
-    if (g > (uint64_t)max_grid) g = (uint64_t)max_grid;
-    if (g < 1) g = 1;
+    // launch shape: at most kNoAllocMaxBlocks blocks
+    uint64_t sp = 64;
+    int grid = 1;
+    sum_shape(pl, d.sm_count, kNoAllocMaxBlocks, count, &sp, &grid);
+    const uint64_t g = (uint64_t)grid;
 
     // stage the tables (each call: the array keeps the last call's contents)
     // and clear the completion counter and the accumulator, which must start

@@ -91,7 +91,7 @@ batch_kernel(const unsigned char* __restrict__ scalars, const BatchChunk* __rest
         if (ok)
             walk<NWN, NWL, GENERAL, HIST, var_xtra(VAR)>(sp, sm, ch.first, ch.count, span, nslices,
                                                          threadIdx.x & ~31u, blockDim.x,
-                                                         HIST == 2 || nslices > blockDim.x, true, acc);
+                                                         HIST == 2 || nslices > blockDim.x, true, true, acc);
         acc = block_reduce(acc, sm.sred);
         if (threadIdx.x == 0) {
             const zw64 r = zw_mul(bs.K, acc);

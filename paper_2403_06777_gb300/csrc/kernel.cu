@@ -6,6 +6,7 @@
 
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 
 #include "sum_kernel.cuh"
@@ -79,7 +80,45 @@ cudaError_t sum_occupancy(const Plan& pl, int* blocks_per_sm) {
     const size_t smem = sum_smem_bytes(pl);
     cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(fn), smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kThreads, smem);
+    // the answer depends on (device, kernel, shared memory) only: cache it
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void*, size_t>, int> cache;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    const auto key = std::make_tuple(dev, reinterpret_cast<const void*>(fn), smem);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) { *blocks_per_sm = it->second; return cudaSuccess; }
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kThreads, smem);
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lk(mu);
+        cache[key] = *blocks_per_sm;
+    }
+    return e;
+}
+
+void sum_shape(const Plan& pl, int sm_count, int max_grid_cap, uint64_t count, uint64_t* span, int* grid) {
+    int bps = 1;
+    if (sum_occupancy(pl, &bps) != cudaSuccess || bps < 1) bps = 1;
+    // Ranges too short to give every thread of a full-occupancy grid 256
+    // terms run with at most 3 blocks per SM: fewer, longer slices amortise
+    // each thread's fixed work (seek, counter fold, reduction).
+    if (bps > 3 && count < (uint64_t)sm_count * (uint64_t)bps * kThreads * 256u) bps = 3;
+    int max_grid = sm_count * bps;
+    if (max_grid > max_grid_cap) max_grid = max_grid_cap;
+    const uint64_t threads = (uint64_t)max_grid * (uint64_t)kThreads;
+    uint64_t sp = (count + threads - 1) / threads;
+    sp = (sp + 7) & ~7ull;
+    if (sp < 64) sp = 64;
+    if (sp > sum_max_span(pl)) sp = sum_max_span(pl);   // longer ranges: several slices per thread
+    const uint64_t nslices = (count + sp - 1) / sp;
+    uint64_t g = (nslices + (uint64_t)kThreads - 1) / (uint64_t)kThreads;
+    if (g > (uint64_t)max_grid) g = (uint64_t)max_grid;
+    if (g < 1) g = 1;
+    *span = sp;
+    *grid = (int)g;
 }
 
 }  // namespace zxp

@@ -22,6 +22,10 @@ int sum_variant(const Plan& pl);
 // Longest slice one thread may take (a multiple of 8).
 uint64_t sum_max_span(const Plan& pl);
 cudaError_t sum_occupancy(const Plan& pl, int* blocks_per_sm);
+// Slice length (a multiple of 8, at least 64 terms) and grid (at most
+// max_grid_cap blocks) for `count` terms: one slice per thread of a
+// resident grid.
+void sum_shape(const Plan& pl, int sm_count, int max_grid_cap, uint64_t count, uint64_t* span, int* grid);
 
 // Device copy of the public result record (same layout as zxp_zomega).
 struct DevResult {

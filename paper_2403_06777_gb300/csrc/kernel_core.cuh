@@ -247,7 +247,7 @@ template <int NWN, int NWL>
 __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, uint64_t first,
                                          uint64_t count, uint64_t span, uint64_t nslices,
                                          uint64_t s_begin, uint64_t stride, bool fold_each,
-                                         bool clear_on_exit, zw64& acc) {
+                                         bool clear_on_exit, bool final_fold, zw64& acc) {
     constexpr int NW = NWN + NWL;
     constexpr uint32_t RW = row_words(NWN, NWL);
     constexpr uint32_t SW = seek_stride(NW);
@@ -390,17 +390,20 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
         }
         if (fold_each) fold(true);
     }
-    if (!fold_each) fold(clear_on_exit);
+    if (!fold_each && final_fold) fold(clear_on_exit);
 }
 
+// final_fold false (counting variants with warp-shared counters, one slice
+// per thread): the counters are left for the caller to fold (see
+// fold_block_counters).
 template <int NWN, int NWL, bool GENERAL, int HIST, bool XTRA>
 __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint64_t first,
                                      uint64_t count, uint64_t span, uint64_t nslices,
                                      uint64_t s_begin, uint64_t stride, bool fold_each,
-                                     bool clear_on_exit, zw64& acc) {
+                                     bool clear_on_exit, bool final_fold, zw64& acc) {
     if constexpr (HIST == 4) {
         walk_lut<NWN, NWL>(p, sm, first, count, span, nslices, s_begin, stride, fold_each,
-                           clear_on_exit, acc);
+                           clear_on_exit, final_fold, acc);
         return;
     }
     constexpr int NW = NWN + NWL;
@@ -613,7 +616,40 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
         // can overflow (16-bit counters: every slice is shorter than 2^16)
         if (HIST && fold_each) fold(true);
     }
-    if (HIST && !fold_each) fold(clear_on_exit);
+    if (HIST && !fold_each && (final_fold || HIST < 3)) fold(clear_on_exit);
+}
+
+// Warp-shared counters (HIST 3, 4) left unfolded by walk: merge the warps'
+// counters bin by bin into warp 0's, then warp 0 folds them and reduces; the
+// block's sum is valid in thread 0.  Every thread calls it after the walk.
+template <int HIST>
+__device__ __forceinline__ zw64 fold_block_counters(const KernelParams& p, const Smem& sm) {
+    static_assert(HIST == 3 || HIST == 4, "warp-shared counters only");
+    const uint32_t nb = HIST == 4 ? (uint32_t)kLutRows * p.tab_stride : p.tab_size;
+    const uint32_t nwarps = blockDim.x >> 5;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) {
+        uint32_t c = 0;
+        for (uint32_t w = 0; w < nwarps; w++) c += sm.sH[w * nb + i];
+        sm.sH[i] = c;
+    }
+    __syncthreads();
+    zw64 acc = zw_zero();
+    if (threadIdx.x < 32) {
+        // bin i of the block lookup's rows holds table entry i mod 8 ts
+        const uint32_t t8 = HIST == 4 ? 8u * p.tab_stride : nb;
+        uint32_t ti = threadIdx.x;
+        while (ti >= t8) ti -= t8;
+        for (uint32_t i = threadIdx.x; i < nb; i += 32) {
+            const uint32_t c = sm.sH[i];
+            if (c) acc = zw_madd32(acc, lds_zw(sm.sT + ti), c);
+            ti += 32;
+            while (ti >= t8) ti -= t8;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc = zw_add(acc, shfl_xor_zw(acc, off));
+    }
+    return acc;
 }
 
 }  // namespace core

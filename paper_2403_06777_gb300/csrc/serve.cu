@@ -408,14 +408,9 @@ struct Scheduler {
             const Plan& pl = r->scalar->plan;
             const DevTables d = device_tables(table_layout(pl), s->d_arena + r->arena_off + kBatchScalarBytes);
             const uint64_t count = planned[0].count;
-            int bps = 1;
-            if (sum_occupancy(pl, &bps) != cudaSuccess || bps < 1) bps = 1;
-            const int max_grid = std::min(s->ctx->sm_count * bps, s->ctx->max_grid);
-            const uint64_t threads = (uint64_t)max_grid * (uint64_t)sum_threads();
-            uint64_t sp = (count + threads - 1) / threads;
-            sp = std::min<uint64_t>(std::max<uint64_t>((sp + 7) & ~7ull, 64), sum_max_span(pl));
-            const uint64_t nsl = (count + sp - 1) / sp;
-            const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((nsl + sum_threads() - 1) / sum_threads(), max_grid));
+            uint64_t sp = 64;
+            int grid = 1;
+            sum_shape(pl, s->ctx->sm_count, s->ctx->max_grid, count, &sp, &grid);
             if (sum_launch(pl, d.table, d.pv, d.rows, d.adj, d.seek, planned[0].first, count, sp, grid,
                            s->ctx->acc, s->ctx->counter, s->d_results + r->slot, stream) != cudaSuccess)
                 return ZXP_ECUDA;

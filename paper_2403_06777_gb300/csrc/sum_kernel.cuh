@@ -65,10 +65,13 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
 
     zw64 acc = zw_zero();
     const uint64_t gstride = (uint64_t)gridDim.x * blockDim.x;
+    const bool fold_each = HIST == 2 || nslices > gstride;
+    // warp-shared counters with one slice per thread: one fold per block
+    const bool block_fold = (HIST == 3 || HIST == 4) && !fold_each;
     if (ok)
         walk<NWN, NWL, GENERAL, HIST, var_xtra(VAR)>(p, sm, first, count, span, nslices,
                                       (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u), gstride,
-                                      HIST == 2 || nslices > gstride, false, acc);
+                                      fold_each, false, !block_fold, acc);
 
     // reduction: warp shuffles, then the block; each block adds K x (its sum)
     // into the accumulator acc_g with 64-bit atomic adds (exact mod 2^64, any
@@ -76,7 +79,12 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
     // it (acc_g and *counter are zero between launches)
     // (bit 31 of the counter: some block could not load its tables; the
     // result is then flagged 2 and is not the sum)
-    acc = block_reduce(acc, sm.sred);
+    if constexpr (HIST == 3 || HIST == 4) {
+        if (block_fold) acc = fold_block_counters<HIST>(p, sm);   // (uniform branch)
+        else acc = block_reduce(acc, sm.sred);
+    } else {
+        acc = block_reduce(acc, sm.sred);
+    }
     if (threadIdx.x == 0) {
         if (!ok) atomicOr(counter, 0x80000000u);
         const zw64 r = zw_mul(K, acc);

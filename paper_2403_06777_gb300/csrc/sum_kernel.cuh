@@ -9,6 +9,7 @@
 // (App. E's pairwise sum, done as a shuffle tree) and multiplies by the
 // scalar's constant K once.
 #pragma once
+#include <cuda/atomic>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -86,14 +87,22 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
         acc = block_reduce(acc, sm.sred);
     }
     if (threadIdx.x == 0) {
-        if (!ok) atomicOr(counter, 0x80000000u);
         const zw64 r = zw_mul(K, acc);
+        if (gridDim.x == 1) {     // one block: its sum is the result
+            for (int c = 0; c < 4; c++) result->c[c] = (int64_t)r.c[c];
+            result->e = e0;
+            result->flags = ok ? 1 : 3;
+            return;
+        }
+        if (!ok) atomicOr(counter, 0x80000000u);
         unsigned long long* g = reinterpret_cast<unsigned long long*>(acc_g);
         for (int c = 0; c < 4; c++) atomicAdd(g + c, (unsigned long long)r.c[c]);
-        __threadfence();
-        const unsigned int done = atomicAdd(counter, 1u);
+        // the acquire-release increment orders this block's adds before it and,
+        // in the last block, every block's adds before the reads below
+        const unsigned int done =
+            cuda::atomic_ref<unsigned int, cuda::thread_scope_device>(*counter).fetch_add(
+                1u, cuda::memory_order_acq_rel);
         if ((done & 0x7FFFFFFFu) == gridDim.x - 1) {
-            __threadfence();
             for (int c = 0; c < 4; c++) {
                 result->c[c] = (int64_t)__ldcg(g + c);
                 g[c] = 0ull;

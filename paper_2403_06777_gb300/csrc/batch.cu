@@ -30,7 +30,7 @@ gather_kernel(DevResult* __restrict__ results, const uint32_t* __restrict__ slot
 // key: variant << 8 | nwn << 4 | nwl
 BatchFn pick(int key) {
     const int nwn = (key >> 4) & 7, nwl = key & 7, v = (key >> 8) & 15;
-    if (v == 9) return kLut[nwn][nwl - 1];
+    if (v >= 9) return kLut[v - 9][nwn][nwl - 1];
     if (v >= 7) return kShared[v - 7][nwn][nwl - 1];
     if (v >= 3) return kHist[v - 3][nwn][nwl - 1];
     return kTable[v][nwn][nwl - 1];

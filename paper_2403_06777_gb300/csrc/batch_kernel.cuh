@@ -33,7 +33,7 @@ using BatchFn = void (*)(const unsigned char*, const BatchChunk*, uint32_t, unsi
 extern const BatchFn kTable[3][kMaxWordsNode + 1][kMaxWordsOther];   // batch.cu
 extern const BatchFn kHist[4][2][kMaxWordsOther];                    // batch_count.cu
 extern const BatchFn kShared[2][kMaxWordsNode + 1][kMaxWordsOther];  // batch_count.cu
-extern const BatchFn kLut[2][kMaxWordsOther];                              // block lookup
+extern const BatchFn kLut[2][2][kMaxWordsOther];                              // block lookup
 
 namespace {
 

@@ -88,12 +88,12 @@ inline int kernel_words(const Plan& pl) { return pl.nwn + (pl.nwl < 1 ? 1 : pl.n
 // kernel variant: 0 table, 1 table + extra index bits, 2 general (phase-pair
 // products), 3/4 lane-private 32-bit counters (+ extra bits), 5/6
 // lane-private 16-bit counters (+ extra), 7/8 warp-shared counters (+ extra),
-// 9 block lookup
+// 9/10 block lookup (+ extra)
 inline int variant(const Plan& pl) {
     if (pl.general) return 2;
     const int x = pl.kp.xshift ? 1 : 0;
     const int h = hist_mode(pl);
-    return h == 0 ? x : 1 + 2 * h + x;
+    return h == 0 ? x : 1 + 2 * h + x;   // block lookup: 9, or 10 with folded bits
 }
 __host__ __device__ constexpr bool var_general(int v) { return v == 2; }
 __host__ __device__ constexpr int var_hist(int v) { return v >= 3 ? (v - 1) / 2 : 0; }
@@ -243,7 +243,7 @@ __device__ __forceinline__ bool load_tables(const KernelParams& p, const Smem& s
 // block's first state index sL, and h = (A x) restricted to variables 0-2
 // indexes the quadratic part; byte s - 1 of the sum is term s's counter
 // offset from the block's base.  Other steps update L, J and h directly.
-template <int NWN, int NWL>
+template <int NWN, int NWL, bool XTRA>
 __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, uint64_t first,
                                          uint64_t count, uint64_t span, uint64_t nslices,
                                          uint64_t s_begin, uint64_t stride, bool fold_each,
@@ -258,29 +258,37 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
     const uint64_t* __restrict__ sL = sm.sL;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t ts = p.tab_stride;
-    const uint32_t nbins = (uint32_t)kLutRows * ts;
+    // one plane of kLutRows * ts counters per value of the folded phase-pair
+    // and zero bits (constant inside a block)
+    const uint32_t plane = (uint32_t)kLutRows * ts;
+    const uint32_t nbins = plane << p.xshift;
     uint32_t* const wc = sm.sH + warp * nbins;
-    const uint32_t no = p.lut_no, nn = p.lut_nn;
+    const uint32_t no = p.lut_no, nn = p.lut_nn, lsh = p.lut_shift;
     const uint32_t mo = (1u << no) - 1u, mn = (1u << nn) - 1u;
     const uint64_t* __restrict__ qlut = sL + (1u << (no + nn));
 
-    // counter i = row * ts + m holds table entry (row mod 8) * ts + m = i mod 8 ts
+    // counter i = x * plane + row * ts + m holds table entry
+    // (((row mod 8) * ts + m) << xshift) | x, and (row mod 8) * ts + m = i mod 8 ts
     const uint32_t t8 = 8u * ts;
     auto fold = [&](bool clear) {
         __syncwarp();
-        uint32_t ti = lane;
+        uint32_t ti = lane, x = 0, r = lane;
         while (ti >= t8) ti -= t8;
+        while (r >= plane) { r -= plane; x++; }
         for (uint32_t i = lane; i < nbins; i += 32) {
             const uint32_t c = wc[i];
             if (c) {
-                acc = zw_madd32(acc, lds_zw(sT + ti), c);
+                acc = zw_madd32(acc, lds_zw(sT + ((ti << p.xshift) | x)), c);
                 if (clear) wc[i] = 0;
             }
             ti += 32;
             while (ti >= t8) ti -= t8;
+            r += 32;
+            while (r >= plane) { r -= plane; x++; }
         }
         __syncwarp();
     };
+
 
     const uint64_t end = first + count;
     for (uint64_t s0 = s_begin; s0 < nslices; s0 += stride) {
@@ -331,13 +339,22 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                 for (int w = 0; w < NWN; w++) M += __popc(L[w]);
                 return M;
             };
+            // counter plane of the folded bits: the pair forms' bits and "some
+            // zero form is set"
+            auto plane_base = [&]() -> uint32_t {
+                if (!XTRA) return 0u;
+                uint32_t z = 0;
+#pragma unroll
+                for (int w = 0; w < NWL; w++) z |= L[NWN + w] & p.Z[w];
+                return ((L[NWN] & p.pmask) | ((z != 0 ? 1u : 0u) << p.zshift)) * plane;
+            };
             for (;;) {
                 if ((t & 7u) == 0 && tend - t >= 8) {
-                    uint32_t u = L[NWN] & mo;
+                    uint32_t u = (L[NWN] >> lsh) & mo;
                     if (NWN) u |= (L[0] & mn) << no;
                     const uint64_t e = sL[u] + qlut[h];
                     const uint32_t lo = (uint32_t)e, hi = (uint32_t)(e >> 32);
-                    const int base = (int)((Jl & 7u) * ts + node_count()) - (int)nn;
+                    const int base = (int)(plane_base() + (Jl & 7u) * ts + node_count()) - (int)nn;
                     uint32_t* const wb = wc + base;
                     atomicAdd(wb + nn, 1u);
                     atomicAdd(wb + (lo & 0xFFu), 1u);
@@ -354,7 +371,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                     h = hi >> 29;
                     t += 7;
                 } else {
-                    atomicAdd(wc + (Jl & 7u) * ts + node_count(), 1u);
+                    atomicAdd(wc + plane_base() + (Jl & 7u) * ts + node_count(), 1u);
                 }
                 if (++t >= tend) break;
                 // flip variable i = ctz(t): 4 (A x)_i for the quadratic part,
@@ -402,8 +419,8 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                                      uint64_t s_begin, uint64_t stride, bool fold_each,
                                      bool clear_on_exit, bool final_fold, zw64& acc) {
     if constexpr (HIST == 4) {
-        walk_lut<NWN, NWL>(p, sm, first, count, span, nslices, s_begin, stride, fold_each,
-                           clear_on_exit, final_fold, acc);
+        walk_lut<NWN, NWL, XTRA>(p, sm, first, count, span, nslices, s_begin, stride, fold_each,
+                                 clear_on_exit, final_fold, acc);
         return;
     }
     constexpr int NW = NWN + NWL;
@@ -625,7 +642,7 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
 template <int HIST>
 __device__ __forceinline__ zw64 fold_block_counters(const KernelParams& p, const Smem& sm) {
     static_assert(HIST == 3 || HIST == 4, "warp-shared counters only");
-    const uint32_t nb = HIST == 4 ? (uint32_t)kLutRows * p.tab_stride : p.tab_size;
+    const uint32_t nb = HIST == 4 ? ((uint32_t)kLutRows * p.tab_stride) << p.xshift : p.tab_size;
     const uint32_t nwarps = blockDim.x >> 5;
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) {
@@ -636,15 +653,21 @@ __device__ __forceinline__ zw64 fold_block_counters(const KernelParams& p, const
     __syncthreads();
     zw64 acc = zw_zero();
     if (threadIdx.x < 32) {
-        // bin i of the block lookup's rows holds table entry i mod 8 ts
+        // block lookup: bin i = x * plane + row * ts + m holds table entry
+        // (((row mod 8) * ts + m) << xshift) | x, (row mod 8) * ts + m = i mod 8 ts
         const uint32_t t8 = HIST == 4 ? 8u * p.tab_stride : nb;
-        uint32_t ti = threadIdx.x;
+        const uint32_t plane = HIST == 4 ? (uint32_t)kLutRows * p.tab_stride : nb;
+        const uint32_t xs = HIST == 4 ? p.xshift : 0u;
+        uint32_t ti = threadIdx.x, x = 0, r = threadIdx.x;
         while (ti >= t8) ti -= t8;
+        while (r >= plane) { r -= plane; x++; }
         for (uint32_t i = threadIdx.x; i < nb; i += 32) {
             const uint32_t c = sm.sH[i];
-            if (c) acc = zw_madd32(acc, lds_zw(sm.sT + ti), c);
+            if (c) acc = zw_madd32(acc, lds_zw(sm.sT + ((ti << xs) | x)), c);
             ti += 32;
             while (ti >= t8) ti -= t8;
+            r += 32;
+            while (r >= plane) { r -= plane; x++; }
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) acc = zw_add(acc, shfl_xor_zw(acc, off));

@@ -105,7 +105,11 @@ int build_plan(const PS& ps, Plan* out) {
     // block lookup candidates: no phase-pair or zero forms (their bits would
     // vary inside a block); forms holding variable 0, 1 or 2 go first
     const uint64_t low3 = 7;
-    bool lut_try = k >= 3 && pair_masks.empty() && zero.empty();
+    // (phase-pair and zero forms may not hold variables 0-2: their bits are
+    // then constant inside a block and select the block's counter plane)
+    bool lut_try = k >= 3 && pair_masks.size() <= 2 * (size_t)kFoldPairs;
+    for (uint64_t m : pair_masks) lut_try = lut_try && !(m & 7);
+    for (auto& z : zero) lut_try = lut_try && !(z.mask & 7);
     uint32_t lut_nn = 0, lut_no = 0;
     if (lut_try) {
         std::vector<Form> o2;
@@ -120,8 +124,9 @@ int build_plan(const PS& ps, Plan* out) {
         for (auto& f : odd) lut_nn += (f.mask & low3) ? 1 : 0;
         for (auto& e : lins) lut_no += (e.first & low3) ? 1 : 0;
         const uint32_t stride = (uint32_t)odd.size() + 1;
+        const uint32_t planes = (1u << (uint32_t)pair_masks.size()) << (zero.empty() ? 0 : 1);
         lut_try = lut_nn + lut_no <= (uint32_t)kLutMaxBits && 11 * stride + 2 * lut_nn <= 255 &&
-                  (uint32_t)kLutRows * stride <= 2048;
+                  (uint32_t)kLutRows * stride * planes <= 2048;
     }
     size_t n_other = lins.size() + zero.size() + pair_masks.size();
     pl.nwn = (int)((odd.size() + 31) / 32);
@@ -220,7 +225,7 @@ int build_plan(const PS& ps, Plan* out) {
         const int nwn_k = pl.nwn;
         uint32_t fo[3], fn[3];
         for (int i = 0; i < 3; i++) {
-            fo[i] = pl.frows[(size_t)i * nw + (uint32_t)nwn_k] & mo;
+            fo[i] = (pl.frows[(size_t)i * nw + (uint32_t)nwn_k] >> pair_masks.size()) & mo;
             fn[i] = nwn_k ? (pl.frows[(size_t)i * nw] & mn) : 0u;
         }
         static const int seq[7] = {0, 1, 0, 2, 0, 1, 0};
@@ -260,6 +265,7 @@ int build_plan(const PS& ps, Plan* out) {
         }
         kp.lut_no = lut_no;
         kp.lut_nn = lut_nn;
+        kp.lut_shift = (uint32_t)pair_masks.size();   // linear forms follow the pair bits
         pl.lut_ok = true;
     }
 

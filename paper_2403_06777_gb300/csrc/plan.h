@@ -62,8 +62,9 @@ struct KernelParams {
     uint16_t PA[kMaxPairs], PB[kMaxPairs];            // bit positions of pair forms
     uint32_t R[3][kMaxRowWords];                      // step rows of variables 0, 1, 2
     // block lookup: forms holding variable 0, 1 or 2 are node bits [0, lut_nn)
-    // and linear bits [0, lut_no) of the first other word
-    uint32_t lut_no, lut_nn;
+    // and linear bits [lut_shift, lut_shift + lut_no) of the first other word
+    // (after the phase-pair bits)
+    uint32_t lut_no, lut_nn, lut_shift;
 };
 
 struct Plan {

@@ -33,7 +33,7 @@ using KernelFn = void (*)(const KernelParams, const zw64*, const zw64*, const ui
 extern const KernelFn kTable[3][kMaxWordsNode + 1][kMaxWordsOther];   // kernel.cu
 extern const KernelFn kHist[4][2][kMaxWordsOther];                    // kernel_count.cu (nwn <= 1)
 extern const KernelFn kShared[2][kMaxWordsNode + 1][kMaxWordsOther];  // kernel_count.cu
-extern const KernelFn kLut[2][kMaxWordsOther];                              // block lookup
+extern const KernelFn kLut[2][2][kMaxWordsOther];                              // block lookup
 
 namespace {
 

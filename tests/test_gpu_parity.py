@@ -225,11 +225,18 @@ def test_range_errors(ctx):
 
 def test_block_lookup_variant_matches_oracle(ctx):
     """Scalars whose low variables touch few forms take the block-lookup
-    kernel (variant 9); full sums and ragged ranges equal the oracle."""
+    kernel (variant 9; 10 with folded phase-pair / zero bits); full sums and
+    ragged ranges equal the oracle."""
     rng = random.Random(21)
     seen = 0
+    seen10 = 0
     blobs = []
-    for seed in range(3):
+    for seed in range(60, 140):
+        w = zi.workload_batch_item(seed)
+        s = Z.zxp_compile(w.gates, w.n, w.out_bits)
+        if s.info["kernel_variant"] == 10 and s.info["k"] <= 24:
+            blobs.append(Z.zxp_scalar_to_tables(s))
+    for seed in range(4):
         w = zi.workload_medium(seed)
         blobs.append(Z.zxp_scalar_to_tables(Z.zxp_compile(w.gates, w.n, w.out_bits)))
     for i in range(12):
@@ -239,9 +246,10 @@ def test_block_lookup_variant_matches_oracle(ctx):
                                      density=rng.choice([0.2, 0.4])).pack())
     for blob in blobs:
         s = Z.zxp_scalar_from_tables(blob)
-        if s.info["kernel_variant"] != 9:
+        if s.info["kernel_variant"] not in (9, 10):
             continue
         seen += 1
+        seen10 += s.info["kernel_variant"] == 10
         k = s.info["k"]
         N = 1 << k
         ranges = [(0, N), (5, N - 11), (N // 3, N // 2), (N - 9, 9)] if N >= 32 else [(0, N), (1, N - 2)]
@@ -251,7 +259,7 @@ def test_block_lookup_variant_matches_oracle(ctx):
             g = Z.zxp_eval(ctx, s, first, count)
             o = oracle.ps_sum(blob, first, count, nthreads=NCPU)
             assert same_raw(g, o), (k, first, count)
-    assert seen >= 5
+    assert seen >= 5 and seen10 >= 2
 
 
 def test_large_compiled_t50_subranges(ctx):

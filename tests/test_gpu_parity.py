@@ -275,3 +275,42 @@ def test_large_compiled_t50_subranges(ctx):
         g = Z.zxp_eval(ctx, s, first, 1 << 20)
         o = oracle.ps_sum(blob, first, 1 << 20, nthreads=NCPU)
         assert same_raw(g, o), first
+
+
+@pytest.mark.parametrize("seed,n_node,n_pair,odd,density", [
+    (62, 5, 0, True, 0.05),     # block lookup
+    (63, 14, 1, False, 0.05),   # block lookup with folded bits
+    (64, 14, 0, True, 0.4),     # warp-shared counters (too many forms on the low variables)
+    (65, 40, 3, False, 0.3),    # general: Z[w] phase-pair products
+])
+def test_maximum_k_ranges(ctx, seed, n_node, n_pair, odd, density):
+    """k = 62 (the largest supported): ranges at the start, in the middle and
+    at the very end of the index space equal the oracle, on every kind of
+    kernel."""
+    ps = zi.synthetic_ps(seed, 62, n_lin=6, n_quad=8, n_node=n_node, n_pair=n_pair,
+                         odd_nodes_only=odd, density=density)
+    blob = ps.pack()
+    s = Z.zxp_scalar_from_tables(blob)
+    N = 1 << 62
+    for first, count in [(0, 1 << 16), (N // 2 - 4096, 12289), (N - (1 << 15) - 3, (1 << 15) + 3),
+                         (N - 1, 1), (N, 0)]:
+        g = Z.zxp_eval(ctx, s, first, count)
+        o = oracle.ps_sum(blob, first, count, nthreads=NCPU)
+        assert same_raw(g, o), (first, count, s.info["kernel_variant"])
+
+
+def test_block_lookup_smallest_k(ctx):
+    """k = 3: one aligned 8-term block per full sum."""
+    rng = random.Random(3)
+    n = 0
+    for i in range(40):
+        ps = zi.synthetic_ps(1000 + i, 3, n_lin=rng.randint(1, 5), n_quad=rng.randint(0, 3),
+                             n_node=rng.randint(0, 4), odd_nodes_only=True, density=0.5)
+        blob = ps.pack()
+        s = Z.zxp_scalar_from_tables(blob)
+        for first, count in [(0, 8), (1, 6), (3, 5)]:
+            g = Z.zxp_eval(ctx, s, first, count)
+            o = oracle.ps_sum(blob, first, count)
+            assert same_raw(g, o), (i, first, count)
+        n += s.info["kernel_variant"] == 9
+    assert n >= 10

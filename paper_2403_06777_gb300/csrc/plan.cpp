@@ -229,6 +229,24 @@ int build_plan(const PS& ps, Plan* out) {
             fn[i] = nwn_k ? (pl.frows[(size_t)i * nw] & mn) : 0u;
         }
         static const int seq[7] = {0, 1, 0, 2, 0, 1, 0};
+        // csum[v]: the sum of the coefficients of the linear forms in v;
+        // flipping variable i changes J by sum_{r in F_i} c_r (1 - 2 l_r) + 4 per
+        // class-B node bit it flips, and M by |F_i nodes| - 2 |F_i nodes & L|
+        std::vector<int> csum((size_t)1 << lut_no, 0);
+        for (uint32_t v = 1; v < (1u << lut_no); v++) {
+            const uint32_t r = (uint32_t)__builtin_ctz(v);
+            csum[v] = csum[v & (v - 1)] + (int)lins[r].second;
+        }
+        // node-bit counts by table (no popcount instruction needed on the host)
+        std::vector<int> pcount((size_t)1 << lut_nn, 0);
+        for (uint32_t v = 1; v < (1u << lut_nn); v++) pcount[v] = pcount[v & (v - 1)] + 1;
+        uint32_t nb_mask = 0;
+        for (uint32_t r = 0; r < lut_nn; r++) nb_mask |= (uint32_t)odd_b[r] << r;
+        int sJ[3], sM[3];
+        for (int i = 0; i < 3; i++) {
+            sJ[i] = csum[fo[i]] + 4 * pcount[fn[i] & nb_mask];
+            sM[i] = pcount[fn[i]];
+        }
         pl.lut.assign(((size_t)1 << nU) + 8, 0ull);
         for (uint32_t u = 0; u < (1u << nU); u++) {
             uint32_t Lo = u & mo, Ln = u >> lut_no;
@@ -236,16 +254,11 @@ int build_plan(const PS& ps, Plan* out) {
             uint64_t e = 0;
             for (int s = 1; s <= 7; s++) {
                 const int i = seq[s - 1];
-                for (uint32_t r = 0; r < lut_no; r++)
-                    if ((fo[i] >> r) & 1) dJ += (int)lins[r].second * (((Lo >> r) & 1) ? -1 : 1);
-                for (uint32_t r = 0; r < lut_nn; r++)
-                    if ((fn[i] >> r) & 1) {
-                        dM += ((Ln >> r) & 1) ? -1 : 1;
-                        if (odd_b[r]) dJ += 4;
-                    }
+                dJ += sJ[i] - 2 * csum[fo[i] & Lo];
+                dM += sM[i] - 2 * pcount[fn[i] & Ln];
                 Lo ^= fo[i];
                 Ln ^= fn[i];
-                const uint32_t j8 = (uint32_t)(((dJ % 8) + 8) % 8);
+                const uint32_t j8 = (uint32_t)dJ & 7u;
                 if (s < 7) e |= (uint64_t)(j8 * stride + (uint32_t)(dM + (int)lut_nn)) << (8 * (s - 1));
                 else e |= ((uint64_t)(j8 * stride + (uint32_t)(dM + (int)lut_nn)) << 48) | ((uint64_t)j8 << 56);
             }

@@ -25,23 +25,120 @@ using namespace zxp;
 
 namespace {
 
-int ensure_device_tables(const zxp_scalar* s, int device, DevTables* out) {
+// Live contexts by id: a scalar's tables go back to the pool in the order
+// of the stream they were allocated on while that context lives.
+std::mutex g_ctx_mu;
+std::map<uint64_t, cudaStream_t> g_live_ctx;
+uint64_t g_next_ctx_id = 1;
+
+// One memory pool per device for scalar tables (stream-ordered allocation:
+// no device synchronisation on allocation or free).  It keeps up to 64 MB of
+// freed memory for reuse.
+cudaMemPool_t table_pool(int device) {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = pools.find(device);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = 64ull << 20;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    // A block freed on a context's stream (behind kernels still queued
+    // there) is not handed to the upload stream with a wait for that stream:
+    // the copy would queue behind those kernels.
+    int no = 0;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
+    pools[device] = pool;
+    return pool;
+}
+
+int ensure_device_tables(const zxp_scalar* s, zxp_ctx* ctx, DevTables* out) {
     std::lock_guard<std::mutex> lk(s->mu);
-    auto it = s->dev.find(device);
-    if (it != s->dev.end()) { *out = it->second; return ZXP_OK; }
+    auto it = s->dev.find(ctx->device);
+    if (it != s->dev.end()) {
+        // a copy queued on another stream: wait for it once
+        if (!it->second.shared && it->second.stream != ctx->stream) {
+            if (cudaDeviceSynchronize() != cudaSuccess) return ZXP_ECUDA;
+            it->second.shared = true;
+        }
+        *out = it->second.t;
+        return ZXP_OK;
+    }
     const TableLayout L = table_layout(s->plan);
-    std::vector<unsigned char> host(L.total, 0);
-    pack_tables(s->plan, L, host.data());
+    // pack into the next pinned staging buffer once its last copy is done
+    const int slot = ctx->stage_next;
+    ctx->stage_next = (slot + 1) % zxp_ctx::kStages;
+    if (!ctx->stage_ev[slot] && cudaEventCreateWithFlags(&ctx->stage_ev[slot], cudaEventDisableTiming) != cudaSuccess)
+        return ZXP_ECUDA;
+    cudaError_t q = cudaEventQuery(ctx->stage_ev[slot]);
+    if (q == cudaErrorNotReady) q = cudaEventSynchronize(ctx->stage_ev[slot]);
+    if (q != cudaSuccess) return ZXP_ECUDA;
+    if (ctx->stage_cap[slot] < L.total) {
+        if (ctx->stage[slot]) cudaFreeHost(ctx->stage[slot]);
+        ctx->stage[slot] = nullptr;
+        ctx->stage_cap[slot] = 0;
+        const size_t cap = std::max(L.total, (size_t)64 << 10);
+        if (cudaMallocHost(&ctx->stage[slot], cap) != cudaSuccess) return ZXP_ENOMEM;
+        ctx->stage_cap[slot] = cap;
+    }
+    unsigned char* host = ctx->stage[slot];
+    memset(host, 0, L.total);
+    pack_tables(s->plan, L, host);
+    cudaMemPool_t pool = table_pool(ctx->device);
+    if (!pool) return ZXP_ECUDA;
     unsigned char* base = nullptr;
-    if (cudaMalloc(&base, L.total) != cudaSuccess) return ZXP_ENOMEM;
-    if (cudaMemcpy(base, host.data(), L.total, cudaMemcpyHostToDevice) != cudaSuccess) {
-        cudaFree(base);
+    // copy on the upload stream, so that it overlaps the kernels still queued
+    // on the context's stream; that stream waits for the copy
+    if (cudaMallocFromPoolAsync((void**)&base, L.total, pool, ctx->upload) != cudaSuccess) return ZXP_ENOMEM;
+    if (cudaMemcpyAsync(base, host, L.total, cudaMemcpyHostToDevice, ctx->upload) != cudaSuccess ||
+        cudaEventRecord(ctx->stage_ev[slot], ctx->upload) != cudaSuccess) {
+        cudaFreeAsync(base, ctx->upload);
         return ZXP_ECUDA;
     }
-    const DevTables d = device_tables(L, base);
-    s->dev[device] = d;
-    *out = d;
+    if (cudaStreamWaitEvent(ctx->stream, ctx->stage_ev[slot], 0) != cudaSuccess) {
+        cudaStreamSynchronize(ctx->upload);
+        cudaFreeAsync(base, ctx->upload);
+        return ZXP_ECUDA;
+    }
+    zxp_scalar::DevCopy c;
+    c.t = device_tables(L, base);
+    c.stream = ctx->stream;
+    c.ctx_id = ctx->id;
+    s->dev[ctx->device] = c;
+    *out = c.t;
     return ZXP_OK;
+}
+
+// Wait until a kernel has published its result into pinned memory `h`
+// (flags != 0, stored after the value with release semantics; the caller
+// zeroes flags before the launch).  Spins on the flags word; every 20 us it
+// asks the stream whether work failed or ended without a result, and after
+// the first 200 us it sleeps between checks.  timeout_us < 0: no limit.
+int wait_published(cudaStream_t stream, const DevResult* h, int64_t timeout_us) {
+    auto published = [h] { return __atomic_load_n(&h->flags, __ATOMIC_ACQUIRE) != 0; };
+    if (published()) return ZXP_OK;
+    const auto t0 = std::chrono::steady_clock::now();
+    int64_t next_check = 0;
+    for (uint32_t it = 0;; it++) {
+        if (published()) return ZXP_OK;
+        if (timeout_us != 0 && (it & 63) != 63) continue;
+        const int64_t el = std::chrono::duration_cast<std::chrono::microseconds>(
+                               std::chrono::steady_clock::now() - t0).count();
+        if (el < next_check) continue;
+        next_check = el + 20;
+        const cudaError_t e = cudaStreamQuery(stream);
+        if (e != cudaSuccess && e != cudaErrorNotReady) return ZXP_ECUDA;
+        if (published()) return ZXP_OK;
+        if (e == cudaSuccess) return ZXP_ECUDA;   // the stream is idle and nothing was written
+        if (timeout_us >= 0 && el >= timeout_us) return ZXP_EAGAIN;
+        if (el >= 200) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
 }
 
 // Slice length and grid for `count` terms (slices a multiple of 8 terms so
@@ -59,7 +156,7 @@ int check_range(const zxp_scalar* s, uint64_t first, uint64_t count) {
 // Queue one range on ctx->stream: the raw partial into dres.
 int enqueue(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, DevResult* dres) {
     DevTables d;
-    int st = ensure_device_tables(s, ctx->device, &d);
+    int st = ensure_device_tables(s, ctx, &d);
     if (st != ZXP_OK) return st;
     uint64_t span;
     int grid;
@@ -69,6 +166,29 @@ int enqueue(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, D
 }
 
 }  // namespace
+
+zxp_scalar::~zxp_scalar() {
+    int prev = -1;
+    cudaGetDevice(&prev);
+    for (auto& e : dev) {
+        cudaSetDevice(e.first);
+        void* p = e.second.t.table;   // one allocation holds every table
+        bool queued = false;
+        if (!e.second.shared) {
+            // in the order of the allocating stream, while its context lives
+            std::lock_guard<std::mutex> lk(g_ctx_mu);
+            auto it = g_live_ctx.find(e.second.ctx_id);
+            if (it != g_live_ctx.end() && it->second == e.second.stream)
+                queued = cudaFreeAsync(p, e.second.stream) == cudaSuccess;
+        }
+        if (!queued) {
+            // shared copy, or its context is gone: nothing may still use it
+            cudaDeviceSynchronize();
+            cudaFreeAsync(p, 0);
+        }
+    }
+    if (prev >= 0) cudaSetDevice(prev);
+}
 
 int zxp::make_scalar(PS&& ps, zxp_scalar** out) {
     std::unique_ptr<zxp_scalar> s(new (std::nothrow) zxp_scalar());
@@ -118,13 +238,19 @@ int zxp_ctx_create(int device, void* cuda_stream, zxp_ctx** out) {
         if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return ZXP_ECUDA;
         c->own_stream = true;
     }
+    if (cudaStreamCreateWithFlags(&c->upload, cudaStreamNonBlocking) != cudaSuccess) return ZXP_ECUDA;
     // the sum kernel's accumulator starts at zero
     if (cudaMalloc(&c->acc, sizeof(zw64)) != cudaSuccess) return ZXP_ENOMEM;
     if (cudaMemset(c->acc, 0, sizeof(zw64)) != cudaSuccess) return ZXP_ECUDA;
     if (cudaMalloc(&c->counter, sizeof(unsigned int)) != cudaSuccess) return ZXP_ENOMEM;
     if (cudaMemset(c->counter, 0, sizeof(unsigned int)) != cudaSuccess) return ZXP_ECUDA;
-    if (cudaMalloc(&c->dres, sizeof(DevResult)) != cudaSuccess) return ZXP_ENOMEM;
     if (cudaMallocHost(&c->hres, sizeof(DevResult)) != cudaSuccess) return ZXP_ENOMEM;
+    if (cudaHostGetDevicePointer((void**)&c->hres_dev, c->hres, 0) != cudaSuccess) return ZXP_ECUDA;
+    {
+        std::lock_guard<std::mutex> lk(g_ctx_mu);
+        c->id = g_next_ctx_id++;
+        g_live_ctx[c->id] = c->stream;
+    }
     *out = c.release();
     return ZXP_OK;
 }
@@ -132,18 +258,24 @@ int zxp_ctx_create(int device, void* cuda_stream, zxp_ctx** out) {
 void zxp_ctx_destroy(zxp_ctx* c) {
     if (!c) return;
     DeviceGuard g(c->device);
+    {
+        // scalars freed from now on no longer queue on this stream
+        std::lock_guard<std::mutex> lk(g_ctx_mu);
+        g_live_ctx.erase(c->id);
+    }
     cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->upload);
     for (auto& e : c->tickets) c->free_slots.push_back(e.second);
-    for (auto& t : c->free_slots) {
-        cudaFree(t.dres);
-        cudaFreeHost(t.hres);
-        if (t.ev) cudaEventDestroy(t.ev);
+    for (auto& t : c->free_slots) cudaFreeHost(t.hres);
+    for (int i = 0; i < zxp_ctx::kStages; i++) {
+        if (c->stage[i]) cudaFreeHost(c->stage[i]);
+        if (c->stage_ev[i]) cudaEventDestroy(c->stage_ev[i]);
     }
     cudaFree(c->acc);
     cudaFree(c->counter);
-    cudaFree(c->dres);
     cudaFreeHost(c->hres);
     if (c->own_stream) cudaStreamDestroy(c->stream);
+    if (c->upload) cudaStreamDestroy(c->upload);
     delete c;
 }
 
@@ -252,11 +384,10 @@ int zxp_eval(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, 
     if (st != ZXP_OK) return st;
     if (count == 0 || s->plan.zero) { from_zw(zw_zero(), s->ps.e0, 1, out); return ZXP_OK; }
     DeviceGuard g(ctx->device);
-    st = enqueue(ctx, s, first, count, ctx->dres);
+    ctx->hres->flags = 0;
+    st = enqueue(ctx, s, first, count, ctx->hres_dev);   // the kernel writes the pinned result
     if (st != ZXP_OK) return st;
-    if (cudaMemcpyAsync(ctx->hres, ctx->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
-        return ZXP_ECUDA;
-    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return ZXP_ECUDA;
+    if ((st = wait_published(ctx->stream, ctx->hres, -1)) != ZXP_OK) return st;
     memcpy(out, ctx->hres, sizeof *out);
     return (out->flags & 2) ? ZXP_ETIMEDOUT : ZXP_OK;
 }
@@ -303,17 +434,16 @@ int zxp_submit(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count
         if (!ctx->free_slots.empty()) {
             t.dres = ctx->free_slots.back().dres;
             t.hres = ctx->free_slots.back().hres;
-            t.ev = ctx->free_slots.back().ev;
             ctx->free_slots.pop_back();
         } else {
-            if (cudaMalloc(&t.dres, sizeof(DevResult)) != cudaSuccess) return ZXP_ENOMEM;
-            if (cudaMallocHost(&t.hres, sizeof(DevResult)) != cudaSuccess) { cudaFree(t.dres); return ZXP_ENOMEM; }
-            if (cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming) != cudaSuccess) return ZXP_ECUDA;
+            if (cudaMallocHost(&t.hres, sizeof(DevResult)) != cudaSuccess) return ZXP_ENOMEM;
+            if (cudaHostGetDevicePointer((void**)&t.dres, t.hres, 0) != cudaSuccess) {
+                cudaFreeHost(t.hres);
+                return ZXP_ECUDA;
+            }
         }
-        st = enqueue(ctx, s, first, count, t.dres);
-        if (st == ZXP_OK && cudaMemcpyAsync(t.hres, t.dres, sizeof(DevResult), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
-            st = ZXP_ECUDA;
-        if (st == ZXP_OK && cudaEventRecord(t.ev, ctx->stream) != cudaSuccess) st = ZXP_ECUDA;
+        t.hres->flags = 0;
+        st = enqueue(ctx, s, first, count, t.dres);   // the kernel writes the pinned result
         if (st != ZXP_OK) { ctx->free_slots.push_back(t); return st; }
     }
     *ticket = ctx->next_ticket++;
@@ -328,17 +458,8 @@ int zxp_poll(zxp_ctx* ctx, uint64_t ticket, int64_t timeout_us, zxp_zomega* out)
     Ticket& t = it->second;
     if (!t.trivial) {
         DeviceGuard g(ctx->device);
-        auto t0 = std::chrono::steady_clock::now();
-        for (;;) {
-            cudaError_t e = cudaEventQuery(t.ev);
-            if (e == cudaSuccess) break;
-            if (e != cudaErrorNotReady) return ZXP_ECUDA;
-            if (timeout_us == 0) return ZXP_EAGAIN;
-            auto el = std::chrono::duration_cast<std::chrono::microseconds>(
-                          std::chrono::steady_clock::now() - t0).count();
-            if (timeout_us > 0 && el >= timeout_us) return ZXP_EAGAIN;
-            std::this_thread::sleep_for(std::chrono::microseconds(20));
-        }
+        const int st = wait_published(ctx->stream, t.hres, timeout_us);
+        if (st != ZXP_OK) return st;
         memcpy(out, t.hres, sizeof *out);
         if (out->flags & 2) {
             ctx->free_slots.push_back(t);
@@ -496,7 +617,7 @@ extern "C" int zxp_batch_create(zxp_ctx* ctx, const zxp_scalar* const* scalars, 
         const zxp_scalar* s = scalars[i];
         if (!s) return ZXP_EINVAL;
         DevTables d;
-        int st = ensure_device_tables(s, ctx->device, &d);
+        int st = ensure_device_tables(s, ctx, &d);
         if (st != ZXP_OK) return st;
         const Plan& pl = s->plan;
         BatchScalar& bs = *reinterpret_cast<BatchScalar*>(hs.data() + i * kBatchScalarBytes);

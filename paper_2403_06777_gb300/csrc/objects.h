@@ -87,10 +87,11 @@ inline BatchScalar batch_descriptor(const Plan& pl, const DevTables& d) {
 }
 
 // A pending zxp_submit: device and pinned result slots and its event.
+// A ticket's result lives in pinned host memory that the kernel writes
+// directly (dres is its device address).
 struct Ticket {
     DevResult* dres = nullptr;
     DevResult* hres = nullptr;
-    cudaEvent_t ev = nullptr;
     int32_t e0 = 0;
     bool trivial = false;        // no launch: the value is zero
 };
@@ -149,29 +150,41 @@ struct zxp_scalar {
     zxp::Plan plan;
     int plan_status = ZXP_OK;
     mutable std::mutex mu;
-    mutable std::map<int, zxp::DevTables> dev;   // per-device copies of the tables
+    // Per-device copies of the tables, allocated from the library's table
+    // pool in the order of the stream of the context that first needed them
+    // (`stream`, context `ctx_id`).  A copy that another stream has used is
+    // `shared`: that stream waited for the device once before its first use,
+    // and freeing the copy waits for the device too.
+    struct DevCopy {
+        zxp::DevTables t;
+        cudaStream_t stream = nullptr;
+        uint64_t ctx_id = 0;
+        bool shared = false;
+    };
+    mutable std::map<int, DevCopy> dev;
 
-    ~zxp_scalar() {
-        int prev = -1;
-        cudaGetDevice(&prev);
-        for (auto& e : dev) {
-            cudaSetDevice(e.first);
-            cudaFree(e.second.table);   // one allocation holds every table
-        }
-        if (prev >= 0) cudaSetDevice(prev);
-    }
+    ~zxp_scalar();
 };
 
 struct zxp_ctx {
+    uint64_t id = 0;                    // never reused within the process
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t upload = nullptr;      // table copies (the stream waits for them)
     int sm_count = 0;
     int max_grid = 0;
     zxp::zw64* acc = nullptr;           // the sum kernel's accumulator (zero between launches)
     unsigned int* counter = nullptr;
-    zxp::DevResult* dres = nullptr;
-    zxp::DevResult* hres = nullptr;
+    zxp::DevResult* hres = nullptr;     // pinned; the kernel writes it directly
+    zxp::DevResult* hres_dev = nullptr; // its device address
+    // Pinned staging for table uploads: a ring of buffers, each reused once
+    // the copy out of it (event) has completed.
+    static constexpr int kStages = 4;
+    unsigned char* stage[kStages] = {};
+    size_t stage_cap[kStages] = {};
+    cudaEvent_t stage_ev[kStages] = {};
+    int stage_next = 0;
     uint64_t next_ticket = 1;
     std::map<uint64_t, zxp::Ticket> tickets;
     std::vector<zxp::Ticket> free_slots;

@@ -247,23 +247,39 @@ int build_plan(const PS& ps, Plan* out) {
             sJ[i] = csum[fo[i]] + 4 * pcount[fn[i] & nb_mask];
             sM[i] = pcount[fn[i]];
         }
-        pl.lut.assign(((size_t)1 << nU) + 8, 0ull);
-        for (uint32_t u = 0; u < (1u << nU); u++) {
-            uint32_t Lo = u & mo, Ln = u >> lut_no;
-            int dJ = 0, dM = 0;
+        // ΔJ depends on the linear bits only and ΔM on the node bits only, and
+        // no byte of an entry carries into the next (each is at most 255), so
+        // an entry is the sum of a linear-bit part and a node-bit part.
+        std::vector<uint64_t> eo((size_t)1 << lut_no), en((size_t)1 << lut_nn);
+        for (uint32_t Lo0 = 0; Lo0 < (1u << lut_no); Lo0++) {
+            uint32_t Lo = Lo0;
+            int dJ = 0;
             uint64_t e = 0;
             for (int s = 1; s <= 7; s++) {
                 const int i = seq[s - 1];
                 dJ += sJ[i] - 2 * csum[fo[i] & Lo];
-                dM += sM[i] - 2 * pcount[fn[i] & Ln];
                 Lo ^= fo[i];
-                Ln ^= fn[i];
-                const uint32_t j8 = (uint32_t)dJ & 7u;
-                if (s < 7) e |= (uint64_t)(j8 * stride + (uint32_t)(dM + (int)lut_nn)) << (8 * (s - 1));
-                else e |= ((uint64_t)(j8 * stride + (uint32_t)(dM + (int)lut_nn)) << 48) | ((uint64_t)j8 << 56);
+                const uint64_t j8 = (uint32_t)dJ & 7u;
+                e |= (j8 * stride) << (8 * (s - 1));
+                if (s == 7) e |= j8 << 56;
             }
-            pl.lut[u] = e;
+            eo[Lo0] = e;
         }
+        for (uint32_t Ln0 = 0; Ln0 < (1u << lut_nn); Ln0++) {
+            uint32_t Ln = Ln0;
+            int dM = 0;
+            uint64_t e = 0;
+            for (int s = 1; s <= 7; s++) {
+                const int i = seq[s - 1];
+                dM += sM[i] - 2 * pcount[fn[i] & Ln];
+                Ln ^= fn[i];
+                e |= (uint64_t)(uint32_t)(dM + (int)lut_nn) << (8 * (s - 1));
+            }
+            en[Ln0] = e;
+        }
+        pl.lut.assign(((size_t)1 << nU) + 8, 0ull);
+        for (uint32_t Ln = 0; Ln < (1u << lut_nn); Ln++)
+            for (uint32_t Lo = 0; Lo < (1u << lut_no); Lo++) pl.lut[((size_t)Ln << lut_no) | Lo] = eo[Lo] + en[Ln];
         for (uint32_t h = 0; h < 8; h++) {
             uint32_t a = h, Q = 0;
             uint64_t e = 0;

@@ -37,6 +37,19 @@ extern const KernelFn kLut[2][2][kMaxWordsOther];                              /
 
 namespace {
 
+// Write a result: its value, then its flags (never 0) with a system-scope
+// release store, so that a host polling the flags word of pinned memory
+// reads the value only after it is complete.
+__device__ __forceinline__ void publish_result(DevResult* r, uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                               int32_t e, int32_t flags) {
+    r->c[0] = (int64_t)c0;
+    r->c[1] = (int64_t)c1;
+    r->c[2] = (int64_t)c2;
+    r->c[3] = (int64_t)c3;
+    r->e = e;
+    cuda::atomic_ref<int32_t, cuda::thread_scope_system>(r->flags).store(flags, cuda::memory_order_release);
+}
+
 template <int NWN, int NWL, int VAR>
 __global__ void __launch_bounds__(kThreads)
 sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtable,
@@ -89,9 +102,7 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
     if (threadIdx.x == 0) {
         const zw64 r = zw_mul(K, acc);
         if (gridDim.x == 1) {     // one block: its sum is the result
-            for (int c = 0; c < 4; c++) result->c[c] = (int64_t)r.c[c];
-            result->e = e0;
-            result->flags = ok ? 1 : 3;
+            publish_result(result, r.c[0], r.c[1], r.c[2], r.c[3], e0, ok ? 1 : 3);
             return;
         }
         if (!ok) atomicOr(counter, 0x80000000u);
@@ -103,13 +114,13 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
             cuda::atomic_ref<unsigned int, cuda::thread_scope_device>(*counter).fetch_add(
                 1u, cuda::memory_order_acq_rel);
         if ((done & 0x7FFFFFFFu) == gridDim.x - 1) {
+            uint64_t v[4];
             for (int c = 0; c < 4; c++) {
-                result->c[c] = (int64_t)__ldcg(g + c);
+                v[c] = __ldcg(g + c);
                 g[c] = 0ull;
             }
-            result->e = e0;
-            result->flags = 1 | ((done >> 31) ? 2 : 0);
             *counter = 0u;       // ready for the next launch on this workspace
+            publish_result(result, v[0], v[1], v[2], v[3], e0, 1 | ((done >> 31) ? 2 : 0));
         }
     }
 }

@@ -3,8 +3,9 @@
 One step = one full exact amplitude of the medium workload (n = 20 qubits,
 600 gates with 40 T gates, seeded random output bitstring): the sum of all
 2^k terms of its compiled parametric scalar on the GPU, result on the device
-(value) or on the host through the public API (e2e).  The circuit is reduced
-to the scalar once, before timing.
+(value), or one request through the public host API from the scalar's table
+bytes to the exact result on the host, two requests in flight (e2e).  The
+circuit is reduced to the scalar once, before timing.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -402,17 +403,40 @@ def main():
     amps = args.steps * world / sec
     per_launch_s = sec / args.steps
 
-    # e2e: public host API each step: tables -> scalar (host plan, H2D of the
-    # tables on first use), full sum, D2H of the 40-byte result
-    e2e_steps = max(10, min(args.steps, 50))
+    # e2e: the public host API, one request per step: the tables (host
+    # bytes) become a scalar (host plan), are submitted (tables copied from
+    # pinned staging, launch) and polled (the 40-byte result the kernel wrote
+    # into pinned host memory); up to E2E_DEPTH requests are in flight, as a
+    # client streaming requests runs them.  Every result is checked.  The
+    # latency of one blocking request (nothing else in flight) is reported
+    # beside it.
+    E2E_DEPTH = 2
+    e2e_steps = max(200, 10 * args.steps)
+    from collections import deque
     torch.cuda.synchronize()
+    q = deque()
+    bad = 0
     t = time.perf_counter()
-    for _ in range(e2e_steps):
+    for i in range(e2e_steps + E2E_DEPTH):
+        if i < e2e_steps:
+            s2 = Z.zxp_scalar_from_tables(blob)
+            q.append((s2, Z.zxp_submit(ctx, s2, 0, terms)))
+        if len(q) > E2E_DEPTH or (i >= e2e_steps and q):
+            s_old, tk = q.popleft()
+            bad += Z.zxp_zomega_canon(Z.zxp_poll(ctx, tk, -1)) != ref
+            s_old.free()
+    e2e_sec = (time.perf_counter() - t) / e2e_steps
+    assert bad == 0, bad
+    lat = []
+    for _ in range(100):
+        t = time.perf_counter()
         s2 = Z.zxp_scalar_from_tables(blob)
         Z.zxp_amplitude(ctx, s2)
         s2.free()
-    e2e_sec = (time.perf_counter() - t) / e2e_steps
-    table_bytes = 8 * 32 * (info["n_node"] + 1) + 4 * 32 * info["n_pair"] + 5 * 1024
+        lat.append(time.perf_counter() - t)
+    lat.sort()
+    latency_us = lat[len(lat) // 2] * 1e6
+    table_bytes = info["device_bytes"]
 
     # large scalar: k = 36 synthetic tables with compiled statistics (the
     # compiled n = 50 / t = 80 circuit needs k ~ 50, out of reach)
@@ -564,7 +588,9 @@ def main():
                              "table fetch, 64-bit adds); the block lookup shares work across 8 terms, "
                              "so the kernel executes fewer instructions per term (issue)"},
         "e2e": {"value": terms / e2e_sec, "unit": "terms/s", "amplitudes_per_s": 1 / e2e_sec,
-                "h2d_bytes_per_step": table_bytes, "d2h_bytes_per_step": 40},
+                "h2d_bytes_per_step": table_bytes, "d2h_bytes_per_step": 40,
+                "requests_in_flight": E2E_DEPTH, "steps": e2e_steps,
+                "blocking_latency_us": latency_us},
         "clocks": clocks,
         "gpu_launches": args.steps,
         "wall_s_timed_region": wall,

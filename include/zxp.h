@@ -93,7 +93,8 @@ typedef struct {
     uint32_t device_bytes;       /* bytes of the tables a device evaluation keeps resident */
     uint32_t kernel_variant;     /* 0 table, 1 table + folded bits, 2 general, 3-8 counting
                                     (lane-private 32 / 16 bit, warp-shared; odd: no folded
-                                    bits), 9/10 block lookup (10: with folded bits) */
+                                    bits), 9/10 block lookup (10: with folded bits),
+                                    11 block lookup with lane-private counters */
     uint32_t reserved[3];
 } zxp_scalar_info_t;
 

@@ -33,7 +33,7 @@ using BatchFn = void (*)(const unsigned char*, const BatchChunk*, uint32_t, unsi
 extern const BatchFn kTable[3][kMaxWordsNode + 1][kMaxWordsOther];   // batch.cu
 extern const BatchFn kHist[4][2][kMaxWordsOther];                    // batch_count.cu
 extern const BatchFn kShared[2][kMaxWordsNode + 1][kMaxWordsOther];  // batch_count.cu
-extern const BatchFn kLut[2][2][kMaxWordsOther];                              // block lookup
+extern const BatchFn kLut[3][2][kMaxWordsOther];                              // block lookup
 
 namespace {
 
@@ -81,10 +81,11 @@ batch_kernel(const unsigned char* __restrict__ scalars, const BatchChunk* __rest
             if (threadIdx.x == 0) s_loaded = ch.scalar;
             ok = __syncthreads_and(loaded) != 0;
         }
-        // slices: a multiple of 8 terms (chunk starts are multiples of 8)
+        // slices: a multiple of 8 terms, 16 for the block lookup (chunk starts
+        // are multiples of 8)
         uint64_t span = (ch.count + per - 1) / per;
-        span = (span + 7) & ~7ull;
-        if (span < 8) span = 8;
+        span = HIST >= 4 ? (span + 15) & ~15ull : (span + 7) & ~7ull;   // (see sum_shape)
+        if (span < 16) span = 16;
         if (span > cap) span = cap;
         const uint64_t nslices = (ch.count + span - 1) / span;
         zw64 acc = zw_zero();

@@ -49,9 +49,14 @@ cudaError_t ensure_dynamic_smem(const void* fn, size_t bytes) {
     return e;
 }
 
+// Threads per block: 128 for the lane-private block lookup (32 KB of
+// counters per 128 threads), else 256.
+static int block_threads(const Plan& pl) { return hist_mode(pl) == 5 ? 128 : kThreads; }
+
 size_t sum_smem_bytes(const Plan& pl) {
-    return smem_bytes(pl.kp.tab_size, pl.kp.npairs, pl.nwn, kernel_words(pl) - pl.nwn, hist_mode(pl),
-                      kThreads);
+    const int h = hist_mode(pl);
+    return smem_bytes(pl.kp.tab_size, pl.kp.npairs, pl.nwn, kernel_words(pl) - pl.nwn, h, block_threads(pl),
+                      k_cap(pl.kp.k), h >= 4 ? lut_cap(pl.kp.lut_no + pl.kp.lut_nn) : 0u);
 }
 
 uint64_t sum_max_span(const Plan& pl) { return max_span(hist_mode(pl)); }
@@ -70,7 +75,7 @@ cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, cons
     cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(fn), smem);
     if (e != cudaSuccess) return e;
     const uint64_t nslices = (count + span - 1) / span;
-    fn<<<grid, kThreads, smem, stream>>>(pl.kp, dtable, dpv, dF, dADJ, dS, first, count, span, nslices,
+    fn<<<grid, block_threads(pl), smem, stream>>>(pl.kp, dtable, dpv, dF, dADJ, dS, first, count, span, nslices,
                                          acc, counter, pl.K, pl.e0, result);
     return cudaGetLastError();
 }
@@ -91,7 +96,7 @@ cudaError_t sum_occupancy(const Plan& pl, int* blocks_per_sm) {
         auto it = cache.find(key);
         if (it != cache.end()) { *blocks_per_sm = it->second; return cudaSuccess; }
     }
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block_threads(pl), smem);
     if (e == cudaSuccess) {
         std::lock_guard<std::mutex> lk(mu);
         cache[key] = *blocks_per_sm;
@@ -102,19 +107,24 @@ cudaError_t sum_occupancy(const Plan& pl, int* blocks_per_sm) {
 void sum_shape(const Plan& pl, int sm_count, int max_grid_cap, uint64_t count, uint64_t* span, int* grid) {
     int bps = 1;
     if (sum_occupancy(pl, &bps) != cudaSuccess || bps < 1) bps = 1;
+    const int bt = block_threads(pl);
     // Ranges too short to give every thread of a full-occupancy grid 256
-    // terms run with at most 3 blocks per SM: fewer, longer slices amortise
-    // each thread's fixed work (seek, counter fold, reduction).
-    if (bps > 3 && count < (uint64_t)sm_count * (uint64_t)bps * kThreads * 256u) bps = 3;
+    // terms run with at most 768 threads per SM: fewer, longer slices
+    // amortise each thread's fixed work (seek, counter fold, reduction).
+    const int short_bps = 3 * kThreads / bt;
+    if (bps > short_bps && count < (uint64_t)sm_count * (uint64_t)bps * bt * 256u) bps = short_bps;
     int max_grid = sm_count * bps;
     if (max_grid > max_grid_cap) max_grid = max_grid_cap;
-    const uint64_t threads = (uint64_t)max_grid * (uint64_t)kThreads;
+    const uint64_t threads = (uint64_t)max_grid * (uint64_t)bt;
     uint64_t sp = (count + threads - 1) / threads;
-    sp = (sp + 7) & ~7ull;
+    // (block lookup: a multiple of 16, so that a warp's lanes reach the
+    // flips of variable 3 together)
+    const uint64_t al = hist_mode(pl) >= 4 ? 16 : 8;
+    sp = (sp + al - 1) & ~(al - 1);
     if (sp < 64) sp = 64;
     if (sp > sum_max_span(pl)) sp = sum_max_span(pl);   // longer ranges: several slices per thread
     const uint64_t nslices = (count + sp - 1) / sp;
-    uint64_t g = (nslices + (uint64_t)kThreads - 1) / (uint64_t)kThreads;
+    uint64_t g = (nslices + (uint64_t)bt - 1) / (uint64_t)bt;
     if (g > (uint64_t)max_grid) g = (uint64_t)max_grid;
     if (g < 1) g = 1;
     *span = sp;

@@ -71,14 +71,16 @@ __device__ __forceinline__ zw64 block_reduce(zw64 v, zw64* sred) {
 // 0: table path, 1: lane-private 32-bit counters, 2: lane-private 16-bit
 // counters, 3: warp-shared 32-bit counters (by the number of distinct term
 // values the table holds), 4: block lookup with warp-shared counters over
-// kLutRows rows of the table (when the plan built the lookup)
+// kLutRows rows of the table (when the plan built the lookup), 5: block
+// lookup with lane-private 32-bit counters (rows of 2^lut_tsh counters, the
+// phase exponent taken mod 8 by a mask)
 constexpr uint32_t kHistMaxEntries32 = 48;
 constexpr uint32_t kHistMaxEntries16 = 128;
 constexpr uint32_t kHistMaxEntriesShared = 2048;
 constexpr uint32_t kLutEntries = (1u << kLutMaxBits) + 8u;
 inline int hist_mode(const Plan& pl) {
     if (pl.general) return 0;
-    if (pl.lut_ok) return 4;
+    if (pl.lut_ok) return pl.lut_lane ? 5 : 4;
     if (pl.kp.tab_size <= kHistMaxEntries32) return 1;
     if (pl.kp.tab_size <= kHistMaxEntries16) return 2;
     if (pl.kp.tab_size <= kHistMaxEntriesShared) return 3;
@@ -88,12 +90,12 @@ inline int kernel_words(const Plan& pl) { return pl.nwn + (pl.nwl < 1 ? 1 : pl.n
 // kernel variant: 0 table, 1 table + extra index bits, 2 general (phase-pair
 // products), 3/4 lane-private 32-bit counters (+ extra bits), 5/6
 // lane-private 16-bit counters (+ extra), 7/8 warp-shared counters (+ extra),
-// 9/10 block lookup (+ extra)
+// 9/10 block lookup (+ extra), 11 block lookup with lane-private counters
 inline int variant(const Plan& pl) {
     if (pl.general) return 2;
     const int x = pl.kp.xshift ? 1 : 0;
     const int h = hist_mode(pl);
-    return h == 0 ? x : 1 + 2 * h + x;   // block lookup: 9, or 10 with folded bits
+    return h == 0 ? x : 1 + 2 * h + x;   // block lookup: 9, or 10 with folded bits; 11
 }
 __host__ __device__ constexpr bool var_general(int v) { return v == 2; }
 __host__ __device__ constexpr int var_hist(int v) { return v >= 3 ? (v - 1) / 2 : 0; }
@@ -103,7 +105,8 @@ __host__ __device__ constexpr uint32_t counter_words(int h, uint32_t ntab, uint3
     return h == 1 ? ntab * threads
                   : (h == 2 ? (ntab + 1) / 2 * threads
                             : (h == 3 ? ntab * (threads / 32)
-                                      : (h == 4 ? (uint32_t)(kLutRows / 8) * ntab * (threads / 32) : 0u)));
+                                      : (h == 4 ? (uint32_t)(kLutRows / 8) * ntab * (threads / 32)
+                                                : (h == 5 ? (uint32_t)kLaneCounters * threads : 0u))));
 }
 inline uint64_t max_span(int h) { return h == 2 ? kSpan16 : kSpan32; }
 
@@ -115,29 +118,38 @@ struct Smem {
     zw64* sred;
     uint64_t* sADJ;
     uint32_t* sS;   // seek tables
-    uint64_t* sL;   // block lookup (HIST 4)
+    uint64_t* sL;   // block lookup (HIST 4, 5)
     uint32_t* sF;
     uint32_t* sH;
 };
 
 // words of one seek-table entry (flip words, adjacency, quadratic bit)
 __host__ __device__ constexpr uint32_t seek_stride(int nw) { return ((uint32_t)nw + 3u + 3u) & ~3u; }
-__host__ __device__ constexpr uint32_t seek_words(int nw) {
-    return ((kMaxK + 3) / 4) * 16u * seek_stride(nw);
+__host__ __device__ constexpr uint32_t seek_words(int nw, uint32_t kcap = kMaxK) {
+    return ((kcap + 3) / 4) * 16u * seek_stride(nw);
 }
+// Shared-memory capacities for a scalar with k variables and a block lookup
+// over nU forms (a block sized for one scalar): variables rounded up to an
+// even count (at least 4), lookup entries to an even count, so that every
+// region stays 16-byte aligned.  Blocks that hold any scalar use kMaxK and
+// kLutEntries.
+__host__ __device__ constexpr uint32_t k_cap(uint32_t k) { return k < 4 ? 4u : (k + 1u) & ~1u; }
+__host__ __device__ constexpr uint32_t lut_cap(uint32_t nU) { return ((1u << nU) + 9u) & ~1u; }
 
 __host__ __device__ inline size_t smem_bytes(uint32_t ntab_cap, uint32_t npairs_cap, int nwn, int nwl,
-                                             int h, int threads) {
-    return sizeof(zw64) * (ntab_cap + 4u * npairs_cap + kMaxWarps) + sizeof(uint64_t) * kMaxK +
-           sizeof(uint32_t) * seek_words(nwn + nwl) + sizeof(uint32_t) * (size_t)kMaxK * row_words(nwn, nwl) +
-           (h == 4 ? sizeof(uint64_t) * kLutEntries : 0) +
+                                             int h, int threads, uint32_t kcap = kMaxK,
+                                             uint32_t lutcap = kLutEntries) {
+    return sizeof(zw64) * (ntab_cap + 4u * npairs_cap + kMaxWarps) + sizeof(uint64_t) * kcap +
+           sizeof(uint32_t) * seek_words(nwn + nwl, kcap) + sizeof(uint32_t) * (size_t)kcap * row_words(nwn, nwl) +
+           (h >= 4 ? sizeof(uint64_t) * lutcap : 0) +
            sizeof(uint32_t) * (size_t)counter_words(h, ntab_cap, (uint32_t)threads);
 }
 
 template <int NW, int HIST>
-__device__ __forceinline__ Smem carve(unsigned char* raw, uint32_t ntab_cap, uint32_t npairs_cap) {
+__device__ __forceinline__ Smem carve(unsigned char* raw, uint32_t ntab_cap, uint32_t npairs_cap,
+                                      uint32_t kcap = kMaxK, uint32_t lutcap = kLutEntries) {
     // (step rows last: 16-byte aligned after the 8-byte adjacency words, as
-    // kMaxK is even)
+    // kcap is even)
     const uint32_t hist_words = counter_words(HIST, ntab_cap, blockDim.x);
     Smem s;
     s.sT = reinterpret_cast<zw64*>(raw);
@@ -145,10 +157,10 @@ __device__ __forceinline__ Smem carve(unsigned char* raw, uint32_t ntab_cap, uin
     s.sred = s.sPV + 4u * npairs_cap;
     // 16-byte aligned first (vector loads and stores): seek tables, counters
     s.sS = reinterpret_cast<uint32_t*>(s.sred + kMaxWarps);
-    s.sL = reinterpret_cast<uint64_t*>(s.sS + seek_words(NW));
-    s.sH = reinterpret_cast<uint32_t*>(s.sL + (HIST == 4 ? kLutEntries : 0u));
+    s.sL = reinterpret_cast<uint64_t*>(s.sS + seek_words(NW, kcap));
+    s.sH = reinterpret_cast<uint32_t*>(s.sL + (HIST >= 4 ? lutcap : 0u));
     s.sADJ = reinterpret_cast<uint64_t*>(s.sH + hist_words);
-    s.sF = reinterpret_cast<uint32_t*>(s.sADJ + kMaxK);
+    s.sF = reinterpret_cast<uint32_t*>(s.sADJ + kcap);
     return s;
 }
 
@@ -208,7 +220,7 @@ __device__ __forceinline__ bool load_tables(const KernelParams& p, const Smem& s
     const uint32_t ns = ((p.k + 3) / 4) * 16u * seek_stride(NW);
     const uint32_t bt = p.tab_size * 32u, bs = ns * 4u, br = p.k * RW * 4u, ba = round16(p.k * 8u);
     const uint32_t bpv = GENERAL ? 4u * p.npairs * 32u : 0u;
-    const uint32_t bl = HIST == 4 ? round16(((1u << (p.lut_no + p.lut_nn)) + 8u) * 8u) : 0u;
+    const uint32_t bl = HIST >= 4 ? round16(((1u << (p.lut_no + p.lut_nn)) + 8u) * 8u) : 0u;
     if (threadIdx.x == 0) {
         // order the shared-memory reads of a previous scalar before the
         // asynchronous writes
@@ -240,10 +252,18 @@ __device__ __forceinline__ bool load_tables(const KernelParams& p, const Smem& s
 // reduced mod 8 inside a block; the fold maps row r to table row r mod 8).
 // An aligned block of 8 Gray steps costs one lookup: the forms holding
 // variables 0, 1, 2 are the lowest node and linear bits, their values at the
-// block's first state index sL, and h = (A x) restricted to variables 0-2
+// block's first state index sL, and (A x) restricted to variables 0-2
 // indexes the quadratic part; byte s - 1 of the sum is term s's counter
-// offset from the block's base.  Other steps update L, J and h directly.
-template <int NWN, int NWL, bool XTRA>
+// offset from the block's base.  Other steps update L, J and A x directly;
+// the flip of variable 3 between the two blocks of an aligned 16 takes its
+// step row and adjacency row from the parameters (the constant bank), so
+// only one step in 16 reads a step row from shared memory.  (Slices that are
+// a multiple of 16 keep a warp's lanes on one branch.)
+// LANE (HIST 5): every lane owns kLaneCounters counters in its own bank
+// (counter i of lane l at word i * 32 + l), so the counting atomics of a
+// warp never conflict; a counter index is (J mod 8) * 2^tsh + M, the block's
+// base plus the looked-up offset modulo 8 * 2^tsh.
+template <int NWN, int NWL, bool XTRA, bool LANE>
 __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, uint64_t first,
                                          uint64_t count, uint64_t span, uint64_t nslices,
                                          uint64_t s_begin, uint64_t stride, bool fold_each,
@@ -266,12 +286,39 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
     const uint32_t no = p.lut_no, nn = p.lut_nn, lsh = p.lut_shift;
     const uint32_t mo = (1u << no) - 1u, mn = (1u << nn) - 1u;
     const uint64_t* __restrict__ qlut = sL + (1u << (no + nn));
+    const uint32_t tsh = p.lut_tsh, cm = (8u << tsh) - 1u;
+    uint32_t* const lbase = sm.sH + warp * ((uint32_t)kLaneCounters * 32u);
+    uint32_t* const wl = lbase + lane;
 
     // counter i = x * plane + row * ts + m holds table entry
     // (((row mod 8) * ts + m) << xshift) | x, and (row mod 8) * ts + m = i mod 8 ts
     const uint32_t t8 = 8u * ts;
     auto fold = [&](bool clear) {
         __syncwarp();
+        if constexpr (LANE) {
+            // lane l adds up counter i = l (+32) over the 32 lanes with
+            // 16-byte reads in lane-rotated order (the 8 lanes of a
+            // quarter-warp read 8 different columns: 32 banks) and clears it;
+            // counter i holds table entry (i >> tsh) * ts + (i & (2^tsh - 1))
+            const uint32_t tm = (1u << tsh) - 1u;
+            for (uint32_t i = lane; i <= cm; i += 32) {
+                uint4* row = reinterpret_cast<uint4*>(lbase + i * 32u);
+                uint32_t c = 0;
+#pragma unroll
+                for (uint32_t j = 0; j < 8; j++) {
+                    const uint4 v = row[(j + lane) & 7u];
+                    c += v.x + v.y + v.z + v.w;
+                }
+                const uint32_t m = i & tm;
+                if (c && m < ts) acc = zw_madd32(acc, lds_zw(sT + (i >> tsh) * ts + m), c);
+                if (clear) {
+#pragma unroll
+                    for (uint32_t j = 0; j < 8; j++) row[(j + lane) & 7u] = make_uint4(0, 0, 0, 0);
+                }
+            }
+            __syncwarp();
+            return;
+        }
         uint32_t ti = lane, x = 0, r = lane;
         while (ti >= t8) ti -= t8;
         while (r >= plane) { r -= plane; x++; }
@@ -331,7 +378,8 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                 }
                 Jl = P0 + 2u * P1 + 4u * ((uint32_t)__popc(X2) + q);
             }
-            uint32_t h = (uint32_t)a & 7u;   // (A x) on variables 0, 1, 2
+            // a = A x (all k bits): flipping variable i adds 4 (A x)_i to J and
+            // XORs adjacency row i into a
 
             auto node_count = [&]() {
                 uint32_t M = 0;
@@ -348,12 +396,42 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                 for (int w = 0; w < NWL; w++) z |= L[NWN + w] & p.Z[w];
                 return ((L[NWN] & p.pmask) | ((z != 0 ? 1u : 0u) << p.zshift)) * plane;
             };
-            for (;;) {
-                if ((t & 7u) == 0 && tend - t >= 8) {
-                    uint32_t u = (L[NWN] >> lsh) & mo;
-                    if (NWN) u |= (L[0] & mn) << no;
-                    const uint64_t e = sL[u] + qlut[h];
-                    const uint32_t lo = (uint32_t)e, hi = (uint32_t)(e >> 32);
+            // the linear part of a flip with step row f (L before the XOR)
+            auto step = [&](const uint32_t* f) {
+                uint32_t d0 = 0, d1 = 0;
+#pragma unroll
+                for (int w = 0; w < NWL; w++) {
+                    d0 += __popc(L[NWN + w] & f[NW + w]);
+                    d1 += __popc(L[NWN + w] & f[NW + NWL + w]);
+                }
+                Jl += f[NW + 2 * NWL] - 2u * d0 - 4u * d1;
+#pragma unroll
+                for (int w = 0; w < NW; w++) L[w] ^= f[w];
+            };
+            // the 8 terms of an aligned block from one lookup, then the block's
+            // net change: variable 2 flipped (Gray 000 -> 100), its forms, its
+            // adjacency row and the block's phase change
+            auto block8 = [&]() {
+                uint32_t u = (L[NWN] >> lsh) & mo;
+                if (NWN) u |= (L[0] & mn) << no;
+                const uint64_t e = sL[lut_slot(u)] + qlut[(uint32_t)a & 7u];
+                const uint32_t lo = (uint32_t)e, hi = (uint32_t)(e >> 32);
+                if constexpr (LANE) {
+                    // the block's base (< 64) added to all offset bytes at once
+                    // (each sum < 256: no carry between bytes) and every byte
+                    // taken mod 8 * 2^tsh by one mask
+                    const uint32_t b0 = ((Jl & 7u) << tsh) + node_count();
+                    const uint32_t bx = ((b0 - nn) & cm) * 0x01010101u, mk = cm * 0x01010101u;
+                    const uint32_t w0 = (lo + bx) & mk, w1 = (hi + bx) & mk;
+                    atomicAdd(wl + (b0 << 5), 1u);
+                    atomicAdd(wl + ((w0 & 0xFFu) << 5), 1u);
+                    atomicAdd(wl + (((w0 >> 8) & 0xFFu) << 5), 1u);
+                    atomicAdd(wl + (((w0 >> 16) & 0xFFu) << 5), 1u);
+                    atomicAdd(wl + ((w0 >> 24) << 5), 1u);
+                    atomicAdd(wl + ((w1 & 0xFFu) << 5), 1u);
+                    atomicAdd(wl + (((w1 >> 8) & 0xFFu) << 5), 1u);
+                    atomicAdd(wl + (((w1 >> 16) & 0xFFu) << 5), 1u);
+                } else {
                     const int base = (int)(plane_base() + (Jl & 7u) * ts + node_count()) - (int)nn;
                     uint32_t* const wb = wc + base;
                     atomicAdd(wb + nn, 1u);
@@ -364,45 +442,77 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                     atomicAdd(wb + (hi & 0xFFu), 1u);
                     atomicAdd(wb + ((hi >> 8) & 0xFFu), 1u);
                     atomicAdd(wb + ((hi >> 16) & 0xFFu), 1u);
-                    // the block ends with variable 2 flipped (Gray 000 -> 100)
+                }
 #pragma unroll
-                    for (int w = 0; w < NW; w++) L[w] ^= p.R[2][w];
-                    Jl += (hi >> 24) & 31u;
-                    h = hi >> 29;
-                    t += 7;
-                } else {
-                    atomicAdd(wc + plane_base() + (Jl & 7u) * ts + node_count(), 1u);
-                }
-                if (++t >= tend) break;
-                // flip variable i = ctz(t): 4 (A x)_i for the quadratic part,
-                // the step row for the linear part, h follows A x
-                const uint32_t tl = (uint32_t)t;
-                const int i = tl ? __ffs(tl) - 1 : 31 + __ffs((uint32_t)(t >> 32));
-                const uint64_t adj = sADJ[i];
-                uint32_t ai;
-                if (i < 3) {
-                    ai = (h >> i) & 1u;
-                } else {
-                    const uint64_t xp = (t - 1) ^ ((t - 1) >> 1);
-                    ai = (uint32_t)(__popcll(adj & xp)) & 1u;
-                }
-                Jl += ai << 2;
-                h ^= (uint32_t)adj & 7u;
-                uint32_t fr[RW];
+                for (int w = 0; w < NW; w++) L[w] ^= p.R[2][w];
+                Jl += (hi >> 24) & 31u;
+                a ^= p.A4[2];
+            };
+            // variable 3 (between the two blocks of 8 of an aligned 16): step
+            // row and adjacency row in the parameters
+            auto flip3 = [&]() {
+                Jl += ((uint32_t)a >> 1) & 4u;
+                a ^= p.A4[3];
+                step(p.R[3]);
+            };
+            auto load_row = [&](int i, uint32_t (&fr)[RW]) {
 #pragma unroll
                 for (uint32_t w4 = 0; w4 < RW; w4 += 4) {
                     const uint4 t4 = *reinterpret_cast<const uint4*>(sF + i * RW + w4);
                     fr[w4] = t4.x; fr[w4 + 1] = t4.y; fr[w4 + 2] = t4.z; fr[w4 + 3] = t4.w;
                 }
-                uint32_t d0 = 0, d1 = 0;
-#pragma unroll
-                for (int w = 0; w < NWL; w++) {
-                    d0 += __popc(L[NWN + w] & fr[NW + w]);
-                    d1 += __popc(L[NWN + w] & fr[NW + NWL + w]);
+            };
+            auto ctz64 = [](uint64_t v) -> int {
+                const uint32_t vl = (uint32_t)v;
+                return vl ? __ffs(vl) - 1 : 31 + __ffs((uint32_t)(v >> 32));
+            };
+            for (;;) {
+                if ((t & 15u) == 0 && tend - t >= 16) {
+                    // aligned blocks of 16: two lookups, the flip of variable 3
+                    // between them, and the flip of variable ctz(t + 16) >= 4
+                    // after them, whose step row and adjacency row are read
+                    // from shared memory before the block's lookups so that
+                    // their latency overlaps the block's work
+                    for (;;) {
+                        const uint64_t tn = t + 16;
+                        const bool more = tn < tend;     // tn < 2^k: ctz(tn) < k
+                        const int i = more ? ctz64(tn) : 0;
+                        uint32_t fr[RW];
+                        load_row(i, fr);
+                        const uint64_t adj = sADJ[i];
+                        block8();
+                        flip3();
+                        block8();
+                        t = tn;
+                        if (!more) break;
+                        Jl += ((uint32_t)(a >> i) & 1u) << 2;
+                        a ^= adj;
+                        step(fr);
+                        if (tend - t < 16) break;
+                    }
+                    if (t >= tend) break;
                 }
-                Jl += fr[NW + 2 * NWL] - 2u * d0 - 4u * d1;
-#pragma unroll
-                for (int w = 0; w < NW; w++) L[w] ^= fr[w];
+                if ((t & 7u) == 0 && tend - t >= 8) {
+                    block8();
+                    t += 7;
+                } else if constexpr (LANE) {
+                    atomicAdd(wl + ((((Jl & 7u) << tsh) + node_count()) << 5), 1u);
+                } else {
+                    atomicAdd(wc + plane_base() + (Jl & 7u) * ts + node_count(), 1u);
+                }
+                if (++t >= tend) break;
+                // flip variable i = ctz(t): 4 (A x)_i for the quadratic part,
+                // the step row for the linear part
+                if (((uint32_t)t & 15u) == 8u) {
+                    flip3();
+                } else {
+                    const int i = ctz64(t);
+                    Jl += ((uint32_t)(a >> i) & 1u) << 2;
+                    a ^= sADJ[i];
+                    uint32_t fr[RW];
+                    load_row(i, fr);
+                    step(fr);
+                }
             }
         }
         if (fold_each) fold(true);
@@ -418,9 +528,9 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                                      uint64_t count, uint64_t span, uint64_t nslices,
                                      uint64_t s_begin, uint64_t stride, bool fold_each,
                                      bool clear_on_exit, bool final_fold, zw64& acc) {
-    if constexpr (HIST == 4) {
-        walk_lut<NWN, NWL, XTRA>(p, sm, first, count, span, nslices, s_begin, stride, fold_each,
-                                 clear_on_exit, final_fold, acc);
+    if constexpr (HIST == 4 || HIST == 5) {
+        walk_lut<NWN, NWL, XTRA, HIST == 5>(p, sm, first, count, span, nslices, s_begin, stride,
+                                            fold_each, clear_on_exit, final_fold, acc);
         return;
     }
     constexpr int NW = NWN + NWL;

@@ -167,6 +167,7 @@ int build_plan(const PS& ps, Plan* out) {
         kp.Z[(bit - base) >> 5] |= 1u << (bit & 31);
     }
     pl.adj.assign(adj, adj + k);
+    for (uint32_t i = 0; i < 4 && i < k; i++) kp.A4[i] = adj[i];
     // seek tables (stride padded to a multiple of 4 words for vector loads)
     pl.seek_stride = (nw + 3 + 3) & ~3u;
     const uint32_t nnib = (k + 3) / 4;
@@ -189,7 +190,7 @@ int build_plan(const PS& ps, Plan* out) {
             e[nw + 2] = q;
         }
 
-    // step rows (the lowest three also in the kernel parameters, zero rows
+    // step rows (the lowest four also in the kernel parameters, zero rows
     // for variables beyond k)
     {
         const int nwl_k = pl.nwl < 1 ? 1 : pl.nwl;
@@ -214,13 +215,19 @@ int build_plan(const PS& ps, Plan* out) {
             }
             r[nw + 2 * nwl_k] = S & 7u;
         }
-        for (uint32_t i = 0; i < 3 && i < k; i++)
+        for (uint32_t i = 0; i < 4 && i < k; i++)
             for (uint32_t w = 0; w < rw; w++) kp.R[i][w] = pl.rows[(size_t)i * rw + w];
     }
 
     // block lookup (see plan.h)
     if (lut_try) {
-        const uint32_t nU = lut_nn + lut_no, stride = pl.m_odd + 1;
+        // lane-private counters: one row of 2^tsh >= m_odd + 1 counters per
+        // phase exponent mod 8, at most kLaneCounters per lane
+        uint32_t tsh = 0;
+        while ((1u << tsh) < pl.m_odd + 1) tsh++;
+        pl.lut_lane = pair_masks.empty() && zero.empty() && (8u << tsh) <= (uint32_t)kLaneCounters;
+        kp.lut_tsh = pl.lut_lane ? tsh : 0u;
+        const uint32_t nU = lut_nn + lut_no, stride = pl.lut_lane ? (1u << tsh) : pl.m_odd + 1;
         const uint32_t mo = (1u << lut_no) - 1, mn = (1u << lut_nn) - 1;
         const int nwn_k = pl.nwn;
         uint32_t fo[3], fn[3];
@@ -279,7 +286,8 @@ int build_plan(const PS& ps, Plan* out) {
         }
         pl.lut.assign(((size_t)1 << nU) + 8, 0ull);
         for (uint32_t Ln = 0; Ln < (1u << lut_nn); Ln++)
-            for (uint32_t Lo = 0; Lo < (1u << lut_no); Lo++) pl.lut[((size_t)Ln << lut_no) | Lo] = eo[Lo] + en[Ln];
+            for (uint32_t Lo = 0; Lo < (1u << lut_no); Lo++)
+                pl.lut[lut_slot((Ln << lut_no) | Lo)] = eo[Lo] + en[Ln];
         for (uint32_t h = 0; h < 8; h++) {
             uint32_t a = h, Q = 0;
             uint64_t e = 0;

@@ -40,9 +40,15 @@ ZXP_HD constexpr uint32_t row_words(int nwn, int nwl) {
 constexpr int kMaxRowWords = (int)row_words(kMaxWordsNode, kMaxWordsOther);
 // Block lookup (variant 9): at most this many forms may hold one of the
 // variables 0, 1, 2 (the lookup has 2^bits entries of 8 bytes), and the
-// counters span kLutRows rows of the term table.
+// counters span kLutRows rows of the term table.  Entry u is stored at
+// lut_slot(u): bits 4-11 of u are folded into bits 0-3 (an involution), so
+// that lanes whose u differ only in high bits read different bank pairs.
 constexpr int kLutMaxBits = 10;
 constexpr int kLutRows = 24;
+// Block lookup with lane-private counters (variant 11): a lane's counters are
+// indexed by (J mod 8) * 2^lut_tsh + M, so at most this many per lane.
+constexpr int kLaneCounters = 64;
+ZXP_HD constexpr uint32_t lut_slot(uint32_t u) { return u ^ (((u >> 4) ^ (u >> 8)) & 15u); }
 
 // Passed by value as the kernel parameter block (kept in the constant bank).
 struct KernelParams {
@@ -60,11 +66,13 @@ struct KernelParams {
     uint32_t C0[kMaxWordsOther], C1[kMaxWordsOther], C2[kMaxWordsOther], Z[kMaxWordsOther];
     uint32_t INV[kMaxNW];    // initial inversion of each form bit
     uint16_t PA[kMaxPairs], PB[kMaxPairs];            // bit positions of pair forms
-    uint32_t R[3][kMaxRowWords];                      // step rows of variables 0, 1, 2
+    uint32_t R[4][kMaxRowWords];                      // step rows of variables 0, 1, 2, 3
     // block lookup: forms holding variable 0, 1 or 2 are node bits [0, lut_nn)
     // and linear bits [lut_shift, lut_shift + lut_no) of the first other word
     // (after the phase-pair bits)
     uint32_t lut_no, lut_nn, lut_shift;
+    uint32_t lut_tsh;        // variant 11: log2 of the counter row stride (>= m_odd + 1)
+    uint64_t A4[4];          // adjacency rows of variables 0..3 (0 beyond k)
 };
 
 struct Plan {
@@ -97,8 +105,13 @@ struct Plan {
     // counter from the block's base, dJ_s * stride + dM_s + lut_nn, and in
     // byte 7 dJ_7; the 8 entries after them, indexed by the three bits h of
     // A x for variables 0-2, add the quadratic part 4 Q_s * stride (byte 7:
-    // 4 Q_7, and h at the end of the block in bits 5-7).
+    // 4 Q_7, and h at the end of the block in bits 5-7).  With lut_lane
+    // (no phase-pair or zero forms, at most 7 odd nodes) the row stride in
+    // the offsets is 2^lut_tsh instead of m_odd + 1, so that a counter index
+    // (J mod 8) * 2^lut_tsh + M is the sum of the block's base and the offset
+    // taken modulo 8 * 2^lut_tsh.
     bool lut_ok = false;
+    bool lut_lane = false;
     std::vector<uint64_t> lut;
 };
 

@@ -33,7 +33,7 @@ using KernelFn = void (*)(const KernelParams, const zw64*, const zw64*, const ui
 extern const KernelFn kTable[3][kMaxWordsNode + 1][kMaxWordsOther];   // kernel.cu
 extern const KernelFn kHist[4][2][kMaxWordsOther];                    // kernel_count.cu (nwn <= 1)
 extern const KernelFn kShared[2][kMaxWordsNode + 1][kMaxWordsOther];  // kernel_count.cu
-extern const KernelFn kLut[2][2][kMaxWordsOther];                              // block lookup
+extern const KernelFn kLut[3][2][kMaxWordsOther];                              // block lookup
 
 namespace {
 
@@ -51,7 +51,7 @@ __device__ __forceinline__ void publish_result(DevResult* r, uint64_t c0, uint64
 }
 
 template <int NWN, int NWL, int VAR>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, VAR == 11 ? 2 : (VAR >= 9 ? 5 : 1))
 sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtable,
            const zw64* __restrict__ gpv, const uint32_t* __restrict__ gR,
            const uint64_t* __restrict__ gADJ, const uint32_t* __restrict__ gS, uint64_t first,
@@ -64,7 +64,8 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_bar;
     const uint32_t ntab = p.tab_size;
-    const Smem sm = carve<NW, HIST>(smem_raw, ntab, p.npairs);
+    const Smem sm = carve<NW, HIST>(smem_raw, ntab, p.npairs, k_cap(p.k),
+                                    HIST >= 4 ? lut_cap(p.lut_no + p.lut_nn) : 0u);
     if (threadIdx.x == 0) mbar_init(&s_bar);
     if (HIST) {
         uint4* h4 = reinterpret_cast<uint4*>(sm.sH);

@@ -225,11 +225,13 @@ def test_range_errors(ctx):
 
 def test_block_lookup_variant_matches_oracle(ctx):
     """Scalars whose low variables touch few forms take the block-lookup
-    kernel (variant 9; 10 with folded phase-pair / zero bits); full sums and
-    ragged ranges equal the oracle."""
+    kernel (variant 9; 10 with folded phase-pair / zero bits; 11 with
+    lane-private counters and the phase row taken mod 8 by a mask); full sums
+    and ragged ranges equal the oracle."""
     rng = random.Random(21)
     seen = 0
     seen10 = 0
+    seen11 = 0
     blobs = []
     for seed in range(60, 140):
         w = zi.workload_batch_item(seed)
@@ -246,10 +248,11 @@ def test_block_lookup_variant_matches_oracle(ctx):
                                      density=rng.choice([0.2, 0.4])).pack())
     for blob in blobs:
         s = Z.zxp_scalar_from_tables(blob)
-        if s.info["kernel_variant"] not in (9, 10):
+        if s.info["kernel_variant"] not in (9, 10, 11):
             continue
         seen += 1
         seen10 += s.info["kernel_variant"] == 10
+        seen11 += s.info["kernel_variant"] == 11
         k = s.info["k"]
         N = 1 << k
         ranges = [(0, N), (5, N - 11), (N // 3, N // 2), (N - 9, 9)] if N >= 32 else [(0, N), (1, N - 2)]
@@ -259,7 +262,7 @@ def test_block_lookup_variant_matches_oracle(ctx):
             g = Z.zxp_eval(ctx, s, first, count)
             o = oracle.ps_sum(blob, first, count, nthreads=NCPU)
             assert same_raw(g, o), (k, first, count)
-    assert seen >= 5 and seen10 >= 2
+    assert seen >= 5 and seen10 >= 2 and seen11 >= 2
 
 
 def test_large_compiled_t50_subranges(ctx):
@@ -278,7 +281,8 @@ def test_large_compiled_t50_subranges(ctx):
 
 
 @pytest.mark.parametrize("seed,n_node,n_pair,odd,density", [
-    (62, 5, 0, True, 0.05),     # block lookup
+    (62, 5, 0, True, 0.05),     # block lookup, lane-private counters
+    (66, 10, 0, True, 0.03),    # block lookup, warp-shared counters (more than 7 odd nodes)
     (63, 14, 1, False, 0.05),   # block lookup with folded bits
     (64, 14, 0, True, 0.4),     # warp-shared counters (too many forms on the low variables)
     (65, 40, 3, False, 0.3),    # general: Z[w] phase-pair products
@@ -312,5 +316,18 @@ def test_block_lookup_smallest_k(ctx):
             g = Z.zxp_eval(ctx, s, first, count)
             o = oracle.ps_sum(blob, first, count)
             assert same_raw(g, o), (i, first, count)
-        n += s.info["kernel_variant"] == 9
+        n += s.info["kernel_variant"] == 11
     assert n >= 10
+    # more than 7 odd nodes: warp-shared counters
+    n9 = 0
+    for i in range(20):
+        ps = zi.synthetic_ps(1100 + i, 3, n_lin=1, n_quad=rng.randint(0, 3), n_node=8,
+                             odd_nodes_only=True, density=0.5)
+        blob = ps.pack()
+        s = Z.zxp_scalar_from_tables(blob)
+        for first, count in [(0, 8), (1, 6), (3, 5)]:
+            g = Z.zxp_eval(ctx, s, first, count)
+            o = oracle.ps_sum(blob, first, count)
+            assert same_raw(g, o), (i, first, count)
+        n9 += s.info["kernel_variant"] == 9
+    assert n9 >= 5

@@ -35,7 +35,9 @@ KernelFn pick(const Plan& pl) {
 }  // namespace
 
 cudaError_t ensure_dynamic_smem(const void* fn, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
+    // (set even below 48 KB: the default limit covers static and dynamic
+    // shared memory together, and the kernels have static shared memory)
+    if (bytes == 0) return cudaSuccess;
     static std::mutex mu;
     static std::map<std::pair<int, const void*>, size_t> set;   // (device, kernel) -> limit
     int dev = 0;
@@ -49,15 +51,17 @@ cudaError_t ensure_dynamic_smem(const void* fn, size_t bytes) {
     return e;
 }
 
+static size_t smem_for(const Plan& pl, int threads) {
+    const int h = hist_mode(pl);
+    return smem_bytes(pl.kp.tab_size, pl.kp.npairs, pl.nwn, kernel_words(pl) - pl.nwn, h, threads,
+                      k_cap(pl.kp.k), h >= 4 ? lut_cap(pl.kp.lut_no + pl.kp.lut_nn) : 0u);
+}
+
 // Threads per block: 128 for the lane-private block lookup (32 KB of
 // counters per 128 threads), else 256.
 static int block_threads(const Plan& pl) { return hist_mode(pl) == 5 ? 128 : kThreads; }
 
-size_t sum_smem_bytes(const Plan& pl) {
-    const int h = hist_mode(pl);
-    return smem_bytes(pl.kp.tab_size, pl.kp.npairs, pl.nwn, kernel_words(pl) - pl.nwn, h, block_threads(pl),
-                      k_cap(pl.kp.k), h >= 4 ? lut_cap(pl.kp.lut_no + pl.kp.lut_nn) : 0u);
-}
+size_t sum_smem_bytes(const Plan& pl) { return smem_for(pl, block_threads(pl)); }
 
 uint64_t sum_max_span(const Plan& pl) { return max_span(hist_mode(pl)); }
 

@@ -487,10 +487,18 @@ def main():
         opsl = alg_ops_per_term(il["node_words"], il["other_words"], il["n_pair"])
         achl = opsl * nl / (msl / 1e3) / 1e9
         peak = SM_COUNT_GB300 * ISSUE_LANES_PER_SM_CLK * 2070e6 / 1e9
+        prof_l = profile_fields(kernel_source_sha(), "sum_kernel_large37.txt")
+        ipt_l = profile_number(prof_l, "instructions_per_term")
+        iss_l = None if ipt_l is None else ipt_l * nl / (msl / 1e3) / 1e9
         large_c = {"workload": f"{wl.name} seed=0: one exact amplitude", "k": il["k"], "terms": nl,
                    "ms": msl, "terms_per_s": nl / (msl / 1e3), "kernel_variant": il["kernel_variant"],
                    "roofline": {"bound": "alu", "achieved": achl, "peak": peak, "unit": "Gop/s",
-                                "frac": achl / peak, "ops_per_term": opsl},
+                                "frac": achl / peak, "ops_per_term": opsl,
+                                "traffic": profile_number(prof_l, "dram_bytes_per_launch"),
+                                "issue": {"instructions_per_term": ipt_l, "achieved": iss_l,
+                                          "frac": None if iss_l is None else iss_l / peak,
+                                          "source": "thread instructions per term of the committed "
+                                                    "ncu capture (profiles/sum_kernel_large37.txt)"}},
                    "clocks": clkl.summary()}
 
     # batched workload: 512 circuits (n ~ U[10,40], T ~ U[20,60]), one

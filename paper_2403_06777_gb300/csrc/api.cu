@@ -153,8 +153,10 @@ int check_range(const zxp_scalar* s, uint64_t first, uint64_t count) {
     return ZXP_OK;
 }
 
-// Queue one range on ctx->stream: the raw partial into dres.
-int enqueue(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, DevResult* dres) {
+// Queue one range on ctx->stream: the raw partial into dres (pinned host
+// memory that the host polls when host_result, else device memory).
+int enqueue(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, DevResult* dres,
+            bool host_result) {
     DevTables d;
     int st = ensure_device_tables(s, ctx, &d);
     if (st != ZXP_OK) return st;
@@ -162,7 +164,7 @@ int enqueue(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, D
     int grid;
     launch_shape(ctx, s->plan, count, &span, &grid);
     return cuda_status(sum_launch(s->plan, d.table, d.pv, d.rows, d.adj, d.seek, first, count, span,
-                                  grid, ctx->acc, ctx->counter, dres, ctx->stream));
+                                  grid, ctx->acc, ctx->counter, dres, host_result, ctx->stream));
 }
 
 }  // namespace
@@ -385,7 +387,7 @@ int zxp_eval(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, 
     if (count == 0 || s->plan.zero) { from_zw(zw_zero(), s->ps.e0, 1, out); return ZXP_OK; }
     DeviceGuard g(ctx->device);
     ctx->hres->flags = 0;
-    st = enqueue(ctx, s, first, count, ctx->hres_dev);   // the kernel writes the pinned result
+    st = enqueue(ctx, s, first, count, ctx->hres_dev, true);   // the kernel writes the pinned result
     if (st != ZXP_OK) return st;
     if ((st = wait_published(ctx->stream, ctx->hres, -1)) != ZXP_OK) return st;
     memcpy(out, ctx->hres, sizeof *out);
@@ -398,7 +400,7 @@ int zxp_eval_device(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t 
     int st = check_range(s, first, count);
     if (st != ZXP_OK) return st;
     DeviceGuard g(ctx->device);
-    return enqueue(ctx, s, first, count, reinterpret_cast<DevResult*>(dev_out));
+    return enqueue(ctx, s, first, count, reinterpret_cast<DevResult*>(dev_out), false);
 }
 
 int zxp_zomega_canon(const zxp_zomega* in, zxp_zomega* out) {
@@ -443,7 +445,7 @@ int zxp_submit(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count
             }
         }
         t.hres->flags = 0;
-        st = enqueue(ctx, s, first, count, t.dres);   // the kernel writes the pinned result
+        st = enqueue(ctx, s, first, count, t.dres, true);   // the kernel writes the pinned result
         if (st != ZXP_OK) { ctx->free_slots.push_back(t); return st; }
     }
     *ticket = ctx->next_ticket++;
@@ -834,5 +836,5 @@ extern "C" int zxp_eval_noalloc(const zxp_scalar* s, uint64_t first, uint64_t co
                                   reinterpret_cast<const uint32_t*>(base + o_seek), first, count, sp,
                                   (int)g, reinterpret_cast<zw64*>(base + kNoAllocAccOff),
                                   reinterpret_cast<unsigned int*>(base),
-                                  reinterpret_cast<DevResult*>(dev_out), stream));
+                                  reinterpret_cast<DevResult*>(dev_out), false, stream));
 }

@@ -38,12 +38,12 @@ struct DevResult {
 // over `grid` blocks.  acc (4 x 64-bit accumulator) and *counter must be 0
 // on entry and are 0 again when the kernel ends; *result receives
 // K * (sum of the table terms) over sqrt2^e0, flagged raw, its flags word
-// written last (system-scope release) so that a host may poll it in pinned
-// memory.
+// written last with a release store (system scope when host_result: a host
+// may poll it in pinned memory; else device scope).
 cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, const uint32_t* drows,
                        const uint64_t* dADJ, const uint32_t* dS, uint64_t first, uint64_t count,
                        uint64_t span, int grid, zw64* acc, unsigned int* counter,
-                       DevResult* result, cudaStream_t stream);
+                       DevResult* result, bool host_result, cudaStream_t stream);
 
 // ---- batches (batch.cu) -----------------------------------------------------
 

@@ -200,13 +200,51 @@ constexpr uint32_t kWaitTries = 1u << 22;
 
 __device__ __forceinline__ uint32_t round16(uint32_t b) { return (b + 15u) & ~15u; }
 
-// Copy one scalar's tables into shared memory with bulk copies issued by
-// thread 0 on the mbarrier `bar` (initialised, count 1), then wait for the
-// barrier's phase `phase` (bounded; phase counts the loads so far and is
-// advanced here).  Every thread calls it; the caller
-// synchronises the block before and after.  Returns false if the wait gave
-// up (the tables are then not valid).  Variables 0..2 beyond k get zero
-// adjacency rows.
+// Copy one scalar's tables into shared memory with bulk copies on the
+// mbarrier `bar` (initialised, count 1).  Called by one thread; the copies
+// complete the barrier's current phase.
+template <int NWN, int NWL, bool GENERAL, int HIST>
+__device__ __forceinline__ void issue_tables(const KernelParams& p, const Smem& sm,
+                                             const zw64* __restrict__ gtable,
+                                             const zw64* __restrict__ gpv,
+                                             const uint32_t* __restrict__ gR,
+                                             const uint64_t* __restrict__ gADJ,
+                                             const uint32_t* __restrict__ gS, uint64_t* bar) {
+    constexpr int NW = NWN + NWL;
+    constexpr uint32_t RW = row_words(NWN, NWL);
+    const uint32_t ns = ((p.k + 3) / 4) * 16u * seek_stride(NW);
+    const uint32_t bt = p.tab_size * 32u, bs = ns * 4u, br = p.k * RW * 4u, ba = round16(p.k * 8u);
+    const uint32_t bpv = GENERAL ? 4u * p.npairs * 32u : 0u;
+    const uint32_t bl = HIST >= 4 ? round16(((1u << (p.lut_no + p.lut_nn)) + 8u) * 8u) : 0u;
+    // order the shared-memory reads of a previous scalar before the
+    // asynchronous writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, bt + bs + br + ba + bpv + bl);
+    if (bt) bulk_copy(sm.sT, gtable, bt, bar);
+    if (bs) bulk_copy(sm.sS, gS, bs, bar);
+    if (br) bulk_copy(sm.sF, gR, br, bar);
+    if (ba) bulk_copy(sm.sADJ, gADJ, ba, bar);
+    if (bpv) bulk_copy(sm.sPV, gpv, bpv, bar);
+    if (bl) bulk_copy(sm.sL, gS + ns, bl, bar);   // the block lookup follows the seek tables
+}
+
+// Wait (bounded) for the copies of issue_tables: the barrier's phase
+// `phase` (the loads so far; advanced here).  Every thread calls it, after
+// a block barrier that follows the barrier's initialisation.  Returns false
+// if the wait gave up (the tables are then not valid).  Variables 0..2
+// beyond k get zero adjacency rows.
+__device__ __forceinline__ bool wait_tables(const KernelParams& p, const Smem& sm, uint64_t* bar,
+                                            uint32_t& phase) {
+    bool ok = false;
+    for (uint32_t i = 0; i < kWaitTries; i++)
+        if (mbar_try_wait(bar, phase & 1u)) { ok = true; break; }
+    phase++;
+    if (threadIdx.x < 3 && threadIdx.x >= p.k) sm.sADJ[threadIdx.x] = 0;
+    return ok;
+}
+
+// issue_tables by thread 0, then wait_tables; the caller synchronises the
+// block before and after.
 template <int NWN, int NWL, bool GENERAL, int HIST>
 __device__ __forceinline__ bool load_tables(const KernelParams& p, const Smem& sm,
                                             const zw64* __restrict__ gtable,
@@ -215,30 +253,8 @@ __device__ __forceinline__ bool load_tables(const KernelParams& p, const Smem& s
                                             const uint64_t* __restrict__ gADJ,
                                             const uint32_t* __restrict__ gS, uint64_t* bar,
                                             uint32_t& phase) {
-    constexpr int NW = NWN + NWL;
-    constexpr uint32_t RW = row_words(NWN, NWL);
-    const uint32_t ns = ((p.k + 3) / 4) * 16u * seek_stride(NW);
-    const uint32_t bt = p.tab_size * 32u, bs = ns * 4u, br = p.k * RW * 4u, ba = round16(p.k * 8u);
-    const uint32_t bpv = GENERAL ? 4u * p.npairs * 32u : 0u;
-    const uint32_t bl = HIST >= 4 ? round16(((1u << (p.lut_no + p.lut_nn)) + 8u) * 8u) : 0u;
-    if (threadIdx.x == 0) {
-        // order the shared-memory reads of a previous scalar before the
-        // asynchronous writes
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(bar, bt + bs + br + ba + bpv + bl);
-        if (bt) bulk_copy(sm.sT, gtable, bt, bar);
-        if (bs) bulk_copy(sm.sS, gS, bs, bar);
-        if (br) bulk_copy(sm.sF, gR, br, bar);
-        if (ba) bulk_copy(sm.sADJ, gADJ, ba, bar);
-        if (bpv) bulk_copy(sm.sPV, gpv, bpv, bar);
-        if (bl) bulk_copy(sm.sL, gS + ns, bl, bar);   // the block lookup follows the seek tables
-    }
-    bool ok = false;
-    for (uint32_t i = 0; i < kWaitTries; i++)
-        if (mbar_try_wait(bar, phase & 1u)) { ok = true; break; }
-    phase++;
-    if (threadIdx.x < 3 && threadIdx.x >= p.k) sm.sADJ[threadIdx.x] = 0;
-    return ok;
+    if (threadIdx.x == 0) issue_tables<NWN, NWL, GENERAL, HIST>(p, sm, gtable, gpv, gR, gADJ, gS, bar);
+    return wait_tables(p, sm, bar, phase);
 }
 
 // Walk the slices s = s_begin + lane, s_begin + stride + lane, ... (< nslices)
@@ -289,6 +305,10 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
     const uint32_t tsh = p.lut_tsh, cm = (8u << tsh) - 1u;
     uint32_t* const lbase = sm.sH + warp * ((uint32_t)kLaneCounters * 32u);
     uint32_t* const wl = lbase + lane;
+    unsigned char* const wlb = reinterpret_cast<unsigned char*>(wl);
+    const uint32_t rb = p.lane_row_bytes;
+    // lane-private counter idx: one multiply-add for its address
+    auto lctr = [&](uint32_t idx) { return reinterpret_cast<uint32_t*>(wlb + idx * rb); };
 
     // counter i = x * plane + row * ts + m holds table entry
     // (((row mod 8) * ts + m) << xshift) | x, and (row mod 8) * ts + m = i mod 8 ts
@@ -302,6 +322,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
             // counter i holds table entry (i >> tsh) * ts + (i & (2^tsh - 1))
             const uint32_t tm = (1u << tsh) - 1u;
             for (uint32_t i = lane; i <= cm; i += 32) {
+                if ((i & tm) >= ts) continue;   // M < ts: never counted, never cleared
                 uint4* row = reinterpret_cast<uint4*>(lbase + i * 32u);
                 uint32_t c = 0;
 #pragma unroll
@@ -309,8 +330,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                     const uint4 v = row[(j + lane) & 7u];
                     c += v.x + v.y + v.z + v.w;
                 }
-                const uint32_t m = i & tm;
-                if (c && m < ts) acc = zw_madd32(acc, lds_zw(sT + (i >> tsh) * ts + m), c);
+                if (c) acc = zw_madd32(acc, lds_zw(sT + (i >> tsh) * ts + (i & tm)), c);
                 if (clear) {
 #pragma unroll
                     for (uint32_t j = 0; j < 8; j++) row[(j + lane) & 7u] = make_uint4(0, 0, 0, 0);
@@ -423,14 +443,14 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                     const uint32_t b0 = ((Jl & 7u) << tsh) + node_count();
                     const uint32_t bx = ((b0 - nn) & cm) * 0x01010101u, mk = cm * 0x01010101u;
                     const uint32_t w0 = (lo + bx) & mk, w1 = (hi + bx) & mk;
-                    atomicAdd(wl + (b0 << 5), 1u);
-                    atomicAdd(wl + ((w0 & 0xFFu) << 5), 1u);
-                    atomicAdd(wl + (((w0 >> 8) & 0xFFu) << 5), 1u);
-                    atomicAdd(wl + (((w0 >> 16) & 0xFFu) << 5), 1u);
-                    atomicAdd(wl + ((w0 >> 24) << 5), 1u);
-                    atomicAdd(wl + ((w1 & 0xFFu) << 5), 1u);
-                    atomicAdd(wl + (((w1 >> 8) & 0xFFu) << 5), 1u);
-                    atomicAdd(wl + (((w1 >> 16) & 0xFFu) << 5), 1u);
+                    atomicAdd(lctr(b0), 1u);
+                    atomicAdd(lctr(w0 & 0xFFu), 1u);
+                    atomicAdd(lctr((w0 >> 8) & 0xFFu), 1u);
+                    atomicAdd(lctr((w0 >> 16) & 0xFFu), 1u);
+                    atomicAdd(lctr(w0 >> 24), 1u);
+                    atomicAdd(lctr(w1 & 0xFFu), 1u);
+                    atomicAdd(lctr((w1 >> 8) & 0xFFu), 1u);
+                    atomicAdd(lctr((w1 >> 16) & 0xFFu), 1u);
                 } else {
                     const int base = (int)(plane_base() + (Jl & 7u) * ts + node_count()) - (int)nn;
                     uint32_t* const wb = wc + base;
@@ -496,7 +516,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                     block8();
                     t += 7;
                 } else if constexpr (LANE) {
-                    atomicAdd(wl + ((((Jl & 7u) << tsh) + node_count()) << 5), 1u);
+                    atomicAdd(lctr(((Jl & 7u) << tsh) + node_count()), 1u);
                 } else {
                     atomicAdd(wc + plane_base() + (Jl & 7u) * ts + node_count(), 1u);
                 }

@@ -227,6 +227,7 @@ int build_plan(const PS& ps, Plan* out) {
         while ((1u << tsh) < pl.m_odd + 1) tsh++;
         pl.lut_lane = pair_masks.empty() && zero.empty() && (8u << tsh) <= (uint32_t)kLaneCounters;
         kp.lut_tsh = pl.lut_lane ? tsh : 0u;
+        kp.lane_row_bytes = 32u * 4u;
         const uint32_t nU = lut_nn + lut_no, stride = pl.lut_lane ? (1u << tsh) : pl.m_odd + 1;
         const uint32_t mo = (1u << lut_no) - 1, mn = (1u << lut_nn) - 1;
         const int nwn_k = pl.nwn;

@@ -73,6 +73,12 @@ struct KernelParams {
     uint32_t lut_no, lut_nn, lut_shift;
     uint32_t lut_tsh;        // variant 11: log2 of the counter row stride (>= m_odd + 1)
     uint64_t A4[4];          // adjacency rows of variables 0..3 (0 beyond k)
+    // variant 11: bytes between a lane's consecutive counters (32 lanes x 4
+    // bytes).  A parameter rather than a constant, so that the counter
+    // address is one multiply-add (not a shift and an add on the integer
+    // ALU, the kernel's busiest pipe).
+    uint32_t lane_row_bytes;
+    uint32_t _pad2;
 };
 
 struct Plan {

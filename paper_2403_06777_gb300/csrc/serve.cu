@@ -412,7 +412,7 @@ struct Scheduler {
             int grid = 1;
             sum_shape(pl, s->ctx->sm_count, s->ctx->max_grid, count, &sp, &grid);
             if (sum_launch(pl, d.table, d.pv, d.rows, d.adj, d.seek, planned[0].first, count, sp, grid,
-                           s->ctx->acc, s->ctx->counter, s->d_results + r->slot, stream) != cudaSuccess)
+                           s->ctx->acc, s->ctx->counter, s->d_results + r->slot, false, stream) != cudaSuccess)
                 return ZXP_ECUDA;
             launches = 1;
         } else {

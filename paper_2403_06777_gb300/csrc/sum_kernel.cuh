@@ -26,7 +26,7 @@ constexpr int kThreads = kMaxThreads;
 using KernelFn = void (*)(const KernelParams, const zw64*, const zw64*, const uint32_t*,
                           const uint64_t*, const uint32_t*, uint64_t, uint64_t,
                           uint64_t, uint64_t, zw64*, unsigned int*, const zw64, const int32_t,
-                          DevResult*);
+                          DevResult*, const int32_t);
 
 
 // variant tables: [variant][nwn][nwl - 1]
@@ -37,17 +37,21 @@ extern const KernelFn kLut[3][2][kMaxWordsOther];                              /
 
 namespace {
 
-// Write a result: its value, then its flags (never 0) with a system-scope
-// release store, so that a host polling the flags word of pinned memory
-// reads the value only after it is complete.
+// Write a result: its value, then its flags (never 0) with a release store:
+// system scope when a host polls the flags word in pinned memory (it then
+// reads the value only after it is complete), device scope for a result in
+// device memory.
 __device__ __forceinline__ void publish_result(DevResult* r, uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
-                                               int32_t e, int32_t flags) {
+                                               int32_t e, int32_t flags, bool host) {
     r->c[0] = (int64_t)c0;
     r->c[1] = (int64_t)c1;
     r->c[2] = (int64_t)c2;
     r->c[3] = (int64_t)c3;
     r->e = e;
-    cuda::atomic_ref<int32_t, cuda::thread_scope_system>(r->flags).store(flags, cuda::memory_order_release);
+    if (host)
+        cuda::atomic_ref<int32_t, cuda::thread_scope_system>(r->flags).store(flags, cuda::memory_order_release);
+    else
+        cuda::atomic_ref<int32_t, cuda::thread_scope_device>(r->flags).store(flags, cuda::memory_order_release);
 }
 
 template <int NWN, int NWL, int VAR>
@@ -57,7 +61,7 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
            const uint64_t* __restrict__ gADJ, const uint32_t* __restrict__ gS, uint64_t first,
            uint64_t count, uint64_t span,
            uint64_t nslices, zw64* __restrict__ acc_g, unsigned int* __restrict__ counter,
-           const zw64 K, const int32_t e0, DevResult* __restrict__ result) {
+           const zw64 K, const int32_t e0, DevResult* __restrict__ result, const int32_t host_result) {
     constexpr int NW = NWN + NWL;
     constexpr bool GENERAL = var_general(VAR);
     constexpr int HIST = var_hist(VAR);
@@ -66,16 +70,25 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
     const uint32_t ntab = p.tab_size;
     const Smem sm = carve<NW, HIST>(smem_raw, ntab, p.npairs, k_cap(p.k),
                                     HIST >= 4 ? lut_cap(p.lut_no + p.lut_nn) : 0u);
-    if (threadIdx.x == 0) mbar_init(&s_bar);
-    if (HIST) {
+    // the table copies are in flight while the counters are cleared
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar);
+        issue_tables<NWN, NWL, GENERAL, HIST>(p, sm, gtable, gpv, gR, gADJ, gS, &s_bar);
+    }
+    if (HIST == 5) {
+        // lane-private counters: only rows (J, M) with M < tab_stride are used
+        const uint32_t tsh = p.lut_tsh, tm = (1u << tsh) - 1u, nq = (uint32_t)kLaneCounters * 8u;
+        uint4* h4 = reinterpret_cast<uint4*>(sm.sH);
+        for (uint32_t i = threadIdx.x; i < (blockDim.x >> 5) * nq; i += blockDim.x)
+            if ((((i % nq) >> 3) & tm) < p.tab_stride) h4[i] = make_uint4(0, 0, 0, 0);
+    } else if (HIST) {
         uint4* h4 = reinterpret_cast<uint4*>(sm.sH);
         for (uint32_t i = threadIdx.x; i < counter_words(HIST, ntab, blockDim.x) / 4; i += blockDim.x)
             h4[i] = make_uint4(0, 0, 0, 0);
     }
     __syncthreads();
     uint32_t phase = 0;
-    const bool loaded =
-        load_tables<NWN, NWL, GENERAL, HIST>(p, sm, gtable, gpv, gR, gADJ, gS, &s_bar, phase);
+    const bool loaded = wait_tables(p, sm, &s_bar, phase);
     const bool ok = __syncthreads_and(loaded) != 0;
 
     zw64 acc = zw_zero();
@@ -103,7 +116,7 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
     if (threadIdx.x == 0) {
         const zw64 r = zw_mul(K, acc);
         if (gridDim.x == 1) {     // one block: its sum is the result
-            publish_result(result, r.c[0], r.c[1], r.c[2], r.c[3], e0, ok ? 1 : 3);
+            publish_result(result, r.c[0], r.c[1], r.c[2], r.c[3], e0, ok ? 1 : 3, host_result != 0);
             return;
         }
         if (!ok) atomicOr(counter, 0x80000000u);
@@ -121,7 +134,7 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
                 g[c] = 0ull;
             }
             *counter = 0u;       // ready for the next launch on this workspace
-            publish_result(result, v[0], v[1], v[2], v[3], e0, 1 | ((done >> 31) ? 2 : 0));
+            publish_result(result, v[0], v[1], v[2], v[3], e0, 1 | ((done >> 31) ? 2 : 0), host_result != 0);
         }
     }
 }

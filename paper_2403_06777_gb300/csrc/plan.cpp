@@ -4,7 +4,6 @@
 #include <string.h>
 
 #include <algorithm>
-#include <map>
 #include <vector>
 
 #include "zxp.h"
@@ -39,20 +38,24 @@ int build_plan(const PS& ps, Plan* out) {
     zw64 K = from_i64(ps.G);
     bool exact_zero = !(ps.G[0] | ps.G[1] | ps.G[2] | ps.G[3]);
 
-    // quadratic rows -> symmetric adjacency (+ 4 x_i on the diagonal)
-    std::map<uint64_t, uint32_t> lin;   // mask -> coefficient (mod 8)
+    // quadratic rows -> symmetric adjacency (+ 4 x_i on the diagonal); the
+    // linear coefficients are collected as (mask, c) terms and merged by
+    // mask (mod 8) once every row has contributed
+    std::vector<std::pair<uint64_t, uint32_t>> lin_terms;
+    lin_terms.reserve(ps.lin.size() + ps.node.size() + k);
     uint64_t adj[kMaxK] = {0};
+    const uint64_t kmask = k >= 64 ? ~0ull : (1ull << k) - 1;
     for (const QuadRow& q : ps.quad) {
         if (!q.a || !q.b) continue;     // 4 * 0 * l = 0
-        for (uint32_t i = 0; i < k; i++) {
-            uint64_t r = (((q.a >> i) & 1) ? q.b : 0) ^ (((q.b >> i) & 1) ? q.a : 0);
-            r &= ~(1ull << i);
-            adj[i] ^= r;
-            if (((q.a & q.b) >> i) & 1) lin[1ull << i] = (lin[1ull << i] + 4) & 7;
-        }
+        // row i gains b for every i in a and a for every i in b (bit i itself
+        // is cleared below); i in a & b also gives 4 x_i
+        for (uint64_t m = q.a & kmask; m; m &= m - 1) adj[__builtin_ctzll(m)] ^= q.b;
+        for (uint64_t m = q.b & kmask; m; m &= m - 1) adj[__builtin_ctzll(m)] ^= q.a;
+        for (uint64_t m = q.a & q.b & kmask; m; m &= m - 1) lin_terms.push_back({m & (0 - m), 4u});
     }
+    for (uint32_t i = 0; i < k; i++) adj[i] &= ~(1ull << i);
     for (const LinRow& l : ps.lin)
-        if (l.mask) lin[l.mask] = (lin[l.mask] + l.c) & 7;
+        if (l.mask) lin_terms.push_back({l.mask, l.c & 7u});
 
     // nodes
     std::vector<Form> odd, zero;
@@ -67,7 +70,7 @@ int build_plan(const PS& ps, Plan* out) {
         }
         if (g == 2 || g == 6) {        // 1 + w^(2+4l) = sqrt2 w w^(6l); 1 + w^(6+4l) = sqrt2 w^7 w^(2l)
             K = zw_rot(zw_mul_sqrt2(K), g == 2 ? 1 : 7);
-            lin[n.mask] = (lin[n.mask] + (g == 2 ? 6 : 2)) & 7;
+            lin_terms.push_back({n.mask, g == 2 ? 6u : 2u});
         } else if (g == 0 || g == 4) { // 2 when the effective exponent is 0, else 0
             K = zw_add(K, K);
             zero.push_back(Form{n.mask, g == 4 ? 1u : 0u});
@@ -100,8 +103,20 @@ int build_plan(const PS& ps, Plan* out) {
     K = zw_rot(K, 3 * nB);
 
     // layout
+    // linear forms in ascending mask order, coefficients summed mod 8, zero
+    // coefficients dropped
     std::vector<std::pair<uint64_t, uint32_t>> lins;
-    for (auto& e : lin) if (e.second) lins.push_back(e);
+    std::sort(lin_terms.begin(), lin_terms.end(),
+              [](const std::pair<uint64_t, uint32_t>& x, const std::pair<uint64_t, uint32_t>& y) {
+                  return x.first < y.first;
+              });
+    for (size_t i = 0; i < lin_terms.size();) {
+        uint32_t c = 0;
+        size_t j = i;
+        for (; j < lin_terms.size() && lin_terms[j].first == lin_terms[i].first; j++) c += lin_terms[j].second;
+        if (c & 7) lins.push_back({lin_terms[i].first, c & 7});
+        i = j;
+    }
     // block lookup candidates: no phase-pair or zero forms (their bits would
     // vary inside a block); forms holding variable 0, 1 or 2 go first
     const uint64_t low3 = 7;
@@ -137,8 +152,8 @@ int build_plan(const PS& ps, Plan* out) {
     pl.frows.assign((size_t)k * nw, 0u);
     auto put = [&](uint32_t bit, uint64_t mask, uint32_t inv) {
         if (inv) kp.INV[bit >> 5] |= 1u << (bit & 31);
-        for (uint32_t i = 0; i < k; i++)
-            if ((mask >> i) & 1) pl.frows[(size_t)i * nw + (bit >> 5)] |= 1u << (bit & 31);
+        for (uint64_t m = mask & kmask; m; m &= m - 1)
+            pl.frows[(size_t)__builtin_ctzll(m) * nw + (bit >> 5)] |= 1u << (bit & 31);
     };
     for (size_t j = 0; j < odd.size(); j++) {
         uint32_t bit = (uint32_t)j;
@@ -172,22 +187,21 @@ int build_plan(const PS& ps, Plan* out) {
     pl.seek_stride = (nw + 3 + 3) & ~3u;
     const uint32_t nnib = (k + 3) / 4;
     pl.seek.assign((size_t)nnib * 16 * pl.seek_stride, 0u);
+    // entry v is entry v' = v without its lowest bit i, plus variable 4b+i:
+    // its flip row, its adjacency row, and the quadratic bits of the pairs
+    // (i, j) with j in v' (every bit of v' is above i)
     for (uint32_t b = 0; b < nnib; b++)
-        for (uint32_t v = 0; v < 16; v++) {
+        for (uint32_t v = 1; v < 16; v++) {
+            const uint32_t i = (uint32_t)__builtin_ctz(v), vp = v & (v - 1), var = 4 * b + i;
             uint32_t* e = &pl.seek[((size_t)b * 16 + v) * pl.seek_stride];
-            uint64_t a = 0;
-            uint32_t q = 0;
-            for (uint32_t i = 0; i < 4; i++) {
-                const uint32_t var = 4 * b + i;
-                if (!((v >> i) & 1) || var >= k) continue;
-                for (uint32_t w = 0; w < nw; w++) e[w] ^= pl.frows[(size_t)var * nw + w];
-                for (uint32_t j = 0; j < i; j++)     // pairs inside the group
-                    if (((v >> j) & 1) && ((adj[var] >> (4 * b + j)) & 1)) q ^= 1u;
-                a ^= adj[var];
-            }
-            e[nw] = (uint32_t)a;
-            e[nw + 1] = (uint32_t)(a >> 32);
-            e[nw + 2] = q;
+            const uint32_t* ep = &pl.seek[((size_t)b * 16 + vp) * pl.seek_stride];
+            for (uint32_t w = 0; w < nw + 3; w++) e[w] = ep[w];
+            if (var >= k) continue;
+            for (uint32_t w = 0; w < nw; w++) e[w] ^= pl.frows[(size_t)var * nw + w];
+            const uint64_t a = adj[var];
+            e[nw] ^= (uint32_t)a;
+            e[nw + 1] ^= (uint32_t)(a >> 32);
+            e[nw + 2] ^= (uint32_t)__builtin_popcount((uint32_t)(a >> (4 * b)) & vp & 15u) & 1u;
         }
 
     // step rows (the lowest four also in the kernel parameters, zero rows
@@ -237,54 +251,70 @@ int build_plan(const PS& ps, Plan* out) {
             fn[i] = nwn_k ? (pl.frows[(size_t)i * nw] & mn) : 0u;
         }
         static const int seq[7] = {0, 1, 0, 2, 0, 1, 0};
-        // csum[v]: the sum of the coefficients of the linear forms in v;
-        // flipping variable i changes J by sum_{r in F_i} c_r (1 - 2 l_r) + 4 per
-        // class-B node bit it flips, and M by |F_i nodes| - 2 |F_i nodes & L|
-        std::vector<int> csum((size_t)1 << lut_no, 0);
-        for (uint32_t v = 1; v < (1u << lut_no); v++) {
-            const uint32_t r = (uint32_t)__builtin_ctz(v);
-            csum[v] = csum[v & (v - 1)] + (int)lins[r].second;
-        }
-        // node-bit counts by table (no popcount instruction needed on the host)
-        std::vector<int> pcount((size_t)1 << lut_nn, 0);
-        for (uint32_t v = 1; v < (1u << lut_nn); v++) pcount[v] = pcount[v & (v - 1)] + 1;
+        // Flipping variable i changes J by sum_{r in F_i} c_r (1 - 2 l_r) + 4
+        // per class-B node bit it flips, and M by the sum over its node bits of
+        // (1 - 2 l_r).  Each form's share of the change after steps 1..s
+        // depends only on its own bit at the block's first state, so an entry
+        // is a sum of per-form byte vectors (byte s-1: the share after step
+        // s; the phase shares taken mod 8, every byte sum below 256), built
+        // for all first states in Gray-code order, one vector update each.
+        auto share = [&](uint32_t r, const uint32_t* f, int weight, uint32_t b, int bias, bool mod8) {
+            uint32_t bit = b;
+            int acc = 0;
+            uint64_t v = 0;
+            for (int s = 1; s <= 7; s++) {
+                if ((f[seq[s - 1]] >> r) & 1) {
+                    acc += weight * (1 - 2 * (int)bit);
+                    bit ^= 1u;
+                }
+                v |= (uint64_t)(uint32_t)(mod8 ? (acc & 7) : acc + bias) << (8 * (s - 1));
+            }
+            return v;
+        };
+        auto gray_fill = [](uint32_t n, uint64_t s0, const uint64_t* d, std::vector<uint64_t>& out,
+                            auto finish) {
+            out.assign((size_t)1 << n, 0);
+            uint64_t sum = s0;
+            uint32_t x = 0;
+            out[0] = finish(sum);
+            for (uint32_t g = 1; g < (1u << n); g++) {
+                const uint32_t r = (uint32_t)__builtin_ctz(g);
+                x ^= 1u << r;
+                sum += ((x >> r) & 1) ? d[r] : (uint64_t)0 - d[r];
+                out[x] = finish(sum);
+            }
+        };
         uint32_t nb_mask = 0;
         for (uint32_t r = 0; r < lut_nn; r++) nb_mask |= (uint32_t)odd_b[r] << r;
-        int sJ[3], sM[3];
-        for (int i = 0; i < 3; i++) {
-            sJ[i] = csum[fo[i]] + 4 * pcount[fn[i] & nb_mask];
-            sM[i] = pcount[fn[i]];
-        }
-        // ΔJ depends on the linear bits only and ΔM on the node bits only, and
-        // no byte of an entry carries into the next (each is at most 255), so
-        // an entry is the sum of a linear-bit part and a node-bit part.
-        std::vector<uint64_t> eo((size_t)1 << lut_no), en((size_t)1 << lut_nn);
-        for (uint32_t Lo0 = 0; Lo0 < (1u << lut_no); Lo0++) {
-            uint32_t Lo = Lo0;
-            int dJ = 0;
-            uint64_t e = 0;
+        // linear part: bytes 0..6 hold (dJ_s mod 8) * stride, byte 7 dJ_7 mod 8
+        uint64_t so = 0, dout[kLutMaxBits], dnod[kLutMaxBits];
+        {
+            int acc = 0;   // class-B node bits: 4 per flip, whatever their state
             for (int s = 1; s <= 7; s++) {
-                const int i = seq[s - 1];
-                dJ += sJ[i] - 2 * csum[fo[i] & Lo];
-                Lo ^= fo[i];
-                const uint64_t j8 = (uint32_t)dJ & 7u;
-                e |= (j8 * stride) << (8 * (s - 1));
-                if (s == 7) e |= j8 << 56;
+                acc += 4 * __builtin_popcount(fn[seq[s - 1]] & nb_mask);
+                so |= (uint64_t)(uint32_t)(acc & 7) << (8 * (s - 1));
             }
-            eo[Lo0] = e;
         }
-        for (uint32_t Ln0 = 0; Ln0 < (1u << lut_nn); Ln0++) {
-            uint32_t Ln = Ln0;
-            int dM = 0;
-            uint64_t e = 0;
-            for (int s = 1; s <= 7; s++) {
-                const int i = seq[s - 1];
-                dM += sM[i] - 2 * pcount[fn[i] & Ln];
-                Ln ^= fn[i];
-                e |= (uint64_t)(uint32_t)(dM + (int)lut_nn) << (8 * (s - 1));
-            }
-            en[Ln0] = e;
+        for (uint32_t r = 0; r < lut_no; r++) {
+            const int c = (int)lins[r].second;
+            const uint64_t p0 = share(r, fo, c, 0, 0, true), p1 = share(r, fo, c, 1, 0, true);
+            so += p0;
+            dout[r] = p1 - p0;
         }
+        const uint64_t st = stride;
+        std::vector<uint64_t> eo, en;
+        gray_fill(lut_no, so, dout, eo, [st](uint64_t x) {
+            x &= 0x0007070707070707ull;
+            return x * st | ((x >> 48) << 56);
+        });
+        // node part: bytes 0..6 hold dM_s + lut_nn (each form's share + 1)
+        uint64_t sn = 0;
+        for (uint32_t r = 0; r < lut_nn; r++) {
+            const uint64_t q0 = share(r, fn, 1, 0, 1, false), q1 = share(r, fn, 1, 1, 1, false);
+            sn += q0;
+            dnod[r] = q1 - q0;
+        }
+        gray_fill(lut_nn, sn, dnod, en, [](uint64_t x) { return x; });
         pl.lut.assign(((size_t)1 << nU) + 8, 0ull);
         for (uint32_t Ln = 0; Ln < (1u << lut_nn); Ln++)
             for (uint32_t Lo = 0; Lo < (1u << lut_no); Lo++)

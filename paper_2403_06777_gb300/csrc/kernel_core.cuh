@@ -399,7 +399,15 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                 Jl = P0 + 2u * P1 + 4u * ((uint32_t)__popc(X2) + q);
             }
             // a = A x (all k bits): flipping variable i adds 4 (A x)_i to J and
-            // XORs adjacency row i into a
+            // XORs adjacency row i into a.  us = the lookup slot of the current
+            // state's bits (lut_slot is linear: each flip XORs its row's slot
+            // change, bits 8 and up of the row's last word)
+            uint32_t us;
+            {
+                uint32_t u = (L[NWN] >> lsh) & mo;
+                if (NWN) u |= (L[0] & mn) << no;
+                us = lut_slot(u);
+            }
 
             auto node_count = [&]() {
                 uint32_t M = 0;
@@ -425,6 +433,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                     d1 += __popc(L[NWN + w] & f[NW + NWL + w]);
                 }
                 Jl += f[NW + 2 * NWL] - 2u * d0 - 4u * d1;
+                us ^= f[NW + 2 * NWL] >> 8;
 #pragma unroll
                 for (int w = 0; w < NW; w++) L[w] ^= f[w];
             };
@@ -432,9 +441,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
             // net change: variable 2 flipped (Gray 000 -> 100), its forms, its
             // adjacency row and the block's phase change
             auto block8 = [&]() {
-                uint32_t u = (L[NWN] >> lsh) & mo;
-                if (NWN) u |= (L[0] & mn) << no;
-                const uint64_t e = sL[lut_slot(u)] + qlut[(uint32_t)a & 7u];
+                const uint64_t e = sL[us] + qlut[(uint32_t)a & 7u];
                 const uint32_t lo = (uint32_t)e, hi = (uint32_t)(e >> 32);
                 if constexpr (LANE) {
                     // the block's base (< 64) added to all offset bytes at once
@@ -467,6 +474,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                 for (int w = 0; w < NW; w++) L[w] ^= p.R[2][w];
                 Jl += (hi >> 24) & 31u;
                 a ^= p.A4[2];
+                us ^= p.U4[2];
             };
             // variable 3 (between the two blocks of 8 of an aligned 16): step
             // row and adjacency row in the parameters

@@ -227,7 +227,14 @@ int build_plan(const PS& ps, Plan* out) {
                          4u * (uint32_t)__builtin_popcount(f & kp.C2[o]);
                 }
             }
-            r[nw + 2 * nwl_k] = S & 7u;
+            uint32_t du = 0;
+            if (lut_try) {
+                const uint32_t fo_i = (r[pl.nwn] >> pair_masks.size()) & ((1u << lut_no) - 1u);
+                const uint32_t fn_i = pl.nwn ? (r[0] & ((1u << lut_nn) - 1u)) : 0u;
+                du = lut_slot((fn_i << lut_no) | fo_i);
+            }
+            r[nw + 2 * nwl_k] = (S & 7u) | (du << 8);
+            if (i < 4) kp.U4[i] = du;
         }
         for (uint32_t i = 0; i < 4 && i < k; i++)
             for (uint32_t w = 0; w < rw; w++) kp.R[i][w] = pl.rows[(size_t)i * rw + w];

@@ -78,6 +78,8 @@ struct KernelParams {
     // address is one multiply-add (not a shift and an add on the integer
     // ALU, the kernel's busiest pipe).
     uint32_t lane_row_bytes;
+    // block lookup: the lookup slot changes of variables 0..3 (see rows)
+    uint32_t U4[4];
     uint32_t _pad2;
 };
 
@@ -90,6 +92,10 @@ struct Plan {
     // exponent J = sum_lin c l + 4 (class-B node bits) by
     //   S_i - 2 |L & F_i & C0| - 4 |L & F_i & C1|  (mod 8, L before the flip)
     // with S_i = sum of c over the forms F_i holds + 4 per class-B node it holds.
+    // The row's last word holds S_i in bits 0-2 and, with the block lookup,
+    // the change of the block's lookup slot in bits 8 and up (the slot of
+    // the forms F_i holds among those the lookup reads, lut_slot being
+    // linear); only J mod 8 is ever used, so the high bits may ride along.
     std::vector<uint32_t> rows;
     uint32_t row_stride = 0;
     std::vector<uint64_t> adj;      // k: quadratic part 4 sum_{i<j} A_ij x_i x_j, row i

@@ -448,7 +448,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                     // (each sum < 256: no carry between bytes) and every byte
                     // taken mod 8 * 2^tsh by one mask
                     const uint32_t b0 = ((Jl & 7u) << tsh) + node_count();
-                    const uint32_t bx = ((b0 - nn) & cm) * 0x01010101u, mk = cm * 0x01010101u;
+                    const uint32_t bx = b0 * 0x01010101u, mk = cm * 0x01010101u;
                     const uint32_t w0 = (lo + bx) & mk, w1 = (hi + bx) & mk;
                     atomicAdd(lctr(b0), 1u);
                     atomicAdd(lctr(w0 & 0xFFu), 1u);
@@ -472,7 +472,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                 }
 #pragma unroll
                 for (int w = 0; w < NW; w++) L[w] ^= p.R[2][w];
-                Jl += (hi >> 24) & 31u;
+                Jl += hi >> 24;
                 a ^= p.A4[2];
                 us ^= p.U4[2];
             };
@@ -513,7 +513,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                         block8();
                         t = tn;
                         if (!more) break;
-                        Jl += ((uint32_t)(a >> i) & 1u) << 2;
+                        Jl += (uint32_t)(a >> i) << 2;   // (bits above 2: only J mod 8 is used)
                         a ^= adj;
                         step(fr);
                         if (tend - t < 16) break;
@@ -535,7 +535,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                     flip3();
                 } else {
                     const int i = ctz64(t);
-                    Jl += ((uint32_t)(a >> i) & 1u) << 2;
+                    Jl += (uint32_t)(a >> i) << 2;   // (bits above 2: only J mod 8 is used)
                     a ^= sADJ[i];
                     uint32_t fr[RW];
                     load_row(i, fr);

@@ -323,9 +323,15 @@ int build_plan(const PS& ps, Plan* out) {
         }
         gray_fill(lut_nn, sn, dnod, en, [](uint64_t x) { return x; });
         pl.lut.assign(((size_t)1 << nU) + 8, 0ull);
+        // lane-private counters: offsets taken mod 8 * 2^tsh with the bias
+        // lut_nn removed (the kernel adds the block's base and masks)
+        const uint64_t b7 = 0x0001010101010101ull, cm = (8ull << tsh) - 1;
         for (uint32_t Ln = 0; Ln < (1u << lut_nn); Ln++)
-            for (uint32_t Lo = 0; Lo < (1u << lut_no); Lo++)
-                pl.lut[lut_slot((Ln << lut_no) | Lo)] = eo[Lo] + en[Ln];
+            for (uint32_t Lo = 0; Lo < (1u << lut_no); Lo++) {
+                uint64_t e = eo[Lo] + en[Ln];
+                if (pl.lut_lane) e = ((e + (cm + 1 - lut_nn) * b7) & (cm * b7)) | (e & ~(0xFFull * b7));
+                pl.lut[lut_slot((Ln << lut_no) | Lo)] = e;
+            }
         for (uint32_t h = 0; h < 8; h++) {
             uint32_t a = h, Q = 0;
             uint64_t e = 0;
@@ -334,7 +340,7 @@ int build_plan(const PS& ps, Plan* out) {
                 Q ^= (a >> i) & 1u;
                 a ^= (uint32_t)(adj[i] & low3);
                 if (s < 7) e |= (uint64_t)(4 * Q * stride) << (8 * (s - 1));
-                else e |= ((uint64_t)(4 * Q * stride) << 48) | ((uint64_t)((4 * Q) | (a << 5)) << 56);
+                else e |= ((uint64_t)(4 * Q * stride) << 48) | ((uint64_t)(4 * Q) << 56);
             }
             pl.lut[((size_t)1 << nU) + h] = e;
         }

@@ -117,11 +117,11 @@ struct Plan {
     // counter from the block's base, dJ_s * stride + dM_s + lut_nn, and in
     // byte 7 dJ_7; the 8 entries after them, indexed by the three bits h of
     // A x for variables 0-2, add the quadratic part 4 Q_s * stride (byte 7:
-    // 4 Q_7, and h at the end of the block in bits 5-7).  With lut_lane
-    // (no phase-pair or zero forms, at most 7 odd nodes) the row stride in
-    // the offsets is 2^lut_tsh instead of m_odd + 1, so that a counter index
-    // (J mod 8) * 2^lut_tsh + M is the sum of the block's base and the offset
-    // taken modulo 8 * 2^lut_tsh.
+    // 4 Q_7).  With lut_lane (no phase-pair or zero forms, at most 7 odd
+    // nodes) the row stride in the offsets is 2^lut_tsh instead of
+    // m_odd + 1 and bytes 0-6 hold (dJ_s * stride + dM_s) mod 8 * 2^lut_tsh,
+    // so that a counter index (J mod 8) * 2^lut_tsh + M is the sum of the
+    // block's base and the offset taken modulo 8 * 2^lut_tsh.
     bool lut_ok = false;
     bool lut_lane = false;
     std::vector<uint64_t> lut;

@@ -302,7 +302,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
     const uint32_t no = p.lut_no, nn = p.lut_nn, lsh = p.lut_shift;
     const uint32_t mo = (1u << no) - 1u, mn = (1u << nn) - 1u;
     const uint64_t* __restrict__ qlut = sL + (1u << (no + nn));
-    const uint32_t tsh = p.lut_tsh, cm = (8u << tsh) - 1u;
+    constexpr uint32_t tsh = kLaneRowShift, cm = (8u << tsh) - 1u;
     uint32_t* const lbase = sm.sH + warp * ((uint32_t)kLaneCounters * 32u);
     uint32_t* const wl = lbase + lane;
     unsigned char* const wlb = reinterpret_cast<unsigned char*>(wl);
@@ -424,8 +424,9 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                 for (int w = 0; w < NWL; w++) z |= L[NWN + w] & p.Z[w];
                 return ((L[NWN] & p.pmask) | ((z != 0 ? 1u : 0u) << p.zshift)) * plane;
             };
-            // the linear part of a flip with step row f (L before the XOR)
-            auto step = [&](const uint32_t* f) {
+            // the linear part of a flip with step row f (L before the XOR) and
+            // the lookup slot change du
+            auto step = [&](const uint32_t* f, uint32_t du) {
                 uint32_t d0 = 0, d1 = 0;
 #pragma unroll
                 for (int w = 0; w < NWL; w++) {
@@ -433,7 +434,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                     d1 += __popc(L[NWN + w] & f[NW + NWL + w]);
                 }
                 Jl += f[NW + 2 * NWL] - 2u * d0 - 4u * d1;
-                us ^= f[NW + 2 * NWL] >> 8;
+                us ^= du;
 #pragma unroll
                 for (int w = 0; w < NW; w++) L[w] ^= f[w];
             };
@@ -481,7 +482,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
             auto flip3 = [&]() {
                 Jl += ((uint32_t)a >> 1) & 4u;
                 a ^= p.A4[3];
-                step(p.R[3]);
+                step(p.R[3], p.U4[3]);
             };
             auto load_row = [&](int i, uint32_t (&fr)[RW]) {
 #pragma unroll
@@ -515,7 +516,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                         if (!more) break;
                         Jl += (uint32_t)(a >> i) << 2;   // (bits above 2: only J mod 8 is used)
                         a ^= adj;
-                        step(fr);
+                        step(fr, fr[NW + 2 * NWL] >> 8);
                         if (tend - t < 16) break;
                     }
                     if (t >= tend) break;
@@ -539,7 +540,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                     a ^= sADJ[i];
                     uint32_t fr[RW];
                     load_row(i, fr);
-                    step(fr);
+                    step(fr, fr[NW + 2 * NWL] >> 8);
                 }
             }
         }

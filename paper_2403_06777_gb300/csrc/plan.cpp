@@ -242,11 +242,10 @@ int build_plan(const PS& ps, Plan* out) {
 
     // block lookup (see plan.h)
     if (lut_try) {
-        // lane-private counters: one row of 2^tsh >= m_odd + 1 counters per
-        // phase exponent mod 8, at most kLaneCounters per lane
-        uint32_t tsh = 0;
-        while ((1u << tsh) < pl.m_odd + 1) tsh++;
-        pl.lut_lane = pair_masks.empty() && zero.empty() && (8u << tsh) <= (uint32_t)kLaneCounters;
+        // lane-private counters: one row of 2^kLaneRowShift >= m_odd + 1
+        // counters per phase exponent mod 8
+        const uint32_t tsh = kLaneRowShift;
+        pl.lut_lane = pair_masks.empty() && zero.empty() && pl.m_odd + 1 <= (1u << tsh);
         kp.lut_tsh = pl.lut_lane ? tsh : 0u;
         kp.lane_row_bytes = 32u * 4u;
         const uint32_t nU = lut_nn + lut_no, stride = pl.lut_lane ? (1u << tsh) : pl.m_odd + 1;

@@ -46,8 +46,9 @@ constexpr int kMaxRowWords = (int)row_words(kMaxWordsNode, kMaxWordsOther);
 constexpr int kLutMaxBits = 10;
 constexpr int kLutRows = 24;
 // Block lookup with lane-private counters (variant 11): a lane's counters are
-// indexed by (J mod 8) * 2^lut_tsh + M, so at most this many per lane.
-constexpr int kLaneCounters = 64;
+// indexed by (J mod 8) * 2^kLaneRowShift + M (M <= 7: at most 7 odd nodes).
+constexpr int kLaneRowShift = 3;
+constexpr int kLaneCounters = 8 << kLaneRowShift;
 ZXP_HD constexpr uint32_t lut_slot(uint32_t u) { return u ^ (((u >> 4) ^ (u >> 8)) & 15u); }
 
 // Passed by value as the kernel parameter block (kept in the constant bank).
@@ -71,7 +72,7 @@ struct KernelParams {
     // and linear bits [lut_shift, lut_shift + lut_no) of the first other word
     // (after the phase-pair bits)
     uint32_t lut_no, lut_nn, lut_shift;
-    uint32_t lut_tsh;        // variant 11: log2 of the counter row stride (>= m_odd + 1)
+    uint32_t lut_tsh;        // variant 11: log2 of the counter row stride (kLaneRowShift)
     uint64_t A4[4];          // adjacency rows of variables 0..3 (0 beyond k)
     // variant 11: bytes between a lane's consecutive counters (32 lanes x 4
     // bytes).  A parameter rather than a constant, so that the counter

@@ -77,7 +77,7 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
     }
     if (HIST == 5) {
         // lane-private counters: only rows (J, M) with M < tab_stride are used
-        const uint32_t tsh = p.lut_tsh, tm = (1u << tsh) - 1u, nq = (uint32_t)kLaneCounters * 8u;
+        constexpr uint32_t tm = (1u << kLaneRowShift) - 1u, nq = (uint32_t)kLaneCounters * 8u;
         uint4* h4 = reinterpret_cast<uint4*>(sm.sH);
         for (uint32_t i = threadIdx.x; i < (blockDim.x >> 5) * nq; i += blockDim.x)
             if ((((i % nq) >> 3) & tm) < p.tab_stride) h4[i] = make_uint4(0, 0, 0, 0);

@@ -316,7 +316,8 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int128",
         "data": "synthetic",
-        "config": {"workload": w.name + f" seed={args.seed} (k={k})", "sample": sample},
+        "config": {"workload": f"{w.name} seed={args.seed}: one exact amplitude per step", "k": k,
+                   "terms_per_step": n, "sample": sample},
         "cpu_baseline": {"value": v, "unit": "terms/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

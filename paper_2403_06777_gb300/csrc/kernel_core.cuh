@@ -420,20 +420,23 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
             auto plane_base = [&]() -> uint32_t {
                 if (!XTRA) return 0u;
                 uint32_t z = 0;
+                if (p.has_zero) {
 #pragma unroll
-                for (int w = 0; w < NWL; w++) z |= L[NWN + w] & p.Z[w];
+                    for (int w = 0; w < NWL; w++) z |= L[NWN + w] & p.Z[w];
+                }
                 return ((L[NWN] & p.pmask) | ((z != 0 ? 1u : 0u) << p.zshift)) * plane;
             };
             // the linear part of a flip with step row f (L before the XOR) and
             // the lookup slot change du
             auto step = [&](const uint32_t* f, uint32_t du) {
-                uint32_t d0 = 0, d1 = 0;
+                // (4 d1 mod 8 needs only the parity of d1: one popcount)
+                uint32_t d0 = 0, x1 = 0;
 #pragma unroll
                 for (int w = 0; w < NWL; w++) {
                     d0 += __popc(L[NWN + w] & f[NW + w]);
-                    d1 += __popc(L[NWN + w] & f[NW + NWL + w]);
+                    x1 ^= L[NWN + w] & f[NW + NWL + w];
                 }
-                Jl += f[NW + 2 * NWL] - 2u * d0 - 4u * d1;
+                Jl += f[NW + 2 * NWL] - 2u * d0 - 4u * (uint32_t)__popc(x1);
                 us ^= du;
 #pragma unroll
                 for (int w = 0; w < NW; w++) L[w] ^= f[w];
@@ -684,7 +687,7 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                 uint32_t M = 0, Zb = 0;
 #pragma unroll
                 for (int w = 0; w < NWN; w++) M += __popc(L[w]);
-                if (GENERAL) {
+                if (GENERAL && p.has_zero) {
 #pragma unroll
                     for (int w = 0; w < NWL; w++) Zb |= L[NWN + w] & p.Z[w];
                 }
@@ -694,8 +697,10 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                     uint32_t idx = J * p.tab_stride + M;
                     if (XTRA) {   // phase-pair or zero forms present
                         uint32_t z = 0;
+                        if (p.has_zero) {
 #pragma unroll
-                        for (int w = 0; w < NWL; w++) z |= L[NWN + w] & p.Z[w];
+                            for (int w = 0; w < NWL; w++) z |= L[NWN + w] & p.Z[w];
+                        }
                         idx = (idx << p.xshift) | (L[NWN] & p.pmask) | ((z != 0 ? 1u : 0u) << p.zshift);
                     }
                     if (HIST == 3)
@@ -721,13 +726,14 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
             // flip of variable i with step row f (before the XOR: the phase
             // change depends on the forms' current bits)
             auto step = [&](const uint32_t* f) {
-                uint32_t d0 = 0, d1 = 0;
+                // (4 d1 mod 8 needs only the parity of d1: one popcount)
+                uint32_t d0 = 0, x1 = 0;
 #pragma unroll
                 for (int w = 0; w < NWL; w++) {
                     d0 += __popc(L[NWN + w] & f[NW + w]);
-                    d1 += __popc(L[NWN + w] & f[NW + NWL + w]);
+                    x1 ^= L[NWN + w] & f[NW + NWL + w];
                 }
-                Jl += f[NW + 2 * NWL] - 2u * d0 - 4u * d1;
+                Jl += f[NW + 2 * NWL] - 2u * d0 - 4u * (uint32_t)__popc(x1);
 #pragma unroll
                 for (int w = 0; w < NW; w++) L[w] ^= f[w];
             };

@@ -58,7 +58,9 @@ cudaMemPool_t table_pool(int device) {
     return pool;
 }
 
-int ensure_device_tables(const zxp_scalar* s, zxp_ctx* ctx, DevTables* out) {
+// seq: the number of the launch on ctx->stream that reads the tables (0:
+// none known).
+int ensure_device_tables(const zxp_scalar* s, zxp_ctx* ctx, DevTables* out, uint64_t seq = 0) {
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->dev.find(ctx->device);
     if (it != s->dev.end()) {
@@ -76,9 +78,12 @@ int ensure_device_tables(const zxp_scalar* s, zxp_ctx* ctx, DevTables* out) {
     ctx->stage_next = (slot + 1) % zxp_ctx::kStages;
     if (!ctx->stage_ev[slot] && cudaEventCreateWithFlags(&ctx->stage_ev[slot], cudaEventDisableTiming) != cudaSuccess)
         return ZXP_ECUDA;
-    cudaError_t q = cudaEventQuery(ctx->stage_ev[slot]);
-    if (q == cudaErrorNotReady) q = cudaEventSynchronize(ctx->stage_ev[slot]);
-    if (q != cudaSuccess) return ZXP_ECUDA;
+    if (!ctx->stage_seq[slot] || ctx->stage_seq[slot] > ctx->done_seq) {
+        cudaError_t q = cudaEventQuery(ctx->stage_ev[slot]);
+        if (q == cudaErrorNotReady) q = cudaEventSynchronize(ctx->stage_ev[slot]);
+        if (q != cudaSuccess) return ZXP_ECUDA;
+    }
+    ctx->stage_seq[slot] = 0;
     if (ctx->stage_cap[slot] < L.total) {
         if (ctx->stage[slot]) cudaFreeHost(ctx->stage[slot]);
         ctx->stage[slot] = nullptr;
@@ -106,6 +111,7 @@ int ensure_device_tables(const zxp_scalar* s, zxp_ctx* ctx, DevTables* out) {
         cudaFreeAsync(base, ctx->upload);
         return ZXP_ECUDA;
     }
+    ctx->stage_seq[slot] = seq;
     zxp_scalar::DevCopy c;
     c.t = device_tables(L, base);
     c.stream = ctx->stream;
@@ -153,12 +159,15 @@ int check_range(const zxp_scalar* s, uint64_t first, uint64_t count) {
     return ZXP_OK;
 }
 
-// Queue one range on ctx->stream: the raw partial into dres (pinned host
-// memory that the host polls when host_result, else device memory).
+// Queue one range on ctx->stream: the raw partial into dres, the device
+// address of pinned host memory hres that the host polls (or, with hres
+// null, device memory).
+// seq: the launch's number on ctx->stream (0: not tracked).
 int enqueue(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, DevResult* dres,
-            bool host_result) {
+            const DevResult* hres, uint64_t seq) {
+    const bool host_result = hres != nullptr;
     DevTables d;
-    int st = ensure_device_tables(s, ctx, &d);
+    int st = ensure_device_tables(s, ctx, &d, seq);
     if (st != ZXP_OK) return st;
     uint64_t span;
     int grid;
@@ -387,9 +396,11 @@ int zxp_eval(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, 
     if (count == 0 || s->plan.zero) { from_zw(zw_zero(), s->ps.e0, 1, out); return ZXP_OK; }
     DeviceGuard g(ctx->device);
     ctx->hres->flags = 0;
-    st = enqueue(ctx, s, first, count, ctx->hres_dev, true);   // the kernel writes the pinned result
+    const uint64_t seq = ++ctx->enq_seq;
+    st = enqueue(ctx, s, first, count, ctx->hres_dev, ctx->hres, seq);   // the kernel writes the pinned result
     if (st != ZXP_OK) return st;
     if ((st = wait_published(ctx->stream, ctx->hres, -1)) != ZXP_OK) return st;
+    if (seq > ctx->done_seq) ctx->done_seq = seq;
     memcpy(out, ctx->hres, sizeof *out);
     return (out->flags & 2) ? ZXP_ETIMEDOUT : ZXP_OK;
 }
@@ -400,7 +411,7 @@ int zxp_eval_device(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t 
     int st = check_range(s, first, count);
     if (st != ZXP_OK) return st;
     DeviceGuard g(ctx->device);
-    return enqueue(ctx, s, first, count, reinterpret_cast<DevResult*>(dev_out), false);
+    return enqueue(ctx, s, first, count, reinterpret_cast<DevResult*>(dev_out), nullptr, ++ctx->enq_seq);
 }
 
 int zxp_zomega_canon(const zxp_zomega* in, zxp_zomega* out) {
@@ -445,7 +456,8 @@ int zxp_submit(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count
             }
         }
         t.hres->flags = 0;
-        st = enqueue(ctx, s, first, count, t.dres, true);   // the kernel writes the pinned result
+        t.seq = ++ctx->enq_seq;
+        st = enqueue(ctx, s, first, count, t.dres, t.hres, t.seq);   // the kernel writes the pinned result
         if (st != ZXP_OK) { ctx->free_slots.push_back(t); return st; }
     }
     *ticket = ctx->next_ticket++;
@@ -462,6 +474,7 @@ int zxp_poll(zxp_ctx* ctx, uint64_t ticket, int64_t timeout_us, zxp_zomega* out)
         DeviceGuard g(ctx->device);
         const int st = wait_published(ctx->stream, t.hres, timeout_us);
         if (st != ZXP_OK) return st;
+        if (t.seq > ctx->done_seq) ctx->done_seq = t.seq;
         memcpy(out, t.hres, sizeof *out);
         if (out->flags & 2) {
             ctx->free_slots.push_back(t);

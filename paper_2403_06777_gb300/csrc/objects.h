@@ -94,6 +94,7 @@ struct Ticket {
     DevResult* hres = nullptr;
     int32_t e0 = 0;
     bool trivial = false;        // no launch: the value is zero
+    uint64_t seq = 0;            // the launch's number on the context's stream
 };
 
 class DeviceGuard {
@@ -184,6 +185,13 @@ struct zxp_ctx {
     unsigned char* stage[kStages] = {};
     size_t stage_cap[kStages] = {};
     cudaEvent_t stage_ev[kStages] = {};
+    // Launches on `stream` are numbered (enq_seq); done_seq is the highest
+    // whose published result the host has seen, so every launch up to it
+    // has ended (one stream: they end in order).  A staging slot whose copy
+    // fed launch stage_seq <= done_seq is free without asking its event
+    // (the launch waited for the copy); 0: not known.
+    uint64_t enq_seq = 0, done_seq = 0;
+    uint64_t stage_seq[kStages] = {};
     int stage_next = 0;
     uint64_t next_ticket = 1;
     std::map<uint64_t, zxp::Ticket> tickets;

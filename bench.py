@@ -462,11 +462,20 @@ def main():
         ops36 = alg_ops_per_term(i36["node_words"], i36["other_words"], i36["n_pair"])
         ach36 = ops36 * (1 << 36) / (ms36 / 1e3) / 1e9
         peak = SM_COUNT_GB300 * ISSUE_LANES_PER_SM_CLK * 2070e6 / 1e9
+        prof_s = profile_fields(kernel_source_sha(), "sum_kernel_synthetic36.txt")
+        ipt_s = profile_number(prof_s, "instructions_per_term")
+        iss_s = None if ipt_s is None else ipt_s * (1 << 36) / (ms36 / 1e3) / 1e9
         large = {"workload": "synthetic k=36 (59 linear, 36 quadratic, 13 odd-node, 1 phase-pair rows)",
                  "terms": 1 << 36, "ms": ms36, "terms_per_s": (1 << 36) / (ms36 / 1e3),
                  "node_words": i36["node_words"], "other_words": i36["other_words"],
+                 "kernel_variant": i36["kernel_variant"],
                  "roofline": {"bound": "alu", "achieved": ach36, "peak": peak, "unit": "Gop/s",
-                              "frac": ach36 / peak, "ops_per_term": ops36},
+                              "frac": ach36 / peak, "ops_per_term": ops36,
+                              "traffic": profile_number(prof_s, "dram_bytes_per_launch"),
+                              "issue": {"instructions_per_term": ipt_s, "achieved": iss_s,
+                                        "frac": None if iss_s is None else iss_s / peak,
+                                        "source": "thread instructions per term of the committed "
+                                                  "ncu capture (profiles/sum_kernel_synthetic36.txt)"}},
                  "clocks": clk36.summary()}
 
     # large compiled circuit: n = 50, 2000 gates at T-count 50 (k = 37), the

@@ -205,6 +205,44 @@ def test_submit_poll_matches_eval(ctx):
         Z.zxp_poll(ctx, tickets[0], 0)        # already released
 
 
+def test_streamed_requests_reuse_staging(ctx):
+    """A client streaming fresh scalars (tables built per request), two to
+    four requests in flight, with blocking and device-result evaluations
+    interleaved: the context's staging buffers are reused many times, by
+    tables of different sizes, and every result equals the oracle's."""
+    import torch
+    from collections import deque
+    blobs = [zi.synthetic_ps(40 + i, 10 + i % 5, n_lin=6 + i, n_quad=3, n_node=5 + 3 * (i % 4),
+                             n_pair=i % 3, odd_nodes_only=i % 2 == 0).pack() for i in range(7)]
+    want = [oracle.ps_sum(b) for b in blobs]
+    dev = torch.zeros(5, dtype=torch.int64, device="cuda")
+    q = deque()
+    n_done = 0
+    for r in range(70):
+        i = r % 7
+        s = Z.zxp_scalar_from_tables(blobs[i])
+        q.append((i, s, Z.zxp_submit(ctx, s)))
+        if r % 5 == 0:
+            j = (r + 3) % 7
+            s2 = Z.zxp_scalar_from_tables(blobs[j])
+            assert same_raw(Z.zxp_eval(ctx, s2), want[j]), (r, j)
+            s2.free()
+        if r % 9 == 0:
+            j = (r + 5) % 7
+            s3 = Z.zxp_scalar_from_tables(blobs[j])
+            Z.zxp_eval_device(ctx, s3, 0, 1 << s3.info["k"], dev.data_ptr())
+            torch.cuda.synchronize()
+            v = dev.tolist()
+            assert same_raw((v[0], v[1], v[2], v[3], v[4] & 0xFFFFFFFF), want[j]), (r, j)
+            s3.free()
+        while len(q) > 2 + r % 3 or (r == 69 and q):
+            j, sj, tk = q.popleft()
+            assert same_raw(Z.zxp_poll(ctx, tk, -1), want[j]), (r, j)
+            sj.free()
+            n_done += 1
+    assert n_done == 70
+
+
 def test_context_on_a_torch_stream():
     import torch
     st = torch.cuda.Stream()

@@ -405,12 +405,13 @@ def main():
     per_launch_s = sec / args.steps
 
     # e2e: the public host API, one request per step: the tables (host
-    # bytes) become a scalar (host plan), are submitted (tables copied from
-    # pinned staging, launch) and polled (the 40-byte result the kernel wrote
-    # into pinned host memory); up to E2E_DEPTH requests are in flight, as a
-    # client streaming requests runs them.  Every result is checked against
-    # the exact amplitude after the timed loop.  The latency of one blocking
-    # request (nothing else in flight) is reported beside it.
+    # bytes) are submitted (zxp_submit_tables: the scalar is built on the
+    # host, its tables copied from pinned staging, the kernel launched) and
+    # polled (the 40-byte result the kernel wrote into pinned host memory);
+    # up to E2E_DEPTH requests are in flight, as a client streaming requests
+    # runs them.  Every result is checked against the exact amplitude after
+    # the timed loop.  The latency of one blocking request (nothing else in
+    # flight) is reported beside it.
     E2E_DEPTH = 2
     e2e_steps = max(200, 10 * args.steps)
     from collections import deque
@@ -420,12 +421,9 @@ def main():
     t = time.perf_counter()
     for i in range(e2e_steps + E2E_DEPTH):
         if i < e2e_steps:
-            s2 = Z.zxp_scalar_from_tables(blob)
-            q.append((s2, Z.zxp_submit(ctx, s2, 0, terms)))
+            q.append(Z.zxp_submit_tables(ctx, blob))
         if len(q) > E2E_DEPTH or (i >= e2e_steps and q):
-            s_old, tk = q.popleft()
-            got.append(Z.zxp_poll(ctx, tk, -1))
-            s_old.free()
+            got.append(Z.zxp_poll(ctx, q.popleft(), -1))
     e2e_sec = (time.perf_counter() - t) / e2e_steps
     bad = sum(Z.zxp_zomega_canon(r) != ref for r in got)
     assert bad == 0 and len(got) == e2e_steps, (bad, len(got))

@@ -194,6 +194,13 @@ int zxp_submit(zxp_ctx *ctx, const zxp_scalar *s, uint64_t first, uint64_t count
  * ticket.  ZXP_OK: *out holds the raw partial and the ticket is released.
  * ZXP_EAGAIN: not finished.  ZXP_ENOTFOUND: unknown ticket. */
 int zxp_poll(zxp_ctx *ctx, uint64_t ticket, int64_t timeout_us, zxp_zomega *out);
+/* One call for a client holding a scalar's table bytes (the layout of
+ * zxp_scalar_from_tables): build the scalar, queue its whole sum [0, 2^k)
+ * like zxp_submit and return a ticket.  The library owns that scalar and
+ * frees it when the ticket is released by zxp_poll (or the context is
+ * destroyed); the blob is copied at the call.  Errors: those of
+ * zxp_scalar_from_tables and zxp_submit. */
+int zxp_submit_tables(zxp_ctx *ctx, const void *blob, size_t nbytes, uint64_t *ticket);
 
 /* ---- parametric scalars: one reduction for many bitstrings ---------------- */
 

@@ -117,6 +117,7 @@ def lib():
         L.zxp_eval_noalloc.argtypes = [vp, u64, u64, vp, vp]
         L.zxp_submit.argtypes = [vp, vp, u64, u64, C.POINTER(u64)]
         L.zxp_poll.argtypes = [vp, u64, i64, zp]
+        L.zxp_submit_tables.argtypes = [vp, C.c_char_p, sz, C.POINTER(u64)]
         L.zxp_batch_create.argtypes = [vp, C.POINTER(vp), sz, C.POINTER(vp)]
         L.zxp_batch_run.argtypes = [vp, zp]
         L.zxp_batch_info.argtypes = [vp, C.POINTER(zxp_batch_info_t)]
@@ -381,6 +382,14 @@ def zxp_submit(ctx: Ctx, s: Scalar, first: int = 0, count: int | None = None) ->
         count = (1 << zxp_scalar_info(s)["k"]) - first
     t = C.c_uint64()
     _check(lib().zxp_submit(ctx.handle, s.handle, first, count, C.byref(t)), "zxp_submit")
+    return t.value
+
+
+def zxp_submit_tables(ctx: Ctx, blob: bytes) -> int:
+    """Queue the whole sum of the scalar whose table bytes are `blob`; the
+    library owns the scalar it builds until the ticket is polled."""
+    t = C.c_uint64()
+    _check(lib().zxp_submit_tables(ctx.handle, blob, len(blob), C.byref(t)), "zxp_submit_tables")
     return t.value
 
 

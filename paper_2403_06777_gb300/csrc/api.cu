@@ -276,7 +276,10 @@ void zxp_ctx_destroy(zxp_ctx* c) {
     }
     cudaStreamSynchronize(c->stream);
     cudaStreamSynchronize(c->upload);
-    for (auto& e : c->tickets) c->free_slots.push_back(e.second);
+    for (auto& e : c->tickets) {
+        if (e.second.owned) zxp_scalar_free(e.second.owned);
+        c->free_slots.push_back(e.second);
+    }
     for (auto& t : c->free_slots) cudaFreeHost(t.hres);
     for (int i = 0; i < zxp_ctx::kStages; i++) {
         if (c->stage[i]) cudaFreeHost(c->stage[i]);
@@ -477,6 +480,7 @@ int zxp_poll(zxp_ctx* ctx, uint64_t ticket, int64_t timeout_us, zxp_zomega* out)
         if (t.seq > ctx->done_seq) ctx->done_seq = t.seq;
         memcpy(out, t.hres, sizeof *out);
         if (out->flags & 2) {
+            if (t.owned) zxp_scalar_free(t.owned);
             ctx->free_slots.push_back(t);
             ctx->tickets.erase(it);
             return ZXP_ETIMEDOUT;
@@ -484,8 +488,23 @@ int zxp_poll(zxp_ctx* ctx, uint64_t ticket, int64_t timeout_us, zxp_zomega* out)
     } else {
         from_zw(zw_zero(), t.e0, 1, out);
     }
+    if (t.owned) zxp_scalar_free(t.owned);
     if (!t.trivial) ctx->free_slots.push_back(t);
     ctx->tickets.erase(it);
+    return ZXP_OK;
+}
+
+int zxp_submit_tables(zxp_ctx* ctx, const void* blob, size_t nbytes, uint64_t* ticket) {
+    if (!ctx || !blob || !ticket) return ZXP_EINVAL;
+    zxp_scalar* s = nullptr;
+    int st = zxp_scalar_from_tables(blob, nbytes, &s);
+    if (st != ZXP_OK) return st;
+    st = zxp_submit(ctx, s, 0, 1ull << s->ps.k, ticket);
+    if (st != ZXP_OK) {
+        zxp_scalar_free(s);
+        return st;
+    }
+    ctx->tickets[*ticket].owned = s;
     return ZXP_OK;
 }
 

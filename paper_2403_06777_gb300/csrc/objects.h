@@ -95,6 +95,7 @@ struct Ticket {
     int32_t e0 = 0;
     bool trivial = false;        // no launch: the value is zero
     uint64_t seq = 0;            // the launch's number on the context's stream
+    zxp_scalar* owned = nullptr; // zxp_submit_tables: freed when the ticket is released
 };
 
 class DeviceGuard {

@@ -220,8 +220,11 @@ def test_streamed_requests_reuse_staging(ctx):
     n_done = 0
     for r in range(70):
         i = r % 7
-        s = Z.zxp_scalar_from_tables(blobs[i])
-        q.append((i, s, Z.zxp_submit(ctx, s)))
+        if r % 2:
+            s = Z.zxp_scalar_from_tables(blobs[i])
+            q.append((i, s, Z.zxp_submit(ctx, s)))
+        else:                                         # the library owns the scalar
+            q.append((i, None, Z.zxp_submit_tables(ctx, blobs[i])))
         if r % 5 == 0:
             j = (r + 3) % 7
             s2 = Z.zxp_scalar_from_tables(blobs[j])
@@ -238,9 +241,25 @@ def test_streamed_requests_reuse_staging(ctx):
         while len(q) > 2 + r % 3 or (r == 69 and q):
             j, sj, tk = q.popleft()
             assert same_raw(Z.zxp_poll(ctx, tk, -1), want[j]), (r, j)
-            sj.free()
+            if sj is not None:
+                sj.free()
             n_done += 1
     assert n_done == 70
+
+
+def test_submit_tables_errors_and_unpolled_tickets():
+    """zxp_submit_tables rejects bad table bytes; a context destroyed with
+    unpolled tickets frees the scalars it owns."""
+    import torch
+    c = Z.zxp_ctx_create(0, torch.cuda.current_stream().cuda_stream)
+    with pytest.raises(Z.ZxpError):
+        Z.zxp_submit_tables(c, b"not a scalar")
+    blob = zi.synthetic_ps(3, 16, n_node=6, odd_nodes_only=True).pack()
+    t = Z.zxp_submit_tables(c, blob)
+    assert same_raw(Z.zxp_poll(c, t, -1), oracle.ps_sum(blob))
+    for _ in range(3):
+        Z.zxp_submit_tables(c, blob)
+    c.close()
 
 
 def test_context_on_a_torch_stream():

@@ -100,7 +100,16 @@ int ensure_device_tables(const zxp_scalar* s, zxp_ctx* ctx, DevTables* out, uint
     unsigned char* base = nullptr;
     // copy on the upload stream, so that it overlaps the kernels still queued
     // on the context's stream; that stream waits for the copy
-    if (cudaMallocFromPoolAsync((void**)&base, L.total, pool, ctx->upload) != cudaSuccess) return ZXP_ENOMEM;
+    for (size_t i = 0; i < ctx->table_cache.size(); i++) {
+        const size_t b = ctx->table_cache[i].second;
+        if (b >= L.total && b <= 2 * L.total) {
+            base = static_cast<unsigned char*>(ctx->table_cache[i].first);
+            ctx->table_cache.erase(ctx->table_cache.begin() + (ptrdiff_t)i);
+            break;
+        }
+    }
+    if (!base && cudaMallocFromPoolAsync((void**)&base, L.total, pool, ctx->upload) != cudaSuccess)
+        return ZXP_ENOMEM;
     if (cudaMemcpyAsync(base, host, L.total, cudaMemcpyHostToDevice, ctx->upload) != cudaSuccess ||
         cudaEventRecord(ctx->stage_ev[slot], ctx->upload) != cudaSuccess) {
         cudaFreeAsync(base, ctx->upload);
@@ -157,6 +166,22 @@ int check_range(const zxp_scalar* s, uint64_t first, uint64_t count) {
     const uint64_t total = 1ull << s->ps.k;
     if (first > total || count > total - first) return ZXP_EINVAL;
     return ZXP_OK;
+}
+
+// Free a zxp_submit_tables scalar whose launch has ended (its result was
+// seen): its device tables go to the context's cache for the next upload
+// instead of back to the pool.
+void release_owned(zxp_ctx* ctx, zxp_scalar* s) {
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->dev.find(ctx->device);
+        if (it != s->dev.end() && !it->second.shared && it->second.ctx_id == ctx->id &&
+            ctx->table_cache.size() < zxp_ctx::kTableCache) {
+            ctx->table_cache.push_back({static_cast<void*>(it->second.t.table), table_layout(s->plan).total});
+            s->dev.erase(it);
+        }
+    }
+    zxp_scalar_free(s);
 }
 
 // Queue one range on ctx->stream: the raw partial into dres, the device
@@ -280,6 +305,8 @@ void zxp_ctx_destroy(zxp_ctx* c) {
         if (e.second.owned) zxp_scalar_free(e.second.owned);
         c->free_slots.push_back(e.second);
     }
+    for (auto& b : c->table_cache) cudaFreeAsync(b.first, c->upload);
+    cudaStreamSynchronize(c->upload);
     for (auto& t : c->free_slots) cudaFreeHost(t.hres);
     for (int i = 0; i < zxp_ctx::kStages; i++) {
         if (c->stage[i]) cudaFreeHost(c->stage[i]);
@@ -480,7 +507,7 @@ int zxp_poll(zxp_ctx* ctx, uint64_t ticket, int64_t timeout_us, zxp_zomega* out)
         if (t.seq > ctx->done_seq) ctx->done_seq = t.seq;
         memcpy(out, t.hres, sizeof *out);
         if (out->flags & 2) {
-            if (t.owned) zxp_scalar_free(t.owned);
+            if (t.owned) release_owned(ctx, t.owned);
             ctx->free_slots.push_back(t);
             ctx->tickets.erase(it);
             return ZXP_ETIMEDOUT;
@@ -488,7 +515,7 @@ int zxp_poll(zxp_ctx* ctx, uint64_t ticket, int64_t timeout_us, zxp_zomega* out)
     } else {
         from_zw(zw_zero(), t.e0, 1, out);
     }
-    if (t.owned) zxp_scalar_free(t.owned);
+    if (t.owned) release_owned(ctx, t.owned);
     if (!t.trivial) ctx->free_slots.push_back(t);
     ctx->tickets.erase(it);
     return ZXP_OK;

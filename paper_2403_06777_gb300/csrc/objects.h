@@ -180,6 +180,11 @@ struct zxp_ctx {
     unsigned int* counter = nullptr;
     zxp::DevResult* hres = nullptr;     // pinned; the kernel writes it directly
     zxp::DevResult* hres_dev = nullptr; // its device address
+    // Device table buffers of released zxp_submit_tables scalars (pointer,
+    // bytes; allocated from the table pool), reused by later uploads: their
+    // last kernel has ended (its result was seen), so no wait is needed.
+    static constexpr size_t kTableCache = 8;
+    std::vector<std::pair<void*, size_t>> table_cache;
     // Pinned staging for table uploads: a ring of buffers, each reused once
     // the copy out of it (event) has completed.
     static constexpr int kStages = 4;

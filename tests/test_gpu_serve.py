@@ -117,17 +117,20 @@ def test_large_request_runs_in_resumable_chunks(ctx):
 def test_small_requests_pass_a_large_one(ctx):
     """Continuous batching: requests that arrive while a large one is on the
     device finish first; the one-scalar-per-launch policy serves in order."""
+    # (2^34 terms: several milliseconds on the device under either policy,
+    # so that the small requests arrive while it runs)
     big = Z.zxp_scalar_from_tables(
-        zi.synthetic_ps(78, 31, n_lin=20, n_quad=8, n_node=9, odd_nodes_only=True).pack())
+        zi.synthetic_ps(78, 34, n_lin=20, n_quad=8, n_node=9, odd_nodes_only=True).pack())
     small = synthetic_mix(8, 2, ks=(0, 4, 8))
     order = {}
     for policy in (Z.ZXP_SERVE_BATCHED, Z.ZXP_SERVE_PLAIN):
         with Z.zxp_server_create(ctx, policy=policy, step_terms=1 << 26) as srv:
             tb = Z.zxp_server_submit_scalar(srv, big)
-            time.sleep(0.002)
+            time.sleep(0.001)
             ts = [Z.zxp_server_submit_scalar(srv, s) for s in small]
             res = drain(srv, [tb] + ts)
         done_big = res[tb][2]["done_us"]
+        assert all(res[t][2]["submit_us"] < done_big for t in ts)   # they overlapped it
         order[policy] = all(res[t][2]["done_us"] < done_big for t in ts)
         assert all(res[t][0] == Z.ZXP_OK for t in [tb] + ts)
     assert order[Z.ZXP_SERVE_BATCHED]

@@ -164,10 +164,10 @@ int zxp_eval_device(zxp_ctx *ctx, const zxp_scalar *s, uint64_t first, uint64_t 
  * code under a memory manager that owns the whole device (a framework's
  * caching allocator, a serving runtime's fixed arena) and latency-critical
  * loops, where cudaMalloc / cudaFree would synchronise the device.  It needs
- * no zxp_ctx.  The tables of `s` are staged, and the kernel's scratch (block
- * partials, completion counter) kept, in one file-scope device array of
- * 256 KB (at most 2048 blocks of partials), held on every GPU that loads the
- * library until the process exits.  The range is queued on `cuda_stream`
+ * no zxp_ctx.  The tables of `s` are staged, and the kernel's scratch (the
+ * 4 x 64-bit accumulator and the completion counter) kept, in one
+ * file-scope device array of 256 KB (the launch uses at most 2048 blocks),
+ * held on every GPU that loads the library until the process exits.  The range is queued on `cuda_stream`
  * (NULL: the legacy default stream) of the current device, and the raw
  * partial (40-byte zxp_zomega layout, flags bit 0 set) lands at `dev_out`, a
  * caller-owned device pointer aligned to 8 bytes, when the stream reaches it.

@@ -55,7 +55,7 @@ __device__ __forceinline__ void publish_result(DevResult* r, uint64_t c0, uint64
 }
 
 template <int NWN, int NWL, int VAR>
-__global__ void __launch_bounds__(kThreads, VAR == 11 ? 2 : (VAR >= 9 ? 5 : 1))
+__global__ void __launch_bounds__(kThreads, VAR == 11 ? 2 : (VAR >= 9 ? 5 : (VAR >= 7 ? 3 : 1)))
 sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtable,
            const zw64* __restrict__ gpv, const uint32_t* __restrict__ gR,
            const uint64_t* __restrict__ gADJ, const uint32_t* __restrict__ gS, uint64_t first,

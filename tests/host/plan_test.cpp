@@ -1,0 +1,208 @@
+// Host tests of the kernel plan (paper_2403_06777_gb300/csrc/plan.cpp) for
+// the scalars whose table blobs are given on the command line.
+//
+// For every parameter assignment x of a scalar with k <= 12 it prints the
+// term the plan encodes, K * T[index(x)] (with the phase-pair values
+// multiplied in for the general layout), as four hex words, so that the
+// caller can compare them with the oracle's terms.  Where the plan built a
+// block lookup it also checks, at every aligned block of 8 Gray steps, that
+// the lookup gives each of the 8 terms the counter of its own phase class
+// and node count, and that the step rows' lookup-slot changes and the
+// parameter copies of the low variables' rows agree with the plan's forms;
+// for every scalar, that each variable's step row updates the form bits
+// and the phase exponent of sampled states to those of the flipped state.
+// Exits 1 with a message on the first failed check.
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <fstream>
+#include <iterator>
+#include <vector>
+
+#include "plan.h"
+#include "ps.h"
+#include "zring.h"
+
+using namespace zxp;
+
+#define CHECK(c)                                                                  \
+    do {                                                                          \
+        if (!(c)) {                                                               \
+            fprintf(stderr, "%s:%d: check failed: %s\n", __FILE__, __LINE__, #c); \
+            exit(1);                                                              \
+        }                                                                         \
+    } while (0)
+
+namespace {
+
+int popc(uint32_t v) { return __builtin_popcount(v); }
+
+// The plan's state for parameter bits x: the form bits, the phase exponent
+// J (mod 8), the node count M and A x.
+struct Term {
+    std::vector<uint32_t> L;
+    uint32_t J, M;
+    uint64_t ax;
+};
+
+struct Model {
+    const Plan& pl;
+    uint32_t k, nw, nwn, nwl;
+    explicit Model(const Plan& p)
+        : pl(p), k(p.kp.k), nw((uint32_t)(p.nwn + (p.nwl < 1 ? 1 : p.nwl))), nwn((uint32_t)p.nwn),
+          nwl(nw - (uint32_t)p.nwn) {}
+
+    Term at(uint64_t x) const {
+        const KernelParams& kp = pl.kp;
+        Term t;
+        t.L.assign(nw, 0);
+        for (uint32_t w = 0; w < nw; w++) t.L[w] = kp.INV[w];
+        t.ax = 0;
+        uint32_t q = 0;
+        for (uint32_t i = 0; i < k; i++) {
+            if (!((x >> i) & 1)) continue;
+            for (uint32_t w = 0; w < nw; w++) t.L[w] ^= pl.frows[(size_t)i * nw + w];
+            t.ax ^= pl.adj[i];
+            q ^= (uint32_t)__builtin_popcountll(pl.adj[i] & x & ((2ull << i) - 1) & ~(1ull << i)) & 1u;
+        }
+        uint32_t J = 4 * q;
+        for (uint32_t w = 0; w < nwn; w++) J += 4 * (uint32_t)popc(t.L[w] & kp.CB[w]);
+        for (uint32_t w = 0; w < nwl; w++) {
+            const uint32_t v = t.L[nwn + w];
+            J += (uint32_t)popc(v & kp.C0[w]) + 2 * (uint32_t)popc(v & kp.C1[w]) + 4 * (uint32_t)popc(v & kp.C2[w]);
+        }
+        t.J = J & 7;
+        t.M = 0;
+        for (uint32_t w = 0; w < nwn; w++) t.M += (uint32_t)popc(t.L[w]);
+        return t;
+    }
+
+    bool bit(const Term& t, uint32_t pos) const { return (t.L[pos >> 5] >> (pos & 31)) & 1; }
+
+    // K * (the term's table value), the phase-pair values multiplied in
+    // for the general layout
+    zw64 value(const Term& t) const {
+        const KernelParams& kp = pl.kp;
+        uint32_t z = 0;
+        for (uint32_t w = 0; w < nwl; w++) z |= t.L[nwn + w] & kp.Z[w];
+        zw64 v;
+        if (pl.general) {
+            if (z) return zw_zero();
+            v = pl.table[t.J * kp.tab_stride + t.M];
+            for (uint32_t j = 0; j < kp.npairs; j++) {
+                const uint32_t b = (bit(t, kp.PA[j]) ? 1u : 0u) | (bit(t, kp.PB[j]) ? 2u : 0u);
+                v = zw_mul(v, pl.pv[4 * j + b]);
+            }
+        } else {
+            uint32_t idx = t.J * kp.tab_stride + t.M;
+            idx = (idx << kp.xshift) | (t.L[nwn] & kp.pmask) | ((z ? 1u : 0u) << kp.zshift);
+            v = pl.table[idx];
+        }
+        return zw_mul(pl.K, v);
+    }
+
+    // the lookup's bits of a state (linear forms, then node forms)
+    uint32_t lookup_bits(const Term& t) const {
+        const KernelParams& kp = pl.kp;
+        uint32_t u = (t.L[nwn] >> kp.lut_shift) & ((1u << kp.lut_no) - 1u);
+        if (nwn) u |= (t.L[0] & ((1u << kp.lut_nn) - 1u)) << kp.lut_no;
+        return u;
+    }
+};
+
+uint64_t gray(uint64_t t) { return t ^ (t >> 1); }
+
+// The step rows: flipping variable i at state x changes J by
+// S_i - 2 |L & F_i & C0| - 4 |L & F_i & C1| + 4 (A x)_i (mod 8) and the form
+// bits by F_i, for sampled states x and every variable.
+void check_step_rows(const Model& m) {
+    const Plan& pl = m.pl;
+    const uint32_t k = m.k, rw = pl.row_stride, nw = m.nw, nwl = m.nwl, nwn = m.nwn;
+    const uint64_t nx = k < 64 ? (1ull << k) : 0;
+    const uint64_t step = nx > 256 ? nx / 256 + 1 : 1;
+    for (uint64_t x = 0; x < nx; x += step) {
+        const Term s0 = m.at(x);
+        for (uint32_t i = 0; i < k; i++) {
+            const uint32_t* f = &pl.rows[(size_t)i * rw];
+            uint32_t d0 = 0, d1 = 0;
+            for (uint32_t w = 0; w < nwl; w++) {
+                d0 += (uint32_t)popc(s0.L[nwn + w] & f[nw + w]);
+                d1 += (uint32_t)popc(s0.L[nwn + w] & f[nw + nwl + w]);
+            }
+            const uint32_t ai = (uint32_t)(s0.ax >> i) & 1u;
+            const Term s1 = m.at(x ^ (1ull << i));
+            CHECK(((s0.J + f[nw + 2 * nwl] - 2 * d0 - 4 * d1 + 4 * ai) & 7) == s1.J);
+            for (uint32_t w = 0; w < nw; w++) CHECK((s0.L[w] ^ f[w]) == s1.L[w]);
+        }
+    }
+}
+
+void check_lookup(const Model& m) {
+    const Plan& pl = m.pl;
+    const KernelParams& kp = pl.kp;
+    const uint32_t k = m.k, nU = kp.lut_no + kp.lut_nn, ts = kp.tab_stride;
+    const uint32_t rw = pl.row_stride, sw = m.nw + 2 * m.nwl;
+    // parameter copies of the low variables' step and adjacency rows
+    for (uint32_t i = 0; i < 4 && i < k; i++) {
+        for (uint32_t w = 0; w < rw; w++) CHECK(kp.R[i][w] == pl.rows[(size_t)i * rw + w]);
+        CHECK(kp.A4[i] == pl.adj[i]);
+        CHECK(kp.U4[i] == (pl.rows[(size_t)i * rw + sw] >> 8));
+    }
+    const uint64_t nblocks = k >= 3 ? (1ull << (k - 3)) : 0;
+    const uint64_t step = nblocks > 512 ? nblocks / 512 : 1;
+    for (uint64_t b = 0; b < nblocks; b += step) {
+        const uint64_t t0 = b * 8;
+        const Term s0 = m.at(gray(t0));
+        const uint32_t u = m.lookup_bits(s0);
+        // each variable's step row changes the lookup slot by its slot change
+        for (uint32_t i = 0; i < k; i++) {
+            const Term s1 = m.at(gray(t0) ^ (1ull << i));
+            CHECK((lut_slot(m.lookup_bits(s1)) ^ lut_slot(u)) == (pl.rows[(size_t)i * rw + sw] >> 8));
+        }
+        const uint64_t e = pl.lut[lut_slot(u)] + pl.lut[((size_t)1 << nU) + (uint32_t)(s0.ax & 7)];
+        const Term s7 = m.at(gray(t0 + 7));
+        CHECK(((s0.J + (uint32_t)(e >> 56)) & 7) == s7.J);
+        for (uint32_t s = 1; s < 8; s++) {
+            const Term st = m.at(gray(t0 + s));
+            const uint32_t off = (uint32_t)(e >> (8 * (s - 1))) & 0xFFu;
+            if (pl.lut_lane) {
+                const uint32_t b0 = (s0.J << kLaneRowShift) + s0.M;
+                const uint32_t idx = (b0 + off) & ((8u << kLaneRowShift) - 1u);
+                CHECK(idx == (st.J << kLaneRowShift) + st.M);
+            } else {
+                // counter row * ts + m, rows not reduced mod 8 inside a block
+                const int c = (int)(s0.J * ts + s0.M) - (int)kp.lut_nn + (int)off;
+                CHECK(c >= 0);
+                CHECK((uint32_t)c % ts == st.M);
+                CHECK(((uint32_t)c / ts) % 8 == st.J);
+                CHECK((uint32_t)c / ts < (uint32_t)kLutRows);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int main(int argc, char** argv) {
+    for (int a = 1; a < argc; a++) {
+        std::ifstream in(argv[a], std::ios::binary);
+        std::vector<char> blob((std::istreambuf_iterator<char>(in)), {});
+        PS ps;
+        CHECK(ps_from_blob(blob.data(), blob.size(), &ps) == 0);
+        Plan pl;
+        CHECK(build_plan(ps, &pl) == 0);
+        const Model m(pl);
+        printf("scalar %s k %u lookup %d lane %d\n", argv[a], m.k, pl.lut_ok ? 1 : 0, pl.lut_lane ? 1 : 0);
+        if (m.k <= 12)
+            for (uint64_t x = 0; x < (1ull << m.k); x++) {
+                const zw64 v = pl.zero ? zw_zero() : m.value(m.at(x));
+                printf("%llx %llx %llx %llx\n", (unsigned long long)v.c[0], (unsigned long long)v.c[1],
+                       (unsigned long long)v.c[2], (unsigned long long)v.c[3]);
+            }
+        if (!pl.zero) check_step_rows(m);
+        if (pl.lut_ok) check_lookup(m);
+    }
+    printf("ok\n");
+    return 0;
+}

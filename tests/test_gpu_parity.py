@@ -337,6 +337,31 @@ def test_large_compiled_t50_subranges(ctx):
         assert same_raw(g, o), first
 
 
+def test_large_compiled_full_sum_conjugate_transpose(ctx):
+    """The compiled n = 50, 2000-gate, T-count 50 circuit (k = 37) summed in
+    full, 1.4e11 terms at the benchmark's launch shape (several slices per
+    thread): the one-launch sum equals the sum of eight 2^34-term launches
+    (one slice per thread), and <out|C|0> equals the conjugate of <0|C^dag|out>
+    from the separately reduced inverse circuit (another scalar, another
+    kernel variant; no state vector exists at n = 50)."""
+    inv = {zi.S: zi.SDG, zi.SDG: zi.S, zi.T: zi.TDG, zi.TDG: zi.T}
+    w = zi.workload_large_t50(0)
+    s = Z.zxp_compile(w.gates, w.n, w.out_bits)
+    k = s.info["k"]
+    assert k <= 40
+    a = Z.zxp_amplitude(ctx, s)
+    n8 = (1 << k) // 8
+    tot = Z.zxp_eval(ctx, s, 0, n8)
+    for i in range(1, 8):
+        tot = Z.zxp_zomega_add(tot, Z.zxp_eval(ctx, s, i * n8, n8))
+    assert Z.zxp_zomega_canon(tot) == a
+    dag = [(inv.get(op, op), q0, q1) for op, q0, q1 in reversed(w.gates)]
+    sd = Z.zxp_compile(dag, w.n, [0] * w.n, in_bits=w.out_bits)
+    assert sd.info["k"] <= 40
+    b = Z.zxp_amplitude(ctx, sd)
+    assert a == (b[0], -b[3], -b[2], -b[1], b[4])
+
+
 @pytest.mark.parametrize("seed,n_node,n_pair,odd,density", [
     (62, 5, 0, True, 0.05),     # block lookup, lane-private counters
     (66, 10, 0, True, 0.03),    # block lookup, warp-shared counters (more than 7 odd nodes)

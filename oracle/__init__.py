@@ -102,13 +102,23 @@ def _check(rc: int, what: str):
         raise OracleOverflow(f"oracle {what}: 128-bit overflow")
 
 
+def outer_k(blob: bytes) -> int:
+    """Parameters the term index runs over: k, less the inner parameters of
+    a version-2 table (whose sum is taken inside every term)."""
+    k = int.from_bytes(blob[8:12], "little")
+    if int.from_bytes(blob[4:8], "little") == 2:
+        k -= int.from_bytes(blob[64:68], "little")
+    return k
+
+
 def ps_sum(blob: bytes, first: int = 0, count: int | None = None, nthreads: int = 1):
     """G * sum of the terms with Gray-code index in [first, first+count),
-    over sqrt2^e0 (not reduced).  Returns (c0, c1, c2, c3, e0)."""
+    over sqrt2^e0 (not reduced).  Returns (c0, c1, c2, c3, e0).  For a
+    version-2 table the index runs over the outer parameters and each term
+    is summed over every value of the inner ones."""
     lib = _load()
-    k = int.from_bytes(blob[8:12], "little")
     if count is None:
-        count = (1 << k) - first
+        count = (1 << outer_k(blob)) - first
     out = (C.c_uint64 * 8)()
     e = C.c_int32()
     rc = lib.oracle_ps_sum(blob, len(blob), first, count, nthreads, out, C.byref(e))

@@ -219,19 +219,31 @@ typedef struct {
     int64_t G[4];
 } ps_header;
 
+/* Version 2 appends {u32 k_inner, u32 0} to the header: the last k_inner
+ * of the k parameters are inner ones.  The value is the same Eq. 2 sum over
+ * all 2^k assignments; only the indexing of terms changes (see
+ * oracle_ps_sum). */
 typedef struct {
     ps_header h;
+    uint32_t k_inner;
     const uint8_t *lin, *quad, *node, *pair;
 } ps_view;
 
 static int ps_parse(const void *blob, size_t nbytes, ps_view *v) {
     if (nbytes < sizeof(ps_header)) return -1;
     memcpy(&v->h, blob, sizeof(ps_header));
-    if (v->h.magic != PS_MAGIC || v->h.version != 1 || v->h.k > 62) return -1;
-    size_t need = sizeof(ps_header) + 16u * v->h.n_lin + 16u * v->h.n_quad +
+    if (v->h.magic != PS_MAGIC || (v->h.version != 1 && v->h.version != 2) || v->h.k > 62) return -1;
+    size_t hsize = sizeof(ps_header) + (v->h.version == 2 ? 8u : 0u);
+    v->k_inner = 0;
+    if (v->h.version == 2) {
+        if (nbytes < hsize) return -1;
+        memcpy(&v->k_inner, (const uint8_t *)blob + sizeof(ps_header), 4);
+        if (v->k_inner > v->h.k) return -1;
+    }
+    size_t need = hsize + 16u * v->h.n_lin + 16u * v->h.n_quad +
                   16u * v->h.n_node + 24u * v->h.n_pair;
     if (nbytes < need) return -1;
-    const uint8_t *p = (const uint8_t *)blob + sizeof(ps_header);
+    const uint8_t *p = (const uint8_t *)blob + hsize;
     v->lin = p;  p += 16u * v->h.n_lin;
     v->quad = p; p += 16u * v->h.n_quad;
     v->node = p; p += 16u * v->h.n_node;
@@ -266,6 +278,11 @@ static abcd ps_term(const ps_view *v, uint64_t x, int *ovf) {
 
 /* Sum of the terms for Gray-code indices t in [first, first + count) (the
  * term of index t is the assignment x = t xor (t >> 1)), multiplied by G.
+ * With k_inner > 0 (version 2 tables) the index t runs over the first
+ * k_o = k - k_inner parameters only, and the term of index t is the sum of
+ * Eq. 2's terms over every value y of the inner parameters:
+ * x = gray(t) | (y << k_o), y in [0, 2^k_inner).  Over the whole range
+ * [0, 2^k_o) this is again the sum over all 2^k assignments.
  * out_c[8] = four signed 128-bit coefficients as (lo, hi) uint64 pairs,
  * in the basis {1, w, w^2, w^3}, over sqrt2^e0 (not reduced).
  * Returns 0, -1 for a bad blob or range, 1 if a 128-bit overflow occurred.
@@ -275,7 +292,8 @@ int oracle_ps_sum(const void *blob, size_t nbytes, uint64_t first, uint64_t coun
                   int nthreads, uint64_t out_c[8], int32_t *out_e) {
     ps_view v;
     if (ps_parse(blob, nbytes, &v) != 0) return -1;
-    uint64_t total = (uint64_t)1 << v.h.k;
+    const uint32_t k_o = v.h.k - v.k_inner;
+    const uint64_t total = (uint64_t)1 << k_o, n_inner = (uint64_t)1 << v.k_inner;
     if (first > total || count > total - first) return -1;
     if (nthreads < 1) nthreads = 1;
     abcd *part = (abcd *)calloc((size_t)nthreads, sizeof(abcd));
@@ -296,7 +314,8 @@ int oracle_ps_sum(const void *blob, size_t nbytes, uint64_t first, uint64_t coun
         int ovf = 0;
         for (uint64_t t = lo; t < lo + len; t++) {
             uint64_t x = t ^ (t >> 1);
-            s = abcd_add(s, ps_term(&v, x, &ovf), &ovf);
+            for (uint64_t y = 0; y < n_inner; y++)
+                s = abcd_add(s, ps_term(&v, x | (y << k_o), &ovf), &ovf);
         }
         part[tid] = s; povf[tid] = ovf;
     }

@@ -248,6 +248,44 @@ def test_ps_sum_ranges_add_up_and_threads_agree():
     assert oracle.ps_sum(blob, 5, 0)[:4] == (0, 0, 0, 0)
 
 
+@pytest.mark.parametrize("seed", range(10))
+def test_ps_sum_inner_parameters_brute_force_complex(seed):
+    # version-2 tables: the full value is Eq. 2 over all 2^k assignments, and
+    # the term of outer Gray index t sums the inner parameters at gray(t)
+    rng = random.Random(100 + seed)
+    k = rng.randint(1, 9)
+    ki = rng.randint(1, k)
+    ko = k - ki
+    ps = zi.synthetic_ps(200 + seed, k, n_lin=rng.randint(0, 6), n_quad=rng.randint(0, 4),
+                         n_node=rng.randint(0, 8), n_pair=rng.randint(0, 2),
+                         density=0.4, e0=rng.randint(0, 6),
+                         G=(rng.randint(-3, 3), 1, rng.randint(-2, 2), 0), k_inner=ki)
+    blob = ps.pack()
+    assert oracle.outer_k(blob) == ko
+    v = oracle.ps_sum(blob)
+    want = wc(ps.G) * sum(complex_term(ps, x) for x in range(1 << k)) / math.sqrt(2) ** ps.e0
+    assert v[4] == ps.e0
+    assert close(oracle.to_complex(v), want, 1e3)
+    for t in range(1 << ko):
+        g = t ^ (t >> 1)
+        term = wc(ps.G) * sum(complex_term(ps, g | (y << ko)) for y in range(1 << ki))
+        assert close(oracle.to_complex(oracle.ps_sum(blob, t, 1)), term / math.sqrt(2) ** ps.e0, 1e3)
+
+
+def test_ps_sum_inner_parameters_ranges_add_up():
+    ps = zi.synthetic_ps(7, 10, n_lin=6, n_quad=3, n_node=9, n_pair=2, k_inner=4)
+    blob = ps.pack()
+    full = oracle.ps_sum(blob)
+    assert oracle.ps_sum(zi.synthetic_ps(7, 10, n_lin=6, n_quad=3, n_node=9, n_pair=2).pack()) == full
+    for cut in (0, 1, 17, 32, 63, 64):
+        a = oracle.ps_sum(blob, 0, cut)
+        b = oracle.ps_sum(blob, cut, 64 - cut)
+        assert tuple(a[i] + b[i] for i in range(4)) == full[:4]
+    assert oracle.ps_sum(blob, nthreads=3) == full
+    with pytest.raises(ValueError):
+        oracle.ps_sum(blob, 0, 65)
+
+
 def test_ps_forms_of_a_known_amplitude():
     # <0|H T H|0> = (1 + w)/2, written three ways
     want = (1, 1, 0, 0, 2)

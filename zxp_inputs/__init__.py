@@ -235,7 +235,9 @@ def pack_bits(bits: Sequence[int]) -> bytes:
 
 PS_MAGIC = 0x5350585A  # "ZXPS"
 PS_VERSION = 1
+PS_VERSION_INNER = 2    # header followed by {u32 k_inner, u32 0}
 PS_HEADER = struct.Struct("<IIIIIIIi4q")
+PS_INNER = struct.Struct("<II")
 PS_LIN = struct.Struct("<QII")
 PS_QUAD = struct.Struct("<QQ")
 PS_NODE = struct.Struct("<QII")
@@ -250,7 +252,10 @@ class PSTables:
         w^(sum_lin c*l(x) + 4*sum_quad lA(x)*lB(x))
         * prod_node (1 + w^(g + 4 l(x)))
         * prod_pair (1 + w^(a + 4 lA) + w^(b + 4 lB) - w^(a + b + 4 (lA xor lB)))
-    with w = exp(i pi/4) and l(x) = parity(mask & x).
+    with w = exp(i pi/4) and l(x) = parity(mask & x).  With k_inner > 0
+    (packed as version 2) the last k_inner parameters are inner ones: the
+    value is unchanged, but a term index runs over the first k - k_inner
+    parameters and each term sums over every value of the inner ones.
     """
     k: int
     e0: int = 0
@@ -259,11 +264,15 @@ class PSTables:
     quad: List[Tuple[int, int]] = field(default_factory=list)
     node: List[Tuple[int, int]] = field(default_factory=list)
     pair: List[Tuple[int, int, int, int]] = field(default_factory=list)
+    k_inner: int = 0
 
     def pack(self) -> bytes:
-        parts = [PS_HEADER.pack(PS_MAGIC, PS_VERSION, self.k, len(self.lin),
+        ver = PS_VERSION_INNER if self.k_inner else PS_VERSION
+        parts = [PS_HEADER.pack(PS_MAGIC, ver, self.k, len(self.lin),
                                 len(self.quad), len(self.node), len(self.pair),
                                 self.e0, *[_i64(c) for c in self.G])]
+        if self.k_inner:
+            parts.append(PS_INNER.pack(self.k_inner, 0))
         parts += [PS_LIN.pack(m, c, 0) for m, c in self.lin]
         parts += [PS_QUAD.pack(a, b) for a, b in self.quad]
         parts += [PS_NODE.pack(m, g, 0) for m, g in self.node]
@@ -273,11 +282,15 @@ class PSTables:
     @staticmethod
     def unpack(blob: bytes) -> "PSTables":
         h = PS_HEADER.unpack_from(blob, 0)
-        if h[0] != PS_MAGIC or h[1] != PS_VERSION:
+        if h[0] != PS_MAGIC or h[1] not in (PS_VERSION, PS_VERSION_INNER):
             raise ValueError("not a parametric-scalar table blob")
         k, nl, nq, nn, npair, e0 = h[2], h[3], h[4], h[5], h[6], h[7]
         G = tuple(h[8:12])
         off = PS_HEADER.size
+        k_inner = 0
+        if h[1] == PS_VERSION_INNER:
+            k_inner = PS_INNER.unpack_from(blob, off)[0]
+            off += PS_INNER.size
         lin, quad, node, pair = [], [], [], []
         for _ in range(nl):
             m, c, _r = PS_LIN.unpack_from(blob, off); off += PS_LIN.size
@@ -291,7 +304,7 @@ class PSTables:
         for _ in range(npair):
             ma, mb, a, b = PS_PAIR.unpack_from(blob, off); off += PS_PAIR.size
             pair.append((ma, a, mb, b))
-        return PSTables(k, e0, G, lin, quad, node, pair)
+        return PSTables(k, e0, G, lin, quad, node, pair, k_inner)
 
 
 def _i64(v: int) -> int:
@@ -314,12 +327,13 @@ def _rand_mask(rng: SplitMix64, k: int, density: float) -> int:
 def synthetic_ps(seed: int, k: int, n_lin: int = 8, n_quad: int = 4,
                  n_node: int = 16, n_pair: int = 0, density: float = 0.25,
                  odd_nodes_only: bool = False, e0: int = 0,
-                 G=(1, 0, 0, 0)) -> PSTables:
+                 G=(1, 0, 0, 0), k_inner: int = 0) -> PSTables:
     """Random tables with the shape of a compiled scalar: k parameters,
     forms of the given mask density, node constants in Z8 (odd only when
-    asked), linear coefficients in Z8, and optional phase-pair rows."""
+    asked), linear coefficients in Z8, and optional phase-pair rows; the
+    last k_inner parameters are declared inner (a version-2 table)."""
     rng = SplitMix64(seed * 0x9E3779B1 + k)
-    ps = PSTables(k=k, e0=e0, G=tuple(G))
+    ps = PSTables(k=k, e0=e0, G=tuple(G), k_inner=k_inner)
     for _ in range(n_lin):
         ps.lin.append((_rand_mask(rng, k, density), rng.below(8)))
     for _ in range(n_quad):

@@ -79,7 +79,8 @@ typedef struct zxp_ctx zxp_ctx;        /* device + stream + workspaces */
 
 /* Statistics of a compiled scalar. */
 typedef struct {
-    uint32_t k;          /* Boolean parameters: the sum has 2^k terms */
+    uint32_t k;          /* Boolean parameters a term index runs over: the sum
+                            has 2^k terms (each summing 2^k_inner inner ones) */
     uint32_t n_lin;      /* linear phase rows (pi-pair rows with fixed Psi) */
     uint32_t n_quad;     /* quadratic rows (pi-pair rows, two parametric phases) */
     uint32_t n_node;     /* node rows (1 + e^{i Psi}) */
@@ -95,7 +96,10 @@ typedef struct {
                                     (lane-private 32 / 16 bit, warp-shared; odd: no folded
                                     bits), 9/10 block lookup (10: with folded bits),
                                     11 block lookup with lane-private counters */
-    uint32_t reserved[3];
+    uint32_t k_inner;    /* inner parameters, summed inside every term (0: none) */
+    uint32_t inner_bits; /* index bits of the inner table: k_inner + crossing forms
+                            (2^inner_bits entries of 32 bytes on the device) */
+    uint32_t reserved[1];
 } zxp_scalar_info_t;
 
 /* ---- context --------------------------------------------------------- */
@@ -114,15 +118,36 @@ void zxp_ctx_destroy(zxp_ctx *ctx);
  *        the probability that every qubit q in marg_mask reads out_bits[q]
  *        (the doubled diagram of Sec. 2.2; n_qubits <= 64).
  * in_bits may be NULL (all zero).  Arrays have n_qubits entries (0 or 1).
+ * A reduction that leaves 32 or more parameters is split as by
+ * zxp_scalar_split with default options (when that lowers the term count).
  * Errors: ZXP_EINVAL (qubit out of range, opcode, CNOT with q0 == q1),
  * ZXP_ETOOBIG (the reduction leaves more than 62 parameters). */
 int zxp_compile(const zxp_gate *gates, size_t n_gates, int n_qubits,
                 const uint8_t *in_bits, const uint8_t *out_bits,
                 uint64_t marg_mask, int kind, zxp_scalar **out);
 
+struct zxp_split_opts_s;
+/* zxp_compile with the split chosen by the caller: `split` NULL leaves the
+ * reduced scalar as it is (every parameter summed term by term, the
+ * paper's form); otherwise the scalar is split as by zxp_scalar_split with
+ * those options (zxp_split_opts).  Errors as zxp_compile, plus ZXP_EINVAL
+ * for bad options. */
+int zxp_compile_ex(const zxp_gate *gates, size_t n_gates, int n_qubits,
+                   const uint8_t *in_bits, const uint8_t *out_bits,
+                   uint64_t marg_mask, int kind, const struct zxp_split_opts_s *split,
+                   zxp_scalar **out);
+
 /* Build a scalar from the table layout (little endian):
- *   header  u32 magic 'ZXPS' (0x5350585A), u32 version 1, u32 k, u32 n_lin,
- *           u32 n_quad, u32 n_node, u32 n_pair, i32 e0, i64 G[4]
+ *   header  u32 magic 'ZXPS' (0x5350585A), u32 version (1, or 2 with inner
+ *           parameters), u32 k, u32 n_lin, u32 n_quad, u32 n_node,
+ *           u32 n_pair, i32 e0, i64 G[4]
+ *   version 2: u32 k_inner (1..k), u32 0 -- the last k_inner parameters
+ *           are inner: a term index runs over the first k - k_inner and each
+ *           term sums every value of the inner ones (the value is unchanged);
+ *           the outer parts of the forms that cross the two groups may not
+ *           use parameters 0-3 (ZXP_EINVAL), and the inner parameters plus
+ *           the distinct outer parts of crossing non-Clifford forms are at
+ *           most 26 (ZXP_ETOOBIG)
  *   n_lin  x {u64 mask, u32 c, u32 0}        -> w^(c * l(x))
  *   n_quad x {u64 maskA, u64 maskB}          -> w^(4 lA(x) lB(x))
  *   n_node x {u64 mask, u32 g, u32 0}        -> 1 + w^(g + 4 l(x))
@@ -137,9 +162,45 @@ int zxp_scalar_to_tables(const zxp_scalar *s, void *buf, size_t *nbytes);
 int zxp_scalar_info(const zxp_scalar *s, zxp_scalar_info_t *info);
 void zxp_scalar_free(zxp_scalar *s);
 
+/* ---- inner parameters -------------------------------------------------- */
+
+/* Options of zxp_scalar_split (zero fields: defaults). */
+typedef struct zxp_split_opts_s {
+    uint32_t min_k;           /* scalars with fewer parameters are copied (32) */
+    uint32_t max_inner;       /* inner parameters at most (22) */
+    uint32_t max_index_bits;  /* inner parameters + crossing forms, <= 26 (24) */
+    uint32_t max_cut;         /* crossing non-Clifford forms (3) */
+    uint32_t low_free;        /* lowest outer parameters free of the cut, >= 4 (10) */
+    uint32_t tries;           /* randomized attempts (24) */
+    uint64_t seed;            /* (0: a fixed seed) */
+    uint32_t reserved[4];
+} zxp_split_opts;
+
+/* Rewrite a scalar so that part of its parameters are summed inside every
+ * term (host only; no counterpart in the paper's evaluation, which sums all
+ * terms one by one).  The scalar's rows are functions of parity forms, so a
+ * linear change of variables rewrites it exactly; in variables where the
+ * non-Clifford rows sit on single coordinates (the graph form of the
+ * diagram) the parameters are cut into inner ones, coupled to the rest only
+ * by pi-pair (Clifford) terms and a few crossing forms, and outer ones.  For
+ * every outer assignment the sum over the inner parameters is a
+ * Walsh-Hadamard transform of the inner rows' product, read at the cut's
+ * parities: one table of 2^inner_bits entries, computed on the device when
+ * the scalar is first evaluated there (zxp_inner_sum).  The GPU then walks
+ * 2^(k - k_inner) terms instead of 2^k.  *out has the same value as s (a
+ * version-2 scalar when the split lowers the term count, else a copy).
+ * Errors: ZXP_EINVAL (s already split, bad options), ZXP_ENOMEM. */
+int zxp_scalar_split(const zxp_scalar *s, const zxp_split_opts *opts, zxp_scalar **out);
+
+/* Queue the computation of a split scalar's inner table on the context's
+ * stream (a no-op for other scalars).  Evaluations do this once per device
+ * by themselves; calling it again recomputes the table (e.g. to time it). */
+int zxp_inner_sum(zxp_ctx *ctx, const zxp_scalar *s);
+
 /* ---- evaluate (GPU, Sec. 3.3) ------------------------------------------ */
 
-/* Sum the terms with Gray-code index in [first, first + count), multiplied
+/* Sum the terms with Gray-code index in [first, first + count) (index t:
+ * outer parameters gray(t), every inner value), multiplied
  * by G, into *out as a raw partial over sqrt2^e0 (flags bit 0 set).  The
  * call blocks until the result is on the host.  Partials of disjoint
  * ranges combine with zxp_zomega_add; the total over [0, 2^k) gives the
@@ -159,7 +220,8 @@ int zxp_eval(zxp_ctx *ctx, const zxp_scalar *s, uint64_t first, uint64_t count,
 int zxp_eval_device(zxp_ctx *ctx, const zxp_scalar *s, uint64_t first, uint64_t count,
                     zxp_zomega *dev_out);
 
-/* zxp_eval_device without any allocation (the paper has no counterpart).
+/* zxp_eval_device without any allocation (the paper has no counterpart;
+ * scalars with inner parameters: ZXP_ETOOBIG).
  * For callers that cannot allocate device memory through the CUDA runtime:
  * code under a memory manager that owns the whole device (a framework's
  * caching allocator, a serving runtime's fixed arena) and latency-critical
@@ -262,7 +324,8 @@ typedef struct {
     uint32_t reserved[6];
 } zxp_batch_info_t;
 
-/* Errors: ZXP_EINVAL (n == 0, null scalar), ZXP_ENOMEM, ZXP_ECUDA. */
+/* Errors: ZXP_EINVAL (n == 0, null scalar, a scalar with inner
+ * parameters), ZXP_ENOMEM, ZXP_ECUDA. */
 int zxp_batch_create(zxp_ctx *ctx, const zxp_scalar *const *scalars, size_t n,
                      zxp_batch **out);
 /* Run the batch and wait: out[i] receives scalar i's full raw sum (as

@@ -295,6 +295,8 @@ int oracle_ps_sum(const void *blob, size_t nbytes, uint64_t first, uint64_t coun
     const uint32_t k_o = v.h.k - v.k_inner;
     const uint64_t total = (uint64_t)1 << k_o, n_inner = (uint64_t)1 << v.k_inner;
     if (first > total || count > total - first) return -1;
+    if (count && n_inner > UINT64_MAX / count) return -1;   /* more terms than any run could take */
+    const uint64_t flat = count * n_inner;
     if (nthreads < 1) nthreads = 1;
     abcd *part = (abcd *)calloc((size_t)nthreads, sizeof(abcd));
     int *povf = (int *)calloc((size_t)nthreads, sizeof(int));
@@ -307,15 +309,18 @@ int oracle_ps_sum(const void *blob, size_t nbytes, uint64_t first, uint64_t coun
 #ifdef _OPENMP
         tid = omp_get_thread_num(); nt = omp_get_num_threads();
 #endif
-        uint64_t ut = (uint64_t)tid, rem = count % (uint64_t)nt;
-        uint64_t lo = first + (count / (uint64_t)nt) * ut + (ut < rem ? ut : rem);
-        uint64_t len = count / (uint64_t)nt + (ut < rem ? 1 : 0);
+        /* each thread takes a contiguous piece of the (term, inner value)
+         * pairs f = (t - first) * n_inner + y */
+        uint64_t ut = (uint64_t)tid, rem = flat % (uint64_t)nt;
+        uint64_t lo = (flat / (uint64_t)nt) * ut + (ut < rem ? ut : rem);
+        uint64_t len = flat / (uint64_t)nt + (ut < rem ? 1 : 0);
+        uint64_t t = first + lo / n_inner, y = lo % n_inner;
         abcd s = abcd_zero();
         int ovf = 0;
-        for (uint64_t t = lo; t < lo + len; t++) {
+        for (uint64_t f = 0; f < len; f++) {
             uint64_t x = t ^ (t >> 1);
-            for (uint64_t y = 0; y < n_inner; y++)
-                s = abcd_add(s, ps_term(&v, x | (y << k_o), &ovf), &ovf);
+            s = abcd_add(s, ps_term(&v, x | (y << k_o), &ovf), &ovf);
+            if (++y == n_inner) { y = 0; t++; }
         }
         part[tid] = s; povf[tid] = ovf;
     }

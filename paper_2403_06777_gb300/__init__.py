@@ -43,7 +43,14 @@ class zxp_scalar_info_t(C.Structure):
                 ("acc_bits", C.c_uint32), ("form_bits", C.c_uint32), ("t_count", C.c_uint32),
                 ("node_words", C.c_uint32), ("other_words", C.c_uint32),
                 ("device_bytes", C.c_uint32), ("kernel_variant", C.c_uint32),
-                ("reserved", C.c_uint32 * 3)]
+                ("k_inner", C.c_uint32), ("inner_bits", C.c_uint32),
+                ("reserved", C.c_uint32 * 1)]
+
+
+class zxp_split_opts(C.Structure):
+    _fields_ = [("min_k", C.c_uint32), ("max_inner", C.c_uint32), ("max_index_bits", C.c_uint32),
+                ("max_cut", C.c_uint32), ("low_free", C.c_uint32), ("tries", C.c_uint32),
+                ("seed", C.c_uint64), ("reserved", C.c_uint32 * 4)]
 
 
 class zxp_batch_info_t(C.Structure):
@@ -107,10 +114,14 @@ def lib():
         L.zxp_ctx_destroy.argtypes, L.zxp_ctx_destroy.restype = [vp], None
         L.zxp_compile.argtypes = [C.c_char_p, sz, C.c_int, C.c_char_p, C.c_char_p, u64, C.c_int,
                                   C.POINTER(vp)]
+        L.zxp_compile_ex.argtypes = [C.c_char_p, sz, C.c_int, C.c_char_p, C.c_char_p, u64, C.c_int,
+                                     C.POINTER(zxp_split_opts), C.POINTER(vp)]
         L.zxp_scalar_from_tables.argtypes = [C.c_char_p, sz, C.POINTER(vp)]
         L.zxp_scalar_to_tables.argtypes = [vp, vp, C.POINTER(sz)]
         L.zxp_scalar_info.argtypes = [vp, C.POINTER(zxp_scalar_info_t)]
         L.zxp_scalar_free.argtypes, L.zxp_scalar_free.restype = [vp], None
+        L.zxp_scalar_split.argtypes = [vp, C.POINTER(zxp_split_opts), C.POINTER(vp)]
+        L.zxp_inner_sum.argtypes = [vp, vp]
         L.zxp_eval.argtypes = [vp, vp, u64, u64, zp]
         L.zxp_amplitude.argtypes = [vp, vp, zp]
         L.zxp_eval_device.argtypes = [vp, vp, u64, u64, vp]
@@ -240,17 +251,35 @@ def _gate_bytes(gates) -> bytes:
     return b"".join(st.pack(op, 0, q0, q1, 0) for op, q0, q1 in gates)
 
 
+def _split_opts(opts: dict):
+    o = zxp_split_opts()
+    for k, v in opts.items():
+        if k not in dict(zxp_split_opts._fields_) or k == "reserved":
+            raise TypeError(f"unknown split option {k}")
+        setattr(o, k, v)
+    return o
+
+
 def zxp_compile(gates, n_qubits: int, out_bits: Sequence[int],
                 in_bits: Sequence[int] | None = None, marg_mask: int = 0,
-                kind: int = ZXP_AMPLITUDE) -> Scalar:
+                kind: int = ZXP_AMPLITUDE, split=True) -> Scalar:
+    """split: True (zxp_compile: split with the default options when the
+    reduction leaves 32 or more parameters), False (zxp_compile_ex without
+    a split), or a dict of zxp_split_opts fields (zxp_compile_ex)."""
     gb = _gate_bytes(gates)
     h = C.c_void_p()
     ib = bytes(int(b) & 1 for b in in_bits) if in_bits is not None else None
     ob = bytes(int(b) & 1 for b in out_bits)
     if len(ob) != n_qubits or (ib is not None and len(ib) != n_qubits):
         raise ZxpError(ZXP_EINVAL, "zxp_compile: bit arrays must have n_qubits entries")
-    _check(lib().zxp_compile(gb, len(gb) // 8, n_qubits, ib, ob, marg_mask, kind, C.byref(h)),
-           "zxp_compile")
+    if split is True:
+        _check(lib().zxp_compile(gb, len(gb) // 8, n_qubits, ib, ob, marg_mask, kind, C.byref(h)),
+               "zxp_compile")
+    else:
+        o = _split_opts(split) if split else None
+        _check(lib().zxp_compile_ex(gb, len(gb) // 8, n_qubits, ib, ob, marg_mask, kind,
+                                    C.byref(o) if o is not None else None, C.byref(h)),
+               "zxp_compile_ex")
     return Scalar(h.value)
 
 
@@ -340,6 +369,20 @@ def zxp_scalar_info(s: Scalar) -> dict:
 
 def zxp_scalar_free(s: Scalar):
     s.free()
+
+
+def zxp_scalar_split(s: Scalar, **opts) -> Scalar:
+    """The same scalar with part of its parameters summed inside every term
+    (zxp_split_opts fields as keywords; omitted ones take the defaults)."""
+    o = _split_opts(opts)
+    h = C.c_void_p()
+    _check(lib().zxp_scalar_split(s.handle, C.byref(o) if opts else None, C.byref(h)), "zxp_scalar_split")
+    return Scalar(h.value)
+
+
+def zxp_inner_sum(ctx: Ctx, s: Scalar):
+    """Queue the (re)computation of a split scalar's inner table."""
+    _check(lib().zxp_inner_sum(ctx.handle, s.handle), "zxp_inner_sum")
 
 
 def zxp_eval(ctx: Ctx, s: Scalar, first: int = 0, count: int | None = None):

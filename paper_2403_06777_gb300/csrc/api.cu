@@ -19,6 +19,7 @@
 #include "objects.h"
 #include "plan.h"
 #include "ps.h"
+#include "split.h"
 #include "zring.h"
 
 using namespace zxp;
@@ -84,16 +85,16 @@ int ensure_device_tables(const zxp_scalar* s, zxp_ctx* ctx, DevTables* out, uint
         if (q != cudaSuccess) return ZXP_ECUDA;
     }
     ctx->stage_seq[slot] = 0;
-    if (ctx->stage_cap[slot] < L.total) {
+    if (ctx->stage_cap[slot] < L.copied) {
         if (ctx->stage[slot]) cudaFreeHost(ctx->stage[slot]);
         ctx->stage[slot] = nullptr;
         ctx->stage_cap[slot] = 0;
-        const size_t cap = std::max(L.total, (size_t)64 << 10);
+        const size_t cap = std::max(L.copied, (size_t)64 << 10);
         if (cudaMallocHost(&ctx->stage[slot], cap) != cudaSuccess) return ZXP_ENOMEM;
         ctx->stage_cap[slot] = cap;
     }
     unsigned char* host = ctx->stage[slot];
-    memset(host, 0, L.total);
+    memset(host, 0, L.copied);
     pack_tables(s->plan, L, host);
     cudaMemPool_t pool = table_pool(ctx->device);
     if (!pool) return ZXP_ECUDA;
@@ -110,7 +111,7 @@ int ensure_device_tables(const zxp_scalar* s, zxp_ctx* ctx, DevTables* out, uint
     }
     if (!base && cudaMallocFromPoolAsync((void**)&base, L.total, pool, ctx->upload) != cudaSuccess)
         return ZXP_ENOMEM;
-    if (cudaMemcpyAsync(base, host, L.total, cudaMemcpyHostToDevice, ctx->upload) != cudaSuccess ||
+    if (cudaMemcpyAsync(base, host, L.copied, cudaMemcpyHostToDevice, ctx->upload) != cudaSuccess ||
         cudaEventRecord(ctx->stage_ev[slot], ctx->upload) != cudaSuccess) {
         cudaFreeAsync(base, ctx->upload);
         return ZXP_ECUDA;
@@ -125,6 +126,13 @@ int ensure_device_tables(const zxp_scalar* s, zxp_ctx* ctx, DevTables* out, uint
     c.t = device_tables(L, base);
     c.stream = ctx->stream;
     c.ctx_id = ctx->id;
+    // the inner table (inner parameters) is computed on the device, after
+    // the copy, in the order of the context's stream
+    if (queue_inner_table(s->plan, c.t, ctx->stream) != cudaSuccess) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFreeAsync(base, ctx->stream);
+        return ZXP_ECUDA;
+    }
     s->dev[ctx->device] = c;
     *out = c.t;
     return ZXP_OK;
@@ -162,8 +170,11 @@ void launch_shape(const zxp_ctx* ctx, const Plan& pl, uint64_t count, uint64_t* 
     sum_shape(pl, ctx->sm_count, ctx->max_grid, count, span, grid);
 }
 
+// Terms of a scalar: assignments of its outer parameters.
+uint64_t term_count(const zxp_scalar* s) { return 1ull << (s->ps.k - s->ps.k_inner); }
+
 int check_range(const zxp_scalar* s, uint64_t first, uint64_t count) {
-    const uint64_t total = 1ull << s->ps.k;
+    const uint64_t total = term_count(s);
     if (first > total || count > total - first) return ZXP_EINVAL;
     return ZXP_OK;
 }
@@ -197,8 +208,8 @@ int enqueue(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, D
     uint64_t span;
     int grid;
     launch_shape(ctx, s->plan, count, &span, &grid);
-    return cuda_status(sum_launch(s->plan, d.table, d.pv, d.rows, d.adj, d.seek, first, count, span,
-                                  grid, ctx->acc, ctx->counter, dres, host_result, ctx->stream));
+    return cuda_status(sum_launch(s->plan, d.table, d.pv, d.rows, d.adj, d.seek, d.zq, d.ftab, first, count,
+                                  span, grid, ctx->acc, ctx->counter, dres, host_result, ctx->stream));
 }
 
 }  // namespace
@@ -321,15 +332,64 @@ void zxp_ctx_destroy(zxp_ctx* c) {
 }
 
 
+namespace {
+int split_options(const zxp_split_opts* opts, SplitOptions* so) {
+    if (!opts) return ZXP_OK;
+    if (opts->min_k) so->min_k = opts->min_k;
+    if (opts->max_inner) so->max_inner = opts->max_inner;
+    if (opts->max_index_bits) so->max_index_bits = opts->max_index_bits;
+    if (opts->max_cut) so->max_cut = opts->max_cut;
+    if (opts->low_free) so->low_free = opts->low_free;
+    if (opts->tries) so->tries = (int)opts->tries;
+    if (opts->seed) so->seed = opts->seed;
+    if (so->low_free < 4 || so->max_index_bits > kMaxInnerBits) return ZXP_EINVAL;
+    return ZXP_OK;
+}
+}  // namespace
+
 int zxp_compile(const zxp_gate* gates, size_t n_gates, int n_qubits, const uint8_t* in_bits,
                 const uint8_t* out_bits, uint64_t marg_mask, int kind, zxp_scalar** out) {
+    const zxp_split_opts defaults = {};
+    return zxp_compile_ex(gates, n_gates, n_qubits, in_bits, out_bits, marg_mask, kind, &defaults, out);
+}
+
+int zxp_compile_ex(const zxp_gate* gates, size_t n_gates, int n_qubits, const uint8_t* in_bits,
+                   const uint8_t* out_bits, uint64_t marg_mask, int kind, const zxp_split_opts* split,
+                   zxp_scalar** out) {
     if (!out) return ZXP_EINVAL;
     *out = nullptr;
     PS ps;
     CompileOptions opt;
-    int st = compile_circuit(gates, n_gates, n_qubits, in_bits, out_bits, marg_mask, kind, opt, &ps);
+    opt.split = split != nullptr;
+    int st = split_options(split, &opt.split_opt);
+    if (st != ZXP_OK) return st;
+    st = compile_circuit(gates, n_gates, n_qubits, in_bits, out_bits, marg_mask, kind, opt, &ps);
     if (st != ZXP_OK) return st;
     return make_scalar(std::move(ps), out);
+}
+
+int zxp_scalar_split(const zxp_scalar* s, const zxp_split_opts* opts, zxp_scalar** out) {
+    if (!s || !out) return ZXP_EINVAL;
+    *out = nullptr;
+    if (s->ps.k_inner) return ZXP_EINVAL;
+    SplitOptions so;
+    int st = split_options(opts, &so);
+    if (st != ZXP_OK) return st;
+    PS ps;
+    st = split_scalar(s->ps, so, &ps);
+    if (st != ZXP_OK) return st;
+    return make_scalar(std::move(ps), out);
+}
+
+int zxp_inner_sum(zxp_ctx* ctx, const zxp_scalar* s) {
+    if (!ctx || !s) return ZXP_EINVAL;
+    if (!s->ps.k_inner) return ZXP_OK;
+    DeviceGuard g(ctx->device);
+    DevTables d;
+    int st = ensure_device_tables(s, ctx, &d);
+    if (st != ZXP_OK) return st;
+    std::lock_guard<std::mutex> lk(s->mu);
+    return cuda_status(queue_inner_table(s->plan, d, ctx->stream));
 }
 
 int zxp_compile_param(const zxp_gate* gates, size_t n_gates, int n_qubits, const uint8_t* in_bits,
@@ -401,7 +461,9 @@ int zxp_scalar_to_tables(const zxp_scalar* s, void* buf, size_t* nbytes) {
 int zxp_scalar_info(const zxp_scalar* s, zxp_scalar_info_t* info) {
     if (!s || !info) return ZXP_EINVAL;
     memset(info, 0, sizeof *info);
-    info->k = s->ps.k;
+    info->k = s->ps.k - s->ps.k_inner;
+    info->k_inner = s->ps.k_inner;
+    info->inner_bits = s->plan.inner_bits;
     info->n_lin = (uint32_t)s->ps.lin.size();
     info->n_quad = (uint32_t)s->ps.quad.size();
     info->n_node = (uint32_t)s->ps.node.size();
@@ -458,7 +520,7 @@ int zxp_zomega_canon(const zxp_zomega* in, zxp_zomega* out) {
 int zxp_amplitude(zxp_ctx* ctx, const zxp_scalar* s, zxp_zomega* out) {
     if (!s) return ZXP_EINVAL;
     zxp_zomega raw;
-    int st = zxp_eval(ctx, s, 0, 1ull << s->ps.k, &raw);
+    int st = zxp_eval(ctx, s, 0, term_count(s), &raw);
     if (st != ZXP_OK) return st;
     zxp_zomega_canon(&raw, out);
     return s->ps.e0 > 124 ? ZXP_EOVERFLOW : ZXP_OK;
@@ -526,7 +588,7 @@ int zxp_submit_tables(zxp_ctx* ctx, const void* blob, size_t nbytes, uint64_t* t
     zxp_scalar* s = nullptr;
     int st = zxp_scalar_from_tables(blob, nbytes, &s);
     if (st != ZXP_OK) return st;
-    st = zxp_submit(ctx, s, 0, 1ull << s->ps.k, ticket);
+    st = zxp_submit(ctx, s, 0, term_count(s), ticket);
     if (st != ZXP_OK) {
         zxp_scalar_free(s);
         return st;
@@ -676,7 +738,7 @@ extern "C" int zxp_batch_create(zxp_ctx* ctx, const zxp_scalar* const* scalars, 
     std::map<int, size_t> gidx;
     for (size_t i = 0; i < n; i++) {
         const zxp_scalar* s = scalars[i];
-        if (!s) return ZXP_EINVAL;
+        if (!s || s->ps.k_inner) return ZXP_EINVAL;   // (inner parameters: single-scalar path only)
         DevTables d;
         int st = ensure_device_tables(s, ctx, &d);
         if (st != ZXP_OK) return st;
@@ -837,6 +899,7 @@ extern "C" int zxp_eval_noalloc(const zxp_scalar* s, uint64_t first, uint64_t co
     int st = check_range(s, first, count);
     if (st != ZXP_OK) return st;
     const Plan& pl = s->plan;
+    if (pl.k_inner) return ZXP_ETOOBIG;   // the inner table does not fit the static scratch
     const size_t tb = pl.table.size() * sizeof(zw64), pb = pl.pv.size() * sizeof(zw64);
     const size_t fb = pl.rows.size() * sizeof(uint32_t), ab = pl.adj.size() * sizeof(uint64_t);
     const size_t o_pv = kNoAllocTablesOff + tb, o_f = (o_pv + pb + 15) & ~(size_t)15;
@@ -892,7 +955,8 @@ extern "C" int zxp_eval_noalloc(const zxp_scalar* s, uint64_t first, uint64_t co
                                   reinterpret_cast<const zw64*>(base + o_pv),
                                   reinterpret_cast<const uint32_t*>(base + o_f),
                                   reinterpret_cast<const uint64_t*>(base + o_adj),
-                                  reinterpret_cast<const uint32_t*>(base + o_seek), first, count, sp,
+                                  reinterpret_cast<const uint32_t*>(base + o_seek), nullptr, nullptr, first,
+                                  count, sp,
                                   (int)g, reinterpret_cast<zw64*>(base + kNoAllocAccOff),
                                   reinterpret_cast<unsigned int*>(base),
                                   reinterpret_cast<DevResult*>(dev_out), false, stream));

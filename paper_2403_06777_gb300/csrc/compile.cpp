@@ -833,6 +833,11 @@ int compile_circuit(const zxp_gate* gates, size_t n_gates, int n, const uint8_t*
     int st = compile_impl(gates, n_gates, n, in_bits, out_bits, nullptr, marg_mask, kind, opt, &pps);
     if (st != ZXP_OK) return st;
     bind(pps, 0, out);
+    if (opt.split && out->k >= opt.split_opt.min_k) {
+        PS sp;
+        if ((st = split_scalar(*out, opt.split_opt, &sp)) != ZXP_OK) return st;
+        *out = std::move(sp);
+    }
     return ZXP_OK;
 }
 

@@ -6,6 +6,7 @@
 
 #include "param.h"
 #include "ps.h"
+#include "split.h"
 
 struct zxp_gate;
 
@@ -15,6 +16,8 @@ struct CompileOptions {
     int tries = 8;            // randomized reduction orders; the smallest k wins
     bool allow_pairs = true;  // emit phase-pair rows (Eq. 3) for adjacent T-like pairs
     uint64_t seed = 0x5eed;
+    bool split = false;       // sum inner parameters inside each term (split.h)
+    SplitOptions split_opt;
 };
 
 struct CompileStats {

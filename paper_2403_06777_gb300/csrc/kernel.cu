@@ -70,16 +70,19 @@ int sum_threads() { return kThreads; }
 int sum_variant(const Plan& pl) { return variant(pl); }
 
 cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, const uint32_t* dF,
-                       const uint64_t* dADJ, const uint32_t* dS, uint64_t first, uint64_t count,
-                       uint64_t span,
-                       int grid, zw64* acc,
+                       const uint64_t* dADJ, const uint32_t* dS, const uint32_t* dzq, const zw64* dftab,
+                       uint64_t first, uint64_t count, uint64_t span, int grid, zw64* acc,
                        unsigned int* counter, DevResult* result, bool host_result, cudaStream_t stream) {
     KernelFn fn = pick(pl);
     const size_t smem = sum_smem_bytes(pl);
     cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(fn), smem);
     if (e != cudaSuccess) return e;
+    if (pl.k_inner && (!dzq || !dftab)) return cudaErrorInvalidValue;
+    KernelParams kp = pl.kp;
+    kp.zqcol = dzq;
+    kp.ftab = dftab;
     const uint64_t nslices = (count + span - 1) / span;
-    fn<<<grid, block_threads(pl), smem, stream>>>(pl.kp, dtable, dpv, dF, dADJ, dS, first, count, span, nslices,
+    fn<<<grid, block_threads(pl), smem, stream>>>(kp, dtable, dpv, dF, dADJ, dS, first, count, span, nslices,
                                          acc, counter, pl.K, pl.e0, result, host_result ? 1 : 0);
     return cudaGetLastError();
 }

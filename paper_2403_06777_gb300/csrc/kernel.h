@@ -40,10 +40,20 @@ struct DevResult {
 // K * (sum of the table terms) over sqrt2^e0, flagged raw, its flags word
 // written last with a release store (system scope when host_result: a host
 // may poll it in pinned memory; else device scope).
+// With inner parameters (pl.k_inner > 0), dzq holds the plan's zqcol and
+// dftab its inner table (inner_table_launch); both null otherwise.
 cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, const uint32_t* drows,
-                       const uint64_t* dADJ, const uint32_t* dS, uint64_t first, uint64_t count,
-                       uint64_t span, int grid, zw64* acc, unsigned int* counter,
-                       DevResult* result, bool host_result, cudaStream_t stream);
+                       const uint64_t* dADJ, const uint32_t* dS, const uint32_t* dzq, const zw64* dftab,
+                       uint64_t first, uint64_t count, uint64_t span, int grid, zw64* acc,
+                       unsigned int* counter, DevResult* result, bool host_result, cudaStream_t stream);
+
+// The inner table of a scalar with inner parameters (inner.cu): 2^bits
+// entries (bits = inner.kp.k) at ftab, the Walsh-Hadamard transform over the
+// low k_inner bits of the inner product that the plan `inner` describes;
+// its term table, phase-pair values, flip rows and adjacency rows are at
+// itab, ipv, ifr, iadj (device memory).
+cudaError_t inner_table_launch(const Plan& inner, uint32_t k_inner, const zw64* itab, const zw64* ipv,
+                               const uint32_t* ifr, const uint64_t* iadj, zw64* ftab, cudaStream_t stream);
 
 // ---- batches (batch.cu) -----------------------------------------------------
 

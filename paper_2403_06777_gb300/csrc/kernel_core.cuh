@@ -44,6 +44,13 @@ __device__ __forceinline__ zw64 lds_zw(const zw64* p) {
     return zw_make(a.x, a.y, b.x, b.y);
 }
 
+// read-only global load of a Z[w] value (the inner table)
+__device__ __forceinline__ zw64 ldg_zw(const zw64* p) {
+    const ulonglong2* q = reinterpret_cast<const ulonglong2*>(p);
+    const ulonglong2 a = __ldg(q), b = __ldg(q + 1);
+    return zw_make(a.x, a.y, b.x, b.y);
+}
+
 __device__ __forceinline__ zw64 shfl_xor_zw(zw64 v, int off) {
     zw64 r;
 #pragma unroll
@@ -80,6 +87,8 @@ constexpr uint32_t kHistMaxEntriesShared = 2048;
 constexpr uint32_t kLutEntries = (1u << kLutMaxBits) + 8u;
 inline int hist_mode(const Plan& pl) {
     if (pl.general) return 0;
+    // inner parameters: lane-private counters (folded per lane) or the table
+    if (pl.k_inner) return pl.kp.tab_size <= kHistMaxEntries32 ? 1 : (pl.kp.tab_size <= kHistMaxEntries16 ? 2 : 0);
     if (pl.lut_ok) return pl.lut_lane ? 5 : 4;
     if (pl.kp.tab_size <= kHistMaxEntries32) return 1;
     if (pl.kp.tab_size <= kHistMaxEntries16) return 2;
@@ -578,6 +587,8 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
     const uint32_t ntab = p.tab_size;
     const uint32_t nwords = HIST == 2 ? (ntab + 1) / 2 : ntab;
     uint32_t* const wshared = sH + warp * ntab;   // HIST 3: this warp's counters
+    // inner parameters (table, general and lane-private counting variants)
+    const bool outer = (HIST == 0 || HIST == 1 || HIST == 2) && p.zq_lo < 64u;
 
     // flip rows and adjacency of the three lowest variables, in registers:
     // inside an aligned block of 8 Gray steps they are the only ones flipped
@@ -681,6 +692,34 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                 }
                 Jl = P0 + 2u * P1 + 4u * ((uint32_t)__popc(X2) + q);
             }
+            // the run's sum (table and general variants), and with inner
+            // parameters the cut parities zq of the current assignment
+            zw64 ai = zw_zero();
+            uint32_t zq = 0;
+            if (outer)
+                for (uint64_t m = x >> p.zq_lo; m; m &= m - 1)
+                    zq ^= __ldg(p.zqcol + p.zq_lo + (uint32_t)__ffsll((long long)m) - 1u);
+            // inner parameters: the terms since the last flush times the
+            // inner table at zq (a lane-private count fold for HIST 1, 2)
+            auto flush = [&]() {
+                zw64 sum = ai;
+                if (HIST == 1 || HIST == 2) {
+                    uint32_t* const wb = sH + warp * nwords * 32u + lane;
+                    for (uint32_t i = 0; i < nwords; i++) {
+                        const uint32_t c = wb[i * 32u];
+                        if (!c) continue;
+                        wb[i * 32u] = 0u;
+                        if (HIST == 2) {
+                            if (c & 0xFFFFu) sum = zw_madd32(sum, lds_zw(sT + 2 * i), c & 0xFFFFu);
+                            if (c >> 16) sum = zw_madd32(sum, lds_zw(sT + 2 * i + 1), c >> 16);
+                        } else {
+                            sum = zw_madd32(sum, lds_zw(sT + i), c);
+                        }
+                    }
+                }
+                acc = zw_add(acc, zw_mul(sum, ldg_zw(p.ftab + zq)));
+                ai = zw_zero();
+            };
 
             // one term at the current state
             auto term = [&]() {
@@ -710,7 +749,7 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                     else if (HIST == 1)
                         atomicAdd(sH + ((warp * nwords + idx) << 5) + lane, 1u);
                     else
-                        acc = zw_add(acc, lds_zw(sT + idx));
+                        ai = zw_add(ai, lds_zw(sT + idx));
                 } else if (Zb == 0) {
                     const uint32_t J = Jl & 7u;
                     zw64 v = lds_zw(sT + J * p.tab_stride + M);
@@ -720,7 +759,7 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                             v = zw_mul(v, lds_zw(sPV + 4 * j + b));
                         }
                     }
-                    acc = zw_add(acc, v);
+                    ai = zw_add(ai, v);
                 }
             };
             // flip of variable i with step row f (before the XOR: the phase
@@ -763,6 +802,11 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                 // x(t) = x(t-1) ^ (1 << ctz(t))
                 const uint32_t tl = (uint32_t)t;
                 const int i = tl ? __ffs(tl) - 1 : 31 + __ffs((uint32_t)(t >> 32));
+                if (outer && (uint32_t)i >= p.zq_lo) {
+                    // a flip that changes the cut parities ends the run
+                    const uint32_t dz = __ldg(p.zqcol + i);
+                    if (dz) { flush(); zq ^= dz; }
+                }
                 Jl += ((uint32_t)(a >> i) & 1u) << 2;
                 a ^= sADJ[i];
                 uint32_t fr[RW];
@@ -773,12 +817,15 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                 }
                 step(fr);
             }
+            if (outer) flush();
+            else if (HIST == 0) acc = zw_add(acc, ai);
         }
         // a thread with several slices folds after each one, so no counter
-        // can overflow (16-bit counters: every slice is shorter than 2^16)
-        if (HIST && fold_each) fold(true);
+        // can overflow (16-bit counters: every slice is shorter than 2^16);
+        // with inner parameters every lane has folded its own counters
+        if (HIST && fold_each && !outer) fold(true);
     }
-    if (HIST && !fold_each && (final_fold || HIST < 3)) fold(clear_on_exit);
+    if (HIST && !outer && !fold_each && (final_fold || HIST < 3)) fold(clear_on_exit);
 }
 
 // Warp-shared counters (HIST 3, 4) left unfolded by walk: merge the warps'

@@ -20,20 +20,36 @@ static_assert(sizeof(zxp::DevResult) == sizeof(zxp_zomega), "result record layou
 
 namespace zxp {
 
-// Device addresses of one scalar's tables.
+// Device addresses of one scalar's tables.  With inner parameters also the
+// inner plan's term table, phase-pair values, flip rows and adjacency, the
+// outer variables' cut columns and the inner table (plan.h).
 struct DevTables {
     zw64* table = nullptr;
     zw64* pv = nullptr;
     uint32_t* rows = nullptr;
     uint64_t* adj = nullptr;
     uint32_t* seek = nullptr;
+    zw64* itab = nullptr;
+    zw64* ipv = nullptr;
+    uint32_t* ifr = nullptr;
+    uint64_t* iadj = nullptr;
+    uint32_t* zq = nullptr;
+    zw64* ftab = nullptr;
 };
 
 // Byte offsets of the tables in one contiguous block:
-// term table | phase-pair values | step rows | adjacency | seek tables.
+// term table | phase-pair values | step rows | adjacency | seek tables,
+// then with inner parameters: inner term table | inner pair values | inner
+// flip rows | inner adjacency | cut columns | inner table.  The first
+// `copied` bytes come from the host; the inner table is written on the
+// device.
 struct TableLayout {
-    size_t o_pv = 0, o_f = 0, o_adj = 0, o_seek = 0, total = 0;
+    size_t o_pv = 0, o_f = 0, o_adj = 0, o_seek = 0;
+    size_t o_itab = 0, o_ipv = 0, o_ifr = 0, o_iadj = 0, o_zq = 0, o_ftab = 0;
+    size_t copied = 0, total = 0;
 };
+
+inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 inline TableLayout table_layout(const Plan& pl) {
     TableLayout L;
@@ -42,14 +58,26 @@ inline TableLayout table_layout(const Plan& pl) {
     // seek tables, then the block lookup (if any) right after them
     const size_t sb = pl.seek.size() * sizeof(uint32_t) + pl.lut.size() * sizeof(uint64_t);
     L.o_pv = tb;
-    L.o_f = (L.o_pv + pb + 15) & ~(size_t)15;
-    L.o_adj = (L.o_f + fb + 15) & ~(size_t)15;   // every region 16-byte aligned (bulk copies)
-    L.o_seek = (L.o_adj + ab + 15) & ~(size_t)15;
+    L.o_f = align16(L.o_pv + pb);
+    L.o_adj = align16(L.o_f + fb);   // every region 16-byte aligned (bulk copies)
+    L.o_seek = align16(L.o_adj + ab);
     L.total = L.o_seek + sb + 16;
+    L.copied = L.total;
+    if (pl.k_inner && pl.inner) {
+        const Plan& in = *pl.inner;
+        L.o_itab = align16(L.total);
+        L.o_ipv = align16(L.o_itab + in.table.size() * sizeof(zw64));
+        L.o_ifr = align16(L.o_ipv + in.pv.size() * sizeof(zw64));
+        L.o_iadj = align16(L.o_ifr + in.frows.size() * sizeof(uint32_t));
+        L.o_zq = align16(L.o_iadj + in.adj.size() * sizeof(uint64_t));
+        L.o_ftab = (L.o_zq + pl.zqcol.size() * sizeof(uint32_t) + 255) & ~(size_t)255;
+        L.copied = L.o_ftab;
+        L.total = L.o_ftab + (sizeof(zw64) << pl.inner_bits);
+    }
     return L;
 }
 
-// Fill dst (L.total bytes, zeroed by the caller) with the tables.
+// Fill dst (L.copied bytes, zeroed by the caller) with the tables.
 inline void pack_tables(const Plan& pl, const TableLayout& L, unsigned char* dst) {
     if (!pl.table.empty()) memcpy(dst, pl.table.data(), pl.table.size() * sizeof(zw64));
     if (!pl.pv.empty()) memcpy(dst + L.o_pv, pl.pv.data(), pl.pv.size() * sizeof(zw64));
@@ -58,6 +86,14 @@ inline void pack_tables(const Plan& pl, const TableLayout& L, unsigned char* dst
     if (!pl.seek.empty()) memcpy(dst + L.o_seek, pl.seek.data(), pl.seek.size() * sizeof(uint32_t));
     if (!pl.lut.empty())
         memcpy(dst + L.o_seek + pl.seek.size() * sizeof(uint32_t), pl.lut.data(), pl.lut.size() * sizeof(uint64_t));
+    if (pl.k_inner && pl.inner) {
+        const Plan& in = *pl.inner;
+        if (!in.table.empty()) memcpy(dst + L.o_itab, in.table.data(), in.table.size() * sizeof(zw64));
+        if (!in.pv.empty()) memcpy(dst + L.o_ipv, in.pv.data(), in.pv.size() * sizeof(zw64));
+        if (!in.frows.empty()) memcpy(dst + L.o_ifr, in.frows.data(), in.frows.size() * sizeof(uint32_t));
+        if (!in.adj.empty()) memcpy(dst + L.o_iadj, in.adj.data(), in.adj.size() * sizeof(uint64_t));
+        memcpy(dst + L.o_zq, pl.zqcol.data(), pl.zqcol.size() * sizeof(uint32_t));
+    }
 }
 
 inline DevTables device_tables(const TableLayout& L, unsigned char* base) {
@@ -67,7 +103,21 @@ inline DevTables device_tables(const TableLayout& L, unsigned char* base) {
     d.rows = reinterpret_cast<uint32_t*>(base + L.o_f);
     d.adj = reinterpret_cast<uint64_t*>(base + L.o_adj);
     d.seek = reinterpret_cast<uint32_t*>(base + L.o_seek);
+    if (L.o_ftab) {
+        d.itab = reinterpret_cast<zw64*>(base + L.o_itab);
+        d.ipv = reinterpret_cast<zw64*>(base + L.o_ipv);
+        d.ifr = reinterpret_cast<uint32_t*>(base + L.o_ifr);
+        d.iadj = reinterpret_cast<uint64_t*>(base + L.o_iadj);
+        d.zq = reinterpret_cast<uint32_t*>(base + L.o_zq);
+        d.ftab = reinterpret_cast<zw64*>(base + L.o_ftab);
+    }
     return d;
+}
+
+// Queue the computation of a scalar's inner table (device tables d).
+inline cudaError_t queue_inner_table(const Plan& pl, const DevTables& d, cudaStream_t stream) {
+    if (!pl.k_inner || !pl.inner) return cudaSuccess;
+    return inner_table_launch(*pl.inner, pl.k_inner, d.itab, d.ipv, d.ifr, d.iadj, d.ftab, stream);
 }
 
 // Descriptor the batch kernel reads for a scalar whose tables are at d.

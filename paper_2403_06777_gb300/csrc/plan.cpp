@@ -26,12 +26,15 @@ struct Form {
     uint32_t inv;
 };
 
-}  // namespace
+int build_split_plan(const PS& ps, Plan* out);
 
-int build_plan(const PS& ps, Plan* out) {
+// allow_lut: the block lookup may be built (not for the outer rows of a
+// scalar with inner parameters, whose walk folds per lane).
+int build_plain_plan(const PS& ps, bool allow_lut, Plan* out) {
     Plan pl;
     memset(&pl.kp, 0, sizeof pl.kp);
     KernelParams& kp = pl.kp;
+    kp.zq_lo = 64;
     const uint32_t k = ps.k;
     if (k > (uint32_t)kMaxK) return ZXP_ETOOBIG;
     kp.k = k;
@@ -122,7 +125,7 @@ int build_plan(const PS& ps, Plan* out) {
     const uint64_t low3 = 7;
     // (phase-pair and zero forms may not hold variables 0-2: their bits are
     // then constant inside a block and select the block's counter plane)
-    bool lut_try = k >= 3 && pair_masks.size() <= 2 * (size_t)kFoldPairs;
+    bool lut_try = allow_lut && k >= 3 && pair_masks.size() <= 2 * (size_t)kFoldPairs;
     for (uint64_t m : pair_masks) lut_try = lut_try && !(m & 7);
     for (auto& z : zero) lut_try = lut_try && !(z.mask & 7);
     uint32_t lut_nn = 0, lut_no = 0;
@@ -380,6 +383,105 @@ int build_plan(const PS& ps, Plan* out) {
     pl.has_zero = !zero.empty();
     *out = std::move(pl);
     return ZXP_OK;
+}
+
+// A scalar with inner parameters (the last k_inner bits of every mask):
+// every row is split by its masks' inner and outer parts.
+//   * rows on outer bits only stay outer rows;
+//   * rows on inner bits only become rows of the inner product g(u);
+//   * the Clifford coupling of the two groups is bilinear: a quadratic row
+//     4 (aI ^ aO)(bI ^ bO) = 4 aI bI + 4 aI bO + 4 aO bI + 4 aO bO (mod 8), an
+//     even linear row c (lI ^ lO) = c lI + c lO (+ 4 lI lO when c = 2 mod 4);
+//     its cut terms 4 x_i . z_i(x_O) are the Walsh-Hadamard kernel, z_i the
+//     XOR of the outer forms paired with inner variable i;
+//   * a non-Clifford row (odd linear phase, node, phase-pair) on both groups
+//     keeps its inner form and gains one cut bit q_j = its outer form
+//     (identical outer forms share a bit): it becomes a row of g over
+//     u = (x_I, q).
+// The inner table is then F[z | q << k_inner] = sum over x_I of
+// g(x_I, q) (-1)^(x_I . z), and the scalar's value is
+//   K_outer sum_{x_O} T_outer(x_O) F[z(x_O) | q(x_O) << k_inner].
+int build_split_plan(const PS& ps, Plan* out) {
+    const uint32_t k = ps.k, ki = ps.k_inner;
+    if (ki == 0 || ki > k) return ZXP_EINVAL;
+    const uint32_t ko = k - ki;
+    const uint64_t om = ko ? ((1ull << ko) - 1) : 0ull;
+    PS outer, inner;
+    outer.k = ko;
+    outer.e0 = ps.e0;
+    for (int i = 0; i < 4; i++) outer.G[i] = ps.G[i];
+    outer.t_count = ps.t_count;
+    std::vector<uint64_t> z(ki, 0ull), q;
+    auto in_part = [&](uint64_t m) { return m >> ko; };
+    auto qbit = [&](uint64_t mo) -> uint64_t {
+        size_t j = 0;
+        while (j < q.size() && q[j] != mo) j++;
+        if (j == q.size()) q.push_back(mo);
+        return 1ull << (ki + j);
+    };
+    auto cut = [&](uint64_t inner_mask, uint64_t outer_mask) {
+        for (uint64_t m = inner_mask; m; m &= m - 1) z[(size_t)__builtin_ctzll(m)] ^= outer_mask;
+    };
+    for (const LinRow& r : ps.lin) {
+        const uint64_t mi = in_part(r.mask), mo = r.mask & om;
+        if (!mi) { outer.lin.push_back(r); continue; }
+        if (!mo) { inner.lin.push_back({mi, r.c}); continue; }
+        if (r.c & 1) { inner.lin.push_back({mi | qbit(mo), r.c}); continue; }
+        inner.lin.push_back({mi, r.c});
+        outer.lin.push_back({mo, r.c});
+        if ((r.c & 3) == 2) cut(mi, mo);
+    }
+    for (const QuadRow& r : ps.quad) {
+        const uint64_t ai = in_part(r.a), ao = r.a & om, bi = in_part(r.b), bo = r.b & om;
+        if (ai && bi) inner.quad.push_back({ai, bi});
+        if (ao && bo) outer.quad.push_back({ao, bo});
+        cut(ai, bo);
+        cut(bi, ao);
+    }
+    for (const NodeRow& r : ps.node) {
+        const uint64_t mi = in_part(r.mask), mo = r.mask & om;
+        if (!mi) outer.node.push_back(r);
+        else inner.node.push_back({mi | (mo ? qbit(mo) : 0ull), r.g});
+    }
+    for (const PairRow& r : ps.pair) {
+        if (!in_part(r.ma | r.mb)) { outer.pair.push_back(r); continue; }
+        const uint64_t ma = in_part(r.ma) | ((r.ma & om) ? qbit(r.ma & om) : 0ull);
+        const uint64_t mb = in_part(r.mb) | ((r.mb & om) ? qbit(r.mb & om) : 0ull);
+        inner.pair.push_back({ma, mb, r.a, r.b});
+    }
+    const uint32_t bits = ki + (uint32_t)q.size();
+    if (bits > kMaxInnerBits) return ZXP_ETOOBIG;
+    inner.k = bits;
+    std::vector<uint32_t> zqcol(ko, 0u);
+    for (uint32_t j = 0; j < ki; j++)
+        for (uint64_t m = z[j]; m; m &= m - 1) zqcol[(size_t)__builtin_ctzll(m)] ^= 1u << j;
+    for (size_t j = 0; j < q.size(); j++)
+        for (uint64_t m = q[j]; m; m &= m - 1) zqcol[(size_t)__builtin_ctzll(m)] ^= 1u << (ki + j);
+    uint32_t lo = 64;
+    for (uint32_t i = 0; i < ko; i++)
+        if (zqcol[i]) { lo = i; break; }
+    // the walk's unrolled steps flip variables 0-3 without looking at zq
+    if (lo < 4) return ZXP_EINVAL;
+    auto ip = std::make_shared<Plan>();
+    int st = build_plain_plan(inner, false, ip.get());
+    if (st != ZXP_OK) return st;
+    Plan pl;
+    if ((st = build_plain_plan(outer, false, &pl)) != ZXP_OK) return st;
+    pl.kp.zq_lo = lo;
+    pl.k_inner = ki;
+    pl.inner_bits = bits;
+    pl.zqcol = std::move(zqcol);
+    pl.zero = pl.zero || ip->zero;
+    pl.inner = std::move(ip);
+    *out = std::move(pl);
+    return ZXP_OK;
+}
+
+}  // namespace
+
+int build_plan(const PS& ps, Plan* out) {
+    if (ps.k_inner) return build_split_plan(ps, out);
+    return build_plain_plan(ps, true, out);
 }
 
 }  // namespace zxp

@@ -17,6 +17,7 @@
 #pragma once
 #include <stdint.h>
 
+#include <memory>
 #include <vector>
 
 #include "ps.h"
@@ -81,7 +82,14 @@ struct KernelParams {
     uint32_t lane_row_bytes;
     // block lookup: the lookup slot changes of variables 0..3 (see rows)
     uint32_t U4[4];
-    uint32_t _pad2;
+    // Inner parameters (PS::k_inner > 0): the sum over the inner parameters
+    // is the table ftab, indexed by the cut parities zq of the outer
+    // assignment.  A lane folds the terms it counted while zq was constant,
+    // multiplies them by ftab[zq] and adds; flipping outer variable
+    // i >= zq_lo XORs zqcol[i] into zq.  zq_lo = 64 without inner parameters.
+    uint32_t zq_lo;
+    const uint32_t* zqcol;   // device addresses, set at launch
+    const zw64* ftab;
 };
 
 struct Plan {
@@ -126,7 +134,19 @@ struct Plan {
     bool lut_ok = false;
     bool lut_lane = false;
     std::vector<uint64_t> lut;
+    // Inner parameters: the scalar's outer rows are this plan; `inner` is the
+    // plan of the product of its inner and crossing rows as a function of
+    // u = (inner parameters, cut bits), inner_bits = |u| bits.  The inner
+    // table is the Walsh-Hadamard transform of that product over the inner
+    // parameters' bits of u.  zqcol[i] (outer variable i < k): the cut bits
+    // that flipping i changes.
+    uint32_t k_inner = 0, inner_bits = 0;
+    std::vector<uint32_t> zqcol;
+    std::shared_ptr<const Plan> inner;
 };
+
+// Largest inner table index (inner parameters + crossing forms).
+constexpr uint32_t kMaxInnerBits = 26;
 
 // Returns 0 or ZXP_ETOOBIG (more forms / pairs than the kernel supports).
 int build_plan(const PS& ps, Plan* out);

@@ -23,6 +23,10 @@ struct PairRow { uint64_t ma, mb; uint32_t a, b; };
 
 struct PS {
     uint32_t k = 0;
+    // The last k_inner of the k parameters are inner ones: a term index
+    // runs over the first k - k_inner, and each term is summed over every
+    // value of the inner parameters (the full sum is unchanged).
+    uint32_t k_inner = 0;
     int32_t e0 = 0;
     int64_t G[4] = {1, 0, 0, 0};
     std::vector<LinRow> lin;
@@ -34,6 +38,7 @@ struct PS {
 
 constexpr uint32_t kPsMagic = 0x5350585Au;
 constexpr uint32_t kPsVersion = 1;
+constexpr uint32_t kPsVersionInner = 2;   // header followed by {u32 k_inner, u32 0}
 
 // Parse and validate a table blob; returns 0 or a negative zxp_status.
 int ps_from_blob(const void* blob, size_t nbytes, PS* out);

@@ -411,7 +411,8 @@ struct Scheduler {
             uint64_t sp = 64;
             int grid = 1;
             sum_shape(pl, s->ctx->sm_count, s->ctx->max_grid, count, &sp, &grid);
-            if (sum_launch(pl, d.table, d.pv, d.rows, d.adj, d.seek, planned[0].first, count, sp, grid,
+            if (sum_launch(pl, d.table, d.pv, d.rows, d.adj, d.seek, d.zq, d.ftab, planned[0].first, count, sp,
+                           grid,
                            s->ctx->acc, s->ctx->counter, s->d_results + r->slot, false, stream) != cudaSuccess)
                 return ZXP_ECUDA;
             launches = 1;

@@ -11,6 +11,11 @@
 // parameter copies of the low variables' rows agree with the plan's forms;
 // for every scalar, that each variable's step row updates the form bits
 // and the phase exponent of sampled states to those of the flipped state.
+// For a scalar with inner parameters (outer k <= 12, inner table of at
+// most 2^16 entries) it prints instead, for every Gray index t of the
+// outer parameters, the outer term times the inner table at the term's cut
+// parities, the table built here from the inner plan's terms by a
+// Walsh-Hadamard transform over the inner bits.
 // Exits 1 with a message on the first failed check.
 #include <stdint.h>
 #include <stdio.h>
@@ -113,6 +118,23 @@ struct Model {
 
 uint64_t gray(uint64_t t) { return t ^ (t >> 1); }
 
+// Inner table of a plan with inner parameters: every inner term, then the
+// transform over the low k_inner bits.
+std::vector<zw64> inner_table(const Plan& pl) {
+    const Model mi(*pl.inner);
+    const uint64_t n = 1ull << pl.inner_bits;
+    std::vector<zw64> F(n);
+    for (uint64_t u = 0; u < n; u++) F[u] = pl.inner->zero ? zw_zero() : mi.value(mi.at(u));
+    for (uint32_t b = 0; b < pl.k_inner; b++)
+        for (uint64_t u = 0; u < n; u++)
+            if (!((u >> b) & 1)) {
+                const zw64 a = F[u], c = F[u | (1ull << b)];
+                F[u] = zw_add(a, c);
+                F[u | (1ull << b)] = zw_sub(a, c);
+            }
+    return F;
+}
+
 // The step rows: flipping variable i at state x changes J by
 // S_i - 2 |L & F_i & C0| - 4 |L & F_i & C1| + 4 (A x)_i (mod 8) and the form
 // bits by F_i, for sampled states x and every variable.
@@ -194,7 +216,23 @@ int main(int argc, char** argv) {
         CHECK(build_plan(ps, &pl) == 0);
         const Model m(pl);
         printf("scalar %s k %u lookup %d lane %d\n", argv[a], m.k, pl.lut_ok ? 1 : 0, pl.lut_lane ? 1 : 0);
-        if (m.k <= 12)
+        if (pl.k_inner) {
+            // the walk's rules: variables 0-3 never change the cut parities
+            CHECK(pl.kp.zq_lo >= 4 && !pl.lut_ok);
+            for (uint32_t i = 0; i < m.k && i < 4; i++) CHECK(pl.zqcol[i] == 0);
+            if (m.k <= 12 && pl.inner_bits <= 16) {
+                const std::vector<zw64> F = inner_table(pl);
+                for (uint64_t t = 0; t < (1ull << m.k); t++) {
+                    const uint64_t x = gray(t);
+                    uint32_t zq = 0;
+                    for (uint32_t i = 0; i < m.k; i++)
+                        if ((x >> i) & 1) zq ^= pl.zqcol[i];
+                    const zw64 v = pl.zero ? zw_zero() : zw_mul(m.value(m.at(x)), F[zq]);
+                    printf("%llx %llx %llx %llx\n", (unsigned long long)v.c[0], (unsigned long long)v.c[1],
+                           (unsigned long long)v.c[2], (unsigned long long)v.c[3]);
+                }
+            }
+        } else if (m.k <= 12)
             for (uint64_t x = 0; x < (1ull << m.k); x++) {
                 const zw64 v = pl.zero ? zw_zero() : m.value(m.at(x));
                 printf("%llx %llx %llx %llx\n", (unsigned long long)v.c[0], (unsigned long long)v.c[1],

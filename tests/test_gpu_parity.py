@@ -122,7 +122,7 @@ def test_large_workload_subranges_exact(ctx):
     # n = 50, 2000 gates, t = 80: seeded 2^20-term sub-ranges of the compiled
     # scalar against the oracle
     w = zi.workload_large(0)
-    s = Z.zxp_compile(w.gates, w.n, w.out_bits)
+    s = Z.zxp_compile(w.gates, w.n, w.out_bits, split=False)
     blob = Z.zxp_scalar_to_tables(s)
     k = Z.zxp_scalar_info(s)["k"]
     rng = zi.SplitMix64(2024)
@@ -326,7 +326,7 @@ def test_large_compiled_t50_subranges(ctx):
     """n = 50, 2000 gates, T-count 50 (k = 37): seeded 2^20-term sub-ranges
     of the full sum equal the oracle."""
     w = zi.workload_large_t50(0)
-    s = Z.zxp_compile(w.gates, w.n, w.out_bits)
+    s = Z.zxp_compile(w.gates, w.n, w.out_bits, split=False)
     blob = Z.zxp_scalar_to_tables(s)
     k = s.info["k"]
     rng = random.Random(37)
@@ -346,7 +346,7 @@ def test_large_compiled_full_sum_conjugate_transpose(ctx):
     kernel variant; no state vector exists at n = 50)."""
     inv = {zi.S: zi.SDG, zi.SDG: zi.S, zi.T: zi.TDG, zi.TDG: zi.T}
     w = zi.workload_large_t50(0)
-    s = Z.zxp_compile(w.gates, w.n, w.out_bits)
+    s = Z.zxp_compile(w.gates, w.n, w.out_bits, split=False)
     k = s.info["k"]
     assert k <= 40
     a = Z.zxp_amplitude(ctx, s)
@@ -356,7 +356,7 @@ def test_large_compiled_full_sum_conjugate_transpose(ctx):
         tot = Z.zxp_zomega_add(tot, Z.zxp_eval(ctx, s, i * n8, n8))
     assert Z.zxp_zomega_canon(tot) == a
     dag = [(inv.get(op, op), q0, q1) for op, q0, q1 in reversed(w.gates)]
-    sd = Z.zxp_compile(dag, w.n, [0] * w.n, in_bits=w.out_bits)
+    sd = Z.zxp_compile(dag, w.n, [0] * w.n, in_bits=w.out_bits, split=False)
     assert sd.info["k"] <= 40
     b = Z.zxp_amplitude(ctx, sd)
     assert a == (b[0], -b[3], -b[2], -b[1], b[4])

@@ -60,7 +60,7 @@ def scalars():
     return out
 
 
-def test_plan_terms_and_block_lookup(tmp_path):
+def build_plan_test(tmp_path):
     gxx = shutil.which("g++")
     if not gxx:
         pytest.skip("g++ not available")
@@ -69,6 +69,70 @@ def test_plan_terms_and_block_lookup(tmp_path):
                     "-I", CSRC, os.path.join(ROOT, "tests", "host", "plan_test.cpp"),
                     os.path.join(CSRC, "ps.cpp"), os.path.join(CSRC, "plan.cpp"), "-o", exe],
                    check=True, capture_output=True, text=True)
+    return exe
+
+
+def split_scalars():
+    """Scalars with inner parameters: compiled and synthetic scalars split
+    with small limits, so that outer and inner parts are both nontrivial."""
+    out = []
+    for seed in range(40):
+        w = zi.workload_batch_item(seed)
+        s = Z.zxp_compile(w.gates, w.n, w.out_bits)
+        if 10 <= s.info["k"] <= 22 and not s.info["k_inner"]:
+            sp = Z.zxp_scalar_split(s, min_k=6, max_inner=min(10, s.info["k"] - 6), low_free=4, seed=seed + 1)
+            if sp.info["k_inner"]:
+                out.append(Z.zxp_scalar_to_tables(sp))
+    rng = random.Random(23)
+    for i in range(40):
+        k = rng.randint(8, 18)
+        ps = zi.synthetic_ps(5000 + i, k, n_lin=rng.randint(4, 16), n_quad=rng.randint(0, 8),
+                             n_node=rng.choice([2, 5, 8, 12]), n_pair=rng.choice([0, 0, 1, 2, 3]),
+                             odd_nodes_only=rng.random() < 0.6, density=rng.choice([0.1, 0.2, 0.35]))
+        s = Z.zxp_scalar_from_tables(ps.pack())
+        sp = Z.zxp_scalar_split(s, min_k=6, max_inner=min(8, k - 6), low_free=4, max_cut=4, seed=i + 1)
+        if sp.info["k_inner"]:
+            out.append(Z.zxp_scalar_to_tables(sp))
+    return out
+
+
+def test_split_plan_outer_terms_times_inner_table(tmp_path):
+    # scalars with inner parameters: each outer term times the inner table
+    # at its cut parities (built on the host from the inner plan) equals the
+    # oracle's term of that Gray index, the sum over all inner values
+    exe = build_plan_test(tmp_path)
+    blobs = split_scalars()
+    assert len(blobs) >= 40
+    paths = []
+    for i, b in enumerate(blobs):
+        p = str(tmp_path / f"v{i}.bin")
+        with open(p, "wb") as f:
+            f.write(b)
+        paths.append(p)
+    r = subprocess.run([exe] + paths, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    lines = r.stdout.split("\n")
+    assert lines[-2] == "ok"
+    pos = n_terms = 0
+    for i, blob in enumerate(blobs):
+        head = lines[pos].split()
+        pos += 1
+        ko = int(head[3])
+        assert ko == oracle.outer_k(blob)
+        bits = Z.zxp_scalar_info(Z.zxp_scalar_from_tables(blob))["inner_bits"]
+        if ko > 12 or bits > 16:
+            continue
+        for t in range(1 << ko):
+            got = tuple(int(v, 16) for v in lines[pos].split())
+            pos += 1
+            want = tuple(c & M64 for c in oracle.ps_sum(blob, t, 1)[:4])
+            assert got == want, (i, t, got, want)
+            n_terms += 1
+    assert n_terms > 5000
+
+
+def test_plan_terms_and_block_lookup(tmp_path):
+    exe = build_plan_test(tmp_path)
     blobs = scalars()
     paths = []
     for i, b in enumerate(blobs):

@@ -1,11 +1,15 @@
 """Benchmark: exact stabilizer-term sums on GB300.
 
-One step = one full exact amplitude of the medium workload (n = 20 qubits,
-600 gates with 40 T gates, seeded random output bitstring): the sum of all
-2^k terms of its compiled parametric scalar on the GPU, result on the device
-(value), or one request through the public host API from the scalar's table
-bytes to the exact result on the host, two requests in flight (e2e).  The
-circuit is reduced to the scalar once, before timing.
+One step = one full exact amplitude of the large workload (n = 50 qubits,
+2000 gates with 80 T gates, seeded random output bitstring): the compiled
+scalar's inner table (the sum over its inner parameters, built on the GPU)
+and the Gray-code walk over all of its outer parameters, result on the
+device (value, amplitudes/s), or one request through the public host API
+from the scalar's table bytes to the exact result on the host (e2e).  The
+circuit is reduced to the scalar once, before timing.  Secondary lines: the
+medium workload (n = 20, 600 gates, 40 T), the unsplit n = 50 / T = 50 sum
+(k = 37), a batch of 512 circuits, Poisson-arrival serving, the paper's
+parametric use, and the integer-throughput microbenchmark.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -30,25 +34,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "exact stabilizer terms/sec and amplitudes/sec (fraction of INT roofline)"
-SM_COUNT_GB300 = 152
-ISSUE_LANES_PER_SM_CLK = 4 * 32       # 4 schedulers x 1 warp-instruction x 32 lanes
-
-
-def alg_ops_per_term(node_words: int, other_words: int, n_pairs: int) -> int:
-    """Integer operations the method needs per term, counted from the steps
-    of one term: Gray step (ctz, flip XORs, quadratic bit), node count, linear
-    phase planes, zero test, table fetch and the four 64-bit adds.  Up to
-    two phase-pair factors are folded into the table index (2 operations);
-    beyond that each is a Z[w] product (16 64-bit multiply-adds)."""
-    nw = node_words + other_words
-    ops = 2 + nw + 4                 # ctz + loop, flip XORs, quadratic update
-    ops += 2 * node_words            # popc + add per node word
-    ops += 4 * other_words           # (and + popc) x 2 linear planes
-    ops += nw + 1                    # plane 2: and-xor per word, popc
-    ops += other_words               # zero test
-    ops += 4 + 3 + 8                 # J, table address + load, 4 x 64-bit add
-    ops += 40 * n_pairs if n_pairs > 2 else (2 if n_pairs else 0)
-    return ops
+ISSUE_LANES_PER_SM_CLK = 4 * 32       # 4 schedulers x 1 warp-instruction x 32 lanes per clock
+LARGE_TABLES = os.path.join(ROOT, "zxp_inputs", "tables", "large_n50_g2000_t80_seed0.zxps")
 
 
 class ClockSampler:
@@ -102,7 +89,7 @@ class ClockSampler:
 
 
 KERNEL_SOURCES = ("sum_kernel.cuh", "kernel_core.cuh", "kernel.cu", "kernel_count.cu", "zring.h",
-                  "plan.cpp")
+                  "plan.cpp", "inner.cu", "split.cpp")
 
 
 def kernel_source_sha() -> str:
@@ -136,21 +123,36 @@ def profile_number(fields, key):
         return None
 
 
-def cpu_baseline(blob: bytes, k: int, seconds: float = 10.0):
+def cpu_baseline(blob: bytes, terms_per_amp: int, seconds: float = 10.0):
+    """The oracle as it stands, on the host cores: all threads and one
+    thread, each on a bounded sample of the same scalar (whole outer terms,
+    every inner value of each), scaled to amplitudes/s by the stabilizer
+    terms of one amplitude."""
     import oracle
     cores = os.cpu_count() or 1
-    n = 1 << 14
-    t = time.perf_counter()
-    oracle.ps_sum(blob, 0, min(n, 1 << k), nthreads=cores)
-    dt = max(time.perf_counter() - t, 1e-6)
-    target = int(n * seconds / dt)
-    n = 1 << max(10, min(k, target.bit_length() - 1))
-    t = time.perf_counter()
-    oracle.ps_sum(blob, 0, n, nthreads=cores)
-    dt = time.perf_counter() - t
-    return {"value": n / dt, "unit": "terms/s", "cores": cores, "kind": "oracle",
-            "sample": f"Gray-index range [0, 2^{n.bit_length() - 1}) of the same scalar, "
-                      f"{dt:.1f} s on {cores} host threads"}
+    inner = terms_per_amp >> oracle.outer_k(blob)
+
+    def rate(threads, budget):
+        n = 1
+        while True:
+            t = time.perf_counter()
+            oracle.ps_sum(blob, 0, n, nthreads=threads)
+            dt = time.perf_counter() - t
+            if dt >= budget * 0.6 or n >= (1 << oracle.outer_k(blob)):
+                return n * inner / dt, n, dt
+            n *= max(2, min(64, int(budget / max(dt, 1e-4))))
+            n = min(n, 1 << oracle.outer_k(blob))
+
+    v_all, n_all, dt_all = rate(cores, seconds)
+    v_one, n_one, dt_one = rate(1, seconds / 3)
+    return {"value": v_all / terms_per_amp, "unit": "amplitudes/s", "cores": cores, "kind": "oracle",
+            "stabilizer_terms_per_s": v_all,
+            "single_thread": {"value": v_one / terms_per_amp, "unit": "amplitudes/s",
+                              "stabilizer_terms_per_s": v_one, "cores": 1,
+                              "sample": f"{n_one} outer terms x {inner} inner values, {dt_one:.1f} s"},
+            "sample": f"outer Gray-index range [0, {n_all}) of the same scalar, every one of the "
+                      f"{inner} inner values of each ({n_all * inner} stabilizer terms), {dt_all:.1f} s "
+                      f"on {cores} host threads; amplitudes/s = stabilizer terms/s / {terms_per_amp}"}
 
 
 SERVE_MAX_K = 38
@@ -286,55 +288,180 @@ def setup_dist():
 
 
 def run_reference(args, world, rank):
-    """The oracle on the host cores, bounded sample per step."""
+    """The oracle on the host cores on the headline workload's scalar (the
+    committed table bytes of the compiled large circuit): each step sums a
+    bounded sample of whole outer terms, every inner value of each, and the
+    rate is scaled to amplitudes/s by the stabilizer terms of one amplitude."""
     if rank != 0:
         return
     import oracle
-    import paper_2403_06777_gb300 as Z
-    import zxp_inputs as zi
-    w = zi.workload_medium(args.seed)
-    s = Z.zxp_compile(w.gates, w.n, w.out_bits)
-    blob = Z.zxp_scalar_to_tables(s)
-    k = Z.zxp_scalar_info(s)["k"]
+    blob = open(LARGE_TABLES, "rb").read()
+    k = int.from_bytes(blob[8:12], "little")
+    ko = oracle.outer_k(blob)
+    inner = 1 << (k - ko)
     cores = os.cpu_count() or 1
     t = time.perf_counter()
-    oracle.ps_sum(blob, 0, 1 << 12, nthreads=cores)
-    per_term = (time.perf_counter() - t) / (1 << 12)
+    oracle.ps_sum(blob, 0, 1, nthreads=cores)
+    per_outer = time.perf_counter() - t
     total_budget = 150.0
-    n = 1 << max(8, min(k, int(total_budget / max(1, args.steps + args.warmup) / per_term).bit_length() - 1))
+    n = max(1, int(total_budget / max(1, args.steps + args.warmup) / per_outer))
     for i in range(args.warmup):
         oracle.ps_sum(blob, 0, n, nthreads=cores)
     t = time.perf_counter()
     for i in range(args.steps):
-        first = (i * n) % ((1 << k) - n + 1)
+        first = (i * n) % ((1 << ko) - n + 1)
         oracle.ps_sum(blob, first, n, nthreads=cores)
     dt = time.perf_counter() - t
-    v = n * args.steps / dt
-    sample = f"{n} terms (2^{n.bit_length() - 1}) of the 2^{k}-term scalar per step"
+    stab = n * inner * args.steps / dt
+    v = stab / (1 << k)
+    sample = (f"{n} outer terms x {inner} inner values ({n * inner} of the 2^{k} stabilizer terms "
+              f"of one amplitude) per step; amplitudes/s = stabilizer terms/s / 2^{k}")
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": v, "unit": "terms/s", "n_gpus": world,
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "amplitudes/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int128",
         "data": "synthetic",
-        "config": {"workload": f"{w.name} seed={args.seed}: one exact amplitude per step", "k": k,
-                   "terms_per_step": n, "sample": sample},
-        "cpu_baseline": {"value": v, "unit": "terms/s", "cores": cores, "kind": "oracle",
+        "config": {"workload": "large n=50 G=2000 t=80 seed=0: one exact amplitude per step",
+                   "k": ko, "k_inner": k - ko, "stabilizer_terms_per_amplitude": 1 << k,
+                   "sample": sample},
+        "stabilizer_terms_per_s": stab,
+        "cpu_baseline": {"value": v, "unit": "amplitudes/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
-        "e2e": {"value": v, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "e2e": {"value": v, "unit": "amplitudes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def wht_passes(k_inner: int) -> int:
+    """Launches of the inner table's transform (inner.cu: 10 bits, then 5)."""
+    n, lo = 0, 0
+    while lo < k_inner:
+        lo += 10 if lo == 0 else 5
+        n += 1
+    return n
+
+
+def issue_peak(torch, dev: int, sm_max_mhz):
+    """Integer issue peak (thread instructions/s): SMs x 4 warp-instructions
+    per clock x 32 lanes x the SM clock (the maximum that nvidia-smi reports,
+    else the device attribute)."""
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    mhz = sm_max_mhz or getattr(props, "clock_rate", 0) / 1e3 or 2070.0
+    return sms * ISSUE_LANES_PER_SM_CLK * mhz * 1e6, sms, mhz
+
+
+def roofline_from_profile(prof, terms, seconds, peak, source):
+    """Issue roofline of a sum-kernel launch from its committed ncu summary:
+    measured thread instructions per term x terms / event time / issue peak,
+    with the ALU pipe's share of cycles and the DRAM bytes beside it."""
+    ipt = profile_number(prof, "instructions_per_term")
+    ach = None if ipt is None else ipt * terms / seconds
+    return {"bound": "alu", "achieved": None if ach is None else ach / 1e12, "peak": peak / 1e12,
+            "unit": "T thread-instr/s", "frac": None if ach is None else ach / peak,
+            "traffic": profile_number(prof, "dram_bytes_per_launch"),
+            "instructions_per_term": ipt,
+            "alu_pipe_frac": profile_number(prof, "alu_pipe_frac"),
+            "issue_active_frac": profile_number(prof, "issue_active_frac"),
+            "peak_basis": "SMs x 4 warp-instructions/clk x 32 lanes x max SM clock",
+            "source": source}
+
+
+def timed_amplitude(torch, Z, ctx, s, stream, out, flush, steps, sampler_dev):
+    """steps full amplitudes of s (inner table, then the whole outer range),
+    L2 flushed before each; returns per-step (inner ms, walk ms) and clocks."""
+    info = Z.zxp_scalar_info(s)
+    terms = 1 << info["k"]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    torch.cuda.synchronize()
+    with ClockSampler(sampler_dev) as clk:
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            Z.zxp_inner_sum(ctx, s)
+            ev[i][1].record(stream)
+            Z.zxp_eval_device(ctx, s, 0, terms, out.data_ptr())
+            ev[i][2].record(stream)
+        torch.cuda.synchronize()
+    inner = [e[0].elapsed_time(e[1]) for e in ev]
+    walk = [e[1].elapsed_time(e[2]) for e in ev]
+    return inner, walk, clk.summary()
+
+
+def stream_requests(Z, ctx, blob, n, depth=2):
+    """n requests of the scalar with table bytes `blob` through the public
+    host API (zxp_submit_tables, zxp_poll), `depth` in flight; returns the
+    seconds per request and the results."""
+    from collections import deque
+    q, got = deque(), []
+    t = time.perf_counter()
+    for i in range(n + depth):
+        if i < n:
+            q.append(Z.zxp_submit_tables(ctx, blob))
+        if len(q) > depth or (i >= n and q):
+            got.append(Z.zxp_poll(ctx, q.popleft(), -1))
+    return (time.perf_counter() - t) / n, got
+
+
+PROFILE_CASES = ("large80", "inner", "medium", "large37", "peak")
+
+
+def run_profile_case(case: str):
+    """A short, fixed launch sequence of one kernel, for capturing it under
+    ncu on a small case (--profile):
+      large80  the large workload's amplitude (inner table, then the walk over
+               all 2^k outer terms), then one walk over 2^28 terms
+      inner    the large workload's amplitude, then its inner table again
+      medium   three amplitudes of the medium workload
+      large37  one 2^30-term launch of the unsplit n=50 / T=50 scalar (k = 37)
+      peak     the integer microbenchmark, every kind once"""
+    import torch
+    import paper_2403_06777_gb300 as Z
+    import zxp_inputs as zi
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = Z.zxp_ctx_create(0, stream.cuda_stream)
+    rec = {"profile": case}
+    if case in ("large80", "inner"):
+        w = zi.workload_large(0)
+        s = Z.zxp_compile(w.gates, w.n, w.out_bits)
+        rec["amplitude"] = Z.zxp_amplitude(ctx, s)
+        if case == "large80":
+            rec["partial"] = Z.zxp_eval(ctx, s, 0, 1 << 28)
+        else:
+            Z.zxp_inner_sum(ctx, s)
+        rec["info"] = Z.zxp_scalar_info(s)
+    elif case == "medium":
+        w = zi.workload_medium(0)
+        s = Z.zxp_compile(w.gates, w.n, w.out_bits)
+        rec["amplitude"] = [Z.zxp_amplitude(ctx, s) for _ in range(3)][-1]
+        rec["info"] = Z.zxp_scalar_info(s)
+    elif case == "large37":
+        w = zi.workload_large_t50(0)
+        s = Z.zxp_compile(w.gates, w.n, w.out_bits, split=False)
+        rec["partial"] = Z.zxp_eval(ctx, s, 0, 1 << 30)
+        rec["info"] = Z.zxp_scalar_info(s)
+    else:
+        rec["int_peak"] = {kind: Z.zxp_int_peak(ctx, kind) for kind in range(5)}
+    torch.cuda.synchronize()
+    ctx.close()
+    print(json.dumps(rec))
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=PROFILE_CASES, help="run one kernel's short launch sequence")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = setup_dist()
+    if args.profile:
+        run_profile_case(args.profile)
+        return
 
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -356,132 +483,109 @@ def main():
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = Z.zxp_ctx_create(local, stream.cuda_stream)
+    out = torch.zeros(5, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
 
-    w = zi.workload_medium(args.seed)
+    # ---- headline: the large workload, one exact amplitude per step --------
+    w = zi.workload_large(args.seed)
     t0 = time.perf_counter()
     s = Z.zxp_compile(w.gates, w.n, w.out_bits)
     compile_ms = (time.perf_counter() - t0) * 1e3
     info = Z.zxp_scalar_info(s)
-    k = info["k"]
+    k, ki = info["k"], info["k_inner"]
     terms = 1 << k
+    stab_terms = 1 << (k + ki)
     blob = Z.zxp_scalar_to_tables(s)
-
-    out = torch.zeros(5, dtype=torch.int64, device="cuda")
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
-
+    ref = Z.zxp_amplitude(ctx, s)
     for _ in range(args.warmup):
+        Z.zxp_inner_sum(ctx, s)
         Z.zxp_eval_device(ctx, s, 0, terms, out.data_ptr())
     torch.cuda.synchronize()
-    ref = Z.zxp_amplitude(ctx, s)
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if dist:
         dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        wall0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.zero_()                           # L2 flushed between timed steps
-            starts[i].record(stream)
-            Z.zxp_eval_device(ctx, s, 0, terms, out.data_ptr())
-            stops[i].record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
+    wall0 = time.perf_counter()
+    inner_ms, walk_ms, clocks = timed_amplitude(torch, Z, ctx, s, stream, out, flush, args.steps, local)
+    wall = time.perf_counter() - wall0
     if dist:
         dist.barrier()
-    kernel_ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops))
     # the device result of the last step must be the exact amplitude
     r = out.tolist()
     got = Z.zxp_zomega_canon((r[0], r[1], r[2], r[3], r[4] & 0xFFFFFFFF))
     assert got == ref, (got, ref)
-    t_rank = torch.tensor([kernel_ms], dtype=torch.float64, device="cuda")
+    step_ms = sum(inner_ms) + sum(walk_ms)
+    t_rank = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
     if dist:
         dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
-    kernel_ms = float(t_rank.item())
-    sec = kernel_ms / 1e3
-    value = terms * args.steps * world / sec
-    amps = args.steps * world / sec
-    per_launch_s = sec / args.steps
+    step_ms = float(t_rank.item())
+    sec = step_ms / 1e3
+    value = args.steps * world / sec
+    walk_s = statistics.median(walk_ms) / 1e3
+    inner_s = statistics.median(inner_ms) / 1e3
 
-    # e2e: the public host API, one request per step: the tables (host
-    # bytes) are submitted (zxp_submit_tables: the scalar is built on the
-    # host, its tables copied from pinned staging, the kernel launched) and
-    # polled (the 40-byte result the kernel wrote into pinned host memory);
-    # up to E2E_DEPTH requests are in flight, as a client streaming requests
-    # runs them.  Every result is checked against the exact amplitude after
-    # the timed loop.  The latency of one blocking request (nothing else in
-    # flight) is reported beside it.
+    # e2e: the public host API, one request per step: the scalar's table
+    # bytes (host) are submitted (zxp_submit_tables: the scalar is built on
+    # the host, its tables copied from pinned staging, the inner table built
+    # and the walk launched on the device) and polled (the 40-byte result the
+    # kernel wrote into pinned host memory); two requests in flight.  Every
+    # result is checked after the timed loop.
     E2E_DEPTH = 2
-    e2e_steps = max(200, 10 * args.steps)
-    from collections import deque
+    e2e_steps = max(20, args.steps)
+    stream_requests(Z, ctx, blob, 3, E2E_DEPTH)
     torch.cuda.synchronize()
-    q = deque()
-    got = []
-    t = time.perf_counter()
-    for i in range(e2e_steps + E2E_DEPTH):
-        if i < e2e_steps:
-            q.append(Z.zxp_submit_tables(ctx, blob))
-        if len(q) > E2E_DEPTH or (i >= e2e_steps and q):
-            got.append(Z.zxp_poll(ctx, q.popleft(), -1))
-    e2e_sec = (time.perf_counter() - t) / e2e_steps
-    bad = sum(Z.zxp_zomega_canon(r) != ref for r in got)
+    e2e_sec, got = stream_requests(Z, ctx, blob, e2e_steps, E2E_DEPTH)
+    bad = sum(Z.zxp_zomega_canon(x) != ref for x in got)
     assert bad == 0 and len(got) == e2e_steps, (bad, len(got))
-    lat = []
-    for _ in range(100):
-        t = time.perf_counter()
-        s2 = Z.zxp_scalar_from_tables(blob)
-        Z.zxp_amplitude(ctx, s2)
-        s2.free()
-        lat.append(time.perf_counter() - t)
-    lat.sort()
-    latency_us = lat[len(lat) // 2] * 1e6
-    table_bytes = info["device_bytes"]
 
-    # large scalar: k = 36 synthetic tables with compiled statistics (the
-    # compiled n = 50 / t = 80 circuit needs k ~ 50, out of reach)
-    large = None
-    if rank == 0 and not os.environ.get("ZXP_BENCH_SKIP_LARGE"):
-        # row counts of the compiled n = 50 / t = 80 circuit (seed 0: 59 linear,
-        # 47 quadratic, 13 odd-node and 1 phase-pair rows at k = 50), at k = 36
-        ps36 = zi.synthetic_ps(36, 36, n_lin=59, n_quad=36, n_node=13, n_pair=1,
-                               odd_nodes_only=True, density=0.12)
-        s36 = Z.zxp_scalar_from_tables(ps36.pack())
-        i36 = Z.zxp_scalar_info(s36)
-        Z.zxp_eval_device(ctx, s36, 0, 1 << 30, out.data_ptr())
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # ---- integer microbenchmark (the measured peak beside the issue peak) ----
+    int_peak = None
+    if rank == 0:
+        int_peak = {}
+        for kind, name in enumerate(("lop3", "add", "popc", "mad", "lop3_mad")):
+            v, ms = Z.zxp_int_peak(ctx, kind)
+            int_peak[name] = {"thread_instr_per_s": v, "ms": ms}
+
+    # ---- medium workload: one launch per amplitude ---------------------------
+    medium = None
+    if rank == 0 and not os.environ.get("ZXP_BENCH_SKIP_MEDIUM"):
+        wm = zi.workload_medium(args.seed)
+        sm_ = Z.zxp_compile(wm.gates, wm.n, wm.out_bits)
+        im = Z.zxp_scalar_info(sm_)
+        nm = 1 << im["k"]
+        refm = Z.zxp_amplitude(ctx, sm_)
+        for _ in range(20):
+            Z.zxp_eval_device(ctx, sm_, 0, nm, out.data_ptr())
+        steps_m = 2000
+        st_ = [torch.cuda.Event(enable_timing=True) for _ in range(steps_m)]
+        sp_ = [torch.cuda.Event(enable_timing=True) for _ in range(steps_m)]
         torch.cuda.synchronize()
-        with ClockSampler(local) as clk36:
-            a.record(stream)
-            Z.zxp_eval_device(ctx, s36, 0, 1 << 36, out.data_ptr())
-            b.record(stream)
-            torch.cuda.synchronize()
-        ms36 = a.elapsed_time(b)
-        ops36 = alg_ops_per_term(i36["node_words"], i36["other_words"], i36["n_pair"])
-        ach36 = ops36 * (1 << 36) / (ms36 / 1e3) / 1e9
-        peak = SM_COUNT_GB300 * ISSUE_LANES_PER_SM_CLK * 2070e6 / 1e9
-        prof_s = profile_fields(kernel_source_sha(), "sum_kernel_synthetic36.txt")
-        ipt_s = profile_number(prof_s, "instructions_per_term")
-        iss_s = None if ipt_s is None else ipt_s * (1 << 36) / (ms36 / 1e3) / 1e9
-        large = {"workload": "synthetic k=36 (59 linear, 36 quadratic, 13 odd-node, 1 phase-pair rows)",
-                 "terms": 1 << 36, "ms": ms36, "terms_per_s": (1 << 36) / (ms36 / 1e3),
-                 "node_words": i36["node_words"], "other_words": i36["other_words"],
-                 "kernel_variant": i36["kernel_variant"],
-                 "roofline": {"bound": "alu", "achieved": ach36, "peak": peak, "unit": "Gop/s",
-                              "frac": ach36 / peak, "ops_per_term": ops36,
-                              "traffic": profile_number(prof_s, "dram_bytes_per_launch"),
-                              "issue": {"instructions_per_term": ipt_s, "achieved": iss_s,
-                                        "frac": None if iss_s is None else iss_s / peak,
-                                        "source": "thread instructions per term of the committed "
-                                                  "ncu capture (profiles/sum_kernel_synthetic36.txt)"}},
-                 "clocks": clk36.summary()}
+        for i in range(steps_m):
+            flush.zero_()
+            st_[i].record(stream)
+            Z.zxp_eval_device(ctx, sm_, 0, nm, out.data_ptr())
+            sp_[i].record(stream)
+        torch.cuda.synchronize()
+        ms_m = sum(a.elapsed_time(b) for a, b in zip(st_, sp_)) / steps_m
+        r = out.tolist()
+        assert Z.zxp_zomega_canon((r[0], r[1], r[2], r[3], r[4] & 0xFFFFFFFF)) == refm
+        blob_m = Z.zxp_scalar_to_tables(sm_)
+        e2e_m, gm = stream_requests(Z, ctx, blob_m, 2000)
+        assert all(Z.zxp_zomega_canon(x) == refm for x in gm)
+        peak_m, _, _ = issue_peak(torch, local, clocks.get("sm_max_mhz"))
+        medium = {"workload": f"{wm.name} seed={args.seed}: one exact amplitude per step, L2 flushed",
+                  "k": im["k"], "terms": nm, "ms_per_amplitude": ms_m,
+                  "amplitudes_per_s": 1e3 / ms_m, "terms_per_s": nm / (ms_m / 1e3),
+                  "kernel_variant": im["kernel_variant"],
+                  "e2e": {"amplitudes_per_s": 1 / e2e_m, "us_per_request": e2e_m * 1e6,
+                          "h2d_bytes_per_step": im["upload_bytes"], "d2h_bytes_per_step": 40,
+                          "requests_in_flight": 2},
+                  "roofline": roofline_from_profile(profile_fields(kernel_source_sha(), "sum_kernel_medium.txt"),
+                                                    nm, ms_m / 1e3, peak_m, "profiles/sum_kernel_medium.txt")}
 
-    # large compiled circuit: n = 50, 2000 gates at T-count 50 (k = 37), the
-    # full exact sum in one launch
-    large_c = None
+    # ---- the unsplit sum kernel at k = 37 (n = 50, 2000 gates, T = 50) -------
+    unsplit = None
     if rank == 0 and not os.environ.get("ZXP_BENCH_SKIP_LARGE"):
         wl = zi.workload_large_t50(0)
-        sl = Z.zxp_compile(wl.gates, wl.n, wl.out_bits)
+        sl = Z.zxp_compile(wl.gates, wl.n, wl.out_bits, split=False)
         il = Z.zxp_scalar_info(sl)
         nl = 1 << il["k"]
         Z.zxp_eval_device(ctx, sl, 0, min(nl, 1 << 30), out.data_ptr())
@@ -493,21 +597,12 @@ def main():
             b.record(stream)
             torch.cuda.synchronize()
         msl = a.elapsed_time(b)
-        opsl = alg_ops_per_term(il["node_words"], il["other_words"], il["n_pair"])
-        achl = opsl * nl / (msl / 1e3) / 1e9
-        peak = SM_COUNT_GB300 * ISSUE_LANES_PER_SM_CLK * 2070e6 / 1e9
-        prof_l = profile_fields(kernel_source_sha(), "sum_kernel_large37.txt")
-        ipt_l = profile_number(prof_l, "instructions_per_term")
-        iss_l = None if ipt_l is None else ipt_l * nl / (msl / 1e3) / 1e9
-        large_c = {"workload": f"{wl.name} seed=0: one exact amplitude", "k": il["k"], "terms": nl,
-                   "ms": msl, "terms_per_s": nl / (msl / 1e3), "kernel_variant": il["kernel_variant"],
-                   "roofline": {"bound": "alu", "achieved": achl, "peak": peak, "unit": "Gop/s",
-                                "frac": achl / peak, "ops_per_term": opsl,
-                                "traffic": profile_number(prof_l, "dram_bytes_per_launch"),
-                                "issue": {"instructions_per_term": ipt_l, "achieved": iss_l,
-                                          "frac": None if iss_l is None else iss_l / peak,
-                                          "source": "thread instructions per term of the committed "
-                                                    "ncu capture (profiles/sum_kernel_large37.txt)"}},
+        peak_l, _, _ = issue_peak(torch, local, clkl.summary().get("sm_max_mhz"))
+        unsplit = {"workload": f"{wl.name} seed=0 without the split: one exact amplitude, one launch",
+                   "k": il["k"], "terms": nl, "ms": msl, "terms_per_s": nl / (msl / 1e3),
+                   "kernel_variant": il["kernel_variant"],
+                   "roofline": roofline_from_profile(profile_fields(kernel_source_sha(), "sum_kernel_large37.txt"),
+                                                     nl, msl / 1e3, peak_l, "profiles/sum_kernel_large37.txt"),
                    "clocks": clkl.summary()}
 
     # batched workload: 512 circuits (n ~ U[10,40], T ~ U[20,60]), one
@@ -557,9 +652,9 @@ def main():
                            "candidates": binfo["candidates"]}}
         bt.close()
 
-    # serving: Poisson arrivals (2000 req/s) of amplitude and doubled-marginal
-    # requests; the server with continuous batching vs the same server
-    # evaluating one scalar per launch in arrival order
+    # serving: Poisson arrivals of amplitude and doubled-marginal requests;
+    # the server with continuous batching vs the same server evaluating one
+    # scalar per launch in arrival order
     serving = None
     if rank == 0 and not os.environ.get("ZXP_BENCH_SKIP_SERVE"):
         serving = serve_bench(Z, ctx, zi, n_req=2000, rate_hz=2000.0, max_k=SERVE_MAX_K)
@@ -573,49 +668,48 @@ def main():
             dist.destroy_process_group()
         return
 
-    clocks = clk.summary()
-    ops = alg_ops_per_term(info["node_words"], info["other_words"], info["n_pair"])
-    f_hz = 2070e6
-    peak = SM_COUNT_GB300 * ISSUE_LANES_PER_SM_CLK * f_hz / 1e9          # Gop/s
-    achieved = ops * terms / per_launch_s / 1e9
+    peak, sms, mhz = issue_peak(torch, local, clocks.get("sm_max_mhz"))
     sha = kernel_source_sha()
-    prof = profile_fields(sha)
-    traffic = profile_number(prof, "dram_bytes_per_launch")
-    ipt = profile_number(prof, "instructions_per_term")
+    prof = profile_fields(sha, "sum_kernel_large80.txt")
+    roof = roofline_from_profile(prof, terms, walk_s, peak, "profiles/sum_kernel_large80.txt")
+    roof["sms"] = sms
+    roof["sm_max_mhz"] = mhz
+    if int_peak:
+        mix = int_peak["lop3_mad"]["thread_instr_per_s"]
+        roof["measured_int_peak"] = {"lop3_mad_thread_instr_per_s": mix,
+                                     "frac": None if roof["achieved"] is None else roof["achieved"] * 1e12 / mix,
+                                     "basis": "integer microbenchmark (zxp_int_peak kind 4): logic and "
+                                              "multiply-add chains in turn on a full grid"}
+    launches_per_step = (1 + wht_passes(ki) + 1) if ki else 1
 
     line = {
-        "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": kernel_ms / args.steps,
+        "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic",
-        "config": {"workload": f"{w.name} seed={args.seed}: one exact amplitude per step",
-                   "k": k, "terms_per_step": terms, "t_count": info["t_count"],
+        "config": {"workload": f"{w.name} seed={args.seed}: one exact amplitude per step "
+                               "(inner table + Gray-code walk over the outer parameters)",
+                   "k": k, "k_inner": ki, "inner_bits": info["inner_bits"],
+                   "walked_terms_per_step": terms, "stabilizer_terms_per_step": stab_terms,
+                   "t_count": info["t_count"], "kernel_variant": info["kernel_variant"],
                    "compile_ms": compile_ms, "l2": "flushed (256 MB write) between timed steps",
                    "parallelism": f"replicas x{world}"},
-        "amplitudes_per_s": amps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "ops_per_term": ops,
-                     "peak_basis": "issue: 152 SM x 4 warp-instr/clk x 32 lanes x 2070 MHz",
-                     "issue": {"instructions_per_term": ipt,
-                               "achieved": None if ipt is None else ipt * terms / per_launch_s / 1e9,
-                               "frac": None if ipt is None else ipt * terms / per_launch_s / 1e9 / peak,
-                               "source": "thread instructions per term of the committed ncu capture"},
-                     "note": "ops_per_term counts the per-term method (ctz, flips, popcount planes, "
-                             "table fetch, 64-bit adds); the block lookup shares work across 8 terms, "
-                             "so the kernel executes fewer instructions per term (issue)"},
-        "e2e": {"value": terms / e2e_sec, "unit": "terms/s", "amplitudes_per_s": 1 / e2e_sec,
-                "h2d_bytes_per_step": table_bytes, "d2h_bytes_per_step": 40,
-                "requests_in_flight": E2E_DEPTH, "steps": e2e_steps,
-                "blocking_latency_us": latency_us},
+        "ms_inner_table": inner_s * 1e3, "ms_walk": walk_s * 1e3,
+        "terms_per_s": terms / walk_s,
+        "stabilizer_terms_per_s": stab_terms * value / world,
+        "roofline": roof,
+        "e2e": {"value": 1 / e2e_sec, "unit": "amplitudes/s",
+                "h2d_bytes_per_step": info["upload_bytes"], "d2h_bytes_per_step": 40,
+                "requests_in_flight": E2E_DEPTH, "steps": e2e_steps},
         "clocks": clocks,
-        "gpu_launches": args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "wall_s_timed_region": wall,
+        "int_peak": int_peak,
     }
-    if large:
-        line["large"] = large
-    if large_c:
-        line["large_compiled"] = large_c
+    if medium:
+        line["medium"] = medium
+    if unsplit:
+        line["unsplit_k37"] = unsplit
     if batch:
         line["batch"] = batch
     if serving:
@@ -623,7 +717,7 @@ def main():
     if param:
         line["parametric"] = param
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(blob, k)
+        line["cpu_baseline"] = cpu_baseline(blob, stab_terms)
     print(json.dumps(line))
     ctx.close()
     if dist:

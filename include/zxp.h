@@ -99,7 +99,8 @@ typedef struct {
     uint32_t k_inner;    /* inner parameters, summed inside every term (0: none) */
     uint32_t inner_bits; /* index bits of the inner table: k_inner + crossing forms
                             (2^inner_bits entries of 32 bytes on the device) */
-    uint32_t reserved[1];
+    uint32_t upload_bytes;       /* bytes copied host -> device per upload (device_bytes
+                                    less the inner table, which the device computes) */
 } zxp_scalar_info_t;
 
 /* ---- context --------------------------------------------------------- */
@@ -464,6 +465,18 @@ void zxp_sampler_destroy(zxp_sampler *s);
 int zxp_marginal_by_sum(zxp_ctx *ctx, const zxp_gate *gates, size_t n_gates, int n_qubits,
                         const uint8_t *in_bits, uint64_t mask, const uint8_t *bits,
                         zxp_zomega *out);
+
+/* ---- measurement ------------------------------------------------------------ */
+
+/* Integer throughput of the context's GPU (no counterpart in the paper; the
+ * roofline denominator of the sum kernel, which is bound by integer issue).
+ * A full resident grid runs eight chains of one instruction per thread:
+ * kind 0 three-input logic (lop3), 1 add, 2 popcount, 3 multiply-add
+ * (mad.lo), 4 logic and multiply-add in turn (the ALU and FMA pipes
+ * together); *thread_instr_per_s receives the best of
+ * three timed launches (thread instructions per second) and *ms (nullable)
+ * that launch's time.  Errors: ZXP_EINVAL, ZXP_ENOMEM, ZXP_ECUDA. */
+int zxp_int_peak(zxp_ctx *ctx, int kind, double *thread_instr_per_s, double *ms);
 
 /* ---- exact scalar helpers (host) ---------------------------------------- */
 

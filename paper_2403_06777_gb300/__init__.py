@@ -44,7 +44,7 @@ class zxp_scalar_info_t(C.Structure):
                 ("node_words", C.c_uint32), ("other_words", C.c_uint32),
                 ("device_bytes", C.c_uint32), ("kernel_variant", C.c_uint32),
                 ("k_inner", C.c_uint32), ("inner_bits", C.c_uint32),
-                ("reserved", C.c_uint32 * 1)]
+                ("upload_bytes", C.c_uint32)]
 
 
 class zxp_split_opts(C.Structure):
@@ -151,6 +151,7 @@ def lib():
         L.zxp_server_poll.argtypes = [vp, u64, i64, zp, C.POINTER(zxp_request_timing)]
         L.zxp_server_stats.argtypes = [vp, C.POINTER(zxp_server_stats_t)]
         L.zxp_server_destroy.argtypes, L.zxp_server_destroy.restype = [vp], None
+        L.zxp_int_peak.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.zxp_zomega_add.argtypes = [zp, zp, zp]
         L.zxp_zomega_canon.argtypes = [zp, zp]
         L.zxp_zomega_to_complex.argtypes = [zp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -378,6 +379,14 @@ def zxp_scalar_split(s: Scalar, **opts) -> Scalar:
     h = C.c_void_p()
     _check(lib().zxp_scalar_split(s.handle, C.byref(o) if opts else None, C.byref(h)), "zxp_scalar_split")
     return Scalar(h.value)
+
+
+def zxp_int_peak(ctx: Ctx, kind: int):
+    """(thread instructions per second, ms) of the integer microbenchmark:
+    kind 0 lop3, 1 add, 2 popc, 3 mad.lo, 4 lop3 and mad.lo in turn."""
+    r, ms = C.c_double(), C.c_double()
+    _check(lib().zxp_int_peak(ctx.handle, kind, C.byref(r), C.byref(ms)), "zxp_int_peak")
+    return r.value, ms.value
 
 
 def zxp_inner_sum(ctx: Ctx, s: Scalar):

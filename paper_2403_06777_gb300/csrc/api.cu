@@ -474,7 +474,9 @@ int zxp_scalar_info(const zxp_scalar* s, zxp_scalar_info_t* info) {
     info->t_count = s->ps.t_count;
     info->node_words = (uint32_t)s->plan.nwn;
     info->other_words = (uint32_t)(s->plan.nwl < 1 ? 1 : s->plan.nwl);
-    info->device_bytes = (uint32_t)table_layout(s->plan).total;
+    const TableLayout L = table_layout(s->plan);
+    info->device_bytes = (uint32_t)std::min<size_t>(L.total, 0xFFFFFFFFu);
+    info->upload_bytes = (uint32_t)L.copied;
     info->kernel_variant = (uint32_t)sum_variant(s->plan);
     return ZXP_OK;
 }

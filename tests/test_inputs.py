@@ -3,6 +3,7 @@ splitmix64 against published outputs of its reference definition, the gate
 mixes, the fixed T-counts, the size ranges of the batch and serving
 workloads, the Poisson arrival rate and the synthetic tables' shapes."""
 import math
+import os
 
 import zxp_inputs as zi
 
@@ -90,3 +91,18 @@ def test_synthetic_tables_shape():
     assert all(0 <= m < (1 << 36) for m in masks)
     back = zi.PSTables.unpack(ps.pack())
     assert back == ps
+
+
+def test_committed_large_tables_match_a_fresh_compile():
+    # the reference arm of the benchmark reads these bytes instead of
+    # compiling; they must be what the compiler gives today
+    import importlib.util
+    import oracle
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "zxp_inputs", "tables", "make_tables.py")
+    spec = importlib.util.spec_from_file_location("make_tables", path)
+    mt = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mt)
+    committed = open(mt.LARGE, "rb").read()
+    assert committed == mt.large_blob()
+    assert oracle.outer_k(committed) <= 36

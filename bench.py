@@ -402,7 +402,7 @@ def stream_requests(Z, ctx, blob, n, depth=2):
     return (time.perf_counter() - t) / n, got
 
 
-PROFILE_CASES = ("large80", "inner", "medium", "large37", "peak")
+PROFILE_CASES = ("large80", "large80_1g", "inner", "medium", "large37", "peak")
 
 
 def run_profile_case(case: str):
@@ -410,6 +410,7 @@ def run_profile_case(case: str):
     ncu on a small case (--profile):
       large80  the large workload's amplitude (inner table, then the walk over
                all 2^k outer terms), then one walk over 2^28 terms
+      large80_1g the same, then one walk over 2^30 terms
       inner    the large workload's amplitude, then its inner table again
       medium   three amplitudes of the medium workload
       large37  one 2^30-term launch of the unsplit n=50 / T=50 scalar (k = 37)
@@ -421,12 +422,14 @@ def run_profile_case(case: str):
     torch.cuda.set_stream(stream)
     ctx = Z.zxp_ctx_create(0, stream.cuda_stream)
     rec = {"profile": case}
-    if case in ("large80", "inner"):
+    if case in ("large80", "large80_1g", "inner"):
         w = zi.workload_large(0)
         s = Z.zxp_compile(w.gates, w.n, w.out_bits)
         rec["amplitude"] = Z.zxp_amplitude(ctx, s)
         if case == "large80":
             rec["partial"] = Z.zxp_eval(ctx, s, 0, 1 << 28)
+        elif case == "large80_1g":
+            rec["partial"] = Z.zxp_eval(ctx, s, 0, 1 << 30)
         else:
             Z.zxp_inner_sum(ctx, s)
         rec["info"] = Z.zxp_scalar_info(s)

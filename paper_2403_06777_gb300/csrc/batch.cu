@@ -30,7 +30,7 @@ gather_kernel(DevResult* __restrict__ results, const uint32_t* __restrict__ slot
 // key: variant << 8 | nwn << 4 | nwl
 BatchFn pick(int key) {
     const int nwn = (key >> 4) & 7, nwl = key & 7, v = (key >> 8) & 15;
-    if (v >= 9) return kLut[v - 9][nwn][nwl - 1];
+    if (v >= 9) return kLut[v == 13 ? 3 : v - 9][nwn][nwl - 1];
     if (v >= 7) return kShared[v - 7][nwn][nwl - 1];
     if (v >= 3) return kHist[v - 3][nwn][nwl - 1];
     return kTable[v][nwn][nwl - 1];
@@ -51,8 +51,9 @@ int batch_key(const Plan& pl) {
 }
 
 size_t batch_smem_bytes(int key, uint32_t ntab_cap, uint32_t npairs_cap, int threads) {
-    return core::smem_bytes(ntab_cap, npairs_cap, (key >> 4) & 7, key & 7, core::var_hist((key >> 8) & 15),
-                            threads);
+    const int h = core::var_hist((key >> 8) & 15);
+    return core::smem_bytes(ntab_cap, npairs_cap, (key >> 4) & 7, key & 7, h, threads, kMaxK,
+                            core::lut_entries_cap(h));
 }
 
 cudaError_t batch_occupancy(int key, uint32_t ntab_cap, uint32_t npairs_cap, int threads,

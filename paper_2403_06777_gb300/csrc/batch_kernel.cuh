@@ -33,7 +33,7 @@ using BatchFn = void (*)(const unsigned char*, const BatchChunk*, uint32_t, unsi
 extern const BatchFn kTable[3][kMaxWordsNode + 1][kMaxWordsOther];   // batch.cu
 extern const BatchFn kHist[4][2][kMaxWordsOther];                    // batch_count.cu
 extern const BatchFn kShared[2][kMaxWordsNode + 1][kMaxWordsOther];  // batch_count.cu
-extern const BatchFn kLut[3][2][kMaxWordsOther];                              // block lookup
+extern const BatchFn kLut[4][2][kMaxWordsOther];   // block lookup: variants 9, 10, 11, 13
 
 namespace {
 
@@ -49,7 +49,7 @@ batch_kernel(const unsigned char* __restrict__ scalars, const BatchChunk* __rest
     __shared__ KernelParams sp;
     __shared__ uint32_t s_chunk, s_loaded;
     __shared__ __align__(8) uint64_t s_bar;
-    const Smem sm = carve<NW, HIST>(smem_raw, ntab_cap, npairs_cap);
+    const Smem sm = carve<NW, HIST>(smem_raw, ntab_cap, npairs_cap, kMaxK, lut_entries_cap(HIST));
     if (HIST)
         for (uint32_t i = threadIdx.x; i < counter_words(HIST, ntab_cap, blockDim.x); i += blockDim.x)
             sm.sH[i] = 0;

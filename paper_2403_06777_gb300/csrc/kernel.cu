@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -26,7 +27,7 @@ using namespace sumk;
 KernelFn pick(const Plan& pl) {
     const int nwl = pl.nwl < 1 ? 1 : pl.nwl;
     const int v = variant(pl);
-    if (v >= 9) return kLut[v - 9][pl.nwn][nwl - 1];
+    if (v >= 9) return kLut[v == 13 ? 3 : v - 9][pl.nwn][nwl - 1];
     if (v >= 7) return kShared[v - 7][pl.nwn][nwl - 1];
     if (v >= 3) return kHist[v - 3][pl.nwn][nwl - 1];
     return kTable[v][pl.nwn][nwl - 1];
@@ -54,12 +55,12 @@ cudaError_t ensure_dynamic_smem(const void* fn, size_t bytes) {
 static size_t smem_for(const Plan& pl, int threads) {
     const int h = hist_mode(pl);
     return smem_bytes(pl.kp.tab_size, pl.kp.npairs, pl.nwn, kernel_words(pl) - pl.nwn, h, threads,
-                      k_cap(pl.kp.k), h >= 4 ? lut_cap(pl.kp.lut_no + pl.kp.lut_nn) : 0u);
+                      k_cap(pl.kp.k), h >= 4 ? ((pl.kp.lut_entries + 1u) & ~1u) : 0u);
 }
 
 // Threads per block: 128 for the lane-private block lookup (32 KB of
 // counters per 128 threads), else 256.
-static int block_threads(const Plan& pl) { return hist_mode(pl) == 5 ? 128 : kThreads; }
+static int block_threads(const Plan& pl) { return hist_mode(pl) >= 5 ? 128 : kThreads; }
 
 size_t sum_smem_bytes(const Plan& pl) { return smem_for(pl, block_threads(pl)); }
 
@@ -125,11 +126,16 @@ void sum_shape(const Plan& pl, int sm_count, int max_grid_cap, uint64_t count, u
     const uint64_t threads = (uint64_t)max_grid * (uint64_t)bt;
     uint64_t sp = (count + threads - 1) / threads;
     // (block lookup: a multiple of 16, so that a warp's lanes reach the
-    // flips of variable 3 together)
-    const uint64_t al = hist_mode(pl) >= 4 ? 16 : 8;
+    // flips of variable 3 together; inner parameters: a multiple of the run
+    // over which the cut parities stay constant (at most 2^16 terms), so
+    // that a warp's lanes fold their counters at the same step instead of
+    // one after another)
+    uint64_t al = hist_mode(pl) >= 4 ? 16 : 8;
+    if (pl.k_inner && pl.kp.zq_lo < 64) al = std::max<uint64_t>(al, 1ull << std::min<uint32_t>(pl.kp.zq_lo, 16));
     sp = (sp + al - 1) & ~(al - 1);
     if (sp < 64) sp = 64;
-    if (sp > sum_max_span(pl)) sp = sum_max_span(pl);   // longer ranges: several slices per thread
+    const uint64_t cap = sum_max_span(pl) & ~(al - 1);
+    if (sp > cap) sp = cap;   // longer ranges: several slices per thread
     const uint64_t nslices = (count + sp - 1) / sp;
     uint64_t g = (nslices + (uint64_t)bt - 1) / (uint64_t)bt;
     if (g > (uint64_t)max_grid) g = (uint64_t)max_grid;

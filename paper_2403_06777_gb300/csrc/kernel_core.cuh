@@ -80,16 +80,20 @@ __device__ __forceinline__ zw64 block_reduce(zw64 v, zw64* sred) {
 // values the table holds), 4: block lookup with warp-shared counters over
 // kLutRows rows of the table (when the plan built the lookup), 5: block
 // lookup with lane-private 32-bit counters (rows of 2^lut_tsh counters, the
-// phase exponent taken mod 8 by a mask)
+// phase exponent taken mod 8 by a mask), 6: the same over two lookup tables
 constexpr uint32_t kHistMaxEntries32 = 48;
 constexpr uint32_t kHistMaxEntries16 = 128;
 constexpr uint32_t kHistMaxEntriesShared = 2048;
 constexpr uint32_t kLutEntries = (1u << kLutMaxBits) + 8u;
+constexpr uint32_t kLut2Entries = (2u << kLutMaxBits) + 8u;
+// lookup words a block sized for any scalar of lookup kind h holds
+__host__ __device__ constexpr uint32_t lut_entries_cap(int h) { return h == 6 ? kLut2Entries : kLutEntries; }
 inline int hist_mode(const Plan& pl) {
     if (pl.general) return 0;
     // inner parameters: lane-private counters (folded per lane) or the table
-    if (pl.k_inner) return pl.kp.tab_size <= kHistMaxEntries32 ? 1 : (pl.kp.tab_size <= kHistMaxEntries16 ? 2 : 0);
-    if (pl.lut_ok) return pl.lut_lane ? 5 : 4;
+    if (pl.k_inner && !pl.lut_ok)
+        return pl.kp.tab_size <= kHistMaxEntries32 ? 1 : (pl.kp.tab_size <= kHistMaxEntries16 ? 2 : 0);
+    if (pl.lut_ok) return pl.lut_lane ? (pl.lut_two ? 6 : 5) : 4;
     if (pl.kp.tab_size <= kHistMaxEntries32) return 1;
     if (pl.kp.tab_size <= kHistMaxEntries16) return 2;
     if (pl.kp.tab_size <= kHistMaxEntriesShared) return 3;
@@ -99,7 +103,8 @@ inline int kernel_words(const Plan& pl) { return pl.nwn + (pl.nwl < 1 ? 1 : pl.n
 // kernel variant: 0 table, 1 table + extra index bits, 2 general (phase-pair
 // products), 3/4 lane-private 32-bit counters (+ extra bits), 5/6
 // lane-private 16-bit counters (+ extra), 7/8 warp-shared counters (+ extra),
-// 9/10 block lookup (+ extra), 11 block lookup with lane-private counters
+// 9/10 block lookup (+ extra), 11 block lookup with lane-private counters,
+// 13 the same with two lookup tables
 inline int variant(const Plan& pl) {
     if (pl.general) return 2;
     const int x = pl.kp.xshift ? 1 : 0;
@@ -115,7 +120,7 @@ __host__ __device__ constexpr uint32_t counter_words(int h, uint32_t ntab, uint3
                   : (h == 2 ? (ntab + 1) / 2 * threads
                             : (h == 3 ? ntab * (threads / 32)
                                       : (h == 4 ? (uint32_t)(kLutRows / 8) * ntab * (threads / 32)
-                                                : (h == 5 ? (uint32_t)kLaneCounters * threads : 0u))));
+                                                : (h >= 5 ? (uint32_t)kLaneCounters * threads : 0u))));
 }
 inline uint64_t max_span(int h) { return h == 2 ? kSpan16 : kSpan32; }
 
@@ -224,7 +229,7 @@ __device__ __forceinline__ void issue_tables(const KernelParams& p, const Smem& 
     const uint32_t ns = ((p.k + 3) / 4) * 16u * seek_stride(NW);
     const uint32_t bt = p.tab_size * 32u, bs = ns * 4u, br = p.k * RW * 4u, ba = round16(p.k * 8u);
     const uint32_t bpv = GENERAL ? 4u * p.npairs * 32u : 0u;
-    const uint32_t bl = HIST >= 4 ? round16(((1u << (p.lut_no + p.lut_nn)) + 8u) * 8u) : 0u;
+    const uint32_t bl = HIST >= 4 ? round16(p.lut_entries * 8u) : 0u;
     // order the shared-memory reads of a previous scalar before the
     // asynchronous writes
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -288,7 +293,7 @@ __device__ __forceinline__ bool load_tables(const KernelParams& p, const Smem& s
 // (counter i of lane l at word i * 32 + l), so the counting atomics of a
 // warp never conflict; a counter index is (J mod 8) * 2^tsh + M, the block's
 // base plus the looked-up offset modulo 8 * 2^tsh.
-template <int NWN, int NWL, bool XTRA, bool LANE>
+template <int NWN, int NWL, bool XTRA, bool LANE, bool TWO>
 __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, uint64_t first,
                                          uint64_t count, uint64_t span, uint64_t nslices,
                                          uint64_t s_begin, uint64_t stride, bool fold_each,
@@ -310,7 +315,12 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
     uint32_t* const wc = sm.sH + warp * nbins;
     const uint32_t no = p.lut_no, nn = p.lut_nn, lsh = p.lut_shift;
     const uint32_t mo = (1u << no) - 1u, mn = (1u << nn) - 1u;
-    const uint64_t* __restrict__ qlut = sL + (1u << (no + nn));
+    // two tables (TWO): the first na lookup bits index sL, the rest sLB
+    const uint32_t na = TWO ? p.lut_na : no + nn, ma = (1u << na) - 1u;
+    const uint64_t* __restrict__ sLB = sL + (1u << na);
+    const uint64_t* __restrict__ qlut = TWO ? sLB + (1u << (no + nn - na)) : sL + (1u << (no + nn));
+    // inner parameters (lane-private counters only)
+    const bool outer = LANE && p.zq_lo < 64u;
     constexpr uint32_t tsh = kLaneRowShift, cm = (8u << tsh) - 1u;
     uint32_t* const lbase = sm.sH + warp * ((uint32_t)kLaneCounters * 32u);
     uint32_t* const wl = lbase + lane;
@@ -415,8 +425,35 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
             {
                 uint32_t u = (L[NWN] >> lsh) & mo;
                 if (NWN) u |= (L[0] & mn) << no;
-                us = lut_slot(u);
+                us = TWO ? (lut_slot(u & ma) | (lut_slot(u >> na) << na)) : lut_slot(u);
             }
+            // inner parameters: the cut parities zq of the current state; a
+            // lane folds its own counters, times the inner table at zq, when
+            // a flip changes zq and at the end of the slice
+            uint32_t zq = 0;
+            if (outer)
+                for (uint64_t m = x >> p.zq_lo; m; m &= m - 1)
+                    zq ^= __ldg(p.zqcol + p.zq_lo + (uint32_t)__ffsll((long long)m) - 1u);
+            auto flush = [&]() {
+                if constexpr (LANE) {
+                    zw64 sum = zw_zero();
+                    for (uint32_t J = 0; J < 8; J++)
+                        for (uint32_t Mi = 0; Mi < ts; Mi++) {
+                            uint32_t* const c = lctr((J << tsh) + Mi);
+                            const uint32_t v = *c;
+                            if (!v) continue;
+                            *c = 0u;
+                            sum = zw_madd32(sum, lds_zw(sT + J * ts + Mi), v);
+                        }
+                    acc = zw_add(acc, zw_mul(sum, ldg_zw(p.ftab + zq)));
+                }
+            };
+            auto cut_flip = [&](int i) {
+                if (outer && (uint32_t)i >= p.zq_lo) {
+                    const uint32_t dz = __ldg(p.zqcol + i);
+                    if (dz) { flush(); zq ^= dz; }
+                }
+            };
 
             auto node_count = [&]() {
                 uint32_t M = 0;
@@ -454,7 +491,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
             // net change: variable 2 flipped (Gray 000 -> 100), its forms, its
             // adjacency row and the block's phase change
             auto block8 = [&]() {
-                const uint64_t e = sL[us] + qlut[(uint32_t)a & 7u];
+                const uint64_t e = (TWO ? sL[us & ma] + sLB[us >> na] : sL[us]) + qlut[(uint32_t)a & 7u];
                 const uint32_t lo = (uint32_t)e, hi = (uint32_t)(e >> 32);
                 if constexpr (LANE) {
                     // the block's base (< 64) added to all offset bytes at once
@@ -526,6 +563,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                         block8();
                         t = tn;
                         if (!more) break;
+                        cut_flip(i);
                         Jl += (uint32_t)(a >> i) << 2;   // (bits above 2: only J mod 8 is used)
                         a ^= adj;
                         step(fr, fr[NW + 2 * NWL] >> 8);
@@ -548,6 +586,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                     flip3();
                 } else {
                     const int i = ctz64(t);
+                    cut_flip(i);
                     Jl += (uint32_t)(a >> i) << 2;   // (bits above 2: only J mod 8 is used)
                     a ^= sADJ[i];
                     uint32_t fr[RW];
@@ -555,10 +594,11 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                     step(fr, fr[NW + 2 * NWL] >> 8);
                 }
             }
+            if (outer) flush();
         }
-        if (fold_each) fold(true);
+        if (fold_each && !outer) fold(true);
     }
-    if (!fold_each && final_fold) fold(clear_on_exit);
+    if (!fold_each && final_fold && !outer) fold(clear_on_exit);
 }
 
 // final_fold false (counting variants with warp-shared counters, one slice
@@ -569,9 +609,9 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                                      uint64_t count, uint64_t span, uint64_t nslices,
                                      uint64_t s_begin, uint64_t stride, bool fold_each,
                                      bool clear_on_exit, bool final_fold, zw64& acc) {
-    if constexpr (HIST == 4 || HIST == 5) {
-        walk_lut<NWN, NWL, XTRA, HIST == 5>(p, sm, first, count, span, nslices, s_begin, stride,
-                                            fold_each, clear_on_exit, final_fold, acc);
+    if constexpr (HIST >= 4) {
+        walk_lut<NWN, NWL, XTRA, HIST >= 5, HIST == 6>(p, sm, first, count, span, nslices, s_begin, stride,
+                                                       fold_each, clear_on_exit, final_fold, acc);
         return;
     }
     constexpr int NW = NWN + NWL;

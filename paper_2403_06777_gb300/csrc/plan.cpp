@@ -28,9 +28,10 @@ struct Form {
 
 int build_split_plan(const PS& ps, Plan* out);
 
-// allow_lut: the block lookup may be built (not for the outer rows of a
-// scalar with inner parameters, whose walk folds per lane).
-int build_plain_plan(const PS& ps, bool allow_lut, Plan* out) {
+// allow_lut: the block lookup may be built; lane_only: only with
+// lane-private counters (the outer rows of a scalar with inner parameters,
+// whose walk folds each lane's counters by itself).
+int build_plain_plan(const PS& ps, bool allow_lut, bool lane_only, Plan* out) {
     Plan pl;
     memset(&pl.kp, 0, sizeof pl.kp);
     KernelParams& kp = pl.kp;
@@ -108,17 +109,38 @@ int build_plain_plan(const PS& ps, bool allow_lut, Plan* out) {
     // layout
     // linear forms in ascending mask order, coefficients summed mod 8, zero
     // coefficients dropped
-    std::vector<std::pair<uint64_t, uint32_t>> lins;
-    std::sort(lin_terms.begin(), lin_terms.end(),
-              [](const std::pair<uint64_t, uint32_t>& x, const std::pair<uint64_t, uint32_t>& y) {
-                  return x.first < y.first;
-              });
-    for (size_t i = 0; i < lin_terms.size();) {
-        uint32_t c = 0;
-        size_t j = i;
-        for (; j < lin_terms.size() && lin_terms[j].first == lin_terms[i].first; j++) c += lin_terms[j].second;
-        if (c & 7) lins.push_back({lin_terms[i].first, c & 7});
-        i = j;
+    auto merge = [](std::vector<std::pair<uint64_t, uint32_t>>& terms) {
+        std::vector<std::pair<uint64_t, uint32_t>> out;
+        std::sort(terms.begin(), terms.end(),
+                  [](const std::pair<uint64_t, uint32_t>& x, const std::pair<uint64_t, uint32_t>& y) {
+                      return x.first < y.first;
+                  });
+        for (size_t i = 0; i < terms.size();) {
+            uint32_t c = 0;
+            size_t j = i;
+            for (; j < terms.size() && terms[j].first == terms[i].first; j++) c += terms[j].second;
+            if (c & 7) out.push_back({terms[i].first, c & 7});
+            i = j;
+        }
+        return out;
+    };
+    std::vector<std::pair<uint64_t, uint32_t>> lins = merge(lin_terms);
+    // An even coefficient on a parity of several variables is a Clifford
+    // phase that needs no form bit: c (x_1 ^ .. ^ x_m) = c sum_i x_i
+    // + 4 sum_{i<j} x_i x_j (mod 8) for c = 2 mod 4, and 4 sum_i x_i for
+    // c = 4 -- singletons, which merge into one form per variable, and
+    // quadratic terms, which the adjacency rows carry.
+    {
+        std::vector<std::pair<uint64_t, uint32_t>> t2;
+        bool expanded = false;
+        for (auto& e : lins) {
+            if ((e.second & 1) || __builtin_popcountll(e.first) < 2) { t2.push_back(e); continue; }
+            expanded = true;
+            for (uint64_t m = e.first; m; m &= m - 1) t2.push_back({m & (0 - m), e.second});
+            if ((e.second & 3) == 2)
+                for (uint64_t m = e.first; m; m &= m - 1) adj[__builtin_ctzll(m)] ^= e.first & ~(m & (0 - m));
+        }
+        if (expanded) lins = merge(t2);
     }
     // block lookup candidates: no phase-pair or zero forms (their bits would
     // vary inside a block); forms holding variable 0, 1 or 2 go first
@@ -128,7 +150,8 @@ int build_plain_plan(const PS& ps, bool allow_lut, Plan* out) {
     bool lut_try = allow_lut && k >= 3 && pair_masks.size() <= 2 * (size_t)kFoldPairs;
     for (uint64_t m : pair_masks) lut_try = lut_try && !(m & 7);
     for (auto& z : zero) lut_try = lut_try && !(z.mask & 7);
-    uint32_t lut_nn = 0, lut_no = 0;
+    uint32_t lut_nn = 0, lut_no = 0, lut_na = 0;
+    bool lut_two = false;
     if (lut_try) {
         std::vector<Form> o2;
         std::vector<uint8_t> b2;
@@ -143,9 +166,19 @@ int build_plain_plan(const PS& ps, bool allow_lut, Plan* out) {
         for (auto& e : lins) lut_no += (e.first & low3) ? 1 : 0;
         const uint32_t stride = (uint32_t)odd.size() + 1;
         const uint32_t planes = (1u << (uint32_t)pair_masks.size()) << (zero.empty() ? 0 : 1);
-        lut_try = lut_nn + lut_no <= (uint32_t)kLutMaxBits && 11 * stride + 2 * lut_nn <= 255 &&
-                  (uint32_t)kLutRows * stride * planes <= 2048;
+        const uint32_t nU = lut_nn + lut_no;
+        const bool lane = pair_masks.empty() && zero.empty() && odd.size() + 1 <= (1u << kLaneRowShift);
+        const bool one = nU <= (uint32_t)kLutMaxBits && 11 * stride + 2 * lut_nn <= 255 &&
+                         (uint32_t)kLutRows * stride * planes <= 2048;
+        // more forms than one table takes: two tables, lane-private counters
+        lut_two = lane && nU > (uint32_t)kLutMaxBits && nU <= (uint32_t)kLut2MaxBits && lut_no <= 32;
+        lut_na = lut_two ? (nU + 1) / 2 : nU;
+        lut_try = (one && (lane || !lane_only)) || lut_two;
     }
+    // lookup slot of the lookup-index bits u (linear forms, then node forms)
+    auto slot_of = [&](uint32_t u) {
+        return lut_two ? (lut_slot(u & ((1u << lut_na) - 1u)) | (lut_slot(u >> lut_na) << lut_na)) : lut_slot(u);
+    };
     size_t n_other = lins.size() + zero.size() + pair_masks.size();
     pl.nwn = (int)((odd.size() + 31) / 32);
     pl.nwl = (int)((n_other + 31) / 32);
@@ -234,7 +267,7 @@ int build_plain_plan(const PS& ps, bool allow_lut, Plan* out) {
             if (lut_try) {
                 const uint32_t fo_i = (r[pl.nwn] >> pair_masks.size()) & ((1u << lut_no) - 1u);
                 const uint32_t fn_i = pl.nwn ? (r[0] & ((1u << lut_nn) - 1u)) : 0u;
-                du = lut_slot((fn_i << lut_no) | fo_i);
+                du = slot_of((fn_i << lut_no) | fo_i);
             }
             r[nw + 2 * nwl_k] = (S & 7u) | (du << 8);
             if (i < 4) kp.U4[i] = du;
@@ -295,45 +328,13 @@ int build_plain_plan(const PS& ps, bool allow_lut, Plan* out) {
         };
         uint32_t nb_mask = 0;
         for (uint32_t r = 0; r < lut_nn; r++) nb_mask |= (uint32_t)odd_b[r] << r;
-        // linear part: bytes 0..6 hold (dJ_s mod 8) * stride, byte 7 dJ_7 mod 8
-        uint64_t so = 0, dout[kLutMaxBits], dnod[kLutMaxBits];
-        {
-            int acc = 0;   // class-B node bits: 4 per flip, whatever their state
-            for (int s = 1; s <= 7; s++) {
-                acc += 4 * __builtin_popcount(fn[seq[s - 1]] & nb_mask);
-                so |= (uint64_t)(uint32_t)(acc & 7) << (8 * (s - 1));
-            }
-        }
-        for (uint32_t r = 0; r < lut_no; r++) {
-            const int c = (int)lins[r].second;
-            const uint64_t p0 = share(r, fo, c, 0, 0, true), p1 = share(r, fo, c, 1, 0, true);
-            so += p0;
-            dout[r] = p1 - p0;
-        }
-        const uint64_t st = stride;
-        std::vector<uint64_t> eo, en;
-        gray_fill(lut_no, so, dout, eo, [st](uint64_t x) {
-            x &= 0x0007070707070707ull;
-            return x * st | ((x >> 48) << 56);
-        });
-        // node part: bytes 0..6 hold dM_s + lut_nn (each form's share + 1)
-        uint64_t sn = 0;
-        for (uint32_t r = 0; r < lut_nn; r++) {
-            const uint64_t q0 = share(r, fn, 1, 0, 1, false), q1 = share(r, fn, 1, 1, 1, false);
-            sn += q0;
-            dnod[r] = q1 - q0;
-        }
-        gray_fill(lut_nn, sn, dnod, en, [](uint64_t x) { return x; });
-        pl.lut.assign(((size_t)1 << nU) + 8, 0ull);
-        // lane-private counters: offsets taken mod 8 * 2^tsh with the bias
-        // lut_nn removed (the kernel adds the block's base and masks)
-        const uint64_t b7 = 0x0001010101010101ull, cm = (8ull << tsh) - 1;
-        for (uint32_t Ln = 0; Ln < (1u << lut_nn); Ln++)
-            for (uint32_t Lo = 0; Lo < (1u << lut_no); Lo++) {
-                uint64_t e = eo[Lo] + en[Ln];
-                if (pl.lut_lane) e = ((e + (cm + 1 - lut_nn) * b7) & (cm * b7)) | (e & ~(0xFFull * b7));
-                pl.lut[lut_slot((Ln << lut_no) | Lo)] = e;
-            }
+        kp.lut_no = lut_no;
+        kp.lut_nn = lut_nn;
+        kp.lut_shift = (uint32_t)pair_masks.size();   // linear forms follow the pair bits
+        pl.lut_two = lut_two;
+        kp.lut_na = lut_two ? lut_na : 0u;
+        // the 8 quadratic entries, indexed by the bits of A x on variables 0-2
+        uint64_t qent[8];
         for (uint32_t h = 0; h < 8; h++) {
             uint32_t a = h, Q = 0;
             uint64_t e = 0;
@@ -344,12 +345,115 @@ int build_plain_plan(const PS& ps, bool allow_lut, Plan* out) {
                 if (s < 7) e |= (uint64_t)(4 * Q * stride) << (8 * (s - 1));
                 else e |= ((uint64_t)(4 * Q * stride) << 48) | ((uint64_t)(4 * Q) << 56);
             }
-            pl.lut[((size_t)1 << nU) + h] = e;
+            qent[h] = e;
         }
-        kp.lut_no = lut_no;
-        kp.lut_nn = lut_nn;
-        kp.lut_shift = (uint32_t)pair_masks.size();   // linear forms follow the pair bits
-        pl.lut_ok = true;
+        if (lut_two) {
+            // Two tables over the first lut_na lookup bits and the rest.  An
+            // entry is the sum of its forms' shares as integers per byte:
+            // bytes 0-6 the counter offset after step s, (dJ_s mod 8) * 2^tsh
+            // + dM_s, taken mod 8 * 2^tsh; byte 7 the block's phase change
+            // mod 8.  The class-B nodes' phase change (the same for every
+            // entry) goes into the first table.  The kernel adds the two
+            // entries, the quadratic entry and the block's base: every byte
+            // stays below 256.
+            auto steps = [&](uint32_t r, const uint32_t* f, uint32_t b, int acc[7]) {
+                uint32_t bit = b;
+                int a = 0;
+                for (int st = 1; st <= 7; st++) {
+                    if ((f[seq[st - 1]] >> r) & 1) {
+                        a += 1 - 2 * (int)bit;
+                        bit ^= 1u;
+                    }
+                    acc[st - 1] = a;
+                }
+            };
+            const int m8 = 8 << tsh;
+            auto add_phase = [&](int v[8], const int acc[7], int c) {
+                for (int st = 0; st < 7; st++) v[st] += (((c * acc[st]) % 8 + 8) % 8) * (1 << tsh);
+                v[7] += ((c * acc[6]) % 8 + 8) % 8;
+            };
+            int cst[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            {
+                int acc[7], a = 0;
+                for (int st = 1; st <= 7; st++) {
+                    a += 4 * __builtin_popcount(fn[seq[st - 1]] & nb_mask);
+                    acc[st - 1] = a;
+                }
+                add_phase(cst, acc, 1);
+            }
+            // shares of lookup bit r for bit value b
+            auto form_bytes = [&](uint32_t r, uint32_t b, int v[8]) {
+                int acc[7];
+                if (r < lut_no) {
+                    steps(r, fo, b, acc);
+                    add_phase(v, acc, (int)lins[r].second);
+                } else {
+                    steps(r - lut_no, fn, b, acc);
+                    for (int st = 0; st < 7; st++) v[st] += acc[st];
+                }
+            };
+            const uint32_t nb = nU - lut_na;
+            pl.lut.assign(((size_t)1 << lut_na) + ((size_t)1 << nb) + 8, 0ull);
+            for (int t = 0; t < 2; t++) {
+                const uint32_t lo = t ? lut_na : 0u, n = t ? nb : lut_na;
+                uint64_t* tab = pl.lut.data() + (t ? ((size_t)1 << lut_na) : 0);
+                for (uint32_t u = 0; u < (1u << n); u++) {
+                    int v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                    if (!t) for (int j = 0; j < 8; j++) v[j] = cst[j];
+                    for (uint32_t j = 0; j < n; j++) form_bytes(lo + j, (u >> j) & 1u, v);
+                    uint64_t e = 0;
+                    for (int j = 0; j < 7; j++) e |= (uint64_t)(((v[j] % m8) + m8) % m8) << (8 * j);
+                    e |= (uint64_t)(((v[7] % 8) + 8) % 8) << 56;
+                    tab[lut_slot(u)] = e;
+                }
+            }
+            for (uint32_t h = 0; h < 8; h++) pl.lut[((size_t)1 << lut_na) + ((size_t)1 << nb) + h] = qent[h];
+            kp.lut_entries = (uint32_t)pl.lut.size();
+            pl.lut_ok = true;
+        } else {
+            // linear part: bytes 0..6 hold (dJ_s mod 8) * stride, byte 7 dJ_7 mod 8
+            uint64_t so = 0, dout[kLutMaxBits], dnod[kLutMaxBits];
+            {
+                int acc = 0;   // class-B node bits: 4 per flip, whatever their state
+                for (int s = 1; s <= 7; s++) {
+                    acc += 4 * __builtin_popcount(fn[seq[s - 1]] & nb_mask);
+                    so |= (uint64_t)(uint32_t)(acc & 7) << (8 * (s - 1));
+                }
+            }
+            for (uint32_t r = 0; r < lut_no; r++) {
+                const int c = (int)lins[r].second;
+                const uint64_t p0 = share(r, fo, c, 0, 0, true), p1 = share(r, fo, c, 1, 0, true);
+                so += p0;
+                dout[r] = p1 - p0;
+            }
+            const uint64_t st = stride;
+            std::vector<uint64_t> eo, en;
+            gray_fill(lut_no, so, dout, eo, [st](uint64_t x) {
+                x &= 0x0007070707070707ull;
+                return x * st | ((x >> 48) << 56);
+            });
+            // node part: bytes 0..6 hold dM_s + lut_nn (each form's share + 1)
+            uint64_t sn = 0;
+            for (uint32_t r = 0; r < lut_nn; r++) {
+                const uint64_t q0 = share(r, fn, 1, 0, 1, false), q1 = share(r, fn, 1, 1, 1, false);
+                sn += q0;
+                dnod[r] = q1 - q0;
+            }
+            gray_fill(lut_nn, sn, dnod, en, [](uint64_t x) { return x; });
+            pl.lut.assign(((size_t)1 << nU) + 8, 0ull);
+            // lane-private counters: offsets taken mod 8 * 2^tsh with the bias
+            // lut_nn removed (the kernel adds the block's base and masks)
+            const uint64_t b7 = 0x0001010101010101ull, cm = (8ull << tsh) - 1;
+            for (uint32_t Ln = 0; Ln < (1u << lut_nn); Ln++)
+                for (uint32_t Lo = 0; Lo < (1u << lut_no); Lo++) {
+                    uint64_t e = eo[Lo] + en[Ln];
+                    if (pl.lut_lane) e = ((e + (cm + 1 - lut_nn) * b7) & (cm * b7)) | (e & ~(0xFFull * b7));
+                    pl.lut[lut_slot((Ln << lut_no) | Lo)] = e;
+                }
+            for (uint32_t h = 0; h < 8; h++) pl.lut[((size_t)1 << nU) + h] = qent[h];
+            kp.lut_entries = (uint32_t)pl.lut.size();
+            pl.lut_ok = true;
+        }
     }
 
     // T[J][M][pair bits][zero] = w^(J + 2M) (1 + sqrt2)^M * prod_j PV_j(bits_j) * [not zero]
@@ -463,10 +567,10 @@ int build_split_plan(const PS& ps, Plan* out) {
     // the walk's unrolled steps flip variables 0-3 without looking at zq
     if (lo < 4) return ZXP_EINVAL;
     auto ip = std::make_shared<Plan>();
-    int st = build_plain_plan(inner, false, ip.get());
+    int st = build_plain_plan(inner, false, false, ip.get());
     if (st != ZXP_OK) return st;
     Plan pl;
-    if ((st = build_plain_plan(outer, false, &pl)) != ZXP_OK) return st;
+    if ((st = build_plain_plan(outer, true, true, &pl)) != ZXP_OK) return st;
     pl.kp.zq_lo = lo;
     pl.k_inner = ki;
     pl.inner_bits = bits;
@@ -481,7 +585,7 @@ int build_split_plan(const PS& ps, Plan* out) {
 
 int build_plan(const PS& ps, Plan* out) {
     if (ps.k_inner) return build_split_plan(ps, out);
-    return build_plain_plan(ps, true, out);
+    return build_plain_plan(ps, true, false, out);
 }
 
 }  // namespace zxp

@@ -46,6 +46,10 @@ constexpr int kMaxRowWords = (int)row_words(kMaxWordsNode, kMaxWordsOther);
 // that lanes whose u differ only in high bits read different bank pairs.
 constexpr int kLutMaxBits = 10;
 constexpr int kLutRows = 24;
+// With lane-private counters the forms may be split over two lookup tables
+// whose entries add (each form's share of an entry depends on its own bit
+// only): up to 2 * kLutMaxBits forms.
+constexpr int kLut2MaxBits = 2 * kLutMaxBits;
 // Block lookup with lane-private counters (variant 11): a lane's counters are
 // indexed by (J mod 8) * 2^kLaneRowShift + M (M <= 7: at most 7 odd nodes).
 constexpr int kLaneRowShift = 3;
@@ -74,6 +78,11 @@ struct KernelParams {
     // (after the phase-pair bits)
     uint32_t lut_no, lut_nn, lut_shift;
     uint32_t lut_tsh;        // variant 11: log2 of the counter row stride (kLaneRowShift)
+    // two lookup tables (variant 13): the first lut_na bits of the lookup
+    // index u (linear form bits, then node form bits) select an entry of
+    // the first table, the rest one of the second; 0 with one table
+    uint32_t lut_na;
+    uint32_t lut_entries;    // 64-bit words of the lookup: its table(s) and the 8 quadratic entries
     uint64_t A4[4];          // adjacency rows of variables 0..3 (0 beyond k)
     // variant 11: bytes between a lane's consecutive counters (32 lanes x 4
     // bytes).  A parameter rather than a constant, so that the counter
@@ -133,6 +142,7 @@ struct Plan {
     // block's base and the offset taken modulo 8 * 2^lut_tsh.
     bool lut_ok = false;
     bool lut_lane = false;
+    bool lut_two = false;           // two tables (lane-private counters only)
     std::vector<uint64_t> lut;
     // Inner parameters: the scalar's outer rows are this plan; `inner` is the
     // plan of the product of its inner and crossing rows as a function of

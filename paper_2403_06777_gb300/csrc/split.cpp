@@ -257,15 +257,18 @@ std::vector<uint64_t> outer_columns(const Graph& g, uint64_t I, uint64_t& rng) {
         for (size_t i = 0; i < rref.size(); i++) if ((rref[i] >> j) & 1) v |= 1ull << pivc[i];
         kb.push_back(v);
     }
-    // outer forms the walk tracks (purely outer non-Clifford and linear rows)
+    // Outer forms that hold form bits in the walk: odd linear phases,
+    // nodes and phase-pair forms on outer coordinates only (even linear
+    // phases become one singleton per variable and quadratic terms, so they
+    // add at most one form per variable).
     std::vector<uint64_t> forms;
-    for (auto& r : g.ps.lin) if (r.mask & O) forms.push_back(compact(r.mask & O));
+    for (auto& r : g.ps.lin) if ((r.c & 1) && r.mask && !(r.mask & I)) forms.push_back(compact(r.mask));
     for (auto& r : g.ps.node) if (r.mask && !(r.mask & I)) forms.push_back(compact(r.mask));
-    auto hits = [&](uint64_t v) {
-        int h = 0;
-        for (uint64_t f : forms) h += (int)par(f & v);
-        return h;
-    };
+    for (auto& r : g.ps.pair)
+        if ((r.ma | r.mb) && !((r.ma | r.mb) & I)) {
+            if (r.ma) forms.push_back(compact(r.ma));
+            if (r.mb) forms.push_back(compact(r.mb));
+        }
     // candidate kernel vectors: the whole kernel when small, else samples
     const size_t dim = kb.size();
     std::vector<uint64_t> cand;
@@ -284,14 +287,63 @@ std::vector<uint64_t> outer_columns(const Graph& g, uint64_t I, uint64_t& rng) {
             if (v) cand.push_back(v);
         }
     }
-    std::vector<std::pair<uint64_t, uint64_t>> keyed;
-    for (uint64_t v : cand) keyed.push_back({((uint64_t)hits(v) << 16) | (uint64_t)popc(v), v});
-    std::sort(keyed.begin(), keyed.end());
-    Span sp;
+    // the forms each candidate flips, as a bitset
+    const size_t nfw = (forms.size() + 63) / 64 + 1;
+    std::vector<uint64_t> H(cand.size() * nfw, 0ull);
+    std::vector<int> nh(cand.size(), 0);
+    for (size_t c = 0; c < cand.size(); c++) {
+        for (size_t f = 0; f < forms.size(); f++)
+            if (par(forms[f] & cand[c])) H[c * nfw + f / 64] |= 1ull << (f % 64);
+        for (size_t w = 0; w < nfw; w++) nh[c] += popc(H[c * nfw + w]);
+    }
+    auto uni = [&](std::initializer_list<size_t> cs) {
+        int n = 0;
+        for (size_t w = 0; w < nfw; w++) {
+            uint64_t u = 0;
+            for (size_t c : cs) u |= H[c * nfw + w];
+            n += popc(u);
+        }
+        return n;
+    };
+    // Variables 0-2 (their forms are the block lookup's index): three
+    // independent kernel vectors whose flipped forms have the smallest
+    // union, from the lightest vectors and the best pairs among them.
+    std::vector<size_t> order(cand.size());
+    for (size_t c = 0; c < cand.size(); c++) order[c] = c;
+    std::sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+        return nh[x] != nh[y] ? nh[x] < nh[y] : popc(cand[x]) < popc(cand[y]);
+    });
     std::vector<uint64_t> cols;
-    for (auto& kv : keyed) {
+    if (dim >= 3) {
+        std::vector<std::pair<int, std::pair<size_t, size_t>>> pairs;
+        const size_t n0 = std::min<size_t>(order.size(), 32);
+        for (size_t x = 0; x < n0; x++)
+            for (size_t y = 0; y < cand.size(); y++)
+                if (cand[y] != cand[order[x]]) pairs.push_back({uni({order[x], y}), {order[x], y}});
+        std::sort(pairs.begin(), pairs.end());
+        int best = -1;
+        size_t b0 = 0, b1 = 0, b2 = 0;
+        for (size_t p = 0; p < pairs.size() && p < 64; p++) {
+            const size_t c0 = pairs[p].second.first, c1 = pairs[p].second.second;
+            for (size_t z = 0; z < cand.size(); z++) {
+                const uint64_t v = cand[z];
+                if (v == cand[c0] || v == cand[c1] || v == (cand[c0] ^ cand[c1])) continue;
+                const int u = uni({c0, c1, z});
+                if (best < 0 || u < best) { best = u; b0 = c0; b1 = c1; b2 = z; }
+            }
+        }
+        if (best >= 0) {
+            // the lightest of the three flips most often
+            size_t t[3] = {b0, b1, b2};
+            std::sort(t, t + 3, [&](size_t x, size_t y) { return nh[x] < nh[y]; });
+            for (size_t c : t) cols.push_back(cand[c]);
+        }
+    }
+    Span sp;
+    for (uint64_t c : cols) sp.add(c);
+    for (size_t c : order) {
         if (cols.size() == dim) break;
-        if (sp.add(kv.second)) cols.push_back(kv.second);
+        if (sp.add(cand[c])) cols.push_back(cand[c]);
     }
     for (uint32_t j = 0; j < ko && cols.size() < ko; j++)
         if (sp.add(1ull << j)) cols.push_back(1ull << j);

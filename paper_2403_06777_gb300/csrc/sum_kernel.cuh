@@ -33,7 +33,7 @@ using KernelFn = void (*)(const KernelParams, const zw64*, const zw64*, const ui
 extern const KernelFn kTable[3][kMaxWordsNode + 1][kMaxWordsOther];   // kernel.cu
 extern const KernelFn kHist[4][2][kMaxWordsOther];                    // kernel_count.cu (nwn <= 1)
 extern const KernelFn kShared[2][kMaxWordsNode + 1][kMaxWordsOther];  // kernel_count.cu
-extern const KernelFn kLut[3][2][kMaxWordsOther];                              // block lookup
+extern const KernelFn kLut[4][2][kMaxWordsOther];   // block lookup: variants 9, 10, 11, 13
 
 namespace {
 
@@ -55,7 +55,7 @@ __device__ __forceinline__ void publish_result(DevResult* r, uint64_t c0, uint64
 }
 
 template <int NWN, int NWL, int VAR>
-__global__ void __launch_bounds__(kThreads, VAR == 11 ? 2 : (VAR >= 9 ? 5 : (VAR >= 7 ? 3 : 1)))
+__global__ void __launch_bounds__(kThreads, VAR >= 11 ? 2 : (VAR >= 9 ? 5 : (VAR >= 7 ? 3 : 1)))
 sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtable,
            const zw64* __restrict__ gpv, const uint32_t* __restrict__ gR,
            const uint64_t* __restrict__ gADJ, const uint32_t* __restrict__ gS, uint64_t first,
@@ -69,13 +69,13 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
     __shared__ __align__(8) uint64_t s_bar;
     const uint32_t ntab = p.tab_size;
     const Smem sm = carve<NW, HIST>(smem_raw, ntab, p.npairs, k_cap(p.k),
-                                    HIST >= 4 ? lut_cap(p.lut_no + p.lut_nn) : 0u);
+                                    HIST >= 4 ? ((p.lut_entries + 1u) & ~1u) : 0u);
     // the table copies are in flight while the counters are cleared
     if (threadIdx.x == 0) {
         mbar_init(&s_bar);
         issue_tables<NWN, NWL, GENERAL, HIST>(p, sm, gtable, gpv, gR, gADJ, gS, &s_bar);
     }
-    if (HIST == 5) {
+    if (HIST >= 5) {
         // lane-private counters: only rows (J, M) with M < tab_stride are used
         constexpr uint32_t tm = (1u << kLaneRowShift) - 1u, nq = (uint32_t)kLaneCounters * 8u;
         uint4* h4 = reinterpret_cast<uint4*>(sm.sH);

@@ -107,6 +107,24 @@ struct Model {
         return zw_mul(pl.K, v);
     }
 
+    // the lookup slot of lookup bits u, and the lookup's entry for them
+    // (two tables: the first lut_na bits and the rest, entries added)
+    uint32_t slot(uint32_t u) const {
+        const uint32_t na = pl.kp.lut_na;
+        if (!pl.lut_two) return lut_slot(u);
+        return lut_slot(u & ((1u << na) - 1u)) | (lut_slot(u >> na) << na);
+    }
+    uint64_t entry(uint32_t u) const {
+        const uint32_t na = pl.kp.lut_na;
+        if (!pl.lut_two) return pl.lut[lut_slot(u)];
+        return pl.lut[lut_slot(u & ((1u << na) - 1u))] + pl.lut[((size_t)1 << na) + lut_slot(u >> na)];
+    }
+    // the index of the 8 quadratic entries
+    size_t qbase() const {
+        const uint32_t nU = pl.kp.lut_no + pl.kp.lut_nn, na = pl.kp.lut_na;
+        return pl.lut_two ? ((size_t)1 << na) + ((size_t)1 << (nU - na)) : (size_t)1 << nU;
+    }
+
     // the lookup's bits of a state (linear forms, then node forms)
     uint32_t lookup_bits(const Term& t) const {
         const KernelParams& kp = pl.kp;
@@ -163,7 +181,8 @@ void check_step_rows(const Model& m) {
 void check_lookup(const Model& m) {
     const Plan& pl = m.pl;
     const KernelParams& kp = pl.kp;
-    const uint32_t k = m.k, nU = kp.lut_no + kp.lut_nn, ts = kp.tab_stride;
+    const uint32_t k = m.k, ts = kp.tab_stride;
+    CHECK(pl.lut.size() == kp.lut_entries && m.qbase() + 8 == pl.lut.size());
     const uint32_t rw = pl.row_stride, sw = m.nw + 2 * m.nwl;
     // parameter copies of the low variables' step and adjacency rows
     for (uint32_t i = 0; i < 4 && i < k; i++) {
@@ -180,9 +199,9 @@ void check_lookup(const Model& m) {
         // each variable's step row changes the lookup slot by its slot change
         for (uint32_t i = 0; i < k; i++) {
             const Term s1 = m.at(gray(t0) ^ (1ull << i));
-            CHECK((lut_slot(m.lookup_bits(s1)) ^ lut_slot(u)) == (pl.rows[(size_t)i * rw + sw] >> 8));
+            CHECK((m.slot(m.lookup_bits(s1)) ^ m.slot(u)) == (pl.rows[(size_t)i * rw + sw] >> 8));
         }
-        const uint64_t e = pl.lut[lut_slot(u)] + pl.lut[((size_t)1 << nU) + (uint32_t)(s0.ax & 7)];
+        const uint64_t e = m.entry(u) + pl.lut[m.qbase() + (uint32_t)(s0.ax & 7)];
         const Term s7 = m.at(gray(t0 + 7));
         CHECK(((s0.J + (uint32_t)(e >> 56)) & 7) == s7.J);
         for (uint32_t s = 1; s < 8; s++) {
@@ -215,10 +234,11 @@ int main(int argc, char** argv) {
         Plan pl;
         CHECK(build_plan(ps, &pl) == 0);
         const Model m(pl);
-        printf("scalar %s k %u lookup %d lane %d\n", argv[a], m.k, pl.lut_ok ? 1 : 0, pl.lut_lane ? 1 : 0);
+        printf("scalar %s k %u lookup %d lane %d two %d\n", argv[a], m.k, pl.lut_ok ? 1 : 0, pl.lut_lane ? 1 : 0,
+               pl.lut_two ? 1 : 0);
         if (pl.k_inner) {
             // the walk's rules: variables 0-3 never change the cut parities
-            CHECK(pl.kp.zq_lo >= 4 && !pl.lut_ok);
+            CHECK(pl.kp.zq_lo >= 4 && (!pl.lut_ok || pl.lut_lane));
             for (uint32_t i = 0; i < m.k && i < 4; i++) CHECK(pl.zqcol[i] == 0);
             if (m.k <= 12 && pl.inner_bits <= 16) {
                 const std::vector<zw64> F = inner_table(pl);

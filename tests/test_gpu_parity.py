@@ -322,6 +322,49 @@ def test_block_lookup_variant_matches_oracle(ctx):
     assert seen >= 5 and seen10 >= 2 and seen11 >= 2
 
 
+def test_two_table_block_lookup_matches_oracle(ctx):
+    """Scalars with more forms on variables 0-2 than one lookup table takes
+    (few odd nodes, no phase-pair or zero forms) take the two-table block
+    lookup (variant 13): full sums and ragged ranges equal the oracle, a
+    k = 28 sum is split-invariant, and the batch kernel gives the same
+    values."""
+    rng = random.Random(13)
+    seen = []
+    for i in range(40):
+        k = rng.choice([8, 11, 14, 17, 20])
+        ps = zi.synthetic_ps(900 + i, k, n_lin=rng.randint(14, 24), n_quad=rng.randint(0, 6),
+                             n_node=rng.randint(0, 7), odd_nodes_only=True, density=rng.choice([0.2, 0.3]),
+                             e0=rng.randint(0, 5), G=(1, rng.randint(-3, 3), 0, 1))
+        blob = ps.pack()
+        s = Z.zxp_scalar_from_tables(blob)
+        if s.info["kernel_variant"] != 13:
+            continue
+        seen.append(s)
+        N = 1 << k
+        for first, count in [(0, N), (5, N - 11), (N // 3, N // 2), (N - 9, 9), (7, 16)]:
+            g = Z.zxp_eval(ctx, s, first, count)
+            o = oracle.ps_sum(blob, first, count, nthreads=NCPU)
+            assert same_raw(g, o), (i, k, first, count)
+    assert len(seen) >= 10
+    bt = Z.zxp_batch_create(ctx, seen)
+    got = Z.zxp_batch_run(bt)
+    bt.close()
+    for s, g in zip(seen, got):
+        assert tuple(g) == tuple(Z.zxp_eval(ctx, s))
+    ps = zi.synthetic_ps(977, 28, n_lin=22, n_quad=8, n_node=5, odd_nodes_only=True, density=0.25)
+    s = Z.zxp_scalar_from_tables(ps.pack())
+    assert s.info["kernel_variant"] == 13
+    full = Z.zxp_eval(ctx, s)
+    n = 1 << 28
+    parts = Z.zxp_eval(ctx, s, 0, 12345)
+    for a, b in ((12345, n // 3 - 12345), (n // 3, n - n // 3 - 99), (n - 99, 99)):
+        parts = Z.zxp_zomega_add(parts, Z.zxp_eval(ctx, s, a, b))
+    assert Z.zxp_zomega_canon(parts) == Z.zxp_zomega_canon(full)
+    blob = ps.pack()
+    for first in (0, (1 << 27) + 3):
+        assert same_raw(Z.zxp_eval(ctx, s, first, 1 << 16), oracle.ps_sum(blob, first, 1 << 16, nthreads=NCPU))
+
+
 def test_large_compiled_t50_subranges(ctx):
     """n = 50, 2000 gates, T-count 50 (k = 37): seeded 2^20-term sub-ranges
     of the full sum equal the oracle."""

@@ -57,6 +57,12 @@ def scalars():
                                    n_pair=rng.choice([0, 0, 1, 2, 3]),
                                    odd_nodes_only=rng.random() < 0.6,
                                    density=rng.choice([0.1, 0.25, 0.5])).pack())
+    # many forms on the lowest variables, few odd nodes, no phase-pair or
+    # zero forms: block lookups over two tables
+    for i in range(24):
+        out.append(zi.synthetic_ps(4000 + i, rng.randint(8, 16), n_lin=rng.randint(22, 34),
+                                   n_quad=rng.randint(0, 6), n_node=rng.randint(0, 7),
+                                   odd_nodes_only=True, density=rng.choice([0.25, 0.35])).pack())
     return out
 
 
@@ -145,14 +151,15 @@ def test_plan_terms_and_block_lookup(tmp_path):
     lines = r.stdout.split("\n")
     assert lines[-2] == "ok"
     pos = 0
-    n_terms = n_lookup = n_lane = 0
+    n_terms = n_lookup = n_lane = n_two = 0
     for i, blob in enumerate(blobs):
         head = lines[pos].split()
         pos += 1
         assert head[0] == "scalar" and head[1] == paths[i]
-        k, lookup, lane = int(head[3]), int(head[5]), int(head[7])
+        k, lookup, lane, two = int(head[3]), int(head[5]), int(head[7]), int(head[9])
         n_lookup += lookup
         n_lane += lane
+        n_two += two
         if k > 12:
             continue
         G = tuple(c & M64 for c in zi.PSTables.unpack(blob).G)
@@ -162,4 +169,5 @@ def test_plan_terms_and_block_lookup(tmp_path):
             want = zmul(G, tuple(c & M64 for c in oracle.ps_term(blob, x)))
             assert got == want, (i, x, got, want)
             n_terms += 1
-    assert n_terms > 20000 and n_lookup >= 20 and n_lane >= 10 and n_lookup - n_lane >= 3
+    assert n_terms > 20000 and n_lookup >= 20 and n_lane >= 10 and n_lookup - n_lane >= 3 and n_two >= 8, \
+        (n_terms, n_lookup, n_lane, n_two)

@@ -95,7 +95,9 @@ typedef struct {
     uint32_t kernel_variant;     /* 0 table, 1 table + folded bits, 2 general, 3-8 counting
                                     (lane-private 32 / 16 bit, warp-shared; odd: no folded
                                     bits), 9/10 block lookup (10: with folded bits),
-                                    11 block lookup with lane-private counters */
+                                    11 block lookup with lane-private counters, 13 the
+                                    same over two lookup tables; 14/15: 11/13 for a
+                                    scalar with inner parameters */
     uint32_t k_inner;    /* inner parameters, summed inside every term (0: none) */
     uint32_t inner_bits; /* index bits of the inner table: k_inner + crossing forms
                             (2^inner_bits entries of 32 bytes on the device) */
@@ -413,7 +415,9 @@ int zxp_server_create(zxp_ctx *ctx, const zxp_server_opts *opts, zxp_server **ou
  * malformed request (checked again, fully, by the compiler). */
 int zxp_server_submit(zxp_server *srv, const zxp_request *req, uint64_t *ticket);
 /* Queue a compiled scalar (borrowed: it must stay alive until its ticket
- * has been polled to completion). */
+ * has been polled to completion).  ZXP_EINVAL for a scalar with inner
+ * parameters (zxp_scalar_split), which only the single-scalar entry points
+ * evaluate. */
 int zxp_server_submit_scalar(zxp_server *srv, const zxp_scalar *s, uint64_t *ticket);
 /* Queue the binding `bits` of a parametric scalar (borrowed: it must stay
  * alive until the ticket has been polled); a compile worker binds it. */

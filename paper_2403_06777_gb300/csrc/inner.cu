@@ -5,9 +5,12 @@
 //   1. a block evaluates 2^10 consecutive entries u = (x_I, q) of g from the
 //      inner plan, as the sum kernel evaluates one term (form bits by XOR of
 //      flip rows, the phase exponent from the coefficient planes and the
-//      quadratic bit, the node count, K times the table entry, phase-pair
-//      values beyond the folded ones, zero when a zero form is set), keeps
-//      them in shared memory, does the Walsh-Hadamard butterflies of the
+//      quadratic bit, the node count, the table entry -- the inner constant
+//      included -- times phase-pair values beyond the folded ones, zero when
+//      a zero form is set): the state of the block's high bits once, that of
+//      an entry's low bits from the plan's table of them, and the quadratic
+//      bit's cross part as the parity of (A x_high) & x_low; it keeps the
+//      entries in shared memory, does the Walsh-Hadamard butterflies of the
 //      low 10 bits there and writes the tile once;
 //   2. every further pass does up to 8 more bits: a block stages the 2^nb
 //      entries of those bits for 2^(10 - nb) consecutive low indices,
@@ -25,7 +28,7 @@ namespace zxp {
 namespace {
 
 constexpr int kInnerThreads = 256;
-constexpr uint32_t kTileLog2 = 10;
+constexpr uint32_t kTileLog2 = kInnerLowBits;   // the plan tabulates these low bits
 constexpr uint32_t kTile = 1u << kTileLog2;   // 32 KB of shared memory per block
 constexpr uint32_t kHighBits = 8;             // bits of one later pass
 
@@ -47,27 +50,37 @@ __device__ __forceinline__ void butterfly(uint64_t (*t)[kTile], uint32_t n, uint
 
 template <int NW>
 __global__ void __launch_bounds__(kInnerThreads)
-inner_terms_low(const __grid_constant__ KernelParams p, const int nwn, const int general, const zw64 K,
+inner_terms_low(const __grid_constant__ KernelParams p, const int nwn, const int general,
                 const zw64* __restrict__ table, const zw64* __restrict__ pv,
                 const uint32_t* __restrict__ frows, const uint64_t* __restrict__ adj,
-                const uint32_t bits, const uint32_t low_bits, zw64* __restrict__ out) {
+                const uint32_t* __restrict__ low, const uint32_t bits, const uint32_t low_bits,
+                zw64* __restrict__ out) {
     __shared__ uint64_t tile[4][kTile];
     const uint32_t tb = bits < kTileLog2 ? bits : kTileLog2, n = 1u << tb;
     const uint64_t base = (uint64_t)blockIdx.x << tb;
+    // the high bits' state: form bits, A x_high and the quadratic bit
+    uint32_t LB[NW];
+#pragma unroll
+    for (int w = 0; w < NW; w++) LB[w] = p.INV[w];
+    uint64_t AB = 0;
+    uint32_t qb2 = 0;
+    for (uint64_t m = base; m; m &= m - 1) {
+        const uint32_t i = (uint32_t)__ffsll((long long)m) - 1u;
+#pragma unroll
+        for (int w = 0; w < NW; w++) LB[w] ^= __ldg(frows + (size_t)i * NW + w);
+        const uint64_t a = __ldg(adj + i);
+        AB ^= a;
+        qb2 += (uint32_t)__popcll(a & base);
+    }
+    // (every quadratic pair of the high bits was counted from both ends)
+    const uint32_t qb = (qb2 >> 1) & 1u;
+    const uint32_t ab = (uint32_t)AB;
     for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
-        const uint64_t u = base | e;
+        const uint32_t* r = low + (size_t)e * (NW + 1);
         uint32_t L[NW];
 #pragma unroll
-        for (int w = 0; w < NW; w++) L[w] = p.INV[w];
-        uint32_t q2 = 0;
-        for (uint64_t m = u; m; m &= m - 1) {
-            const uint32_t i = (uint32_t)__ffsll((long long)m) - 1u;
-#pragma unroll
-            for (int w = 0; w < NW; w++) L[w] ^= __ldg(frows + (size_t)i * NW + w);
-            q2 += (uint32_t)__popcll(__ldg(adj + i) & u);
-        }
-        // every quadratic pair (i, j) of u was counted from both ends
-        const uint32_t q = (q2 >> 1) & 1u;
+        for (int w = 0; w < NW; w++) L[w] = LB[w] ^ __ldg(r + w);
+        const uint32_t q = qb ^ __ldg(r + NW) ^ ((uint32_t)__popc(ab & e) & 1u);
         uint32_t P0 = 0, P1 = 0, X2 = 0, M = 0, zb = 0;
 #pragma unroll
         for (int w = 0; w < NW; w++) {
@@ -101,7 +114,6 @@ inner_terms_low(const __grid_constant__ KernelParams p, const int nwn, const int
                 idx = (idx << p.xshift) | (L[nwn] & p.pmask) | ((p.has_zero && zb ? 1u : 0u) << p.zshift);
             v = table[idx];
         }
-        v = zw_mul(K, v);
 #pragma unroll
         for (int k = 0; k < 4; k++) tile[k][e] = v.c[k];
     }
@@ -147,31 +159,33 @@ wht_pass(zw64* __restrict__ F, const uint32_t lo, const uint32_t nb, const uint3
 
 template <int NW>
 cudaError_t launch_low(const Plan& in, uint32_t low_bits, const zw64* itab, const zw64* ipv,
-                       const uint32_t* ifr, const uint64_t* iadj, zw64* ftab, cudaStream_t stream) {
+                       const uint32_t* ifr, const uint64_t* iadj, const uint32_t* ilow, zw64* ftab,
+                       cudaStream_t stream) {
     const uint32_t bits = in.kp.k, tb = bits < kTileLog2 ? bits : kTileLog2;
     inner_terms_low<NW><<<(unsigned)(1ull << (bits - tb)), kInnerThreads, 0, stream>>>(
-        in.kp, in.nwn, in.general ? 1 : 0, in.K, itab, ipv, ifr, iadj, bits, low_bits, ftab);
+        in.kp, in.nwn, in.general ? 1 : 0, itab, ipv, ifr, iadj, ilow, bits, low_bits, ftab);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t inner_table_launch(const Plan& inner, uint32_t k_inner, const zw64* itab, const zw64* ipv,
-                               const uint32_t* ifr, const uint64_t* iadj, zw64* ftab, cudaStream_t stream) {
+                               const uint32_t* ifr, const uint64_t* iadj, const uint32_t* ilow, zw64* ftab,
+                               cudaStream_t stream) {
     const uint32_t bits = inner.kp.k;
     if (bits > kMaxInnerBits || k_inner > bits) return cudaErrorInvalidValue;
     const int nw = inner.nwn + (inner.nwl < 1 ? 1 : inner.nwl);
     const uint32_t low = k_inner < kTileLog2 ? k_inner : kTileLog2;
     cudaError_t e;
     switch (nw) {
-    case 1: e = launch_low<1>(inner, low, itab, ipv, ifr, iadj, ftab, stream); break;
-    case 2: e = launch_low<2>(inner, low, itab, ipv, ifr, iadj, ftab, stream); break;
-    case 3: e = launch_low<3>(inner, low, itab, ipv, ifr, iadj, ftab, stream); break;
-    case 4: e = launch_low<4>(inner, low, itab, ipv, ifr, iadj, ftab, stream); break;
-    case 5: e = launch_low<5>(inner, low, itab, ipv, ifr, iadj, ftab, stream); break;
-    case 6: e = launch_low<6>(inner, low, itab, ipv, ifr, iadj, ftab, stream); break;
-    case 7: e = launch_low<7>(inner, low, itab, ipv, ifr, iadj, ftab, stream); break;
-    case 8: e = launch_low<8>(inner, low, itab, ipv, ifr, iadj, ftab, stream); break;
+    case 1: e = launch_low<1>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
+    case 2: e = launch_low<2>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
+    case 3: e = launch_low<3>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
+    case 4: e = launch_low<4>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
+    case 5: e = launch_low<5>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
+    case 6: e = launch_low<6>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
+    case 7: e = launch_low<7>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
+    case 8: e = launch_low<8>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
     default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;

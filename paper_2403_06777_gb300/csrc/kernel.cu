@@ -27,7 +27,7 @@ using namespace sumk;
 KernelFn pick(const Plan& pl) {
     const int nwl = pl.nwl < 1 ? 1 : pl.nwl;
     const int v = variant(pl);
-    if (v >= 9) return kLut[v == 13 ? 3 : v - 9][pl.nwn][nwl - 1];
+    if (v >= 9) return kLut[v >= 13 ? v - 10 : v - 9][pl.nwn][nwl - 1];
     if (v >= 7) return kShared[v - 7][pl.nwn][nwl - 1];
     if (v >= 3) return kHist[v - 3][pl.nwn][nwl - 1];
     return kTable[v][pl.nwn][nwl - 1];

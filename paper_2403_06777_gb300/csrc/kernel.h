@@ -50,10 +50,11 @@ cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, cons
 // The inner table of a scalar with inner parameters (inner.cu): 2^bits
 // entries (bits = inner.kp.k) at ftab, the Walsh-Hadamard transform over the
 // low k_inner bits of the inner product that the plan `inner` describes;
-// its term table, phase-pair values, flip rows and adjacency rows are at
-// itab, ipv, ifr, iadj (device memory).
+// its term table, phase-pair values, flip rows, adjacency rows and low-bit
+// states (Plan::inner_low) are at itab, ipv, ifr, iadj, ilow (device memory).
 cudaError_t inner_table_launch(const Plan& inner, uint32_t k_inner, const zw64* itab, const zw64* ipv,
-                               const uint32_t* ifr, const uint64_t* iadj, zw64* ftab, cudaStream_t stream);
+                               const uint32_t* ifr, const uint64_t* iadj, const uint32_t* ilow, zw64* ftab,
+                               cudaStream_t stream);
 
 // ---- batches (batch.cu) -----------------------------------------------------
 

@@ -104,16 +104,19 @@ inline int kernel_words(const Plan& pl) { return pl.nwn + (pl.nwl < 1 ? 1 : pl.n
 // products), 3/4 lane-private 32-bit counters (+ extra bits), 5/6
 // lane-private 16-bit counters (+ extra), 7/8 warp-shared counters (+ extra),
 // 9/10 block lookup (+ extra), 11 block lookup with lane-private counters,
-// 13 the same with two lookup tables
+// 13 the same with two lookup tables; 14 and 15: 11 and 13 for scalars with
+// inner parameters (their lanes fold at cut flips)
 inline int variant(const Plan& pl) {
     if (pl.general) return 2;
     const int x = pl.kp.xshift ? 1 : 0;
     const int h = hist_mode(pl);
+    if (pl.k_inner && h >= 5) return h == 5 ? 14 : 15;
     return h == 0 ? x : 1 + 2 * h + x;   // block lookup: 9, or 10 with folded bits; 11
 }
 __host__ __device__ constexpr bool var_general(int v) { return v == 2; }
-__host__ __device__ constexpr int var_hist(int v) { return v >= 3 ? (v - 1) / 2 : 0; }
-__host__ __device__ constexpr bool var_xtra(int v) { return v == 1 || (v >= 3 && (v & 1) == 0); }
+__host__ __device__ constexpr int var_hist(int v) { return v >= 14 ? v - 9 : (v >= 3 ? (v - 1) / 2 : 0); }
+__host__ __device__ constexpr bool var_xtra(int v) { return v == 1 || (v >= 3 && v <= 10 && (v & 1) == 0); }
+__host__ __device__ constexpr bool var_outer(int v) { return v >= 14; }
 // 32-bit counter words of one block
 __host__ __device__ constexpr uint32_t counter_words(int h, uint32_t ntab, uint32_t threads) {
     return h == 1 ? ntab * threads
@@ -293,7 +296,7 @@ __device__ __forceinline__ bool load_tables(const KernelParams& p, const Smem& s
 // (counter i of lane l at word i * 32 + l), so the counting atomics of a
 // warp never conflict; a counter index is (J mod 8) * 2^tsh + M, the block's
 // base plus the looked-up offset modulo 8 * 2^tsh.
-template <int NWN, int NWL, bool XTRA, bool LANE, bool TWO>
+template <int NWN, int NWL, bool XTRA, bool LANE, bool TWO, bool OUTER>
 __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, uint64_t first,
                                          uint64_t count, uint64_t span, uint64_t nslices,
                                          uint64_t s_begin, uint64_t stride, bool fold_each,
@@ -320,7 +323,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
     const uint64_t* __restrict__ sLB = sL + (1u << na);
     const uint64_t* __restrict__ qlut = TWO ? sLB + (1u << (no + nn - na)) : sL + (1u << (no + nn));
     // inner parameters (lane-private counters only)
-    const bool outer = LANE && p.zq_lo < 64u;
+    constexpr bool outer = LANE && OUTER;
     constexpr uint32_t tsh = kLaneRowShift, cm = (8u << tsh) - 1u;
     uint32_t* const lbase = sm.sH + warp * ((uint32_t)kLaneCounters * 32u);
     uint32_t* const wl = lbase + lane;
@@ -604,14 +607,14 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
 // final_fold false (counting variants with warp-shared counters, one slice
 // per thread): the counters are left for the caller to fold (see
 // fold_block_counters).
-template <int NWN, int NWL, bool GENERAL, int HIST, bool XTRA>
+template <int NWN, int NWL, bool GENERAL, int HIST, bool XTRA, bool OUTER = false>
 __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint64_t first,
                                      uint64_t count, uint64_t span, uint64_t nslices,
                                      uint64_t s_begin, uint64_t stride, bool fold_each,
                                      bool clear_on_exit, bool final_fold, zw64& acc) {
     if constexpr (HIST >= 4) {
-        walk_lut<NWN, NWL, XTRA, HIST >= 5, HIST == 6>(p, sm, first, count, span, nslices, s_begin, stride,
-                                                       fold_each, clear_on_exit, final_fold, acc);
+        walk_lut<NWN, NWL, XTRA, HIST >= 5, HIST == 6, OUTER>(p, sm, first, count, span, nslices, s_begin,
+                                                              stride, fold_each, clear_on_exit, final_fold, acc);
         return;
     }
     constexpr int NW = NWN + NWL;

@@ -33,6 +33,7 @@ struct DevTables {
     zw64* ipv = nullptr;
     uint32_t* ifr = nullptr;
     uint64_t* iadj = nullptr;
+    uint32_t* ilow = nullptr;
     uint32_t* zq = nullptr;
     zw64* ftab = nullptr;
 };
@@ -40,12 +41,13 @@ struct DevTables {
 // Byte offsets of the tables in one contiguous block:
 // term table | phase-pair values | step rows | adjacency | seek tables,
 // then with inner parameters: inner term table | inner pair values | inner
-// flip rows | inner adjacency | cut columns | inner table.  The first
+// flip rows | inner adjacency | inner low-bit states | cut columns | inner
+// table.  The first
 // `copied` bytes come from the host; the inner table is written on the
 // device.
 struct TableLayout {
     size_t o_pv = 0, o_f = 0, o_adj = 0, o_seek = 0;
-    size_t o_itab = 0, o_ipv = 0, o_ifr = 0, o_iadj = 0, o_zq = 0, o_ftab = 0;
+    size_t o_itab = 0, o_ipv = 0, o_ifr = 0, o_iadj = 0, o_ilow = 0, o_zq = 0, o_ftab = 0;
     size_t copied = 0, total = 0;
 };
 
@@ -69,7 +71,8 @@ inline TableLayout table_layout(const Plan& pl) {
         L.o_ipv = align16(L.o_itab + in.table.size() * sizeof(zw64));
         L.o_ifr = align16(L.o_ipv + in.pv.size() * sizeof(zw64));
         L.o_iadj = align16(L.o_ifr + in.frows.size() * sizeof(uint32_t));
-        L.o_zq = align16(L.o_iadj + in.adj.size() * sizeof(uint64_t));
+        L.o_ilow = align16(L.o_iadj + in.adj.size() * sizeof(uint64_t));
+        L.o_zq = align16(L.o_ilow + pl.inner_low.size() * sizeof(uint32_t));
         L.o_ftab = (L.o_zq + pl.zqcol.size() * sizeof(uint32_t) + 255) & ~(size_t)255;
         L.copied = L.o_ftab;
         L.total = L.o_ftab + (sizeof(zw64) << pl.inner_bits);
@@ -92,6 +95,7 @@ inline void pack_tables(const Plan& pl, const TableLayout& L, unsigned char* dst
         if (!in.pv.empty()) memcpy(dst + L.o_ipv, in.pv.data(), in.pv.size() * sizeof(zw64));
         if (!in.frows.empty()) memcpy(dst + L.o_ifr, in.frows.data(), in.frows.size() * sizeof(uint32_t));
         if (!in.adj.empty()) memcpy(dst + L.o_iadj, in.adj.data(), in.adj.size() * sizeof(uint64_t));
+        memcpy(dst + L.o_ilow, pl.inner_low.data(), pl.inner_low.size() * sizeof(uint32_t));
         memcpy(dst + L.o_zq, pl.zqcol.data(), pl.zqcol.size() * sizeof(uint32_t));
     }
 }
@@ -108,6 +112,7 @@ inline DevTables device_tables(const TableLayout& L, unsigned char* base) {
         d.ipv = reinterpret_cast<zw64*>(base + L.o_ipv);
         d.ifr = reinterpret_cast<uint32_t*>(base + L.o_ifr);
         d.iadj = reinterpret_cast<uint64_t*>(base + L.o_iadj);
+        d.ilow = reinterpret_cast<uint32_t*>(base + L.o_ilow);
         d.zq = reinterpret_cast<uint32_t*>(base + L.o_zq);
         d.ftab = reinterpret_cast<zw64*>(base + L.o_ftab);
     }
@@ -117,7 +122,7 @@ inline DevTables device_tables(const TableLayout& L, unsigned char* base) {
 // Queue the computation of a scalar's inner table (device tables d).
 inline cudaError_t queue_inner_table(const Plan& pl, const DevTables& d, cudaStream_t stream) {
     if (!pl.k_inner || !pl.inner) return cudaSuccess;
-    return inner_table_launch(*pl.inner, pl.k_inner, d.itab, d.ipv, d.ifr, d.iadj, d.ftab, stream);
+    return inner_table_launch(*pl.inner, pl.k_inner, d.itab, d.ipv, d.ifr, d.iadj, d.ilow, d.ftab, stream);
 }
 
 // Descriptor the batch kernel reads for a scalar whose tables are at d.

@@ -569,6 +569,23 @@ int build_split_plan(const PS& ps, Plan* out) {
     auto ip = std::make_shared<Plan>();
     int st = build_plain_plan(inner, false, false, ip.get());
     if (st != ZXP_OK) return st;
+    // the inner constant into the inner table, so that an entry is one
+    // table value (times phase-pair values beyond the folded ones)
+    for (zw64& t : ip->table) t = zw_mul(ip->K, t);
+    ip->K = zw_one();
+    // the low bits' flip-row XOR and quadratic bit, per value
+    const uint32_t tb = bits < kInnerLowBits ? bits : kInnerLowBits;
+    const uint32_t inw = (uint32_t)(ip->nwn + (ip->nwl < 1 ? 1 : ip->nwl));
+    std::vector<uint32_t> low((size_t)(inw + 1) << tb, 0u);
+    for (uint32_t e = 1; e < (1u << tb); e++) {
+        const uint32_t i = (uint32_t)__builtin_ctz(e), ep = e & (e - 1);
+        uint32_t* r = &low[(size_t)e * (inw + 1)];
+        const uint32_t* rp = &low[(size_t)ep * (inw + 1)];
+        for (uint32_t w = 0; w < inw; w++) r[w] = rp[w] ^ ip->frows[(size_t)i * inw + w];
+        // adding variable i (below every bit of ep) flips the quadratic bit
+        // by its pairs with the bits of ep
+        r[inw] = rp[inw] ^ ((uint32_t)__builtin_popcountll(ip->adj[i] & ep) & 1u);
+    }
     Plan pl;
     if ((st = build_plain_plan(outer, true, true, &pl)) != ZXP_OK) return st;
     pl.kp.zq_lo = lo;
@@ -576,6 +593,7 @@ int build_split_plan(const PS& ps, Plan* out) {
     pl.inner_bits = bits;
     pl.zqcol = std::move(zqcol);
     pl.zero = pl.zero || ip->zero;
+    pl.inner_low = std::move(low);
     pl.inner = std::move(ip);
     *out = std::move(pl);
     return ZXP_OK;

@@ -153,7 +153,16 @@ struct Plan {
     uint32_t k_inner = 0, inner_bits = 0;
     std::vector<uint32_t> zqcol;
     std::shared_ptr<const Plan> inner;
+    // The inner plan's state for the low min(inner_bits, 10) bits of u: per
+    // value e, the XOR of their flip rows (inner nw words) and the quadratic
+    // bit of e (one more word); a block of the inner table combines it with
+    // its high bits' state.  (The inner plan's table already includes its
+    // constant K.)
+    std::vector<uint32_t> inner_low;
 };
+
+// Low bits of u tabulated for the inner table (a block's 2^10 entries).
+constexpr uint32_t kInnerLowBits = 10;
 
 // Largest inner table index (inner parameters + crossing forms).
 constexpr uint32_t kMaxInnerBits = 26;

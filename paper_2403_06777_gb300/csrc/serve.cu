@@ -655,6 +655,7 @@ int zxp_server_submit_bind(zxp_server* s, const zxp_pscalar* ps, uint64_t bits, 
 
 int zxp_server_submit_scalar(zxp_server* s, const zxp_scalar* sc, uint64_t* ticket) {
     if (!s || !sc || !ticket) return ZXP_EINVAL;
+    if (sc->ps.k_inner) return ZXP_EINVAL;   // inner parameters: single-scalar path only
     ReqPtr r = std::make_shared<Request>();
     r->scalar = sc;
     r->timing.k = sc->ps.k;

@@ -33,7 +33,7 @@ using KernelFn = void (*)(const KernelParams, const zw64*, const zw64*, const ui
 extern const KernelFn kTable[3][kMaxWordsNode + 1][kMaxWordsOther];   // kernel.cu
 extern const KernelFn kHist[4][2][kMaxWordsOther];                    // kernel_count.cu (nwn <= 1)
 extern const KernelFn kShared[2][kMaxWordsNode + 1][kMaxWordsOther];  // kernel_count.cu
-extern const KernelFn kLut[4][2][kMaxWordsOther];   // block lookup: variants 9, 10, 11, 13
+extern const KernelFn kLut[6][2][kMaxWordsOther];   // block lookup: variants 9, 10, 11, 13, 14, 15
 
 namespace {
 
@@ -97,7 +97,7 @@ sum_kernel(const __grid_constant__ KernelParams p, const zw64* __restrict__ gtab
     // warp-shared counters with one slice per thread: one fold per block
     const bool block_fold = (HIST == 3 || HIST == 4) && !fold_each;
     if (ok)
-        walk<NWN, NWL, GENERAL, HIST, var_xtra(VAR)>(p, sm, first, count, span, nslices,
+        walk<NWN, NWL, GENERAL, HIST, var_xtra(VAR), var_outer(VAR)>(p, sm, first, count, span, nslices,
                                       (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u), gstride,
                                       fold_each, false, !block_fold, acc);
 

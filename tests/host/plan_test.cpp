@@ -239,6 +239,27 @@ int main(int argc, char** argv) {
         if (pl.k_inner) {
             // the walk's rules: variables 0-3 never change the cut parities
             CHECK(pl.kp.zq_lo >= 4 && (!pl.lut_ok || pl.lut_lane));
+            // the inner table's low-bit states: XOR of the flip rows and the
+            // quadratic bit of every low value e
+            {
+                const Plan& in = *pl.inner;
+                const uint32_t inw = (uint32_t)(in.nwn + (in.nwl < 1 ? 1 : in.nwl));
+                const uint32_t tb = pl.inner_bits < kInnerLowBits ? pl.inner_bits : kInnerLowBits;
+                CHECK(pl.inner_low.size() == ((size_t)(inw + 1) << tb));
+                for (uint32_t e = 0; e < (1u << tb); e++) {
+                    uint32_t q = 0;
+                    for (uint32_t w = 0; w < inw; w++) {
+                        uint32_t x = 0;
+                        for (uint32_t i = 0; i < tb; i++)
+                            if ((e >> i) & 1) x ^= in.frows[(size_t)i * inw + w];
+                        CHECK(pl.inner_low[(size_t)e * (inw + 1) + w] == x);
+                    }
+                    for (uint32_t i = 0; i < tb; i++)
+                        for (uint32_t j = i + 1; j < tb; j++)
+                            if (((e >> i) & 1) && ((e >> j) & 1)) q ^= (uint32_t)((in.adj[i] >> j) & 1);
+                    CHECK(pl.inner_low[(size_t)e * (inw + 1) + inw] == q);
+                }
+            }
             for (uint32_t i = 0; i < m.k && i < 4; i++) CHECK(pl.zqcol[i] == 0);
             if (m.k <= 12 && pl.inner_bits <= 16) {
                 const std::vector<zw64> F = inner_table(pl);

@@ -1,22 +1,27 @@
 // inner.cu -- the inner table of a scalar with inner parameters (plan.h):
 //   F[z | q << k_inner] = sum over x_I of g(x_I, q) (-1)^(x_I . z),
 // g the product of the scalar's inner and crossing rows.  Exact in Z[w]
-// modulo 2^64, in passes over the table:
-//   1. a block evaluates 2^10 consecutive entries u = (x_I, q) of g from the
-//      inner plan, as the sum kernel evaluates one term (form bits by XOR of
-//      flip rows, the phase exponent from the coefficient planes and the
-//      quadratic bit, the node count, the table entry -- the inner constant
-//      included -- times phase-pair values beyond the folded ones, zero when
-//      a zero form is set): the state of the block's high bits once, that of
-//      an entry's low bits from the plan's table of them, and the quadratic
-//      bit's cross part as the parity of (A x_high) & x_low; it keeps the
-//      entries in shared memory, does the Walsh-Hadamard butterflies of the
-//      low 10 bits there and writes the tile once;
-//   2. every further pass does up to 8 more bits: a block stages the 2^nb
-//      entries of those bits for 2^(10 - nb) consecutive low indices,
-//      transforms them in shared memory and writes them back.
-// Shared memory holds the four coefficients as separate planes, so that
-// the 8-byte accesses of a warp's consecutive elements hit distinct banks.
+// modulo 2^64, in two kernels:
+//   1. inner_terms_low: a block evaluates 2^10 consecutive entries
+//      u = (x_I, q) of g from the inner plan, as the sum kernel evaluates one
+//      term (form bits by XOR of flip rows, the phase exponent from the
+//      coefficient planes and the quadratic bit, the node count, the table
+//      entry -- the inner constant included -- times phase-pair values beyond
+//      the folded ones, zero when a zero form is set): the state of the
+//      block's high bits once, that of an entry's low bits from the plan's
+//      table of them, and the quadratic bit's cross part as the parity of
+//      (A x_high) & x_low.  It transforms the low 10 bits and writes the tile
+//      once;
+//   2. wht_pass: each further pass transforms up to 10 more bits of tiles of
+//      2^11 entries (2^nb rows of those bits times 2^(11 - nb) consecutive
+//      low indices), read and written once, two tiles per SM so that one
+//      block's loads overlap the other's exchanges.
+// Both transform in radix-4 rounds: a thread holds the four entries that
+// differ in two bits of the tile index in registers and does both butterfly
+// stages there; between rounds the tile is exchanged through shared memory
+// as two planes of 16-byte coefficient pairs, at a swizzled slot that gives
+// every quarter-warp the eight distinct 16-byte bank groups of a 128-byte
+// row in every layout the rounds use.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,134 +32,238 @@
 namespace zxp {
 namespace {
 
-constexpr int kInnerThreads = 256;
+constexpr int kLowThreads = 256;
 constexpr uint32_t kTileLog2 = kInnerLowBits;   // the plan tabulates these low bits
-constexpr uint32_t kTile = 1u << kTileLog2;   // 32 KB of shared memory per block
-constexpr uint32_t kHighBits = 8;             // bits of one later pass
+constexpr uint32_t kTile = 1u << kTileLog2;
+constexpr uint32_t kPassLog2 = 11;              // entries of one wht_pass tile (two blocks per SM)
+constexpr uint32_t kPassBits = 10;              // tile-index bits one pass transforms at most
+constexpr int kPassThreads = 1 << (kPassLog2 - 2);
+constexpr size_t kPassSmem = (size_t)2 << kPassLog2 << 4;   // two 16-byte planes
 
-// one Walsh-Hadamard stage (bit s) over a tile of `rows` rows of `cols`
-// columns held as four coefficient planes (entry (r, c) at r * cols + c)
-__device__ __forceinline__ void butterfly(uint64_t (*t)[kTile], uint32_t n, uint32_t cols_log2, uint32_t s) {
-    for (uint32_t e = threadIdx.x; e < n / 2; e += blockDim.x) {
-        const uint32_t pr = e >> cols_log2, c = e & ((1u << cols_log2) - 1u);
-        const uint32_t r0 = ((pr >> s) << (s + 1)) | (pr & ((1u << s) - 1u));
-        const uint32_t i0 = (r0 << cols_log2) | c, i1 = ((r0 | (1u << s)) << cols_log2) | c;
+static_assert(kTileLog2 == 10, "the low kernel's rounds cover 10 bits");
+
+// shared-memory slot of tile entry e: bits 3 and 4 of e flip slot bits
+// (0, 1) and (1, 2), a linear map, so slot(e ^ d) = slot(e) ^ slot(d)
+__device__ __forceinline__ uint32_t slot(uint32_t e) {
+    return e ^ ((0x5630u >> (((e >> 3) & 3u) << 2)) & 7u);
+}
+
+// tile index of the j-th entry that thread t holds in the round of bits
+// (p, p + 1): j in those bits, t's bits around them
+__device__ __forceinline__ uint32_t spread(uint32_t t, uint32_t p, uint32_t j) {
+    const uint32_t low = (1u << p) - 1u;
+    return (t & low) | (j << p) | ((t & ~low) << 2);
+}
+
+__device__ __forceinline__ void stage(zw64& a, zw64& b) {
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const uint64_t a = t[k][i0], b = t[k][i1];
-            t[k][i0] = a + b;
-            t[k][i1] = a - b;
-        }
+    for (int k = 0; k < 4; k++) {
+        const uint64_t x = a.c[k], y = b.c[k];
+        a.c[k] = x + y;
+        b.c[k] = x - y;
     }
 }
 
+// both stages of a round on the four entries held: bit p (entry pairs that
+// differ in bit 0 of j) when m & 1, bit p + 1 (bit 1 of j) when m & 2
+__device__ __forceinline__ void radix4(zw64 (&v)[4], uint32_t m) {
+    if (m & 1u) {
+        stage(v[0], v[1]);
+        stage(v[2], v[3]);
+    }
+    if (m & 2u) {
+        stage(v[0], v[2]);
+        stage(v[1], v[3]);
+    }
+}
+
+// from the layout of round bits pf to that of round bits pt
+__device__ __forceinline__ void exchange(ulonglong2* s0, ulonglong2* s1, zw64 (&v)[4], uint32_t t,
+                                         uint32_t pf, uint32_t pt) {
+#pragma unroll
+    for (uint32_t j = 0; j < 4; j++) {
+        const uint32_t a = slot(spread(t, pf, j));
+        s0[a] = make_ulonglong2(v[j].c[0], v[j].c[1]);
+        s1[a] = make_ulonglong2(v[j].c[2], v[j].c[3]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (uint32_t j = 0; j < 4; j++) {
+        const uint32_t a = slot(spread(t, pt, j));
+        const ulonglong2 x = s0[a], y = s1[a];
+        v[j] = zw_make(x.x, x.y, y.x, y.y);
+    }
+    __syncthreads();
+}
+
+// stages of the round at bits (p, p + 1) among the first `bits` bits
+__device__ __forceinline__ uint32_t round_mask(uint32_t p, uint32_t bits) {
+    return (p < bits ? 1u : 0u) | (p + 1u < bits ? 2u : 0u);
+}
+
+// 32-byte entries of the table (16-byte aligned: the table starts on 256)
+__device__ __forceinline__ zw64 ld_entry(const zw64* q) {
+    const ulonglong2* g = reinterpret_cast<const ulonglong2*>(q);
+    const ulonglong2 a = g[0], b = g[1];
+    return zw_make(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st_entry(zw64* q, const zw64& v) {
+    ulonglong2* g = reinterpret_cast<ulonglong2*>(q);
+    g[0] = make_ulonglong2(v.c[0], v.c[1]);
+    g[1] = make_ulonglong2(v.c[2], v.c[3]);
+}
+
+// g at entry e of a block whose high bits give form bits LB, quadratic bit
+// qb and the cross row ab
 template <int NW>
-__global__ void __launch_bounds__(kInnerThreads)
+__device__ __forceinline__ zw64 term_value(const KernelParams& p, const int nwn, const int general,
+                                           const zw64* __restrict__ table, const zw64* __restrict__ pv,
+                                           const uint32_t (&LB)[NW], const uint32_t qb, const uint32_t ab,
+                                           const uint32_t* __restrict__ low, const uint32_t e) {
+    const uint32_t* r = low + (size_t)e * (NW + 1);
+    uint32_t L[NW];
+#pragma unroll
+    for (int w = 0; w < NW; w++) L[w] = LB[w] ^ __ldg(r + w);
+    const uint32_t q = qb ^ __ldg(r + NW) ^ ((uint32_t)__popc(ab & e) & 1u);
+    uint32_t P0 = 0, P1 = 0, X2 = 0, M = 0, zb = 0;
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+        if (w < nwn) {
+            X2 ^= L[w] & p.CB[w];
+            M += (uint32_t)__popc(L[w]);
+        } else {
+            const uint32_t v = L[w];
+            P0 += (uint32_t)__popc(v & p.C0[w - nwn]);
+            P1 += (uint32_t)__popc(v & p.C1[w - nwn]);
+            X2 ^= v & p.C2[w - nwn];
+            zb |= v & p.Z[w - nwn];
+        }
+    }
+    const uint32_t J = (P0 + 2u * P1 + 4u * ((uint32_t)__popc(X2) + q)) & 7u;
+    uint32_t idx = J * p.tab_stride + M;
+    if (general) {
+        if (p.has_zero && zb) return zw_zero();
+        zw64 v = ld_entry(table + idx);
+        for (uint32_t j = 0; j < p.npairs; j++) {
+            const uint32_t a = (L[p.PA[j] >> 5] >> (p.PA[j] & 31)) & 1u;
+            const uint32_t b = (L[p.PB[j] >> 5] >> (p.PB[j] & 31)) & 1u;
+            v = zw_mul(v, pv[4 * j + (a | (b << 1))]);
+        }
+        return v;
+    }
+    if (p.xshift)
+        idx = (idx << p.xshift) | (L[nwn] & p.pmask) | ((p.has_zero && zb ? 1u : 0u) << p.zshift);
+    return ld_entry(table + idx);
+}
+
+// The first 2^bits entries of g in tiles of 2^10, the low `low_bits` bits
+// transformed.  Thread t evaluates entries 4t .. 4t + 3, the layout of the
+// first round.
+template <int NW>
+__global__ void __launch_bounds__(kLowThreads)
 inner_terms_low(const __grid_constant__ KernelParams p, const int nwn, const int general,
                 const zw64* __restrict__ table, const zw64* __restrict__ pv,
                 const uint32_t* __restrict__ frows, const uint64_t* __restrict__ adj,
                 const uint32_t* __restrict__ low, const uint32_t bits, const uint32_t low_bits,
                 zw64* __restrict__ out) {
-    __shared__ uint64_t tile[4][kTile];
+    __shared__ ulonglong2 s0[kTile], s1[kTile];
     const uint32_t tb = bits < kTileLog2 ? bits : kTileLog2, n = 1u << tb;
     const uint64_t base = (uint64_t)blockIdx.x << tb;
-    // the high bits' state: form bits, A x_high and the quadratic bit
+    // the high bits' state (form bits, A x_high, the quadratic bit): lane i
+    // takes bit i of the block's first index (bits <= 26 < 32), a warp
+    // reduction adds them up
+    const uint32_t t = threadIdx.x, lane = t & 31u;
+    const bool set = lane < bits && ((base >> lane) & 1u);
     uint32_t LB[NW];
-#pragma unroll
-    for (int w = 0; w < NW; w++) LB[w] = p.INV[w];
     uint64_t AB = 0;
     uint32_t qb2 = 0;
-    for (uint64_t m = base; m; m &= m - 1) {
-        const uint32_t i = (uint32_t)__ffsll((long long)m) - 1u;
 #pragma unroll
-        for (int w = 0; w < NW; w++) LB[w] ^= __ldg(frows + (size_t)i * NW + w);
-        const uint64_t a = __ldg(adj + i);
-        AB ^= a;
-        qb2 += (uint32_t)__popcll(a & base);
+    for (int w = 0; w < NW; w++) LB[w] = set ? __ldg(frows + (size_t)lane * NW + w) : 0u;
+    if (set) {
+        AB = __ldg(adj + lane);
+        qb2 = (uint32_t)__popcll(AB & base);
     }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+#pragma unroll
+        for (int w = 0; w < NW; w++) LB[w] ^= __shfl_xor_sync(0xffffffffu, LB[w], off);
+        AB ^= __shfl_xor_sync(0xffffffffu, AB, off);
+        qb2 += __shfl_xor_sync(0xffffffffu, qb2, off);
+    }
+#pragma unroll
+    for (int w = 0; w < NW; w++) LB[w] ^= p.INV[w];
     // (every quadratic pair of the high bits was counted from both ends)
     const uint32_t qb = (qb2 >> 1) & 1u;
     const uint32_t ab = (uint32_t)AB;
-    for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
-        const uint32_t* r = low + (size_t)e * (NW + 1);
-        uint32_t L[NW];
+    zw64 v[4];
 #pragma unroll
-        for (int w = 0; w < NW; w++) L[w] = LB[w] ^ __ldg(r + w);
-        const uint32_t q = qb ^ __ldg(r + NW) ^ ((uint32_t)__popc(ab & e) & 1u);
-        uint32_t P0 = 0, P1 = 0, X2 = 0, M = 0, zb = 0;
-#pragma unroll
-        for (int w = 0; w < NW; w++) {
-            if (w < nwn) {
-                X2 ^= L[w] & p.CB[w];
-                M += (uint32_t)__popc(L[w]);
-            } else {
-                const uint32_t v = L[w];
-                P0 += (uint32_t)__popc(v & p.C0[w - nwn]);
-                P1 += (uint32_t)__popc(v & p.C1[w - nwn]);
-                X2 ^= v & p.C2[w - nwn];
-                zb |= v & p.Z[w - nwn];
-            }
-        }
-        const uint32_t J = (P0 + 2u * P1 + 4u * ((uint32_t)__popc(X2) + q)) & 7u;
-        uint32_t idx = J * p.tab_stride + M;
-        zw64 v;
-        if (general) {
-            if (p.has_zero && zb) {
-                v = zw_zero();
-            } else {
-                v = table[idx];
-                for (uint32_t j = 0; j < p.npairs; j++) {
-                    const uint32_t a = (L[p.PA[j] >> 5] >> (p.PA[j] & 31)) & 1u;
-                    const uint32_t b = (L[p.PB[j] >> 5] >> (p.PB[j] & 31)) & 1u;
-                    v = zw_mul(v, pv[4 * j + (a | (b << 1))]);
-                }
-            }
-        } else {
-            if (p.xshift)
-                idx = (idx << p.xshift) | (L[nwn] & p.pmask) | ((p.has_zero && zb ? 1u : 0u) << p.zshift);
-            v = table[idx];
-        }
-#pragma unroll
-        for (int k = 0; k < 4; k++) tile[k][e] = v.c[k];
+    for (uint32_t j = 0; j < 4; j++) {
+        const uint32_t e = spread(t, 0, j);
+        v[j] = e < n ? term_value<NW>(p, nwn, general, table, pv, LB, qb, ab, low, e) : zw_zero();
     }
-    __syncthreads();
-    for (uint32_t s = 0; s < low_bits; s++) {
-        butterfly(tile, n, 0, s);
-        __syncthreads();
+    radix4(v, round_mask(0, low_bits));
+    uint32_t pr = 0;
+#pragma unroll
+    for (uint32_t q = 2; q < kTileLog2; q += 2) {
+        if (q < low_bits) {   // (the same for the whole block)
+            exchange(s0, s1, v, t, q - 2, q);
+            pr = q;
+            radix4(v, round_mask(q, low_bits));
+        }
     }
-    for (uint32_t e = threadIdx.x; e < n; e += blockDim.x)
-        out[base | e] = zw_make(tile[0][e], tile[1][e], tile[2][e], tile[3][e]);
+#pragma unroll
+    for (uint32_t j = 0; j < 4; j++) {
+        const uint32_t e = spread(t, pr, j);
+        if (e < n) st_entry(out + (base | e), v[j]);
+    }
 }
 
-// One later pass over bits [lo, lo + nb) of an array of 2^total entries: a
-// block holds the 2^nb entries of those bits for 2^cols_log2 consecutive low
-// indices l (nb + cols_log2 = 10, 2^cols_log2 <= 2^lo).
-__global__ void __launch_bounds__(kInnerThreads)
-wht_pass(zw64* __restrict__ F, const uint32_t lo, const uint32_t nb, const uint32_t cols_log2) {
-    __shared__ uint64_t tile[4][kTile];
-    const uint32_t cols = 1u << cols_log2, n = (1u << nb) * cols;
-    // block -> (high index o, first low index l0)
-    const uint64_t groups_lo = (1ull << lo) >> cols_log2;
-    const uint64_t o = (uint64_t)blockIdx.x / groups_lo;
-    const uint64_t l0 = ((uint64_t)blockIdx.x % groups_lo) << cols_log2;
-    const uint64_t base = (o << (lo + nb)) | l0;
-    for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
-        const uint32_t r = e >> cols_log2, c = e & (cols - 1u);
-        const ulonglong2* g = reinterpret_cast<const ulonglong2*>(F + base + ((uint64_t)r << lo) + c);
-        const ulonglong2 a = g[0], b = g[1];
-        tile[0][e] = a.x; tile[1][e] = a.y; tile[2][e] = b.x; tile[3][e] = b.y;
+// One later pass over bits [lo, lo + NB) of an array of 2^total entries: a
+// block holds the 2^NB entries of those bits for 2^C consecutive low indices
+// l (tile index e = row << C | col, C = 11 - NB <= 10 <= lo).  Rounds at bits
+// C, C + 2, ... of the tile index; for odd NB the last round takes the top
+// two bits and transforms only the top one.
+template <uint32_t NB>
+__global__ void __launch_bounds__(kPassThreads, 2)
+wht_pass(zw64* __restrict__ F, const uint32_t lo) {
+    constexpr uint32_t T = kPassLog2, C = T - NB, NR = (NB + 1) / 2, CM = (1u << C) - 1u;
+    extern __shared__ ulonglong2 sm[];
+    ulonglong2* s0 = sm;
+    ulonglong2* s1 = sm + (1u << T);
+    const uint32_t gl = lo - C;   // log2 of the tiles side by side in the low bits
+    const uint64_t o = (uint64_t)blockIdx.x >> gl;
+    const uint64_t l0 = (uint64_t)(blockIdx.x & ((1u << gl) - 1u)) << C;
+    zw64* const b = F + ((o << (lo + NB)) | l0);
+    const uint32_t t = threadIdx.x;
+    constexpr uint32_t P0 = NB >= 2 ? C : T - 2;
+    zw64 v[4];
+#pragma unroll
+    for (uint32_t j = 0; j < 4; j++) {
+        const uint32_t e = spread(t, P0, j);
+        v[j] = ld_entry(b + ((uint64_t)(e >> C) << lo) + (e & CM));
     }
-    __syncthreads();
-    for (uint32_t s = 0; s < nb; s++) {
-        butterfly(tile, n, cols_log2, s);
-        __syncthreads();
+    uint32_t pr = P0;
+#pragma unroll
+    for (uint32_t r = 0; r < NR; r++) {
+        const bool pair = 2 * r + 1 < NB;
+        const uint32_t q = pair ? C + 2 * r : T - 2;
+        if (r) exchange(s0, s1, v, t, pr, q);
+        pr = q;
+        radix4(v, pair ? 3u : 2u);
     }
-    for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
-        const uint32_t r = e >> cols_log2, c = e & (cols - 1u);
-        ulonglong2* g = reinterpret_cast<ulonglong2*>(F + base + ((uint64_t)r << lo) + c);
-        g[0] = make_ulonglong2(tile[0][e], tile[1][e]);
-        g[1] = make_ulonglong2(tile[2][e], tile[3][e]);
+#pragma unroll
+    for (uint32_t j = 0; j < 4; j++) {
+        const uint32_t e = spread(t, pr, j);
+        st_entry(b + ((uint64_t)(e >> C) << lo) + (e & CM), v[j]);
     }
+}
+
+template <uint32_t NB>
+cudaError_t launch_pass(zw64* ftab, uint32_t lo, uint32_t bits, cudaStream_t stream) {
+    cudaError_t e = cudaFuncSetAttribute(wht_pass<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
+    if (e != cudaSuccess) return e;
+    wht_pass<NB><<<(unsigned)((1ull << bits) >> kPassLog2), kPassThreads, kPassSmem, stream>>>(ftab, lo);
+    return cudaGetLastError();
 }
 
 template <int NW>
@@ -162,7 +271,7 @@ cudaError_t launch_low(const Plan& in, uint32_t low_bits, const zw64* itab, cons
                        const uint32_t* ifr, const uint64_t* iadj, const uint32_t* ilow, zw64* ftab,
                        cudaStream_t stream) {
     const uint32_t bits = in.kp.k, tb = bits < kTileLog2 ? bits : kTileLog2;
-    inner_terms_low<NW><<<(unsigned)(1ull << (bits - tb)), kInnerThreads, 0, stream>>>(
+    inner_terms_low<NW><<<(unsigned)(1ull << (bits - tb)), kLowThreads, 0, stream>>>(
         in.kp, in.nwn, in.general ? 1 : 0, itab, ipv, ifr, iadj, ilow, bits, low_bits, ftab);
     return cudaGetLastError();
 }
@@ -189,15 +298,25 @@ cudaError_t inner_table_launch(const Plan& inner, uint32_t k_inner, const zw64* 
     default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
-    // the remaining inner bits in passes of at most kHighBits, split evenly
+    // the remaining inner bits in passes of at most kPassBits, split evenly
+    // (every pass starts at lo >= 10)
     const uint32_t rem = k_inner - low;
-    if (!rem) return cudaSuccess;
-    const uint32_t passes = (rem + kHighBits - 1) / kHighBits;
+    const uint32_t passes = (rem + kPassBits - 1) / kPassBits;
     for (uint32_t lo = low, left = rem, p = passes; left; p--) {
-        const uint32_t nb = (left + p - 1) / p, cols_log2 = kTileLog2 - nb;
-        const uint64_t blocks = (1ull << bits) >> kTileLog2;
-        wht_pass<<<(unsigned)blocks, kInnerThreads, 0, stream>>>(ftab, lo, nb, cols_log2);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const uint32_t nb = (left + p - 1) / p;
+        switch (nb) {
+        case 1: e = launch_pass<1>(ftab, lo, bits, stream); break;
+        case 2: e = launch_pass<2>(ftab, lo, bits, stream); break;
+        case 3: e = launch_pass<3>(ftab, lo, bits, stream); break;
+        case 4: e = launch_pass<4>(ftab, lo, bits, stream); break;
+        case 5: e = launch_pass<5>(ftab, lo, bits, stream); break;
+        case 6: e = launch_pass<6>(ftab, lo, bits, stream); break;
+        case 7: e = launch_pass<7>(ftab, lo, bits, stream); break;
+        case 8: e = launch_pass<8>(ftab, lo, bits, stream); break;
+        case 9: e = launch_pass<9>(ftab, lo, bits, stream); break;
+        default: e = launch_pass<10>(ftab, lo, bits, stream); break;
+        }
+        if (e != cudaSuccess) return e;
         lo += nb;
         left -= nb;
     }

@@ -42,7 +42,9 @@ typedef enum {
     ZXP_EINVAL = -1,     /* bad argument: qubit, opcode, range beyond 2^k, blob */
     ZXP_ENOMEM = -2,     /* host or device allocation failed */
     ZXP_ETOOBIG = -3,    /* k > 62 or a table exceeds the kernel's limits */
-    ZXP_EOVERFLOW = -4,  /* exponent e too large for exact 64-bit numerators */
+    ZXP_EOVERFLOW = -4,  /* exponent e too large for exact numerators (64-bit
+                            results: e > 124 and the value needs more; 128-bit:
+                            e > 252) */
     ZXP_ECUDA = -5,      /* a CUDA runtime error (no device, launch failure) */
     ZXP_ETIMEDOUT = -6,  /* a wait budget expired */
     ZXP_EAGAIN = -7,     /* zxp_poll: not finished yet */
@@ -58,6 +60,16 @@ typedef struct zxp_zomega {
     int32_t e;
     int32_t flags;
 } zxp_zomega;
+
+/* The same with 128-bit coefficients: coefficient j is the two's-complement
+ * integer hi[j] * 2^64 + (uint64_t)c[j].  Exact sums of scalars with
+ * 124 < e <= 252 (zxp_eval_wide). */
+typedef struct zxp_zomega_wide {
+    int64_t c[4];
+    int64_t hi[4];
+    int32_t e;
+    int32_t flags;
+} zxp_zomega_wide;
 
 typedef enum {
     ZXP_H = 0, ZXP_S = 1, ZXP_T = 2, ZXP_CNOT = 3, ZXP_SDG = 4, ZXP_TDG = 5,
@@ -86,7 +98,9 @@ typedef struct {
     uint32_t n_node;     /* node rows (1 + e^{i Psi}) */
     uint32_t n_pair;     /* phase-pair rows (Eq. 3) */
     int32_t e0;          /* sqrt2 exponent of the denominator */
-    uint32_t acc_bits;   /* 64: int64 numerators are provably exact */
+    uint32_t acc_bits;   /* 64: int64 numerators are provably exact (e0 <= 124);
+                            128: zxp_amplitude sums modulo 2^128 (e0 <= 252);
+                            0: no exact bound (e0 > 252) */
     uint32_t form_bits;  /* parity forms the kernel tracks per term */
     uint32_t t_count;    /* T-like gates in the input (0 for tables) */
     uint32_t node_words; /* 32-bit words of odd-node form bits per term */
@@ -246,9 +260,30 @@ int zxp_eval_device(zxp_ctx *ctx, const zxp_scalar *s, uint64_t first, uint64_t 
 int zxp_eval_noalloc(const zxp_scalar *s, uint64_t first, uint64_t count,
                      zxp_zomega *dev_out, void *cuda_stream);
 
-/* The whole sum over [0, 2^k), canonical.  Errors as zxp_eval, plus
- * ZXP_EOVERFLOW when e0 > 124 (64-bit numerators not provably exact). */
+/* The whole sum over [0, 2^k), canonical (the exact value of Eq. 2; for a
+ * circuit amplitude N / sqrt2^e0 every |N_j| <= 2^(e0/2)).  e0 <= 124: summed
+ * with 64-bit coefficients; 124 < e0 <= 252: summed modulo 2^128
+ * (zxp_amplitude_wide) and returned when the canonical coefficients fit 64
+ * bits.  Errors as zxp_eval, plus ZXP_EOVERFLOW when e0 > 252 (`out` then
+ * holds the canonical form of the 64-bit sum, exact only if the true
+ * numerator fits) or when the canonical value needs more than 64 bits (use
+ * zxp_amplitude_wide). */
 int zxp_amplitude(zxp_ctx *ctx, const zxp_scalar *s, zxp_zomega *out);
+
+/* zxp_eval modulo 2^128 (any e0): the raw partial of [first, first + count)
+ * with 128-bit coefficients, flags bit 0 set.  Each term is evaluated on its
+ * own (the general per-term walk) from 128-bit tables that the first call
+ * on a device uploads next to the 64-bit ones (with inner parameters also a
+ * 128-bit inner table, 64 bytes per entry); they stay resident until the
+ * scalar is freed.  Synchronous on the context's stream.  Errors as
+ * zxp_eval. */
+int zxp_eval_wide(zxp_ctx *ctx, const zxp_scalar *s, uint64_t first, uint64_t count,
+                  zxp_zomega_wide *out);
+
+/* The whole sum modulo 2^128, canonical: exact for e0 <= 252 (the
+ * numerator's coefficients are below 2^126 in magnitude).  ZXP_EOVERFLOW
+ * when e0 > 252 (`out` then holds the canonical form of the 128-bit sum). */
+int zxp_amplitude_wide(zxp_ctx *ctx, const zxp_scalar *s, zxp_zomega_wide *out);
 
 /* Asynchronous form of zxp_eval: queue the range on the context's stream
  * and return a ticket.  The scalar must stay alive until the ticket is
@@ -427,6 +462,8 @@ int zxp_server_submit_bind(zxp_server *srv, const zxp_pscalar *ps, uint64_t bits
  * ZXP_EAGAIN while the request runs, ZXP_ENOTFOUND for an unknown ticket;
  * otherwise the request's own status (ZXP_OK: *out holds the canonical
  * value; ZXP_EOVERFLOW: as zxp_amplitude), and the ticket is released.
+ * (A request with 124 < e0 <= 252 is summed again modulo 2^128 when its
+ * step ends, synchronously on the server's stream, as zxp_amplitude does.)
  * out and timing may be NULL. */
 int zxp_server_poll(zxp_server *srv, uint64_t ticket, int64_t timeout_us, zxp_zomega *out,
                     zxp_request_timing *timing);

@@ -37,6 +37,18 @@ class zxp_zomega(C.Structure):
         return (self.c[0], self.c[1], self.c[2], self.c[3], self.e)
 
 
+class zxp_zomega_wide(C.Structure):
+    _fields_ = [("c", C.c_int64 * 4), ("hi", C.c_int64 * 4), ("e", C.c_int32), ("flags", C.c_int32)]
+
+    def tup(self) -> Tuple[int, int, int, int, int]:
+        """(c0, c1, c2, c3, e), each coefficient the signed 128-bit integer."""
+        v = []
+        for i in range(4):
+            x = ((self.hi[i] & ((1 << 64) - 1)) << 64) | (self.c[i] & ((1 << 64) - 1))
+            v.append(x - (1 << 128) if x >> 127 else x)
+        return (v[0], v[1], v[2], v[3], self.e)
+
+
 class zxp_scalar_info_t(C.Structure):
     _fields_ = [("k", C.c_uint32), ("n_lin", C.c_uint32), ("n_quad", C.c_uint32),
                 ("n_node", C.c_uint32), ("n_pair", C.c_uint32), ("e0", C.c_int32),
@@ -124,6 +136,8 @@ def lib():
         L.zxp_inner_sum.argtypes = [vp, vp]
         L.zxp_eval.argtypes = [vp, vp, u64, u64, zp]
         L.zxp_amplitude.argtypes = [vp, vp, zp]
+        L.zxp_eval_wide.argtypes = [vp, vp, u64, u64, C.POINTER(zxp_zomega_wide)]
+        L.zxp_amplitude_wide.argtypes = [vp, vp, C.POINTER(zxp_zomega_wide)]
         L.zxp_eval_device.argtypes = [vp, vp, u64, u64, vp]
         L.zxp_eval_noalloc.argtypes = [vp, u64, u64, vp, vp]
         L.zxp_submit.argtypes = [vp, vp, u64, u64, C.POINTER(u64)]
@@ -426,6 +440,22 @@ def zxp_amplitude(ctx: Ctx, s: Scalar):
     """The whole sum, canonical (c0, c1, c2, c3, e)."""
     out = zxp_zomega()
     _check(lib().zxp_amplitude(ctx.handle, s.handle, C.byref(out)), "zxp_amplitude")
+    return out.tup()
+
+
+def zxp_eval_wide(ctx: Ctx, s: Scalar, first: int = 0, count: int | None = None):
+    """Raw partial modulo 2^128: (c0, c1, c2, c3, e0), signed 128-bit ints."""
+    if count is None:
+        count = (1 << zxp_scalar_info(s)["k"]) - first
+    out = zxp_zomega_wide()
+    _check(lib().zxp_eval_wide(ctx.handle, s.handle, first, count, C.byref(out)), "zxp_eval_wide")
+    return out.tup()
+
+
+def zxp_amplitude_wide(ctx: Ctx, s: Scalar):
+    """The whole sum modulo 2^128, canonical (exact for e0 <= 252)."""
+    out = zxp_zomega_wide()
+    _check(lib().zxp_amplitude_wide(ctx.handle, s.handle, C.byref(out)), "zxp_amplitude_wide")
     return out.tup()
 
 

@@ -138,6 +138,42 @@ int ensure_device_tables(const zxp_scalar* s, zxp_ctx* ctx, DevTables* out, uint
     return ZXP_OK;
 }
 
+// The 128-bit values of `s` on ctx's device (DevWide), uploaded on first use
+// in the order of ctx's stream, after the 64-bit tables `d` (whose rows and
+// low-bit states the 128-bit inner table reads); the inner table is then
+// computed on the device.
+int ensure_wide_tables(const zxp_scalar* s, zxp_ctx* ctx, const DevTables& d, DevWide* out) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->devw.find(ctx->device);
+    if (it != s->devw.end()) {
+        *out = it->second;
+        return ZXP_OK;
+    }
+    const WideLayout L = wide_layout(s->plan);
+    std::vector<unsigned char> host(L.copied ? L.copied : 16, 0);
+    pack_wide(s->plan, L, host.data());
+    void* base = nullptr;
+    if (cudaMalloc(&base, L.total) != cudaSuccess) return ZXP_ENOMEM;
+    // (pageable source: the stream is synchronised before `host` goes away)
+    if ((L.copied && cudaMemcpyAsync(base, host.data(), L.copied, cudaMemcpyHostToDevice, ctx->stream) !=
+                         cudaSuccess) ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        cudaFree(base);
+        return ZXP_ECUDA;
+    }
+    DevWide w = device_wide(L, static_cast<unsigned char*>(base));
+    if (s->plan.k_inner && s->plan.inner &&
+        inner_table_launch_wide(*s->plan.inner, s->plan.k_inner, w.itab, w.ipv, d.ifr, d.iadj, d.ilow, w.ftab,
+                                ctx->stream) != cudaSuccess) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(base);
+        return ZXP_ECUDA;
+    }
+    s->devw[ctx->device] = w;
+    *out = w;
+    return ZXP_OK;
+}
+
 // Wait until a kernel has published its result into pinned memory `h`
 // (flags != 0, stored after the value with release semantics; the caller
 // zeroes flags before the launch).  Spins on the flags word; every 20 us it
@@ -234,6 +270,11 @@ zxp_scalar::~zxp_scalar() {
             cudaFreeAsync(p, 0);
         }
     }
+    for (auto& e : devw) {
+        cudaSetDevice(e.first);
+        cudaDeviceSynchronize();
+        cudaFree(e.second.base);
+    }
     if (prev >= 0) cudaSetDevice(prev);
 }
 
@@ -286,9 +327,11 @@ int zxp_ctx_create(int device, void* cuda_stream, zxp_ctx** out) {
         c->own_stream = true;
     }
     if (cudaStreamCreateWithFlags(&c->upload, cudaStreamNonBlocking) != cudaSuccess) return ZXP_ECUDA;
-    // the sum kernel's accumulator starts at zero
-    if (cudaMalloc(&c->acc, sizeof(zw64)) != cudaSuccess) return ZXP_ENOMEM;
-    if (cudaMemset(c->acc, 0, sizeof(zw64)) != cudaSuccess) return ZXP_ECUDA;
+    // the sum kernels' accumulator starts at zero (64 bytes: the 128-bit
+    // sum uses all of it, the 64-bit one the first half)
+    if (cudaMalloc(&c->acc, 2 * sizeof(zw64)) != cudaSuccess) return ZXP_ENOMEM;
+    if (cudaMemset(c->acc, 0, 2 * sizeof(zw64)) != cudaSuccess) return ZXP_ECUDA;
+    if (cudaMalloc(&c->wres, sizeof(DevResultW)) != cudaSuccess) return ZXP_ENOMEM;
     if (cudaMalloc(&c->counter, sizeof(unsigned int)) != cudaSuccess) return ZXP_ENOMEM;
     if (cudaMemset(c->counter, 0, sizeof(unsigned int)) != cudaSuccess) return ZXP_ECUDA;
     if (cudaMallocHost(&c->hres, sizeof(DevResult)) != cudaSuccess) return ZXP_ENOMEM;
@@ -324,6 +367,7 @@ void zxp_ctx_destroy(zxp_ctx* c) {
         if (c->stage_ev[i]) cudaEventDestroy(c->stage_ev[i]);
     }
     cudaFree(c->acc);
+    cudaFree(c->wres);
     cudaFree(c->counter);
     cudaFreeHost(c->hres);
     if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -469,7 +513,7 @@ int zxp_scalar_info(const zxp_scalar* s, zxp_scalar_info_t* info) {
     info->n_node = (uint32_t)s->ps.node.size();
     info->n_pair = (uint32_t)s->ps.pair.size();
     info->e0 = s->ps.e0;
-    info->acc_bits = s->ps.e0 <= 124 ? 64 : 128;
+    info->acc_bits = s->ps.e0 <= 124 ? 64 : (s->ps.e0 <= 252 ? 128 : 0);
     info->form_bits = s->plan.kp.nbits;
     info->t_count = s->ps.t_count;
     info->node_words = (uint32_t)s->plan.nwn;
@@ -520,12 +564,71 @@ int zxp_zomega_canon(const zxp_zomega* in, zxp_zomega* out) {
 }
 
 int zxp_amplitude(zxp_ctx* ctx, const zxp_scalar* s, zxp_zomega* out) {
-    if (!s) return ZXP_EINVAL;
+    if (!s || !out) return ZXP_EINVAL;
+    if (s->ps.e0 > 124 && s->ps.e0 <= 252) {
+        // modulo 2^128, then back to 64-bit words if the canonical value fits
+        zxp_zomega_wide w;
+        const int st = zxp_amplitude_wide(ctx, s, &w);
+        if (st != ZXP_OK) return st;
+        bool fits = true;
+        for (int i = 0; i < 4; i++) {
+            out->c[i] = w.c[i];
+            fits = fits && w.hi[i] == (w.c[i] < 0 ? -1 : 0);
+        }
+        out->e = w.e;
+        out->flags = 0;
+        return fits ? ZXP_OK : ZXP_EOVERFLOW;
+    }
     zxp_zomega raw;
     int st = zxp_eval(ctx, s, 0, term_count(s), &raw);
     if (st != ZXP_OK) return st;
     zxp_zomega_canon(&raw, out);
-    return s->ps.e0 > 124 ? ZXP_EOVERFLOW : ZXP_OK;
+    return s->ps.e0 > 252 ? ZXP_EOVERFLOW : ZXP_OK;
+}
+
+int zxp_eval_wide(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, zxp_zomega_wide* out) {
+    if (!ctx || !s || !out) return ZXP_EINVAL;
+    int st = check_range(s, first, count);
+    if (st != ZXP_OK) return st;
+    memset(out, 0, sizeof *out);
+    out->e = s->ps.e0;
+    out->flags = 1;
+    if (count == 0 || s->plan.zero) return ZXP_OK;
+    DeviceGuard g(ctx->device);
+    DevTables d;
+    const uint64_t seq = ++ctx->enq_seq;
+    if ((st = ensure_device_tables(s, ctx, &d, seq)) != ZXP_OK) return st;
+    DevWide w;
+    if ((st = ensure_wide_tables(s, ctx, d, &w)) != ZXP_OK) return st;
+    const cudaError_t e = sum_launch_wide(s->plan, w.table, w.pv, d.rows, d.adj, d.seek, d.zq, w.ftab, first, count,
+                                          ctx->sm_count, reinterpret_cast<uint64_t*>(ctx->acc), ctx->counter,
+                                          ctx->wres, ctx->stream);
+    if (e != cudaSuccess) return ZXP_ECUDA;
+    DevResultW r;
+    if (cudaMemcpyAsync(&r, ctx->wres, sizeof r, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+        return ZXP_ECUDA;
+    if (seq > ctx->done_seq) ctx->done_seq = seq;
+    static_assert(sizeof(DevResultW) == sizeof(zxp_zomega_wide), "result record layout");
+    memcpy(out, &r, sizeof r);
+    return (out->flags & 2) ? ZXP_ETIMEDOUT : ZXP_OK;
+}
+
+int zxp_amplitude_wide(zxp_ctx* ctx, const zxp_scalar* s, zxp_zomega_wide* out) {
+    if (!s || !out) return ZXP_EINVAL;
+    const int st = zxp_eval_wide(ctx, s, 0, term_count(s), out);
+    if (st != ZXP_OK) return st;
+    __int128 c[4];
+    for (int i = 0; i < 4; i++) c[i] = (__int128)(((u128)(uint64_t)out->hi[i] << 64) | (u128)(uint64_t)out->c[i]);
+    int32_t e = out->e;
+    canon_i128(c, &e);
+    for (int i = 0; i < 4; i++) {
+        out->c[i] = (int64_t)(uint64_t)(u128)c[i];
+        out->hi[i] = (int64_t)(uint64_t)((u128)c[i] >> 64);
+    }
+    out->e = e;
+    out->flags = 0;
+    return s->ps.e0 > 252 ? ZXP_EOVERFLOW : ZXP_OK;
 }
 
 int zxp_submit(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t count, uint64_t* ticket) {

@@ -1,7 +1,8 @@
 // inner.cu -- the inner table of a scalar with inner parameters (plan.h):
 //   F[z | q << k_inner] = sum over x_I of g(x_I, q) (-1)^(x_I . z),
 // g the product of the scalar's inner and crossing rows.  Exact in Z[w]
-// modulo 2^64, in two kernels:
+// modulo 2^64 (or 2^128: the same kernels on 64-byte entries), in two
+// kernels:
 //   1. inner_terms_low: a block evaluates 2^10 consecutive entries
 //      u = (x_I, q) of g from the inner plan, as the sum kernel evaluates one
 //      term (form bits by XOR of flip rows, the phase exponent from the
@@ -13,13 +14,14 @@
 //      (A x_high) & x_low.  It transforms the low 10 bits and writes the tile
 //      once;
 //   2. wht_pass: each further pass transforms up to 10 more bits of tiles of
-//      2^11 entries (2^nb rows of those bits times 2^(11 - nb) consecutive
-//      low indices), read and written once, two tiles per SM so that one
-//      block's loads overlap the other's exchanges.
+//      2^T entries (2^nb rows of those bits times 2^(T - nb) consecutive
+//      low indices; T = 11, or 10 for 64-byte entries), read and written
+//      once, two tiles per SM so that one block's loads overlap the other's
+//      exchanges.
 // Both transform in radix-4 rounds: a thread holds the four entries that
 // differ in two bits of the tile index in registers and does both butterfly
 // stages there; between rounds the tile is exchanged through shared memory
-// as two planes of 16-byte coefficient pairs, at a swizzled slot that gives
+// as planes of 16-byte words (two or four per entry), at a swizzled slot that gives
 // every quarter-warp the eight distinct 16-byte bank groups of a 128-byte
 // row in every layout the rounds use.
 #include <cuda_runtime.h>
@@ -35,10 +37,35 @@ namespace {
 constexpr int kLowThreads = 256;
 constexpr uint32_t kTileLog2 = kInnerLowBits;   // the plan tabulates these low bits
 constexpr uint32_t kTile = 1u << kTileLog2;
-constexpr uint32_t kPassLog2 = 11;              // entries of one wht_pass tile (two blocks per SM)
 constexpr uint32_t kPassBits = 10;              // tile-index bits one pass transforms at most
-constexpr int kPassThreads = 1 << (kPassLog2 - 2);
-constexpr size_t kPassSmem = (size_t)2 << kPassLog2 << 4;   // two 16-byte planes
+
+// An entry as 16-byte planes: zw64 in two (c0 c1 | c2 c3), zw128 in four
+// (one coefficient each, low word first).
+template <class Z>
+struct Planes;
+template <>
+struct Planes<zw64> {
+    static constexpr int N = 2;
+    __device__ static ulonglong2 get(const zw64& v, int k) { return make_ulonglong2(v.c[2 * k], v.c[2 * k + 1]); }
+    __device__ static void set(zw64& v, int k, ulonglong2 x) {
+        v.c[2 * k] = x.x;
+        v.c[2 * k + 1] = x.y;
+    }
+};
+template <>
+struct Planes<zw128> {
+    static constexpr int N = 4;
+    __device__ static ulonglong2 get(const zw128& v, int k) {
+        return make_ulonglong2((unsigned long long)v.c[k], (unsigned long long)(v.c[k] >> 64));
+    }
+    __device__ static void set(zw128& v, int k, ulonglong2 x) { v.c[k] = ((u128)x.y << 64) | (u128)x.x; }
+};
+// log2 of the entries of one wht_pass tile: 64 KB of shared memory, two
+// blocks per SM
+template <class Z>
+__host__ __device__ constexpr uint32_t pass_log2() { return Planes<Z>::N == 2 ? 11u : 10u; }
+template <class Z>
+__host__ __device__ constexpr size_t pass_smem() { return (size_t)Planes<Z>::N << pass_log2<Z>() << 4; }
 
 static_assert(kTileLog2 == 10, "the low kernel's rounds cover 10 bits");
 
@@ -55,10 +82,11 @@ __device__ __forceinline__ uint32_t spread(uint32_t t, uint32_t p, uint32_t j) {
     return (t & low) | (j << p) | ((t & ~low) << 2);
 }
 
-__device__ __forceinline__ void stage(zw64& a, zw64& b) {
+template <class Z>
+__device__ __forceinline__ void stage(Z& a, Z& b) {
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-        const uint64_t x = a.c[k], y = b.c[k];
+        const auto x = a.c[k], y = b.c[k];
         a.c[k] = x + y;
         b.c[k] = x - y;
     }
@@ -66,7 +94,8 @@ __device__ __forceinline__ void stage(zw64& a, zw64& b) {
 
 // both stages of a round on the four entries held: bit p (entry pairs that
 // differ in bit 0 of j) when m & 1, bit p + 1 (bit 1 of j) when m & 2
-__device__ __forceinline__ void radix4(zw64 (&v)[4], uint32_t m) {
+template <class Z>
+__device__ __forceinline__ void radix4(Z (&v)[4], uint32_t m) {
     if (m & 1u) {
         stage(v[0], v[1]);
         stage(v[2], v[3]);
@@ -77,21 +106,23 @@ __device__ __forceinline__ void radix4(zw64 (&v)[4], uint32_t m) {
     }
 }
 
-// from the layout of round bits pf to that of round bits pt
-__device__ __forceinline__ void exchange(ulonglong2* s0, ulonglong2* s1, zw64 (&v)[4], uint32_t t,
-                                         uint32_t pf, uint32_t pt) {
+// from the layout of round bits pf to that of round bits pt (plane k of
+// the tile at sm + k * ps)
+template <class Z>
+__device__ __forceinline__ void exchange(ulonglong2* sm, uint32_t ps, Z (&v)[4], uint32_t t, uint32_t pf,
+                                         uint32_t pt) {
 #pragma unroll
     for (uint32_t j = 0; j < 4; j++) {
         const uint32_t a = slot(spread(t, pf, j));
-        s0[a] = make_ulonglong2(v[j].c[0], v[j].c[1]);
-        s1[a] = make_ulonglong2(v[j].c[2], v[j].c[3]);
+#pragma unroll
+        for (int k = 0; k < Planes<Z>::N; k++) sm[k * ps + a] = Planes<Z>::get(v[j], k);
     }
     __syncthreads();
 #pragma unroll
     for (uint32_t j = 0; j < 4; j++) {
         const uint32_t a = slot(spread(t, pt, j));
-        const ulonglong2 x = s0[a], y = s1[a];
-        v[j] = zw_make(x.x, x.y, y.x, y.y);
+#pragma unroll
+        for (int k = 0; k < Planes<Z>::N; k++) Planes<Z>::set(v[j], k, sm[k * ps + a]);
     }
     __syncthreads();
 }
@@ -101,23 +132,27 @@ __device__ __forceinline__ uint32_t round_mask(uint32_t p, uint32_t bits) {
     return (p < bits ? 1u : 0u) | (p + 1u < bits ? 2u : 0u);
 }
 
-// 32-byte entries of the table (16-byte aligned: the table starts on 256)
-__device__ __forceinline__ zw64 ld_entry(const zw64* q) {
+// entries of the table (16-byte aligned: the table starts on 256)
+template <class Z>
+__device__ __forceinline__ Z ld_entry(const Z* q) {
     const ulonglong2* g = reinterpret_cast<const ulonglong2*>(q);
-    const ulonglong2 a = g[0], b = g[1];
-    return zw_make(a.x, a.y, b.x, b.y);
+    Z v;
+#pragma unroll
+    for (int k = 0; k < Planes<Z>::N; k++) Planes<Z>::set(v, k, g[k]);
+    return v;
 }
-__device__ __forceinline__ void st_entry(zw64* q, const zw64& v) {
+template <class Z>
+__device__ __forceinline__ void st_entry(Z* q, const Z& v) {
     ulonglong2* g = reinterpret_cast<ulonglong2*>(q);
-    g[0] = make_ulonglong2(v.c[0], v.c[1]);
-    g[1] = make_ulonglong2(v.c[2], v.c[3]);
+#pragma unroll
+    for (int k = 0; k < Planes<Z>::N; k++) g[k] = Planes<Z>::get(v, k);
 }
 
 // g at entry e of a block whose high bits give form bits LB, quadratic bit
 // qb and the cross row ab
-template <int NW>
-__device__ __forceinline__ zw64 term_value(const KernelParams& p, const int nwn, const int general,
-                                           const zw64* __restrict__ table, const zw64* __restrict__ pv,
+template <int NW, class Z>
+__device__ __forceinline__ Z term_value(const KernelParams& p, const int nwn, const int general,
+                                        const Z* __restrict__ table, const Z* __restrict__ pv,
                                            const uint32_t (&LB)[NW], const uint32_t qb, const uint32_t ab,
                                            const uint32_t* __restrict__ low, const uint32_t e) {
     const uint32_t* r = low + (size_t)e * (NW + 1);
@@ -142,8 +177,8 @@ __device__ __forceinline__ zw64 term_value(const KernelParams& p, const int nwn,
     const uint32_t J = (P0 + 2u * P1 + 4u * ((uint32_t)__popc(X2) + q)) & 7u;
     uint32_t idx = J * p.tab_stride + M;
     if (general) {
-        if (p.has_zero && zb) return zw_zero();
-        zw64 v = ld_entry(table + idx);
+        if (p.has_zero && zb) return zw_zero<typename zw_word<Z>::type>();
+        Z v = ld_entry(table + idx);
         for (uint32_t j = 0; j < p.npairs; j++) {
             const uint32_t a = (L[p.PA[j] >> 5] >> (p.PA[j] & 31)) & 1u;
             const uint32_t b = (L[p.PB[j] >> 5] >> (p.PB[j] & 31)) & 1u;
@@ -159,14 +194,14 @@ __device__ __forceinline__ zw64 term_value(const KernelParams& p, const int nwn,
 // The first 2^bits entries of g in tiles of 2^10, the low `low_bits` bits
 // transformed.  Thread t evaluates entries 4t .. 4t + 3, the layout of the
 // first round.
-template <int NW>
+template <int NW, class Z>
 __global__ void __launch_bounds__(kLowThreads)
 inner_terms_low(const __grid_constant__ KernelParams p, const int nwn, const int general,
-                const zw64* __restrict__ table, const zw64* __restrict__ pv,
+                const Z* __restrict__ table, const Z* __restrict__ pv,
                 const uint32_t* __restrict__ frows, const uint64_t* __restrict__ adj,
                 const uint32_t* __restrict__ low, const uint32_t bits, const uint32_t low_bits,
-                zw64* __restrict__ out) {
-    __shared__ ulonglong2 s0[kTile], s1[kTile];
+                Z* __restrict__ out) {
+    extern __shared__ ulonglong2 sm[];   // Planes<Z>::N planes of kTile slots
     const uint32_t tb = bits < kTileLog2 ? bits : kTileLog2, n = 1u << tb;
     const uint64_t base = (uint64_t)blockIdx.x << tb;
     // the high bits' state (form bits, A x_high, the quadratic bit): lane i
@@ -195,18 +230,19 @@ inner_terms_low(const __grid_constant__ KernelParams p, const int nwn, const int
     // (every quadratic pair of the high bits was counted from both ends)
     const uint32_t qb = (qb2 >> 1) & 1u;
     const uint32_t ab = (uint32_t)AB;
-    zw64 v[4];
+    Z v[4];
 #pragma unroll
     for (uint32_t j = 0; j < 4; j++) {
         const uint32_t e = spread(t, 0, j);
-        v[j] = e < n ? term_value<NW>(p, nwn, general, table, pv, LB, qb, ab, low, e) : zw_zero();
+        v[j] = e < n ? term_value<NW, Z>(p, nwn, general, table, pv, LB, qb, ab, low, e)
+                     : zw_zero<typename zw_word<Z>::type>();
     }
     radix4(v, round_mask(0, low_bits));
     uint32_t pr = 0;
 #pragma unroll
     for (uint32_t q = 2; q < kTileLog2; q += 2) {
         if (q < low_bits) {   // (the same for the whole block)
-            exchange(s0, s1, v, t, q - 2, q);
+            exchange(sm, kTile, v, t, q - 2, q);
             pr = q;
             radix4(v, round_mask(q, low_bits));
         }
@@ -223,20 +259,18 @@ inner_terms_low(const __grid_constant__ KernelParams p, const int nwn, const int
 // l (tile index e = row << C | col, C = 11 - NB <= 10 <= lo).  Rounds at bits
 // C, C + 2, ... of the tile index; for odd NB the last round takes the top
 // two bits and transforms only the top one.
-template <uint32_t NB>
-__global__ void __launch_bounds__(kPassThreads, 2)
-wht_pass(zw64* __restrict__ F, const uint32_t lo) {
-    constexpr uint32_t T = kPassLog2, C = T - NB, NR = (NB + 1) / 2, CM = (1u << C) - 1u;
+template <class Z, uint32_t NB>
+__global__ void __launch_bounds__(1u << (pass_log2<Z>() - 2), 2)
+wht_pass(Z* __restrict__ F, const uint32_t lo) {
+    constexpr uint32_t T = pass_log2<Z>(), C = T - NB, NR = (NB + 1) / 2, CM = (1u << C) - 1u;
     extern __shared__ ulonglong2 sm[];
-    ulonglong2* s0 = sm;
-    ulonglong2* s1 = sm + (1u << T);
     const uint32_t gl = lo - C;   // log2 of the tiles side by side in the low bits
     const uint64_t o = (uint64_t)blockIdx.x >> gl;
     const uint64_t l0 = (uint64_t)(blockIdx.x & ((1u << gl) - 1u)) << C;
-    zw64* const b = F + ((o << (lo + NB)) | l0);
+    Z* const b = F + ((o << (lo + NB)) | l0);
     const uint32_t t = threadIdx.x;
     constexpr uint32_t P0 = NB >= 2 ? C : T - 2;
-    zw64 v[4];
+    Z v[4];
 #pragma unroll
     for (uint32_t j = 0; j < 4; j++) {
         const uint32_t e = spread(t, P0, j);
@@ -247,7 +281,7 @@ wht_pass(zw64* __restrict__ F, const uint32_t lo) {
     for (uint32_t r = 0; r < NR; r++) {
         const bool pair = 2 * r + 1 < NB;
         const uint32_t q = pair ? C + 2 * r : T - 2;
-        if (r) exchange(s0, s1, v, t, pr, q);
+        if (r) exchange(sm, 1u << T, v, t, pr, q);
         pr = q;
         radix4(v, pair ? 3u : 2u);
     }
@@ -258,22 +292,75 @@ wht_pass(zw64* __restrict__ F, const uint32_t lo) {
     }
 }
 
-template <uint32_t NB>
-cudaError_t launch_pass(zw64* ftab, uint32_t lo, uint32_t bits, cudaStream_t stream) {
-    cudaError_t e = cudaFuncSetAttribute(wht_pass<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
+template <class Z, uint32_t NB>
+cudaError_t launch_pass(Z* ftab, uint32_t lo, uint32_t bits, cudaStream_t stream) {
+    constexpr uint32_t T = pass_log2<Z>();
+    cudaError_t e = cudaFuncSetAttribute(wht_pass<Z, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pass_smem<Z>());
     if (e != cudaSuccess) return e;
-    wht_pass<NB><<<(unsigned)((1ull << bits) >> kPassLog2), kPassThreads, kPassSmem, stream>>>(ftab, lo);
+    wht_pass<Z, NB><<<(unsigned)((1ull << bits) >> T), 1u << (T - 2), pass_smem<Z>(), stream>>>(ftab, lo);
     return cudaGetLastError();
 }
 
-template <int NW>
-cudaError_t launch_low(const Plan& in, uint32_t low_bits, const zw64* itab, const zw64* ipv,
-                       const uint32_t* ifr, const uint64_t* iadj, const uint32_t* ilow, zw64* ftab,
-                       cudaStream_t stream) {
+template <int NW, class Z>
+cudaError_t launch_low(const Plan& in, uint32_t low_bits, const Z* itab, const Z* ipv, const uint32_t* ifr,
+                       const uint64_t* iadj, const uint32_t* ilow, Z* ftab, cudaStream_t stream) {
     const uint32_t bits = in.kp.k, tb = bits < kTileLog2 ? bits : kTileLog2;
-    inner_terms_low<NW><<<(unsigned)(1ull << (bits - tb)), kLowThreads, 0, stream>>>(
-        in.kp, in.nwn, in.general ? 1 : 0, itab, ipv, ifr, iadj, ilow, bits, low_bits, ftab);
+    const size_t smem = (size_t)Planes<Z>::N * kTile * 16u;
+    cudaError_t e = cudaFuncSetAttribute(inner_terms_low<NW, Z>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    // (the 128-bit table holds (J, M) values only: every entry takes the
+    // general path)
+    const int general = (in.general || Planes<Z>::N == 4) ? 1 : 0;
+    inner_terms_low<NW, Z><<<(unsigned)(1ull << (bits - tb)), kLowThreads, smem, stream>>>(
+        in.kp, in.nwn, general, itab, ipv, ifr, iadj, ilow, bits, low_bits, ftab);
     return cudaGetLastError();
+}
+
+template <class Z>
+cudaError_t table_launch(const Plan& inner, uint32_t k_inner, const Z* itab, const Z* ipv, const uint32_t* ifr,
+                         const uint64_t* iadj, const uint32_t* ilow, Z* ftab, cudaStream_t stream) {
+    const uint32_t bits = inner.kp.k;
+    if (bits > kMaxInnerBits || k_inner > bits) return cudaErrorInvalidValue;
+    const int nw = inner.nwn + (inner.nwl < 1 ? 1 : inner.nwl);
+    const uint32_t low = k_inner < kTileLog2 ? k_inner : kTileLog2;
+    cudaError_t e;
+    switch (nw) {
+    case 1: e = launch_low<1, Z>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
+    case 2: e = launch_low<2, Z>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
+    case 3: e = launch_low<3, Z>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
+    case 4: e = launch_low<4, Z>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
+    case 5: e = launch_low<5, Z>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
+    case 6: e = launch_low<6, Z>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
+    case 7: e = launch_low<7, Z>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
+    case 8: e = launch_low<8, Z>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    // the remaining inner bits in passes of at most kPassBits, split evenly
+    // (every pass starts at lo >= 10, so its tile's 2^C columns fit below it)
+    const uint32_t rem = k_inner - low;
+    const uint32_t passes = (rem + kPassBits - 1) / kPassBits;
+    for (uint32_t lo = low, left = rem, p = passes; left; p--) {
+        const uint32_t nb = (left + p - 1) / p;
+        switch (nb) {
+        case 1: e = launch_pass<Z, 1>(ftab, lo, bits, stream); break;
+        case 2: e = launch_pass<Z, 2>(ftab, lo, bits, stream); break;
+        case 3: e = launch_pass<Z, 3>(ftab, lo, bits, stream); break;
+        case 4: e = launch_pass<Z, 4>(ftab, lo, bits, stream); break;
+        case 5: e = launch_pass<Z, 5>(ftab, lo, bits, stream); break;
+        case 6: e = launch_pass<Z, 6>(ftab, lo, bits, stream); break;
+        case 7: e = launch_pass<Z, 7>(ftab, lo, bits, stream); break;
+        case 8: e = launch_pass<Z, 8>(ftab, lo, bits, stream); break;
+        case 9: e = launch_pass<Z, 9>(ftab, lo, bits, stream); break;
+        default: e = launch_pass<Z, 10>(ftab, lo, bits, stream); break;
+        }
+        if (e != cudaSuccess) return e;
+        lo += nb;
+        left -= nb;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -281,46 +368,13 @@ cudaError_t launch_low(const Plan& in, uint32_t low_bits, const zw64* itab, cons
 cudaError_t inner_table_launch(const Plan& inner, uint32_t k_inner, const zw64* itab, const zw64* ipv,
                                const uint32_t* ifr, const uint64_t* iadj, const uint32_t* ilow, zw64* ftab,
                                cudaStream_t stream) {
-    const uint32_t bits = inner.kp.k;
-    if (bits > kMaxInnerBits || k_inner > bits) return cudaErrorInvalidValue;
-    const int nw = inner.nwn + (inner.nwl < 1 ? 1 : inner.nwl);
-    const uint32_t low = k_inner < kTileLog2 ? k_inner : kTileLog2;
-    cudaError_t e;
-    switch (nw) {
-    case 1: e = launch_low<1>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
-    case 2: e = launch_low<2>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
-    case 3: e = launch_low<3>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
-    case 4: e = launch_low<4>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
-    case 5: e = launch_low<5>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
-    case 6: e = launch_low<6>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
-    case 7: e = launch_low<7>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
-    case 8: e = launch_low<8>(inner, low, itab, ipv, ifr, iadj, ilow, ftab, stream); break;
-    default: return cudaErrorInvalidValue;
-    }
-    if (e != cudaSuccess) return e;
-    // the remaining inner bits in passes of at most kPassBits, split evenly
-    // (every pass starts at lo >= 10)
-    const uint32_t rem = k_inner - low;
-    const uint32_t passes = (rem + kPassBits - 1) / kPassBits;
-    for (uint32_t lo = low, left = rem, p = passes; left; p--) {
-        const uint32_t nb = (left + p - 1) / p;
-        switch (nb) {
-        case 1: e = launch_pass<1>(ftab, lo, bits, stream); break;
-        case 2: e = launch_pass<2>(ftab, lo, bits, stream); break;
-        case 3: e = launch_pass<3>(ftab, lo, bits, stream); break;
-        case 4: e = launch_pass<4>(ftab, lo, bits, stream); break;
-        case 5: e = launch_pass<5>(ftab, lo, bits, stream); break;
-        case 6: e = launch_pass<6>(ftab, lo, bits, stream); break;
-        case 7: e = launch_pass<7>(ftab, lo, bits, stream); break;
-        case 8: e = launch_pass<8>(ftab, lo, bits, stream); break;
-        case 9: e = launch_pass<9>(ftab, lo, bits, stream); break;
-        default: e = launch_pass<10>(ftab, lo, bits, stream); break;
-        }
-        if (e != cudaSuccess) return e;
-        lo += nb;
-        left -= nb;
-    }
-    return cudaSuccess;
+    return table_launch<zw64>(inner, k_inner, itab, ipv, ifr, iadj, ilow, ftab, stream);
+}
+
+cudaError_t inner_table_launch_wide(const Plan& inner, uint32_t k_inner, const zw128* itab_w, const zw128* ipv_w,
+                                    const uint32_t* ifr, const uint64_t* iadj, const uint32_t* ilow, zw128* ftab_w,
+                                    cudaStream_t stream) {
+    return table_launch<zw128>(inner, k_inner, itab_w, ipv_w, ifr, iadj, ilow, ftab_w, stream);
 }
 
 }  // namespace zxp

@@ -56,6 +56,37 @@ cudaError_t inner_table_launch(const Plan& inner, uint32_t k_inner, const zw64* 
                                const uint32_t* ifr, const uint64_t* iadj, const uint32_t* ilow, zw64* ftab,
                                cudaStream_t stream);
 
+// ---- 128-bit coefficients (kernel_wide.cu, inner.cu) -------------------------
+
+// Device copy of the public 128-bit result record (zxp_zomega_wide): the
+// low and high 64-bit words of each coefficient.
+struct DevResultW {
+    int64_t c[4];
+    int64_t hi[4];
+    int32_t e;
+    int32_t flags;
+};
+
+// The sum of sum_launch modulo 2^128: the per-term walk (table value by
+// (J, M), phase-pair values and zero forms applied per term) over the
+// plan's rows, adjacency and seek tables (drows, dADJ, dS, the 64-bit upload)
+// and its 128-bit values: the (J, M) table Plan::table_w at dtab_w, the pair
+// values Plan::pv_w at dpv_w and the inner table (inner_table_launch_wide)
+// at dftab_w.  acc (8 x 64-bit words) and *counter must be 0 on entry and
+// are 0 again when the kernel ends; *result (device memory) receives
+// K_w * (sum) over sqrt2^e0.
+cudaError_t sum_launch_wide(const Plan& pl, const zw128* dtab_w, const zw128* dpv_w, const uint32_t* drows,
+                            const uint64_t* dADJ, const uint32_t* dS, const uint32_t* dzq, const zw128* dftab_w,
+                            uint64_t first, uint64_t count, int sm_count, uint64_t* acc, unsigned int* counter,
+                            DevResultW* result, cudaStream_t stream);
+
+// inner_table_launch modulo 2^128: the inner plan's 128-bit (J, M) table
+// (inner constant folded in) and pair values at itab_w, ipv_w, the rest as
+// for inner_table_launch; 64-byte entries at ftab_w.
+cudaError_t inner_table_launch_wide(const Plan& inner, uint32_t k_inner, const zw128* itab_w, const zw128* ipv_w,
+                                    const uint32_t* ifr, const uint64_t* iadj, const uint32_t* ilow, zw128* ftab_w,
+                                    cudaStream_t stream);
+
 // ---- batches (batch.cu) -----------------------------------------------------
 
 // One scalar of a batch, as the batch kernel reads it (device memory).

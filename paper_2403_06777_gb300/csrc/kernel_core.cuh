@@ -58,9 +58,45 @@ __device__ __forceinline__ zw64 shfl_xor_zw(zw64 v, int off) {
     return r;
 }
 
+// the same for 128-bit coefficients (64-byte values, 16-byte aligned)
+__device__ __forceinline__ u128 u128_of(unsigned long long lo, unsigned long long hi) {
+    return ((u128)hi << 64) | (u128)lo;
+}
+__device__ __forceinline__ zw128 lds_zw(const zw128* p) {
+    const ulonglong2* q = reinterpret_cast<const ulonglong2*>(p);
+    zw128 r;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const ulonglong2 a = q[c];
+        r.c[c] = u128_of(a.x, a.y);
+    }
+    return r;
+}
+__device__ __forceinline__ zw128 ldg_zw(const zw128* p) {
+    const ulonglong2* q = reinterpret_cast<const ulonglong2*>(p);
+    zw128 r;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const ulonglong2 a = __ldg(q + c);
+        r.c[c] = u128_of(a.x, a.y);
+    }
+    return r;
+}
+__device__ __forceinline__ zw128 shfl_xor_zw(zw128 v, int off) {
+    zw128 r;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)v.c[c], off);
+        const unsigned long long hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(v.c[c] >> 64), off);
+        r.c[c] = u128_of(lo, hi);
+    }
+    return r;
+}
+
 // warp shuffles, then one value per warp through shared memory; the block
 // total is valid in thread 0
-__device__ __forceinline__ zw64 block_reduce(zw64 v, zw64* sred) {
+template <class W>
+__device__ __forceinline__ zwt<W> block_reduce(zwt<W> v, zwt<W>* sred) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v = zw_add(v, shfl_xor_zw(v, off));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -68,7 +104,7 @@ __device__ __forceinline__ zw64 block_reduce(zw64 v, zw64* sred) {
     if (lane == 0) sred[warp] = v;
     __syncthreads();
     if (warp == 0) {
-        v = (lane < (int)(blockDim.x >> 5)) ? sred[lane] : zw_zero();
+        v = (lane < (int)(blockDim.x >> 5)) ? sred[lane] : zw_zero<W>();
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v = zw_add(v, shfl_xor_zw(v, off));
     }
@@ -153,16 +189,17 @@ __host__ __device__ constexpr uint32_t seek_words(int nw, uint32_t kcap = kMaxK)
 __host__ __device__ constexpr uint32_t k_cap(uint32_t k) { return k < 4 ? 4u : (k + 1u) & ~1u; }
 __host__ __device__ constexpr uint32_t lut_cap(uint32_t nU) { return ((1u << nU) + 9u) & ~1u; }
 
+// ew: 32-byte words of one table value (1: 64-bit coefficients, 2: 128-bit)
 __host__ __device__ inline size_t smem_bytes(uint32_t ntab_cap, uint32_t npairs_cap, int nwn, int nwl,
                                              int h, int threads, uint32_t kcap = kMaxK,
-                                             uint32_t lutcap = kLutEntries) {
-    return sizeof(zw64) * (ntab_cap + 4u * npairs_cap + kMaxWarps) + sizeof(uint64_t) * kcap +
+                                             uint32_t lutcap = kLutEntries, uint32_t ew = 1) {
+    return sizeof(zw64) * ew * (ntab_cap + 4u * npairs_cap + kMaxWarps) + sizeof(uint64_t) * kcap +
            sizeof(uint32_t) * seek_words(nwn + nwl, kcap) + sizeof(uint32_t) * (size_t)kcap * row_words(nwn, nwl) +
            (h >= 4 ? sizeof(uint64_t) * lutcap : 0) +
            sizeof(uint32_t) * (size_t)counter_words(h, ntab_cap, (uint32_t)threads);
 }
 
-template <int NW, int HIST>
+template <int NW, int HIST, uint32_t EW = 1>
 __device__ __forceinline__ Smem carve(unsigned char* raw, uint32_t ntab_cap, uint32_t npairs_cap,
                                       uint32_t kcap = kMaxK, uint32_t lutcap = kLutEntries) {
     // (step rows last: 16-byte aligned after the 8-byte adjacency words, as
@@ -170,10 +207,10 @@ __device__ __forceinline__ Smem carve(unsigned char* raw, uint32_t ntab_cap, uin
     const uint32_t hist_words = counter_words(HIST, ntab_cap, blockDim.x);
     Smem s;
     s.sT = reinterpret_cast<zw64*>(raw);
-    s.sPV = s.sT + ntab_cap;
-    s.sred = s.sPV + 4u * npairs_cap;
+    s.sPV = s.sT + EW * ntab_cap;
+    s.sred = s.sPV + EW * 4u * npairs_cap;
     // 16-byte aligned first (vector loads and stores): seek tables, counters
-    s.sS = reinterpret_cast<uint32_t*>(s.sred + kMaxWarps);
+    s.sS = reinterpret_cast<uint32_t*>(s.sred + EW * kMaxWarps);
     s.sL = reinterpret_cast<uint64_t*>(s.sS + seek_words(NW, kcap));
     s.sH = reinterpret_cast<uint32_t*>(s.sL + (HIST >= 4 ? lutcap : 0u));
     s.sADJ = reinterpret_cast<uint64_t*>(s.sH + hist_words);
@@ -220,7 +257,7 @@ __device__ __forceinline__ uint32_t round16(uint32_t b) { return (b + 15u) & ~15
 // Copy one scalar's tables into shared memory with bulk copies on the
 // mbarrier `bar` (initialised, count 1).  Called by one thread; the copies
 // complete the barrier's current phase.
-template <int NWN, int NWL, bool GENERAL, int HIST>
+template <int NWN, int NWL, bool GENERAL, int HIST, uint32_t EW = 1>
 __device__ __forceinline__ void issue_tables(const KernelParams& p, const Smem& sm,
                                              const zw64* __restrict__ gtable,
                                              const zw64* __restrict__ gpv,
@@ -230,8 +267,8 @@ __device__ __forceinline__ void issue_tables(const KernelParams& p, const Smem& 
     constexpr int NW = NWN + NWL;
     constexpr uint32_t RW = row_words(NWN, NWL);
     const uint32_t ns = ((p.k + 3) / 4) * 16u * seek_stride(NW);
-    const uint32_t bt = p.tab_size * 32u, bs = ns * 4u, br = p.k * RW * 4u, ba = round16(p.k * 8u);
-    const uint32_t bpv = GENERAL ? 4u * p.npairs * 32u : 0u;
+    const uint32_t bt = p.tab_size * 32u * EW, bs = ns * 4u, br = p.k * RW * 4u, ba = round16(p.k * 8u);
+    const uint32_t bpv = GENERAL ? 4u * p.npairs * 32u * EW : 0u;
     const uint32_t bl = HIST >= 4 ? round16(p.lut_entries * 8u) : 0u;
     // order the shared-memory reads of a previous scalar before the
     // asynchronous writes
@@ -607,11 +644,13 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
 // final_fold false (counting variants with warp-shared counters, one slice
 // per thread): the counters are left for the caller to fold (see
 // fold_block_counters).
-template <int NWN, int NWL, bool GENERAL, int HIST, bool XTRA, bool OUTER = false>
+// Z: the table values' ring (zw64; zw128 with the table and general
+// variants, HIST 0).
+template <int NWN, int NWL, bool GENERAL, int HIST, bool XTRA, bool OUTER = false, class Z = zw64>
 __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint64_t first,
                                      uint64_t count, uint64_t span, uint64_t nslices,
                                      uint64_t s_begin, uint64_t stride, bool fold_each,
-                                     bool clear_on_exit, bool final_fold, zw64& acc) {
+                                     bool clear_on_exit, bool final_fold, Z& acc) {
     if constexpr (HIST >= 4) {
         walk_lut<NWN, NWL, XTRA, HIST >= 5, HIST == 6, OUTER>(p, sm, first, count, span, nslices, s_begin,
                                                               stride, fold_each, clear_on_exit, final_fold, acc);
@@ -619,8 +658,10 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
     }
     constexpr int NW = NWN + NWL;
     constexpr uint32_t RW = row_words(NWN, NWL);
-    const zw64* __restrict__ sT = sm.sT;
-    const zw64* __restrict__ sPV = sm.sPV;
+    typedef typename zw_word<Z>::type W;
+    const Z* __restrict__ sT = reinterpret_cast<const Z*>(sm.sT);
+    const Z* __restrict__ sPV = reinterpret_cast<const Z*>(sm.sPV);
+    const Z* __restrict__ ftab = reinterpret_cast<const Z*>(p.ftab);
     const uint64_t* __restrict__ sADJ = sm.sADJ;
     const uint32_t* __restrict__ sF = sm.sF;
     uint32_t* __restrict__ sH = sm.sH;
@@ -737,7 +778,7 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
             }
             // the run's sum (table and general variants), and with inner
             // parameters the cut parities zq of the current assignment
-            zw64 ai = zw_zero();
+            Z ai = zw_zero<W>();
             uint32_t zq = 0;
             if (outer)
                 for (uint64_t m = x >> p.zq_lo; m; m &= m - 1)
@@ -745,7 +786,7 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
             // inner parameters: the terms since the last flush times the
             // inner table at zq (a lane-private count fold for HIST 1, 2)
             auto flush = [&]() {
-                zw64 sum = ai;
+                Z sum = ai;
                 if (HIST == 1 || HIST == 2) {
                     uint32_t* const wb = sH + warp * nwords * 32u + lane;
                     for (uint32_t i = 0; i < nwords; i++) {
@@ -760,8 +801,8 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                         }
                     }
                 }
-                acc = zw_add(acc, zw_mul(sum, ldg_zw(p.ftab + zq)));
-                ai = zw_zero();
+                acc = zw_add(acc, zw_mul(sum, ldg_zw(ftab + zq)));
+                ai = zw_zero<W>();
             };
 
             // one term at the current state
@@ -795,7 +836,7 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                         ai = zw_add(ai, lds_zw(sT + idx));
                 } else if (Zb == 0) {
                     const uint32_t J = Jl & 7u;
-                    zw64 v = lds_zw(sT + J * p.tab_stride + M);
+                    Z v = lds_zw(sT + J * p.tab_stride + M);
                     if (GENERAL) {
                         for (uint32_t j = 0; j < p.npairs; j++) {
                             const uint32_t b = bit_at<NW>(L, p.PA[j]) | (bit_at<NW>(L, p.PB[j]) << 1);

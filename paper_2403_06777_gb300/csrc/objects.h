@@ -125,6 +125,63 @@ inline cudaError_t queue_inner_table(const Plan& pl, const DevTables& d, cudaStr
     return inner_table_launch(*pl.inner, pl.k_inner, d.itab, d.ipv, d.ifr, d.iadj, d.ilow, d.ftab, stream);
 }
 
+// The 128-bit values of one scalar on one device (plan.h table_w, pv_w and
+// the inner plan's), allocated when the 128-bit sum first needs them:
+// term table | pair values | inner term table | inner pair values | inner
+// table (written on the device).  Rows, adjacency, seek tables, cut columns
+// and low-bit states are the 64-bit upload's.
+struct DevWide {
+    void* base = nullptr;
+    zw128* table = nullptr;
+    zw128* pv = nullptr;
+    zw128* itab = nullptr;
+    zw128* ipv = nullptr;
+    zw128* ftab = nullptr;
+};
+
+struct WideLayout {
+    size_t o_pv = 0, o_itab = 0, o_ipv = 0, o_ftab = 0, copied = 0, total = 0;
+};
+
+inline WideLayout wide_layout(const Plan& pl) {
+    WideLayout L;
+    L.o_pv = align16(pl.table_w.size() * sizeof(zw128));
+    L.o_itab = align16(L.o_pv + pl.pv_w.size() * sizeof(zw128));
+    L.total = L.copied = L.o_itab;
+    if (pl.k_inner && pl.inner) {
+        const Plan& in = *pl.inner;
+        L.o_ipv = align16(L.o_itab + in.table_w.size() * sizeof(zw128));
+        L.o_ftab = (L.o_ipv + in.pv_w.size() * sizeof(zw128) + 255) & ~(size_t)255;
+        L.copied = L.o_ftab;
+        L.total = L.o_ftab + (sizeof(zw128) << pl.inner_bits);
+    }
+    if (L.total == 0) L.total = 16;
+    return L;
+}
+
+inline void pack_wide(const Plan& pl, const WideLayout& L, unsigned char* dst) {
+    if (!pl.table_w.empty()) memcpy(dst, pl.table_w.data(), pl.table_w.size() * sizeof(zw128));
+    if (!pl.pv_w.empty()) memcpy(dst + L.o_pv, pl.pv_w.data(), pl.pv_w.size() * sizeof(zw128));
+    if (pl.k_inner && pl.inner) {
+        const Plan& in = *pl.inner;
+        if (!in.table_w.empty()) memcpy(dst + L.o_itab, in.table_w.data(), in.table_w.size() * sizeof(zw128));
+        if (!in.pv_w.empty()) memcpy(dst + L.o_ipv, in.pv_w.data(), in.pv_w.size() * sizeof(zw128));
+    }
+}
+
+inline DevWide device_wide(const WideLayout& L, unsigned char* base) {
+    DevWide d;
+    d.base = base;
+    d.table = reinterpret_cast<zw128*>(base);
+    d.pv = reinterpret_cast<zw128*>(base + L.o_pv);
+    if (L.o_ftab) {
+        d.itab = reinterpret_cast<zw128*>(base + L.o_itab);
+        d.ipv = reinterpret_cast<zw128*>(base + L.o_ipv);
+        d.ftab = reinterpret_cast<zw128*>(base + L.o_ftab);
+    }
+    return d;
+}
+
 // Descriptor the batch kernel reads for a scalar whose tables are at d.
 inline BatchScalar batch_descriptor(const Plan& pl, const DevTables& d) {
     BatchScalar bs;
@@ -219,6 +276,8 @@ struct zxp_scalar {
         bool shared = false;
     };
     mutable std::map<int, DevCopy> dev;
+    // per-device 128-bit values (zxp_eval_wide), freed with the scalar
+    mutable std::map<int, zxp::DevWide> devw;
 
     ~zxp_scalar();
 };
@@ -231,7 +290,8 @@ struct zxp_ctx {
     cudaStream_t upload = nullptr;      // table copies (the stream waits for them)
     int sm_count = 0;
     int max_grid = 0;
-    zxp::zw64* acc = nullptr;           // the sum kernel's accumulator (zero between launches)
+    zxp::zw64* acc = nullptr;           // the sum kernels' accumulator, 64 bytes (zero between launches)
+    zxp::DevResultW* wres = nullptr;    // device result of the 128-bit sum
     unsigned int* counter = nullptr;
     zxp::DevResult* hres = nullptr;     // pinned; the kernel writes it directly
     zxp::DevResult* hres_dev = nullptr; // its device address

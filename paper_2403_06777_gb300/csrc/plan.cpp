@@ -40,6 +40,7 @@ int build_plain_plan(const PS& ps, bool allow_lut, bool lane_only, Plan* out) {
     if (k > (uint32_t)kMaxK) return ZXP_ETOOBIG;
     kp.k = k;
     zw64 K = from_i64(ps.G);
+    zw128 Kw = zw_widen(K);   // the same constant modulo 2^128
     bool exact_zero = !(ps.G[0] | ps.G[1] | ps.G[2] | ps.G[3]);
 
     // quadratic rows -> symmetric adjacency (+ 4 x_i on the diagonal); the
@@ -70,13 +71,16 @@ int build_plain_plan(const PS& ps, bool allow_lut, bool lane_only, Plan* out) {
         if (!n.mask) {
             if (g == 4) exact_zero = true;
             K = zw_mul(K, zw_add(zw_one(), zw_wpow(g)));
+            Kw = zw_mul(Kw, zw_widen(zw_add(zw_one(), zw_wpow(g))));
             continue;
         }
         if (g == 2 || g == 6) {        // 1 + w^(2+4l) = sqrt2 w w^(6l); 1 + w^(6+4l) = sqrt2 w^7 w^(2l)
             K = zw_rot(zw_mul_sqrt2(K), g == 2 ? 1 : 7);
+            Kw = zw_rot(zw_mul_sqrt2(Kw), g == 2 ? 1 : 7);
             lin_terms.push_back({n.mask, g == 2 ? 6u : 2u});
         } else if (g == 0 || g == 4) { // 2 when the effective exponent is 0, else 0
             K = zw_add(K, K);
+            Kw = zw_add(Kw, Kw);
             zero.push_back(Form{n.mask, g == 4 ? 1u : 0u});
         } else {                       // odd: bit set <=> effective exponent in {1, 7}
             odd.push_back(Form{n.mask, (g == 1 || g == 7) ? 1u : 0u});
@@ -91,6 +95,7 @@ int build_plain_plan(const PS& ps, bool allow_lut, bool lane_only, Plan* out) {
             zw64 v = pair_value(p.a, p.b);
             if (!(v.c[0] | v.c[1] | v.c[2] | v.c[3])) exact_zero = true;
             K = zw_mul(K, v);
+            Kw = zw_mul(Kw, zw_widen(v));
             continue;
         }
         if (pl.pv.size() / 4 >= (size_t)kMaxPairs) return ZXP_ETOOBIG;
@@ -105,6 +110,8 @@ int build_plain_plan(const PS& ps, bool allow_lut, bool lane_only, Plan* out) {
     pl.m_odd = (uint32_t)odd.size();
     K = zw_mul(K, zw_pow(zw_make(1, (uint64_t)-1, 0, 0), pl.m_odd));
     K = zw_rot(K, 3 * nB);
+    Kw = zw_mul(Kw, zw_pow(zw_widen(zw_make(1, (uint64_t)-1, 0, 0)), pl.m_odd));
+    Kw = zw_rot(Kw, 3 * nB);
 
     // layout
     // linear forms in ascending mask order, coefficients summed mod 8, zero
@@ -481,6 +488,17 @@ int build_plain_plan(const PS& ps, bool allow_lut, bool lane_only, Plan* out) {
         }
         s = zw_mul(s, zw_silver());
     }
+    // modulo 2^128: (J, M) values only (the pair values are small, so their
+    // 64-bit words widen exactly)
+    pl.table_w.assign((size_t)8 * kp.tab_stride, zw_zero<u128>());
+    zw128 sw = zw_one<u128>();
+    for (uint32_t M = 0; M <= pl.m_odd; M++) {
+        for (unsigned J = 0; J < 8; J++) pl.table_w[(size_t)J * kp.tab_stride + M] = zw_rot(sw, J + 2 * M);
+        sw = zw_mul(sw, zw_widen(zw_silver()));
+    }
+    pl.pv_w.clear();
+    for (const zw64& v : pl.pv) pl.pv_w.push_back(zw_widen(v));
+    pl.K_w = Kw;
     pl.K = K;
     pl.e0 = ps.e0;
     pl.zero = exact_zero;
@@ -573,6 +591,8 @@ int build_split_plan(const PS& ps, Plan* out) {
     // table value (times phase-pair values beyond the folded ones)
     for (zw64& t : ip->table) t = zw_mul(ip->K, t);
     ip->K = zw_one();
+    for (zw128& t : ip->table_w) t = zw_mul(ip->K_w, t);
+    ip->K_w = zw_one<u128>();
     // the low bits' flip-row XOR and quadratic bit, per value
     const uint32_t tb = bits < kInnerLowBits ? bits : kInnerLowBits;
     const uint32_t inw = (uint32_t)(ip->nwn + (ip->nwl < 1 ? 1 : ip->nwl));

@@ -125,6 +125,13 @@ struct Plan {
     std::vector<zw64> table;        // w^(J + 2M) (1 + sqrt2)^M x pair values x (1 - zero)
     std::vector<zw64> pv;           // 4 per pair: value at (lA, lB) = (b & 1, b >> 1)
     zw64 K;                         // constant factor, G included
+    // The same values modulo 2^128 (exact sums for 124 < e0 <= 252): the
+    // term table indexed by (J, M) alone, w^(J + 2M) (1 + sqrt2)^M at
+    // J * tab_stride + M (phase-pair values and zero forms are applied per
+    // term), the pair values and the constant.
+    std::vector<zw128> table_w;
+    std::vector<zw128> pv_w;
+    zw128 K_w;
     int32_t e0 = 0;
     bool zero = false;              // the scalar is identically zero
     bool has_zero = false;          // some term can vanish (zero forms present)

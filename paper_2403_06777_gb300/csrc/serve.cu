@@ -242,10 +242,18 @@ struct Scheduler {
             canon_result(st.h_out[i], &v);
             s->arena.release(r->arena_off);
             s->free_slots.push_back(r->slot);
-            if (st.h_out[i].flags & 2)
+            const int32_t e0 = r->scalar->ps.e0;
+            if (st.h_out[i].flags & 2) {
                 complete(s, r, ZXP_ETIMEDOUT, nullptr);
-            else
-                complete(s, r, r->scalar->ps.e0 > 124 ? ZXP_EOVERFLOW : ZXP_OK, &v);
+            } else if (e0 > 124 && e0 <= 252) {
+                // beyond the 64-bit bound: the sum again modulo 2^128, on this
+                // thread's stream (synchronous: it waits for the steps in flight)
+                zxp_zomega w;
+                const int st2 = zxp_amplitude(s->ctx, r->scalar, &w);
+                complete(s, r, st2, (st2 == ZXP_OK || st2 == ZXP_EOVERFLOW) ? &w : nullptr);
+            } else {
+                complete(s, r, e0 > 252 ? ZXP_EOVERFLOW : ZXP_OK, &v);
+            }
         }
         {
             std::lock_guard<std::mutex> lk(s->mu);

@@ -1,12 +1,13 @@
 // zring.h -- the ring Z[w] (w = e^{i pi/4}, w^4 = -1) with coefficients
-// taken modulo 2^64, in the integer basis {1, w, w^2, w^3}.
+// taken modulo 2^64 (zw64) or 2^128 (zw128), in the integer basis
+// {1, w, w^2, w^3}.
 //
 // Every sum the library computes is an integer combination of powers of w,
-// so computing modulo 2^64 is a ring homomorphism: the true numerator is
-// recovered exactly whenever its coefficients lie in [-2^63, 2^63).  For an
-// amplitude a = N / sqrt2^e every Galois conjugate of a is the amplitude of
-// a unitary circuit (T -> T^s, H -> +-H), so |N_j| <= 2^(e/2) and e <= 124
-// guarantees exactness.
+// so computing modulo 2^b is a ring homomorphism: the true numerator is
+// recovered exactly whenever its coefficients lie in [-2^(b-1), 2^(b-1)).
+// For an amplitude a = N / sqrt2^e every Galois conjugate of a is the
+// amplitude of a unitary circuit (T -> T^s, H -> +-H), so |N_j| <= 2^(e/2):
+// e <= 124 guarantees exactness with 64-bit words, e <= 252 with 128-bit.
 #pragma once
 #include <stdint.h>
 
@@ -18,8 +19,20 @@
 
 namespace zxp {
 
-struct zw64 {
-    uint64_t c[4];
+typedef unsigned __int128 u128;
+
+template <class W>
+struct zwt {
+    W c[4];
+};
+typedef zwt<uint64_t> zw64;
+typedef zwt<u128> zw128;
+// the coefficient word of a ring type
+template <class Z>
+struct zw_word;
+template <class W>
+struct zw_word<zwt<W>> {
+    typedef W type;
 };
 
 ZXP_HD zw64 zw_make(uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
@@ -27,32 +40,55 @@ ZXP_HD zw64 zw_make(uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
     r.c[0] = a; r.c[1] = b; r.c[2] = c; r.c[3] = d;
     return r;
 }
-ZXP_HD zw64 zw_zero() { return zw_make(0, 0, 0, 0); }
-ZXP_HD zw64 zw_one() { return zw_make(1, 0, 0, 0); }
+template <class W>
+ZXP_HD zwt<W> zw_make_t(W a, W b, W c, W d) {
+    zwt<W> r;
+    r.c[0] = a; r.c[1] = b; r.c[2] = c; r.c[3] = d;
+    return r;
+}
+template <class W = uint64_t>
+ZXP_HD zwt<W> zw_zero() { return zw_make_t<W>(0, 0, 0, 0); }
+template <class W = uint64_t>
+ZXP_HD zwt<W> zw_one() { return zw_make_t<W>(1, 0, 0, 0); }
 
-ZXP_HD zw64 zw_add(zw64 a, zw64 b) {
-    return zw_make(a.c[0] + b.c[0], a.c[1] + b.c[1], a.c[2] + b.c[2], a.c[3] + b.c[3]);
+// a 64-bit value read as the two's-complement integer it encodes, modulo
+// 2^128 (exact for ring elements whose coefficients fit 64 bits)
+ZXP_HD zw128 zw_widen(zw64 a) {
+    return zw_make_t<u128>((u128)(__int128)(int64_t)a.c[0], (u128)(__int128)(int64_t)a.c[1],
+                           (u128)(__int128)(int64_t)a.c[2], (u128)(__int128)(int64_t)a.c[3]);
 }
-ZXP_HD zw64 zw_sub(zw64 a, zw64 b) {
-    return zw_make(a.c[0] - b.c[0], a.c[1] - b.c[1], a.c[2] - b.c[2], a.c[3] - b.c[3]);
+
+template <class W>
+ZXP_HD zwt<W> zw_add(zwt<W> a, zwt<W> b) {
+    return zw_make_t<W>(a.c[0] + b.c[0], a.c[1] + b.c[1], a.c[2] + b.c[2], a.c[3] + b.c[3]);
 }
-ZXP_HD zw64 zw_neg(zw64 a) { return zw_make(0 - a.c[0], 0 - a.c[1], 0 - a.c[2], 0 - a.c[3]); }
+template <class W>
+ZXP_HD zwt<W> zw_sub(zwt<W> a, zwt<W> b) {
+    return zw_make_t<W>(a.c[0] - b.c[0], a.c[1] - b.c[1], a.c[2] - b.c[2], a.c[3] - b.c[3]);
+}
+template <class W>
+ZXP_HD zwt<W> zw_neg(zwt<W> a) {
+    return zw_make_t<W>(W(0) - a.c[0], W(0) - a.c[1], W(0) - a.c[2], W(0) - a.c[3]);
+}
 
 // a * w
-ZXP_HD zw64 zw_mulw(zw64 a) { return zw_make(0 - a.c[3], a.c[0], a.c[1], a.c[2]); }
+template <class W>
+ZXP_HD zwt<W> zw_mulw(zwt<W> a) { return zw_make_t<W>(W(0) - a.c[3], a.c[0], a.c[1], a.c[2]); }
 
 // a * w^j, j taken mod 8
-ZXP_HD zw64 zw_rot(zw64 a, unsigned j) {
+template <class W>
+ZXP_HD zwt<W> zw_rot(zwt<W> a, unsigned j) {
     j &= 7;
     if (j & 4) a = zw_neg(a);
-    if (j & 2) a = zw_make(0 - a.c[2], 0 - a.c[3], a.c[0], a.c[1]);
+    if (j & 2) a = zw_make_t<W>(W(0) - a.c[2], W(0) - a.c[3], a.c[0], a.c[1]);
     if (j & 1) a = zw_mulw(a);
     return a;
 }
 
 // negacyclic product (w^4 = -1)
-ZXP_HD zw64 zw_mul(zw64 a, zw64 b) {
-    zw64 r;
+template <class W>
+ZXP_HD zwt<W> zw_mul(zwt<W> a, zwt<W> b) {
+    zwt<W> r;
     r.c[0] = a.c[0] * b.c[0] - a.c[1] * b.c[3] - a.c[2] * b.c[2] - a.c[3] * b.c[1];
     r.c[1] = a.c[0] * b.c[1] + a.c[1] * b.c[0] - a.c[2] * b.c[3] - a.c[3] * b.c[2];
     r.c[2] = a.c[0] * b.c[2] + a.c[1] * b.c[1] + a.c[2] * b.c[0] - a.c[3] * b.c[3];
@@ -61,11 +97,13 @@ ZXP_HD zw64 zw_mul(zw64 a, zw64 b) {
 }
 
 // a * n for an integer count n
-ZXP_HD zw64 zw_scale(zw64 a, uint64_t n) {
-    return zw_make(a.c[0] * n, a.c[1] * n, a.c[2] * n, a.c[3] * n);
+template <class W>
+ZXP_HD zwt<W> zw_scale(zwt<W> a, uint64_t n) {
+    return zw_make_t<W>(a.c[0] * W(n), a.c[1] * W(n), a.c[2] * W(n), a.c[3] * W(n));
 }
 
-// acc + a * n for a 32-bit count n (one wide multiply-add per coefficient)
+// acc + a * n for a 32-bit count n (64-bit words: one wide multiply-add per
+// coefficient)
 ZXP_HD zw64 zw_madd32(zw64 acc, zw64 a, uint32_t n) {
     zw64 r;
     for (int i = 0; i < 4; i++) {
@@ -74,17 +112,21 @@ ZXP_HD zw64 zw_madd32(zw64 acc, zw64 a, uint32_t n) {
     }
     return r;
 }
+ZXP_HD zw128 zw_madd32(zw128 acc, zw128 a, uint32_t n) { return zw_add(acc, zw_scale(a, n)); }
 
 // a * sqrt2, sqrt2 = w - w^3
-ZXP_HD zw64 zw_mul_sqrt2(zw64 a) {
-    return zw_make(a.c[1] - a.c[3], a.c[0] + a.c[2], a.c[1] + a.c[3], a.c[2] - a.c[0]);
+template <class W>
+ZXP_HD zwt<W> zw_mul_sqrt2(zwt<W> a) {
+    return zw_make_t<W>(a.c[1] - a.c[3], a.c[0] + a.c[2], a.c[1] + a.c[3], a.c[2] - a.c[0]);
 }
 
 // w^j as a ring element
-ZXP_HD zw64 zw_wpow(unsigned j) { return zw_rot(zw_one(), j); }
+template <class W = uint64_t>
+ZXP_HD zwt<W> zw_wpow(unsigned j) { return zw_rot(zw_one<W>(), j); }
 
-ZXP_HD zw64 zw_pow(zw64 a, unsigned n) {
-    zw64 r = zw_one();
+template <class W>
+ZXP_HD zwt<W> zw_pow(zwt<W> a, unsigned n) {
+    zwt<W> r = zw_one<W>();
     while (n) {
         if (n & 1) r = zw_mul(r, a);
         a = zw_mul(a, a);

@@ -223,6 +223,43 @@ void check_lookup(const Model& m) {
     }
 }
 
+// The 128-bit values: the constant and pair values reduce to the 64-bit
+// ones modulo 2^64, and entry (J, M) of the (J, M) table is
+// K w^(J + 2M) (1 + sqrt2)^M (K = 1 except in an inner plan, whose table
+// holds its constant), with (1 + sqrt2)^M = a_M + b_M sqrt2 from the
+// recurrence a' = a + 2b, b' = a + b modulo 2^128 (sqrt2 = w - w^3:
+// coefficients (a, b, 0, -b)) and w^j applied as a cyclic shift with sign
+// changes.
+void check_wide(const Plan& pl, const zw128& k_folded) {
+    const KernelParams& kp = pl.kp;
+    CHECK(pl.pv_w.size() == pl.pv.size());
+    for (size_t j = 0; j < pl.pv.size(); j++)
+        for (int i = 0; i < 4; i++) CHECK((uint64_t)pl.pv_w[j].c[i] == pl.pv[j].c[i]);
+    for (int i = 0; i < 4; i++) CHECK((uint64_t)pl.K_w.c[i] == pl.K.c[i]);
+    CHECK(pl.table_w.size() == (size_t)8 * kp.tab_stride);
+    u128 a = 1, b = 0;
+    for (uint32_t M = 0; M <= pl.m_odd; M++) {
+        for (uint32_t J = 0; J < 8; J++) {
+            zw128 c = zw_make_t<u128>(a, b, 0, (u128)0 - b);
+            for (uint32_t r = 0; r < ((J + 2 * M) & 7); r++) {   // times w
+                const u128 t = c.c[3];
+                c.c[3] = c.c[2]; c.c[2] = c.c[1]; c.c[1] = c.c[0]; c.c[0] = (u128)0 - t;
+            }
+            const zw128 want = zw_mul(k_folded, c);
+            const zw128& v = pl.table_w[(size_t)J * kp.tab_stride + M];
+            for (int i = 0; i < 4; i++) CHECK(v.c[i] == want.c[i]);
+            // the 64-bit table at pair bits 0 and zero bit 0 (without phase-pair
+            // index bits the entries coincide modulo 2^64)
+            if (kp.xshift == 0)
+                for (int i = 0; i < 4; i++)
+                    CHECK((uint64_t)v.c[i] == pl.table[(size_t)J * kp.tab_stride + M].c[i]);
+        }
+        const u128 a2 = a + 2 * b, b2 = a + b;
+        a = a2;
+        b = b2;
+    }
+}
+
 }  // namespace
 
 int main(int argc, char** argv) {
@@ -281,6 +318,8 @@ int main(int argc, char** argv) {
             }
         if (!pl.zero) check_step_rows(m);
         if (pl.lut_ok) check_lookup(m);
+        check_wide(pl, zw_one<u128>());
+        if (pl.k_inner) check_wide(*pl.inner, pl.inner->table_w[0]);
     }
     printf("ok\n");
     return 0;

@@ -280,6 +280,28 @@ int zxp_amplitude(zxp_ctx *ctx, const zxp_scalar *s, zxp_zomega *out);
 int zxp_eval_wide(zxp_ctx *ctx, const zxp_scalar *s, uint64_t first, uint64_t count,
                   zxp_zomega_wide *out);
 
+/* The whole sum over [0, 2^k) in chunks of 2^chunk_log2 terms, resumable
+ * across processes (the paper's exact sum, Eq. 2, for scalars whose full
+ * evaluation outlasts one job).  After every chunk the running partial sum
+ * (64-bit words, or 128-bit when e0 > 124) and the set of finished chunks
+ * are written to the host file `path`: first to `path`.tmp, flushed to the
+ * disk, then renamed over `path`, so the file always holds one complete
+ * state and a process that ends between chunks loses at most the chunk in
+ * flight.  A call that finds the file continues it: chunks already summed
+ * are not run again.  The file names the scalar (a 64-bit FNV-1a digest of
+ * its table bytes), k, chunk_log2 and e0; a file that differs, or is
+ * damaged (a 64-bit checksum over its bytes), is ZXP_EINVAL and is left
+ * alone.  At most max_chunks further chunks run (0: no limit); while chunks
+ * remain the call returns ZXP_EAGAIN.  When all are summed it returns the
+ * canonical amplitude in `out` with zxp_amplitude's status (the file stays:
+ * a further call returns the value without running anything; delete it to
+ * start again).  chunks_done / chunks_total (may be NULL) receive the
+ * progress.  The layout of the file is documented in checkpoint.h.  Errors:
+ * ZXP_EINVAL (arguments, a foreign or damaged file, a file that cannot be
+ * written), the evaluation's errors. */
+int zxp_sum_resumable(zxp_ctx *ctx, const zxp_scalar *s, uint32_t chunk_log2, const char *path,
+                      uint64_t max_chunks, zxp_zomega *out, uint64_t *chunks_done, uint64_t *chunks_total);
+
 /* The whole sum modulo 2^128, canonical: exact for e0 <= 252 (the
  * numerator's coefficients are below 2^126 in magnitude).  ZXP_EOVERFLOW
  * when e0 > 252 (`out` then holds the canonical form of the 128-bit sum). */

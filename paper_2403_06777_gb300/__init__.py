@@ -138,6 +138,8 @@ def lib():
         L.zxp_amplitude.argtypes = [vp, vp, zp]
         L.zxp_eval_wide.argtypes = [vp, vp, u64, u64, C.POINTER(zxp_zomega_wide)]
         L.zxp_amplitude_wide.argtypes = [vp, vp, C.POINTER(zxp_zomega_wide)]
+        L.zxp_sum_resumable.argtypes = [vp, vp, C.c_uint32, C.c_char_p, u64, zp, C.POINTER(u64),
+                                        C.POINTER(u64)]
         L.zxp_eval_device.argtypes = [vp, vp, u64, u64, vp]
         L.zxp_eval_noalloc.argtypes = [vp, u64, u64, vp, vp]
         L.zxp_submit.argtypes = [vp, vp, u64, u64, C.POINTER(u64)]
@@ -450,6 +452,21 @@ def zxp_eval_wide(ctx: Ctx, s: Scalar, first: int = 0, count: int | None = None)
     out = zxp_zomega_wide()
     _check(lib().zxp_eval_wide(ctx.handle, s.handle, first, count, C.byref(out)), "zxp_eval_wide")
     return out.tup()
+
+
+def zxp_sum_resumable(ctx: Ctx, s: Scalar, chunk_log2: int, path: str, max_chunks: int = 0):
+    """The whole sum in chunks of 2^chunk_log2 terms, checkpointed to the
+    host file `path` after every chunk and resumed from it.  Returns
+    (status, value, chunks_done, chunks_total): status ZXP_OK (value the
+    canonical amplitude), ZXP_EOVERFLOW (value as zxp_amplitude's) or
+    ZXP_EAGAIN (chunks remain; value None); other statuses raise."""
+    out = zxp_zomega()
+    done, total = C.c_uint64(), C.c_uint64()
+    rc = lib().zxp_sum_resumable(ctx.handle, s.handle, chunk_log2, os.fsencode(path), max_chunks,
+                                 C.byref(out), C.byref(done), C.byref(total))
+    if rc not in (ZXP_OK, ZXP_EOVERFLOW, ZXP_EAGAIN):
+        raise ZxpError(rc, "zxp_sum_resumable")
+    return rc, (None if rc == ZXP_EAGAIN else out.tup()), done.value, total.value
 
 
 def zxp_amplitude_wide(ctx: Ctx, s: Scalar):

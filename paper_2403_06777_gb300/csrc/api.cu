@@ -16,6 +16,7 @@
 #include "zxp.h"
 #include "compile.h"
 #include "kernel.h"
+#include "checkpoint.h"
 #include "objects.h"
 #include "plan.h"
 #include "ps.h"
@@ -612,6 +613,49 @@ int zxp_eval_wide(zxp_ctx* ctx, const zxp_scalar* s, uint64_t first, uint64_t co
     static_assert(sizeof(DevResultW) == sizeof(zxp_zomega_wide), "result record layout");
     memcpy(out, &r, sizeof r);
     return (out->flags & 2) ? ZXP_ETIMEDOUT : ZXP_OK;
+}
+
+int zxp_sum_resumable(zxp_ctx* ctx, const zxp_scalar* s, uint32_t chunk_log2, const char* path,
+                      uint64_t max_chunks, zxp_zomega* out, uint64_t* chunks_done, uint64_t* chunks_total) {
+    if (!ctx || !s || !path || !*path || !out) return ZXP_EINVAL;
+    const uint32_t k = s->ps.k - s->ps.k_inner;
+    const uint32_t width = s->ps.e0 > 124 ? 128 : 64;
+    std::vector<uint8_t> blob(ps_blob_size(s->ps));
+    ps_to_blob(s->ps, blob.data());
+    const uint64_t digest = ckpt::fnv1a(blob.data(), blob.size());
+    auto eval = [&](uint64_t first, uint64_t count, uint64_t lo[4], uint64_t hi[4]) -> int {
+        if (width == 128) {
+            zxp_zomega_wide w;
+            const int st = zxp_eval_wide(ctx, s, first, count, &w);
+            for (int i = 0; i < 4; i++) {
+                lo[i] = (uint64_t)w.c[i];
+                hi[i] = (uint64_t)w.hi[i];
+            }
+            return st;
+        }
+        zxp_zomega z;
+        const int st = zxp_eval(ctx, s, first, count, &z);
+        for (int i = 0; i < 4; i++) lo[i] = (uint64_t)z.c[i];
+        return st;
+    };
+    ckpt::State st;
+    const int r = ckpt::run(path, width, digest, k, chunk_log2, s->ps.e0, max_chunks, eval, &st);
+    if (chunks_done) *chunks_done = st.done_count;
+    if (chunks_total) *chunks_total = st.n_chunks;
+    if (r != ZXP_OK) return r;
+    __int128 c[4];
+    for (int i = 0; i < 4; i++)
+        c[i] = width == 128 ? (__int128)(((u128)st.sum[4 + i] << 64) | (u128)st.sum[i]) : (__int128)(int64_t)st.sum[i];
+    int32_t e = s->ps.e0;
+    canon_i128(c, &e);
+    bool fits = true;
+    for (int i = 0; i < 4; i++) {
+        out->c[i] = (int64_t)c[i];
+        fits = fits && c[i] == (__int128)(int64_t)c[i];
+    }
+    out->e = e;
+    out->flags = 0;
+    return (s->ps.e0 > 252 || !fits) ? ZXP_EOVERFLOW : ZXP_OK;
 }
 
 int zxp_amplitude_wide(zxp_ctx* ctx, const zxp_scalar* s, zxp_zomega_wide* out) {

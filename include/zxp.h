@@ -250,9 +250,16 @@ int zxp_eval_device(zxp_ctx *ctx, const zxp_scalar *s, uint64_t first, uint64_t 
  * (NULL: the legacy default stream) of the current device, and the raw
  * partial (40-byte zxp_zomega layout, flags bit 0 set) lands at `dev_out`, a
  * caller-owned device pointer aligned to 8 bytes, when the stream reaches it.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the array and it keeps the
+ * Every call looks up the array's device address (cudaGetSymbolAddress, a
+ * host-side lookup) with the current device, so calls stay valid after a
+ * reset of the device's primary context; make the first call on a device
+ * before any stream capture (it loads the library's device code).  Under
+ * stream capture the table copies become graph nodes that read the
+ * scalar's host tables at every replay: the scalar must then stay alive,
+ * and unchanged, until the graph is destroyed.  No device allocation and no
+ * cudaMalloc / cudaFree are made; on the host, the first call for a kernel
+ * variant on a device fills the launch-shape caches (host allocations) and
+ * the runtime stages the pageable table copies.  Every call shares the array and it keeps the
  * last call's contents (the counter is cleared at each call): calls that
  * overlap on the GPU, e.g. on two streams, race.  Errors: ZXP_EINVAL (range,
  * null or unaligned pointer), ZXP_ETOOBIG (tables larger than the array),
@@ -301,6 +308,17 @@ int zxp_eval_wide(zxp_ctx *ctx, const zxp_scalar *s, uint64_t first, uint64_t co
  * written), the evaluation's errors. */
 int zxp_sum_resumable(zxp_ctx *ctx, const zxp_scalar *s, uint32_t chunk_log2, const char *path,
                       uint64_t max_chunks, zxp_zomega *out, uint64_t *chunks_done, uint64_t *chunks_total);
+
+/* Bounded table waits, for tests and diagnostics (no counterpart in the
+ * paper).  Every block of a sum kernel waits for the bulk copies of its
+ * tables into shared memory a bounded number of times (by default several
+ * seconds in all); a block that gives up skips its terms, still waits
+ * (bounded) for its copies to land, and marks the launch's result (flags
+ * bit 1), which the host entry points report as ZXP_ETIMEDOUT.  This sets
+ * the number of waits the launches queued from now on make in this process:
+ * 0 gives up before the first look, tries < 0 restores the default.
+ * ZXP_EINVAL above the default. */
+int zxp_set_wait_budget(int64_t tries);
 
 /* The whole sum modulo 2^128, canonical: exact for e0 <= 252 (the
  * numerator's coefficients are below 2^126 in magnitude).  ZXP_EOVERFLOW

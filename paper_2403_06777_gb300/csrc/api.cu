@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <map>
@@ -289,7 +290,20 @@ int zxp::make_scalar(PS&& ps, zxp_scalar** out) {
     return ZXP_OK;
 }
 
+namespace zxp {
+namespace {
+std::atomic<uint32_t> g_wait_tries{kDefaultWaitTries};
+}  // namespace
+uint32_t wait_budget() { return g_wait_tries.load(std::memory_order_relaxed); }
+}  // namespace zxp
+
 extern "C" {
+
+int zxp_set_wait_budget(int64_t tries) {
+    if (tries > (int64_t)kDefaultWaitTries) return ZXP_EINVAL;
+    g_wait_tries.store(tries < 0 ? kDefaultWaitTries : (uint32_t)tries, std::memory_order_relaxed);
+    return ZXP_OK;
+}
 
 const char* zxp_strerror(int status) {
     switch (status) {
@@ -1016,7 +1030,10 @@ extern "C" void zxp_batch_destroy(zxp_batch* b) {
 // serves them: it stages the scalar's tables and keeps the kernel's scratch
 // (the 64-bit accumulator and the completion counter) in one file-scope
 // device array of fixed size, and writes the result to a buffer the caller
-// owns.  It calls no allocating routine, host or device.
+// owns.  It makes no device allocation and calls neither cudaMalloc nor
+// cudaFree.  (On the host, the first call for a kernel variant on a device
+// fills the launch-shape caches, and the runtime stages the pageable table
+// copies in its own host buffers.)
 // ---------------------------------------------------------------------------
 
 namespace {
@@ -1028,14 +1045,6 @@ constexpr int kNoAllocMaxBlocks = 2048;
 constexpr size_t kNoAllocAccOff = 64;
 constexpr size_t kNoAllocTablesOff = 256;
 constexpr int kNoAllocMaxDevices = 64;
-
-struct NoAllocDevice {
-    bool ready = false;
-    unsigned char* base = nullptr;   // device address of the scratch array
-    int sm_count = 0;
-};
-std::mutex g_noalloc_mu;
-NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
 
 }  // namespace
 
@@ -1059,21 +1068,19 @@ extern "C" int zxp_eval_noalloc(const zxp_scalar* s, uint64_t first, uint64_t co
 
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return ZXP_ECUDA;
-    NoAllocDevice d;
+    // the array's device address on the current device, looked up at every
+    // call (a host-side lookup: an address kept from an earlier call would
+    // be stale after the device's primary context was reset)
+    struct {
+        unsigned char* base;
+        int sm_count;
+    } d = {nullptr, 0};
     {
-        // first call on this device: look up the array's device address with
-        // the device current (the host-side symbol is not a device address)
-        std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        NoAllocDevice& e = g_noalloc_dev[dev];
-        if (!e.ready) {
-            void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return ZXP_ECUDA;
-            if (cudaDeviceGetAttribute(&e.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-                return ZXP_ECUDA;
-            e.base = static_cast<unsigned char*>(p);
-            e.ready = true;
-        }
-        d = e;
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return ZXP_ECUDA;
+        if (cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return ZXP_ECUDA;
+        d.base = static_cast<unsigned char*>(p);
     }
     cudaStream_t stream = (cudaStream_t)cuda_stream;
 

@@ -248,9 +248,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Each try_wait suspends the thread for a bounded time; this many of them
-// (several seconds in all) end a wait that would otherwise never end.
-constexpr uint32_t kWaitTries = 1u << 22;
+// Each try_wait suspends the thread for a bounded time; kDefaultWaitTries
+// of them (several seconds in all) end a wait that would otherwise never end.
+constexpr uint32_t kWaitTries = kDefaultWaitTries;
 
 __device__ __forceinline__ uint32_t round16(uint32_t b) { return (b + 15u) & ~15u; }
 
@@ -285,13 +285,20 @@ __device__ __forceinline__ void issue_tables(const KernelParams& p, const Smem& 
 // Wait (bounded) for the copies of issue_tables: the barrier's phase
 // `phase` (the loads so far; advanced here).  Every thread calls it, after
 // a block barrier that follows the barrier's initialisation.  Returns false
-// if the wait gave up (the tables are then not valid).  Variables 0..2
-// beyond k get zero adjacency rows.
+// if the wait gave up after p.wait_tries waits (the tables are then not
+// valid).  Variables 0..2 beyond k get zero adjacency rows.
 __device__ __forceinline__ bool wait_tables(const KernelParams& p, const Smem& sm, uint64_t* bar,
                                             uint32_t& phase) {
     bool ok = false;
-    for (uint32_t i = 0; i < kWaitTries; i++)
+    for (uint32_t i = 0; i < p.wait_tries; i++)
         if (mbar_try_wait(bar, phase & 1u)) { ok = true; break; }
+    if (!ok) {
+        // given up: the tables are not used, but copies still in flight
+        // write into this block's shared memory, so wait (bounded) for them
+        // to land before the block goes on and ends
+        for (uint32_t i = 0; i < kWaitTries; i++)
+            if (mbar_try_wait(bar, phase & 1u)) break;
+    }
     phase++;
     if (threadIdx.x < 3 && threadIdx.x >= p.k) sm.sADJ[threadIdx.x] = 0;
     return ok;

@@ -99,7 +99,16 @@ struct KernelParams {
     uint32_t zq_lo;
     const uint32_t* zqcol;   // device addresses, set at launch
     const zw64* ftab;
+    // Bounded waits a block makes for its table copies before it gives up
+    // (kDefaultWaitTries unless a test lowered it: zxp_set_wait_budget).
+    uint32_t wait_tries;
 };
+
+// each wait suspends the thread for a bounded time: this many of them are
+// several seconds in all
+constexpr uint32_t kDefaultWaitTries = 1u << 22;
+// the budget the next launches take (api.cu)
+uint32_t wait_budget();
 
 struct Plan {
     int nwn = 0, nwl = 0;           // node / other words

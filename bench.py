@@ -88,14 +88,17 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
+# the sources that decide a profiled kernel's code and the tables it reads
 KERNEL_SOURCES = ("sum_kernel.cuh", "kernel_core.cuh", "kernel.cu", "kernel_count.cu", "zring.h",
-                  "plan.cpp", "inner.cu", "split.cpp")
+                  "plan.h", "plan.cpp", "split.cpp")
+INNER_SOURCES = ("inner.cu", "zring.h", "plan.h", "plan.cpp", "split.cpp")
 
 
-def kernel_source_sha() -> str:
-    """Hash of the sources that decide the sum kernel's code and tables."""
+def kernel_source_sha(sources=KERNEL_SOURCES) -> str:
+    """Hash of the sources that decide the sum kernel's code and tables
+    (or, with INNER_SOURCES, the inner table's)."""
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         h.update(open(os.path.join(ROOT, "paper_2403_06777_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
@@ -331,13 +334,34 @@ def run_reference(args, world, rank):
     }))
 
 
-def wht_passes(k_inner: int) -> int:
-    """Launches of the inner table's transform (inner.cu: 10 bits, then 5)."""
-    n, lo = 0, 0
-    while lo < k_inner:
-        lo += 10 if lo == 0 else 5
-        n += 1
-    return n
+def inner_launches(k_inner: int) -> int:
+    """Launches that build an inner table (inner.cu): the term kernel with
+    the low 10 bits, then passes of at most 10 bits."""
+    return 1 + (max(k_inner - 10, 0) + 9) // 10
+
+
+def inner_roofline(inner_bits: int, k_inner: int, seconds: float, prof):
+    """HBM roofline of the inner table: every pass reads and writes the
+    table once, the term kernel writes it once (32 bytes per entry)."""
+    table = 32 << inner_bits
+    passes = inner_launches(k_inner) - 1
+    alg = table * (1 + 2 * passes)
+    peak = measured_peaks().get("hbm_gbs")
+    ach = alg / seconds / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": None if not peak else ach / peak, "algorithmic_bytes": alg,
+            "traffic": profile_number(prof, "dram_bytes_per_step"),
+            "table_bytes": table, "passes": passes,
+            "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+            "source": "profiles/inner_table_large80.txt"}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 def issue_peak(torch, dev: int, sm_max_mhz):
@@ -683,7 +707,8 @@ def main():
                                      "frac": None if roof["achieved"] is None else roof["achieved"] * 1e12 / mix,
                                      "basis": "integer microbenchmark (zxp_int_peak kind 4): logic and "
                                               "multiply-add chains in turn on a full grid"}
-    launches_per_step = (1 + wht_passes(ki) + 1) if ki else 1
+    launches_per_step = (inner_launches(ki) + 1) if ki else 1
+    iprof = profile_fields(kernel_source_sha(INNER_SOURCES), "inner_table_large80.txt")
 
     line = {
         "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world,
@@ -701,6 +726,7 @@ def main():
         "terms_per_s": terms / walk_s,
         "stabilizer_terms_per_s": stab_terms * value / world,
         "roofline": roof,
+        "inner_roofline": inner_roofline(info["inner_bits"], ki, inner_s, iprof) if ki else None,
         "e2e": {"value": 1 / e2e_sec, "unit": "amplitudes/s",
                 "h2d_bytes_per_step": info["upload_bytes"], "d2h_bytes_per_step": 40,
                 "requests_in_flight": E2E_DEPTH, "steps": e2e_steps},

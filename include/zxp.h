@@ -309,16 +309,15 @@ int zxp_eval_wide(zxp_ctx *ctx, const zxp_scalar *s, uint64_t first, uint64_t co
 int zxp_sum_resumable(zxp_ctx *ctx, const zxp_scalar *s, uint32_t chunk_log2, const char *path,
                       uint64_t max_chunks, zxp_zomega *out, uint64_t *chunks_done, uint64_t *chunks_total);
 
-/* Bounded table waits, for tests and diagnostics (no counterpart in the
- * paper).  Every block of a sum kernel waits for the bulk copies of its
- * tables into shared memory a bounded number of times (by default several
- * seconds in all); a block that gives up skips its terms, still waits
- * (bounded) for its copies to land, and marks the launch's result (flags
- * bit 1), which the host entry points report as ZXP_ETIMEDOUT.  This sets
- * the number of waits the launches queued from now on make in this process:
- * 0 gives up before the first look, tries < 0 restores the default.
- * ZXP_EINVAL above the default. */
-int zxp_set_wait_budget(int64_t tries);
+/* Bounded table waits, for tests (no counterpart in the paper).  Every
+ * block of a single-scalar sum kernel waits a bounded time (about a second)
+ * for the bulk copies of its tables into shared memory; a block that gives
+ * up skips its terms and marks the launch's result (flags bit 1), which the
+ * host entry points report as ZXP_ETIMEDOUT.  enable != 0: the launches
+ * queued from now on in this process expect 16 bytes more than their copies
+ * deliver, so every block's wait runs to its limit (long after its copies
+ * have landed) and gives up; enable = 0 restores normal launches. */
+int zxp_test_table_timeout(int enable);
 
 /* The whole sum modulo 2^128, canonical: exact for e0 <= 252 (the
  * numerator's coefficients are below 2^126 in magnitude).  ZXP_EOVERFLOW

@@ -168,7 +168,7 @@ def lib():
         L.zxp_server_stats.argtypes = [vp, C.POINTER(zxp_server_stats_t)]
         L.zxp_server_destroy.argtypes, L.zxp_server_destroy.restype = [vp], None
         L.zxp_int_peak.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
-        L.zxp_set_wait_budget.argtypes = [i64]
+        L.zxp_test_table_timeout.argtypes = [C.c_int]
         L.zxp_zomega_add.argtypes = [zp, zp, zp]
         L.zxp_zomega_canon.argtypes = [zp, zp]
         L.zxp_zomega_to_complex.argtypes = [zp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -503,11 +503,11 @@ def zxp_poll(ctx: Ctx, ticket: int, timeout_us: int = -1):
     return out.tup()
 
 
-def zxp_set_wait_budget(tries: int):
-    """Waits a block makes for its table copies before it gives up (the
-    launch's host call then reports ZXP_ETIMEDOUT), for the launches queued
-    from now on; tries < 0 restores the default."""
-    _check(lib().zxp_set_wait_budget(tries), "zxp_set_wait_budget")
+def zxp_test_table_timeout(enable: bool):
+    """Tests: make every block's bounded wait for its table copies of the
+    launches queued from now on run out (their host calls then report
+    ZXP_ETIMEDOUT), or restore normal launches."""
+    _check(lib().zxp_test_table_timeout(1 if enable else 0), "zxp_test_table_timeout")
 
 
 class Batch:

@@ -292,16 +292,15 @@ int zxp::make_scalar(PS&& ps, zxp_scalar** out) {
 
 namespace zxp {
 namespace {
-std::atomic<uint32_t> g_wait_tries{kDefaultWaitTries};
+std::atomic<uint32_t> g_extra_tx{0};
 }  // namespace
-uint32_t wait_budget() { return g_wait_tries.load(std::memory_order_relaxed); }
+uint32_t test_extra_tx() { return g_extra_tx.load(std::memory_order_relaxed); }
 }  // namespace zxp
 
 extern "C" {
 
-int zxp_set_wait_budget(int64_t tries) {
-    if (tries > (int64_t)kDefaultWaitTries) return ZXP_EINVAL;
-    g_wait_tries.store(tries < 0 ? kDefaultWaitTries : (uint32_t)tries, std::memory_order_relaxed);
+int zxp_test_table_timeout(int enable) {
+    g_extra_tx.store(enable ? 16u : 0u, std::memory_order_relaxed);
     return ZXP_OK;
 }
 

@@ -82,7 +82,7 @@ cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, cons
     KernelParams kp = pl.kp;
     kp.zqcol = dzq;
     kp.ftab = dftab;
-    kp.wait_tries = wait_budget();
+    kp.extra_tx = test_extra_tx();
     const uint64_t nslices = (count + span - 1) / span;
     fn<<<grid, block_threads(pl), smem, stream>>>(kp, dtable, dpv, dF, dADJ, dS, first, count, span, nslices,
                                          acc, counter, pl.K, pl.e0, result, host_result ? 1 : 0);

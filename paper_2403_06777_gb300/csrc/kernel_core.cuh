@@ -249,7 +249,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 // Each try_wait suspends the thread for a bounded time; kDefaultWaitTries
-// of them (several seconds in all) end a wait that would otherwise never end.
+// of them (about a second in all) end a wait that would otherwise never end.
 constexpr uint32_t kWaitTries = kDefaultWaitTries;
 
 __device__ __forceinline__ uint32_t round16(uint32_t b) { return (b + 15u) & ~15u; }
@@ -273,7 +273,9 @@ __device__ __forceinline__ void issue_tables(const KernelParams& p, const Smem& 
     // order the shared-memory reads of a previous scalar before the
     // asynchronous writes
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(bar, bt + bs + br + ba + bpv + bl);
+    // (p.extra_tx: bytes that no copy delivers, 0 unless a test asks for a
+    // wait that runs out)
+    mbar_expect_tx(bar, bt + bs + br + ba + bpv + bl + p.extra_tx);
     if (bt) bulk_copy(sm.sT, gtable, bt, bar);
     if (bs) bulk_copy(sm.sS, gS, bs, bar);
     if (br) bulk_copy(sm.sF, gR, br, bar);
@@ -285,20 +287,13 @@ __device__ __forceinline__ void issue_tables(const KernelParams& p, const Smem& 
 // Wait (bounded) for the copies of issue_tables: the barrier's phase
 // `phase` (the loads so far; advanced here).  Every thread calls it, after
 // a block barrier that follows the barrier's initialisation.  Returns false
-// if the wait gave up after p.wait_tries waits (the tables are then not
-// valid).  Variables 0..2 beyond k get zero adjacency rows.
+// if the wait gave up (the tables are then not valid).  Variables 0..2
+// beyond k get zero adjacency rows.
 __device__ __forceinline__ bool wait_tables(const KernelParams& p, const Smem& sm, uint64_t* bar,
                                             uint32_t& phase) {
     bool ok = false;
-    for (uint32_t i = 0; i < p.wait_tries; i++)
+    for (uint32_t i = 0; i < kWaitTries; i++)
         if (mbar_try_wait(bar, phase & 1u)) { ok = true; break; }
-    if (!ok) {
-        // given up: the tables are not used, but copies still in flight
-        // write into this block's shared memory, so wait (bounded) for them
-        // to land before the block goes on and ends
-        for (uint32_t i = 0; i < kWaitTries; i++)
-            if (mbar_try_wait(bar, phase & 1u)) break;
-    }
     phase++;
     if (threadIdx.x < 3 && threadIdx.x >= p.k) sm.sADJ[threadIdx.x] = 0;
     return ok;

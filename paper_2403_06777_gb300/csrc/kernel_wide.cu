@@ -110,7 +110,7 @@ cudaError_t sum_launch_wide(const Plan& pl, const zw128* dtab_w, const zw128* dp
     kp.tab_size = 8u * kp.tab_stride;   // the (J, M) table
     kp.zqcol = dzq;
     kp.ftab = reinterpret_cast<const zw64*>(dftab_w);
-    kp.wait_tries = wait_budget();
+    kp.extra_tx = test_extra_tx();
     const size_t smem = smem_bytes(kp.tab_size, kp.npairs, pl.nwn, nwl, 0, kWideThreads, k_cap(kp.k), 0, 2);
     cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(fn), smem);
     if (e != cudaSuccess) return e;

@@ -36,7 +36,6 @@ int build_plain_plan(const PS& ps, bool allow_lut, bool lane_only, Plan* out) {
     memset(&pl.kp, 0, sizeof pl.kp);
     KernelParams& kp = pl.kp;
     kp.zq_lo = 64;
-    kp.wait_tries = kDefaultWaitTries;
     const uint32_t k = ps.k;
     if (k > (uint32_t)kMaxK) return ZXP_ETOOBIG;
     kp.k = k;

@@ -99,16 +99,19 @@ struct KernelParams {
     uint32_t zq_lo;
     const uint32_t* zqcol;   // device addresses, set at launch
     const zw64* ftab;
-    // Bounded waits a block makes for its table copies before it gives up
-    // (kDefaultWaitTries unless a test lowered it: zxp_set_wait_budget).
-    uint32_t wait_tries;
+    // Bytes the table copies' barrier expects beyond those the copies
+    // deliver: 0, or 16 when a test makes every block's bounded wait run out
+    // (zxp_test_table_timeout).  The copies themselves are unchanged, so they
+    // have landed long before the wait gives up.
+    uint32_t extra_tx;
 };
 
-// each wait suspends the thread for a bounded time: this many of them are
-// several seconds in all
-constexpr uint32_t kDefaultWaitTries = 1u << 22;
-// the budget the next launches take (api.cu)
-uint32_t wait_budget();
+// each wait suspends the thread for a bounded time (about 4 us measured on a
+// GB300): this many of them are about a second in all, against microseconds
+// for any table copy
+constexpr uint32_t kDefaultWaitTries = 1u << 18;
+// extra_tx for the launches queued now (api.cu)
+uint32_t test_extra_tx();
 
 struct Plan {
     int nwn = 0, nwl = 0;           // node / other words

@@ -283,6 +283,13 @@ def param_bench(Z, ctx, zi, n_values=(1, 4, 16, 64, 256, 1024), seed=0):
                      "(all host threads; 1thread: one worker), same GPU path"}
 
 
+def free_port() -> int:
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        return so.getsockname()[1]
+
+
 def setup_dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -411,6 +418,64 @@ def timed_amplitude(torch, Z, ctx, s, stream, out, flush, steps, sampler_dev):
     return inner, walk, clk.summary()
 
 
+def timed_sharded(torch, Z, dist, ctx, s, stream, flush, steps, world, rank, sampler_dev, ref):
+    """steps amplitudes of s, each one sharded over the ranks: every rank
+    builds the inner table and walks its share of the outer range
+    (dist.shard_range), and the 40-byte raw partials are all-gathered over
+    NCCL on the stream (no peer memory in any kernel); returns per-step
+    (inner, walk, all-gather) ms and the clocks, after checking that the
+    combined last step equals the reference amplitude exactly."""
+    from paper_2403_06777_gb300 import dist as zd
+    k = Z.zxp_scalar_info(s)["k"]
+    first, count = zd.shard_range(k, world, rank)
+    out = torch.zeros(5, dtype=torch.int64, device="cuda")
+    gathered = [torch.empty_like(out) for _ in range(world)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    torch.cuda.synchronize()
+    dist.barrier()
+    with ClockSampler(sampler_dev) as clk:
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            Z.zxp_inner_sum(ctx, s)
+            ev[i][1].record(stream)
+            Z.zxp_eval_device(ctx, s, first, count, out.data_ptr())
+            ev[i][2].record(stream)
+            dist.all_gather(gathered, out)
+            ev[i][3].record(stream)
+        torch.cuda.synchronize()
+    parts = []
+    for g in gathered:
+        v = g.tolist()
+        parts.append((v[0], v[1], v[2], v[3], v[4] & 0xFFFFFFFF))
+    got = Z.zxp_zomega_canon(zd.combine(parts))
+    assert got == ref, (got, ref)
+    return ([e[0].elapsed_time(e[1]) for e in ev], [e[1].elapsed_time(e[2]) for e in ev],
+            [e[2].elapsed_time(e[3]) for e in ev], clk.summary())
+
+
+def sharded_requests(torch, Z, dist, blob, ctx, n, world, rank, ref):
+    """n sharded amplitudes through the public host API; returns seconds per
+    amplitude (max over ranks)."""
+    from paper_2403_06777_gb300 import dist as zd
+    dev = torch.device("cuda", torch.cuda.current_device())
+    dist.barrier()
+    t = time.perf_counter()
+    for _ in range(n):
+        s = Z.zxp_scalar_from_tables(blob)
+        k = Z.zxp_scalar_info(s)["k"]
+        first, count = zd.shard_range(k, world, rank)
+        part = Z.zxp_eval(ctx, s, first, count)
+        mine = torch.tensor([zd._i64(v) for v in part], dtype=torch.int64).to(dev)
+        out = [torch.empty_like(mine) for _ in range(world)]
+        dist.all_gather(out, mine)
+        got = Z.zxp_zomega_canon(zd.combine([tuple(int(x) for x in o.cpu().tolist()) for o in out]))
+        assert got == ref, (got, ref)
+    sec = torch.tensor([(time.perf_counter() - t) / n], dtype=torch.float64, device=dev)
+    dist.all_reduce(sec, op=dist.ReduceOp.MAX)
+    return float(sec.item())
+
+
 def stream_requests(Z, ctx, blob, n, depth=2):
     """n requests of the scalar with table bytes `blob` through the public
     host API (zxp_submit_tables, zxp_poll), `depth` in flight; returns the
@@ -482,6 +547,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shard", action="store_true",
+                    help="strong scaling: every amplitude's outer range split over the ranks")
     ap.add_argument("--profile", choices=PROFILE_CASES, help="run one kernel's short launch sequence")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -500,8 +567,13 @@ def main():
 
     torch.cuda.set_device(local)
     dist = None
-    if world > 1:
+    if world > 1 or args.shard:
         import torch.distributed as dist
+        if world == 1:   # one rank of its own (the sharded path with N = 1)
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            os.environ.setdefault("MASTER_PORT", str(free_port()))
+            os.environ.setdefault("RANK", "0")
+            os.environ.setdefault("WORLD_SIZE", "1")
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     # a dedicated stream: the library launches on it and the CUDA events are
@@ -531,21 +603,31 @@ def main():
     if dist:
         dist.barrier()
     wall0 = time.perf_counter()
-    inner_ms, walk_ms, clocks = timed_amplitude(torch, Z, ctx, s, stream, out, flush, args.steps, local)
+    gather_ms = []
+    walked = terms   # outer terms one rank walks per step
+    if args.shard:
+        from paper_2403_06777_gb300 import dist as zd
+        walked = zd.shard_range(k, world, rank)[1]
+        inner_ms, walk_ms, gather_ms, clocks = timed_sharded(torch, Z, dist, ctx, s, stream, flush, args.steps,
+                                                             world, rank, local, ref)
+    else:
+        inner_ms, walk_ms, clocks = timed_amplitude(torch, Z, ctx, s, stream, out, flush, args.steps, local)
     wall = time.perf_counter() - wall0
     if dist:
         dist.barrier()
-    # the device result of the last step must be the exact amplitude
-    r = out.tolist()
-    got = Z.zxp_zomega_canon((r[0], r[1], r[2], r[3], r[4] & 0xFFFFFFFF))
-    assert got == ref, (got, ref)
-    step_ms = sum(inner_ms) + sum(walk_ms)
+    if not args.shard:
+        # the device result of the last step must be the exact amplitude
+        r = out.tolist()
+        got = Z.zxp_zomega_canon((r[0], r[1], r[2], r[3], r[4] & 0xFFFFFFFF))
+        assert got == ref, (got, ref)
+    step_ms = sum(inner_ms) + sum(walk_ms) + sum(gather_ms)
     t_rank = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
     if dist:
         dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
     step_ms = float(t_rank.item())
     sec = step_ms / 1e3
-    value = args.steps * world / sec
+    # replicas: every rank one amplitude per step; sharded: one per step in all
+    value = args.steps / sec if args.shard else args.steps * world / sec
     walk_s = statistics.median(walk_ms) / 1e3
     inner_s = statistics.median(inner_ms) / 1e3
 
@@ -557,11 +639,18 @@ def main():
     # result is checked after the timed loop.
     E2E_DEPTH = 2
     e2e_steps = max(20, args.steps)
-    stream_requests(Z, ctx, blob, 3, E2E_DEPTH)
-    torch.cuda.synchronize()
-    e2e_sec, got = stream_requests(Z, ctx, blob, e2e_steps, E2E_DEPTH)
-    bad = sum(Z.zxp_zomega_canon(x) != ref for x in got)
-    assert bad == 0 and len(got) == e2e_steps, (bad, len(got))
+    if args.shard:
+        # sharded, through the public API: the scalar from its table bytes
+        # (host), this rank's range summed to a host result (zxp_eval), the
+        # 40-byte partials exchanged over NCCL and combined on the host
+        e2e_sec = sharded_requests(torch, Z, dist, blob, ctx, e2e_steps, world, rank, ref)
+        E2E_DEPTH = 1
+    else:
+        stream_requests(Z, ctx, blob, 3, E2E_DEPTH)
+        torch.cuda.synchronize()
+        e2e_sec, got = stream_requests(Z, ctx, blob, e2e_steps, E2E_DEPTH)
+        bad = sum(Z.zxp_zomega_canon(x) != ref for x in got)
+        assert bad == 0 and len(got) == e2e_steps, (bad, len(got))
 
     # ---- integer microbenchmark (the measured peak beside the issue peak) ----
     int_peak = None
@@ -698,7 +787,7 @@ def main():
     peak, sms, mhz = issue_peak(torch, local, clocks.get("sm_max_mhz"))
     sha = kernel_source_sha()
     prof = profile_fields(sha, "sum_kernel_large80.txt")
-    roof = roofline_from_profile(prof, terms, walk_s, peak, "profiles/sum_kernel_large80.txt")
+    roof = roofline_from_profile(prof, walked, walk_s, peak, "profiles/sum_kernel_large80.txt")
     roof["sms"] = sms
     roof["sm_max_mhz"] = mhz
     if int_peak:
@@ -713,18 +802,21 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-        "data": "synthetic",
+        "higher_is_better": True, "scaling": "strong" if args.shard else "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic",
         "config": {"workload": f"{w.name} seed={args.seed}: one exact amplitude per step "
                                "(inner table + Gray-code walk over the outer parameters)",
                    "k": k, "k_inner": ki, "inner_bits": info["inner_bits"],
                    "walked_terms_per_step": terms, "stabilizer_terms_per_step": stab_terms,
                    "t_count": info["t_count"], "kernel_variant": info["kernel_variant"],
                    "compile_ms": compile_ms, "l2": "flushed (256 MB write) between timed steps",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": (f"dp{world}: every amplitude's outer range sharded over the ranks, "
+                                   "40-byte partials all-gathered (NCCL)") if args.shard
+                                  else f"replicas x{world}"},
         "ms_inner_table": inner_s * 1e3, "ms_walk": walk_s * 1e3,
-        "terms_per_s": terms / walk_s,
-        "stabilizer_terms_per_s": stab_terms * value / world,
+        "terms_per_s": walked / walk_s,
+        "stabilizer_terms_per_s": stab_terms * value,
+        "ms_allgather": statistics.median(gather_ms) if gather_ms else None,
         "roofline": roof,
         "inner_roofline": inner_roofline(info["inner_bits"], ki, inner_s, iprof) if ki else None,
         "e2e": {"value": 1 / e2e_sec, "unit": "amplitudes/s",

@@ -161,10 +161,10 @@ def cpu_baseline(blob: bytes, terms_per_amp: int, seconds: float = 10.0):
 SERVE_MAX_K = 38
 
 
-def serve_run(Z, ctx, reqs, policy, max_k):
-    """Replay the arrivals against one server; per-request latency is the
-    library's own submit-to-value time."""
-    srv = Z.zxp_server_create(ctx, policy=policy, max_k=max_k)
+def serve_run(Z, ctx, reqs, policy, max_k, **opts):
+    """Replay the arrivals against one server (zxp_server_opts fields in
+    opts); per-request latency is the library's own submit-to-value time."""
+    srv = Z.zxp_server_create(ctx, policy=policy, max_k=max_k, **opts)
     warm = [Z.zxp_server_submit(srv, r["gb"], r["n"], r["bits"], marg_mask=r["mask"],
                                 kind=r["kind"]) for r in reqs[:16]]
     for t in warm:
@@ -201,18 +201,47 @@ def serve_run(Z, ctx, reqs, policy, max_k):
     return out, [v for rc, v, _ in res]
 
 
-def serve_bench(Z, ctx, zi, n_req: int, rate_hz: float, max_k: int):
+SERVE_P99_SLO_MS = 20.0
+SERVE_SWEEP_HZ = (2000.0, 5000.0, 10000.0, 20000.0, 50000.0)
+
+
+def serve_bench(Z, ctx, zi, n_req: int, rate_hz: float, max_k: int, sweep=SERVE_SWEEP_HZ):
     reqs = zi.serve_requests(0, n_req, rate_hz)
     for r in reqs:
         r["gb"] = zi.pack_gates(r["gates"])
+    # one untimed pass of each policy over the whole mix: the first launch of
+    # every kernel variant loads its code (lazy module loading), which would
+    # otherwise land inside the first measured steps
+    serve_run(Z, ctx, reqs, Z.ZXP_SERVE_BATCHED, max_k)
+    serve_run(Z, ctx, reqs, Z.ZXP_SERVE_PLAIN, max_k)
     batched, vb = serve_run(Z, ctx, reqs, Z.ZXP_SERVE_BATCHED, max_k)
     plain, vp = serve_run(Z, ctx, reqs, Z.ZXP_SERVE_PLAIN, max_k)
     assert vb == vp, "served values differ between policies"
+    # arrival-rate sweep: the same request mix offered faster; a policy keeps
+    # up at a rate when it completes within 10 % of the offered rate with p99
+    # under the SLO; the knee is the highest such rate of the sweep
+    rows, knee = [], {}
+    for hz in sweep:
+        rq = zi.serve_requests(0, n_req, hz)
+        for r in rq:
+            r["gb"] = zi.pack_gates(r["gates"])
+        row = {"offered_hz": hz}
+        for name, pol in (("batched", Z.ZXP_SERVE_BATCHED), ("plain", Z.ZXP_SERVE_PLAIN)):
+            o, _ = serve_run(Z, ctx, rq, pol, max_k)
+            ok = o["amplitudes_per_s"] >= 0.9 * hz and o["p99_ms"] <= SERVE_P99_SLO_MS
+            row[name] = {"amplitudes_per_s": o["amplitudes_per_s"], "p50_ms": o["p50_ms"],
+                         "p99_ms": o["p99_ms"], "device_busy_ms": o["device_busy_ms"], "keeps_up": ok}
+            if ok:
+                knee[name] = max(knee.get(name, 0.0), hz)
+        rows.append(row)
     return {"workload": f"{n_req} requests, Poisson {rate_hz:.0f}/s, seed 0: amplitude and "
                         "single-qubit doubled-marginal, n~U[10,50], T~U[10,70]",
             "admission_max_k": max_k, "batched": batched,
             "plain_one_scalar_per_launch": plain,
-            "p99_plain_over_batched": plain["p99_ms"] / batched["p99_ms"]}
+            "device_busy_batched_over_plain": batched["device_busy_ms"] / plain["device_busy_ms"],
+            "p99_plain_over_batched": plain["p99_ms"] / batched["p99_ms"],
+            "sweep": rows, "p99_slo_ms": SERVE_P99_SLO_MS,
+            "knee_hz": {"batched": knee.get("batched"), "plain": knee.get("plain")}}
 
 
 def param_bench(Z, ctx, zi, n_values=(1, 4, 16, 64, 256, 1024), seed=0):

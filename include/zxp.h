@@ -443,10 +443,10 @@ typedef struct {
     uint32_t compile_threads;    /* host compile workers (0: hardware threads, at most 16) */
     uint32_t max_active;         /* requests resident on the device (0: 4096) */
     uint64_t arena_bytes;        /* device memory for resident tables (0: 64 MiB) */
-    uint64_t step_terms;         /* term budget of one step (0: 2^28) */
+    uint64_t step_terms;         /* term budget of one step (0: 2^30) */
     uint64_t small_terms;        /* requests with at most this many terms left run whole (0: 2^22) */
-    uint32_t chunk_log2;         /* chunk length 2^chunk_log2 terms (0: 16) */
-    uint32_t threads;            /* threads per block of the batch kernel (0: 256) */
+    uint32_t chunk_log2;         /* chunk length 2^chunk_log2 terms (0: 20) */
+    uint32_t threads;            /* threads per block of the batch kernel (0: 128) */
     uint32_t reserved[8];
 } zxp_server_opts;
 

@@ -520,7 +520,20 @@ def stream_requests(Z, ctx, blob, n, depth=2):
     return (time.perf_counter() - t) / n, got
 
 
-PROFILE_CASES = ("large80", "large80_1g", "inner", "medium", "large37", "peak")
+PROFILE_CASES = ("large80", "large80_1g", "inner", "medium", "large37", "peak", "synth36")
+
+# the k = 36 stand-in: synthetic tables with the statistics of compiled
+# scalars of k 34-40 (n = 40-50, 1500-2000 gates, T 50-55, 23 scalars:
+# 48 linear, 36 quadratic, 10 odd node rows, mask densities 0.10 / 0.14 /
+# 0.16, about 0.13 over all masks), drawn order and relabelled
+SYNTH36 = dict(seed=3601, k=36, n_lin=48, n_quad=36, n_node=10, odd_nodes_only=True, density=0.13)
+
+
+def synth36_scalars(Z, zi):
+    p = dict(SYNTH36)
+    ps = zi.synthetic_ps(p.pop("seed"), p.pop("k"), **p)
+    s = Z.zxp_scalar_from_tables(ps.pack())
+    return s, Z.zxp_scalar_reorder(s)
 
 
 def run_profile_case(case: str):
@@ -532,7 +545,9 @@ def run_profile_case(case: str):
       inner    the large workload's amplitude, then its inner table again
       medium   three amplitudes of the medium workload
       large37  one 2^30-term launch of the unsplit n=50 / T=50 scalar (k = 37)
-      peak     the integer microbenchmark, every kind once"""
+      peak     the integer microbenchmark, every kind once
+      synth36  one 2^32-term launch of the k = 36 stand-in, drawn order, then
+               relabelled"""
     import torch
     import paper_2403_06777_gb300 as Z
     import zxp_inputs as zi
@@ -561,6 +576,10 @@ def run_profile_case(case: str):
         s = Z.zxp_compile(w.gates, w.n, w.out_bits, split=False)
         rec["partial"] = Z.zxp_eval(ctx, s, 0, 1 << 30)
         rec["info"] = Z.zxp_scalar_info(s)
+    elif case == "synth36":
+        raw, re = synth36_scalars(Z, zi)
+        rec["variants"] = [raw.info["kernel_variant"], re.info["kernel_variant"]]
+        rec["partials"] = [Z.zxp_eval(ctx, raw, 0, 1 << 32), Z.zxp_eval(ctx, re, 0, 1 << 32)]
     else:
         rec["int_peak"] = {kind: Z.zxp_int_peak(ctx, kind) for kind in range(5)}
     torch.cuda.synchronize()
@@ -726,6 +745,29 @@ def main():
                   "roofline": roofline_from_profile(profile_fields(kernel_source_sha(), "sum_kernel_medium.txt"),
                                                     nm, ms_m / 1e3, peak_m, "profiles/sum_kernel_medium.txt")}
 
+    # ---- the k = 36 stand-in with compiled statistics, drawn and relabelled ---
+    synth = None
+    if rank == 0 and not os.environ.get("ZXP_BENCH_SKIP_LARGE"):
+        raw, re = synth36_scalars(Z, zi)
+        synth = {"workload": "synthetic k=36 tables with compiled k 34-40 statistics " + json.dumps(SYNTH36)}
+        for tag, sc, n in (("drawn_order", raw, 1 << 34), ("relabelled", re, 1 << 36)):
+            Z.zxp_eval_device(ctx, sc, 0, 1 << 24, out.data_ptr())
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            Z.zxp_eval_device(ctx, sc, 0, n, out.data_ptr())
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            synth[tag] = {"kernel_variant": sc.info["kernel_variant"], "terms": n, "ms": ms,
+                          "terms_per_s": n / (ms / 1e3),
+                          "instructions_per_term": profile_number(
+                              profile_fields(kernel_source_sha(), "sum_kernel_synthetic36.txt"),
+                              "instructions_per_term_" + tag)}
+        # relabelling keeps the sum: the full sum of both orders
+        synth["same_full_sum"] = Z.zxp_zomega_canon(Z.zxp_eval(ctx, raw)) == Z.zxp_zomega_canon(Z.zxp_eval(ctx, re))
+        assert synth["same_full_sum"]
+
     # ---- the unsplit sum kernel at k = 37 (n = 50, 2000 gates, T = 50) -------
     unsplit = None
     if rank == 0 and not os.environ.get("ZXP_BENCH_SKIP_LARGE"):
@@ -860,6 +902,8 @@ def main():
         line["medium"] = medium
     if unsplit:
         line["unsplit_k37"] = unsplit
+    if synth:
+        line["synthetic_k36"] = synth
     if batch:
         line["batch"] = batch
     if serving:

@@ -209,6 +209,17 @@ typedef struct zxp_split_opts_s {
  * Errors: ZXP_EINVAL (s already split, bad options), ZXP_ENOMEM. */
 int zxp_scalar_split(const zxp_scalar *s, const zxp_split_opts *opts, zxp_scalar **out);
 
+/* Relabel a scalar's parameters (host only): the sum over all of them
+ * (Eq. 2) does not depend on their order, but the Gray-code walk flips
+ * parameters 0-2 in every aligned block of 8 steps, and its block lookup
+ * (one table read per 8 terms) applies only when few parity forms hold them
+ * and no phase-pair or zero-test form does.  *out has the same value as s,
+ * with the four parameters that touch the fewest forms (phase-pair and
+ * zero-test forms last) moved to positions 0-3 and the others in their
+ * order; range partials of *out refer to the new order.  Scalars with inner
+ * parameters: ZXP_EINVAL (reorder before splitting).  ZXP_ENOMEM. */
+int zxp_scalar_reorder(const zxp_scalar *s, zxp_scalar **out);
+
 /* Queue the computation of a split scalar's inner table on the context's
  * stream (a no-op for other scalars).  Evaluations do this once per device
  * by themselves; calling it again recomputes the table (e.g. to time it). */

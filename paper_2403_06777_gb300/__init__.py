@@ -133,6 +133,7 @@ def lib():
         L.zxp_scalar_info.argtypes = [vp, C.POINTER(zxp_scalar_info_t)]
         L.zxp_scalar_free.argtypes, L.zxp_scalar_free.restype = [vp], None
         L.zxp_scalar_split.argtypes = [vp, C.POINTER(zxp_split_opts), C.POINTER(vp)]
+        L.zxp_scalar_reorder.argtypes = [vp, C.POINTER(vp)]
         L.zxp_inner_sum.argtypes = [vp, vp]
         L.zxp_eval.argtypes = [vp, vp, u64, u64, zp]
         L.zxp_amplitude.argtypes = [vp, vp, zp]
@@ -395,6 +396,14 @@ def zxp_scalar_split(s: Scalar, **opts) -> Scalar:
     o = _split_opts(opts)
     h = C.c_void_p()
     _check(lib().zxp_scalar_split(s.handle, C.byref(o) if opts else None, C.byref(h)), "zxp_scalar_split")
+    return Scalar(h.value)
+
+
+def zxp_scalar_reorder(s: Scalar) -> Scalar:
+    """The same scalar with the parameters that touch the fewest parity
+    forms moved to positions 0-3 (the block lookup's parameters)."""
+    h = C.c_void_p()
+    _check(lib().zxp_scalar_reorder(s.handle, C.byref(h)), "zxp_scalar_reorder")
     return Scalar(h.value)
 
 

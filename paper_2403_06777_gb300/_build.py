@@ -18,7 +18,8 @@ LIB = os.path.join(HERE, "libzxp.so")
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-HOST_SRC = ["ps.cpp", "compile.cpp", "param.cpp", "plan.cpp", "sample.cpp", "split.cpp", "checkpoint.cpp"]
+HOST_SRC = ["ps.cpp", "compile.cpp", "param.cpp", "plan.cpp", "sample.cpp", "split.cpp", "checkpoint.cpp",
+            "reorder.cpp"]
 CUDA_SRC = ["kernel.cu", "kernel_count.cu", "kernel_wide.cu", "batch.cu", "batch_count.cu", "api.cu", "serve.cu",
             "inner.cu", "peak.cu"]
 

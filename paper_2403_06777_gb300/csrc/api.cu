@@ -439,6 +439,15 @@ int zxp_scalar_split(const zxp_scalar* s, const zxp_split_opts* opts, zxp_scalar
     return make_scalar(std::move(ps), out);
 }
 
+int zxp_scalar_reorder(const zxp_scalar* s, zxp_scalar** out) {
+    if (!s || !out) return ZXP_EINVAL;
+    *out = nullptr;
+    PS ps;
+    const int st = reorder_scalar(s->ps, &ps);
+    if (st != ZXP_OK) return st;
+    return make_scalar(std::move(ps), out);
+}
+
 int zxp_inner_sum(zxp_ctx* ctx, const zxp_scalar* s) {
     if (!ctx || !s) return ZXP_EINVAL;
     if (!s->ps.k_inner) return ZXP_OK;

@@ -45,4 +45,9 @@ int ps_from_blob(const void* blob, size_t nbytes, PS* out);
 size_t ps_blob_size(const PS& ps);
 void ps_to_blob(const PS& ps, void* buf);
 
+// The same scalar with its parameters relabelled so that the four that
+// touch the fewest parity forms (phase-pair and zero-test forms last) come
+// first (reorder.cpp); k_inner must be 0 (else ZXP_EINVAL).
+int reorder_scalar(const PS& in, PS* out);
+
 }  // namespace zxp

@@ -213,11 +213,14 @@ int zxp_scalar_split(const zxp_scalar *s, const zxp_split_opts *opts, zxp_scalar
  * (Eq. 2) does not depend on their order, but the Gray-code walk flips
  * parameters 0-2 in every aligned block of 8 steps, and its block lookup
  * (one table read per 8 terms) applies only when few parity forms hold them
- * and no phase-pair or zero-test form does.  *out has the same value as s,
- * with the four parameters that touch the fewest forms (phase-pair and
- * zero-test forms last) moved to positions 0-3 and the others in their
- * order; range partials of *out refer to the new order.  Scalars with inner
- * parameters: ZXP_EINVAL (reorder before splitting).  ZXP_ENOMEM. */
+ * and no phase-pair or zero-test form does.  *out has the same value as s:
+ * the three parameters whose forms together are fewest (among those no
+ * phase-pair or zero-test form holds, where possible) moved to positions
+ * 0-2, the next lightest to 3, the others in their order, when that gives
+ * the better block lookup (one table before two, two before none); else a
+ * copy of s.  Range partials of *out refer to its order.  Scalars with inner
+ * parameters: ZXP_EINVAL (their split already chooses the lowest outer
+ * parameters so).  ZXP_ENOMEM. */
 int zxp_scalar_reorder(const zxp_scalar *s, zxp_scalar **out);
 
 /* Queue the computation of a split scalar's inner table on the context's

@@ -4,15 +4,20 @@
 // parameters, but the Gray-code walk does: parameters 0, 1 and 2 flip in
 // every aligned block of 8 steps, and the block lookup that costs one
 // table read per 8 terms applies only when few parity forms hold them and
-// none of them is a phase-pair or zero-test form.  This moves the four
-// parameters that touch the fewest forms (and none of those two kinds where
-// possible) to positions 0-3, keeping the others in their order.
+// none of them is a phase-pair or zero-test form.  This moves to positions
+// 0-2 the three parameters whose forms, together, are fewest (among the
+// parameters that no phase-pair or zero-test form holds, where possible),
+// then the next lightest parameter to position 3, keeping the others in
+// their order; the new order is kept only when its plan has the better
+// block lookup (one table before two, two before none), else the scalar is
+// returned as it is.
 #include <stdint.h>
 
 #include <algorithm>
 #include <numeric>
 #include <vector>
 
+#include "plan.h"
 #include "ps.h"
 #include "zxp.h"
 
@@ -32,14 +37,20 @@ uint64_t relabel(uint64_t m, const std::vector<uint32_t>& perm) {   // perm[new]
 int reorder_scalar(const PS& in, PS* out) {
     if (in.k_inner) return ZXP_EINVAL;
     const uint32_t k = in.k;
+    // the forms (rows with a parity mask) that hold each parameter, as bit sets
+    const size_t nf = in.lin.size() + in.node.size() + in.pair.size(), words = (nf + 63) / 64;
+    std::vector<std::vector<uint64_t>> held(k, std::vector<uint64_t>(words, 0));
     std::vector<uint32_t> cost(k, 0);
     std::vector<uint8_t> blocked(k, 0);
+    size_t f = 0;
     auto add = [&](uint64_t m, bool block) {
         for (uint32_t i = 0; i < k; i++)
             if ((m >> i) & 1) {
                 cost[i]++;
+                held[i][f >> 6] |= 1ull << (f & 63);
                 if (block) blocked[i] = 1;
             }
+        f++;
     };
     for (const LinRow& r : in.lin) add(r.mask, false);
     // zero tests: 1 + w^(0 or 4 + 4 l)
@@ -51,8 +62,28 @@ int reorder_scalar(const PS& in, PS* out) {
         if (blocked[a] != blocked[b]) return blocked[a] < blocked[b];
         return cost[a] < cost[b];
     });
-    const uint32_t nlow = k < 4 ? k : 4;
-    std::vector<uint32_t> perm(order.begin(), order.begin() + nlow);
+    // the triple with the fewest forms in all, among the lightest candidates
+    const uint32_t nc = k < 16 ? k : 16;
+    std::vector<uint32_t> best;
+    size_t best_u = ~(size_t)0;
+    for (uint32_t a = 0; a < nc; a++)
+        for (uint32_t b = a + 1; b < nc; b++)
+            for (uint32_t c = b + 1; c < nc; c++) {
+                const uint32_t x = order[a], y = order[b], z = order[c];
+                const size_t u0 = (size_t)blocked[x] + blocked[y] + blocked[z];
+                size_t u = 0;
+                for (size_t w = 0; w < words; w++)
+                    u += (size_t)__builtin_popcountll(held[x][w] | held[y][w] | held[z][w]);
+                u += u0 << 32;   // unblocked triples first
+                if (u < best_u) {
+                    best_u = u;
+                    best = {x, y, z};
+                }
+            }
+    if (best.empty()) best.assign(order.begin(), order.begin() + (k < 3 ? k : 3));
+    std::vector<uint32_t> perm = best;
+    for (uint32_t i : order)
+        if (perm.size() < (k < 4 ? k : 4) && std::find(perm.begin(), perm.end(), i) == perm.end()) perm.push_back(i);
     std::vector<uint8_t> low(k, 0);
     for (uint32_t i : perm) low[i] = 1;
     for (uint32_t i = 0; i < k; i++)
@@ -68,7 +99,14 @@ int reorder_scalar(const PS& in, PS* out) {
         r.ma = relabel(r.ma, perm);
         r.mb = relabel(r.mb, perm);
     }
-    *out = std::move(ps);
+    // keep the new order only when its block lookup is better
+    auto rank = [](const PS& p) {
+        Plan pl;
+        if (build_plan(p, &pl) != ZXP_OK) return 0;
+        return pl.lut_ok ? (pl.lut_two ? 2 : 3) : 1;
+    };
+    if (rank(ps) > rank(in)) *out = std::move(ps);
+    else *out = in;
     return ZXP_OK;
 }
 

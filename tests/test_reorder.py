@@ -1,12 +1,11 @@
 """zxp_scalar_reorder (host, no GPU): relabelling a scalar's parameters.
 
 The relabelled scalar has the same rows with their masks' bits permuted by
-one permutation of the parameters (checked row by row here, the permutation
-recovered from the linear rows), so every full sum is unchanged: the oracle
-sums both exactly.  The four lowest parameters of the new order touch the
-fewest forms, and no phase-pair or zero-test form holds parameters 0-3 when
-another choice exists; for scalars with the statistics of compiled k ~ 36-40
-scalars that is what lets the block lookup apply."""
+one permutation of the parameters (checked here: the columns of the masks
+are the same multiset), so every full sum is unchanged: the oracle sums both
+exactly.  A new order is kept only when its plan has the better block lookup
+(else the scalar comes back as it is); for scalars with the statistics of
+compiled k ~ 36-40 scalars that is what lets the block lookup apply."""
 import os
 
 import pytest
@@ -16,15 +15,6 @@ import paper_2403_06777_gb300 as Z
 import zxp_inputs as zi
 
 NCPU = os.cpu_count() or 4
-
-
-def bits(m):
-    return [i for i in range(64) if (m >> i) & 1]
-
-
-def touch(ps, i):
-    n = sum(1 for m, _ in ps.lin if (m >> i) & 1) + sum(1 for m, _ in ps.node if (m >> i) & 1)
-    return n + sum(1 for ma, _, mb, _ in ps.pair if ((ma | mb) >> i) & 1)
 
 
 @pytest.mark.parametrize("seed,k,n_pair", [(1, 10, 0), (2, 12, 2), (3, 9, 1), (4, 3, 0), (5, 14, 3)])
@@ -43,15 +33,12 @@ def test_reorder_is_a_relabelling_with_the_same_sum(seed, k, n_pair):
                 for j in range(k)}
     assert sorted(cols_old.values()) == sorted(cols_new.values())
     assert [c for _, c in q.lin] == [c for _, c in ps.lin] and [g for _, g in q.node] == [g for _, g in ps.node]
-    # the four lowest parameters touch the fewest forms
-    if k > 4:
-        low = max(touch(q, j) for j in range(4))
-        blocked = lambda p, i: any(((ma | mb) >> i) & 1 for ma, _, mb, _ in p.pair) or \
-            any((m >> i) & 1 and g % 4 == 0 for m, g in p.node)
-        free = [i for i in range(k) if not blocked(q, i)]
-        if len(free) >= 4:
-            assert all(not blocked(q, j) for j in range(4))
-            assert low <= sorted(touch(q, i) for i in free)[3]
+    # unchanged, or a better block lookup (variants 9-15 over none; one
+    # table, 9-11, over two, 13)
+    def rank(v):
+        return 1 if v < 9 else (2 if v == 13 else 3)
+    if q.pack() != ps.pack():
+        assert rank(r.info["kernel_variant"]) > rank(s.info["kernel_variant"])
     # the same value (brute force over all 2^k assignments, both orders)
     a = oracle.ps_sum(ps.pack(), 0, 1 << k, nthreads=NCPU)
     b = oracle.ps_sum(q.pack(), 0, 1 << k, nthreads=NCPU)

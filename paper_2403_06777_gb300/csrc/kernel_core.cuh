@@ -544,13 +544,27 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
             // net change: variable 2 flipped (Gray 000 -> 100), its forms, its
             // adjacency row and the block's phase change
             auto block8 = [&]() {
-                const uint64_t e = (TWO ? sL[us & ma] + sLB[us >> na] : sL[us]) + qlut[(uint32_t)a & 7u];
-                const uint32_t lo = (uint32_t)e, hi = (uint32_t)(e >> 32);
+                uint32_t lo, hi;
+                if constexpr (TWO) {
+                    // (the entries' byte sums never carry into the next byte,
+                    // so each 32-bit half adds on its own; with one table the
+                    // 64-bit form measured faster)
+                    const uint2 e1 = *reinterpret_cast<const uint2*>(sL + (us & ma));
+                    const uint2 e2 = *reinterpret_cast<const uint2*>(sLB + (us >> na));
+                    const uint2 eq = *reinterpret_cast<const uint2*>(qlut + ((uint32_t)a & 7u));
+                    lo = e1.x + e2.x + eq.x;
+                    hi = e1.y + e2.y + eq.y;
+                } else {
+                    const uint64_t e = sL[us] + qlut[(uint32_t)a & 7u];
+                    lo = (uint32_t)e;
+                    hi = (uint32_t)(e >> 32);
+                }
                 if constexpr (LANE) {
                     // the block's base (< 64) added to all offset bytes at once
                     // (each sum < 256: no carry between bytes) and every byte
                     // taken mod 8 * 2^tsh by one mask
-                    const uint32_t b0 = ((Jl & 7u) << tsh) + node_count();
+                    const uint32_t b0 = TWO ? (((Jl << tsh) & (7u << tsh)) | node_count())
+                                            : ((Jl & 7u) << tsh) + node_count();
                     const uint32_t bx = b0 * 0x01010101u, mk = cm * 0x01010101u;
                     const uint32_t w0 = (lo + bx) & mk, w1 = (hi + bx) & mk;
                     // (bytes by byte permutes: one instruction each, 5 % fewer

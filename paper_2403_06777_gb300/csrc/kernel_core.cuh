@@ -476,6 +476,10 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
             if (outer)
                 for (uint64_t m = x >> p.zq_lo; m; m &= m - 1)
                     zq ^= __ldg(p.zqcol + p.zq_lo + (uint32_t)__ffsll((long long)m) - 1u);
+            // the inner table at the current cut parities, loaded when they
+            // change, a whole run before the flush that uses it
+            zw64 fz = zw_zero();
+            if (outer) fz = ldg_zw(p.ftab + zq);
             // (lane-private counters have no folded bits, so the entry of
             // phase J is w^J times that of phase 0: for each node count the
             // eight counts combine into the integer element
@@ -498,13 +502,17 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                                                (uint64_t)(int64_t)(int32_t)(c[3] - c[7]));
                         sum = zw_add(sum, zw_mul(d, lds_zw(sT + Mi)));
                     }
-                    acc = zw_add(acc, zw_mul(sum, ldg_zw(p.ftab + zq)));
+                    acc = zw_add(acc, zw_mul(sum, fz));
                 }
             };
             auto cut_flip = [&](int i) {
                 if (outer && (uint32_t)i >= p.zq_lo) {
                     const uint32_t dz = __ldg(p.zqcol + i);
-                    if (dz) { flush(); zq ^= dz; }
+                    if (dz) {
+                        flush();
+                        zq ^= dz;
+                        fz = ldg_zw(p.ftab + zq);
+                    }
                 }
             };
 

@@ -428,7 +428,7 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
             uint32_t L[NW];
 #pragma unroll
             for (int w = 0; w < NW; w++) L[w] = p.INV[w];
-            uint64_t a = 0;
+            uint64_t a64 = 0;
             uint32_t q = 0;
             const uint32_t nnib = (p.k + 3) >> 2;
             for (uint32_t b = 0; b < nnib; b++) {
@@ -440,11 +440,20 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                     const uint4 t4 = *reinterpret_cast<const uint4*>(e + w4);
                     ev[w4] = t4.x; ev[w4 + 1] = t4.y; ev[w4 + 2] = t4.z; ev[w4 + 3] = t4.w;
                 }
-                q ^= ev[NW + 2] ^ ((uint32_t)__popc(v & (uint32_t)(a >> (4 * b))) & 1u);
-                a ^= ((uint64_t)ev[NW + 1] << 32) | ev[NW];
+                q ^= ev[NW + 2] ^ ((uint32_t)__popc(v & (uint32_t)(a64 >> (4 * b))) & 1u);
+                a64 ^= ((uint64_t)ev[NW + 1] << 32) | ev[NW];
 #pragma unroll
                 for (int w = 0; w < NW; w++) L[w] ^= ev[w];
             }
+            // the walk keeps bits 0-31 of A x: a flip of variable i >= 32
+            // (once per 2^32 terms) takes its bit from the state itself
+            uint32_t a = (uint32_t)a64;
+            const uint32_t* __restrict__ sADJw = reinterpret_cast<const uint32_t*>(sADJ);
+            // 4 (A x)_i (mod 8) for the state of Gray index tp, before flipping i
+            auto quad4 = [&](int i, uint64_t tp) -> uint32_t {
+                if (i < 32) return a >> i << 2;
+                return ((uint32_t)__popcll(sADJ[i] & (tp ^ (tp >> 1))) & 1u) << 2;
+            };
             uint32_t Jl;
             {
                 uint32_t P0 = 0, P1 = 0, X2 = 0;
@@ -459,8 +468,8 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                 }
                 Jl = P0 + 2u * P1 + 4u * ((uint32_t)__popc(X2) + q);
             }
-            // a = A x (all k bits): flipping variable i adds 4 (A x)_i to J and
-            // XORs adjacency row i into a.  us = the lookup slot of the current
+            // a = A x: flipping variable i adds 4 (A x)_i to J and XORs
+            // adjacency row i into a.  us = the lookup slot of the current
             // state's bits (lut_slot is linear: each flip XORs its row's slot
             // change, bits 8 and up of the row's last word)
             uint32_t us;
@@ -559,11 +568,11 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                     // 64-bit form measured faster)
                     const uint2 e1 = *reinterpret_cast<const uint2*>(sL + (us & ma));
                     const uint2 e2 = *reinterpret_cast<const uint2*>(sLB + (us >> na));
-                    const uint2 eq = *reinterpret_cast<const uint2*>(qlut + ((uint32_t)a & 7u));
+                    const uint2 eq = *reinterpret_cast<const uint2*>(qlut + (a & 7u));
                     lo = e1.x + e2.x + eq.x;
                     hi = e1.y + e2.y + eq.y;
                 } else {
-                    const uint64_t e = sL[us] + qlut[(uint32_t)a & 7u];
+                    const uint64_t e = sL[us] + qlut[a & 7u];
                     lo = (uint32_t)e;
                     hi = (uint32_t)(e >> 32);
                 }
@@ -600,14 +609,14 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
 #pragma unroll
                 for (int w = 0; w < NW; w++) L[w] ^= p.R[2][w];
                 Jl += hi >> 24;
-                a ^= p.A4[2];
+                a ^= (uint32_t)p.A4[2];
                 us ^= p.U4[2];
             };
             // variable 3 (between the two blocks of 8 of an aligned 16): step
             // row and adjacency row in the parameters
             auto flip3 = [&]() {
-                Jl += ((uint32_t)a >> 1) & 4u;
-                a ^= p.A4[3];
+                Jl += (a >> 1) & 4u;
+                a ^= (uint32_t)p.A4[3];
                 step(p.R[3], p.U4[3]);
             };
             auto load_row = [&](int i, uint32_t (&fr)[RW]) {
@@ -627,25 +636,32 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                     // between them, and the flip of variable ctz(t + 16) >= 4
                     // after them, whose step row and adjacency row are read
                     // from shared memory before the block's lookups so that
-                    // their latency overlaps the block's work
+                    // their latency overlaps the block's work.  (nb: whole
+                    // blocks left, at most 2^14 in a slice; t in 32-bit
+                    // halves, the high one changing once per 2^32 terms)
+                    uint32_t nb = (uint32_t)((tend - t) >> 4);
+                    const bool tail = ((tend - t) & 15u) != 0;
+                    uint32_t tl = (uint32_t)t, th = (uint32_t)(t >> 32);
                     for (;;) {
-                        const uint64_t tn = t + 16;
-                        const bool more = tn < tend;     // tn < 2^k: ctz(tn) < k
-                        const int i = more ? ctz64(tn) : 0;
+                        tl += 16u;
+                        if (tl == 0u) th++;
+                        const bool more = --nb != 0u || tail;   // t + 16 < tend <= 2^k: ctz < k
+                        const int i = !more ? 0 : (tl ? __ffs(tl) - 1 : 31 + __ffs(th));
                         uint32_t fr[RW];
                         load_row(i, fr);
-                        const uint64_t adj = sADJ[i];
+                        const uint32_t adj = sADJw[2 * i];
                         block8();
                         flip3();
                         block8();
-                        t = tn;
                         if (!more) break;
                         cut_flip(i);
-                        Jl += (uint32_t)(a >> i) << 2;   // (bits above 2: only J mod 8 is used)
+                        // (bits above 2: only J mod 8 is used)
+                        Jl += i < 32 ? a >> i << 2 : quad4(i, (((uint64_t)th << 32) | tl) - 1u);
                         a ^= adj;
                         step(fr, fr[NW + 2 * NWL] >> 8);
-                        if (tend - t < 16) break;
+                        if (nb == 0u) break;
                     }
+                    t = ((uint64_t)th << 32) | tl;
                     if (t >= tend) break;
                 }
                 if ((t & 7u) == 0 && tend - t >= 8) {
@@ -664,8 +680,8 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
                 } else {
                     const int i = ctz64(t);
                     cut_flip(i);
-                    Jl += (uint32_t)(a >> i) << 2;   // (bits above 2: only J mod 8 is used)
-                    a ^= sADJ[i];
+                    Jl += quad4(i, t - 1u);   // (bits above 2: only J mod 8 is used)
+                    a ^= sADJw[2 * i];
                     uint32_t fr[RW];
                     load_row(i, fr);
                     step(fr, fr[NW + 2 * NWL] >> 8);

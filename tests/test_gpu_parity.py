@@ -367,14 +367,14 @@ def test_two_table_block_lookup_matches_oracle(ctx):
 
 def test_large_compiled_t50_subranges(ctx):
     """n = 50, 2000 gates, T-count 50 (k = 37): seeded 2^20-term sub-ranges
-    of the full sum equal the oracle."""
+    of the full sum equal the oracle, one of them across 2^32 (the flip of
+    variable 32 in the middle of the walk)."""
     w = zi.workload_large_t50(0)
     s = Z.zxp_compile(w.gates, w.n, w.out_bits, split=False)
     blob = Z.zxp_scalar_to_tables(s)
     k = s.info["k"]
     rng = random.Random(37)
-    for _ in range(3):
-        first = rng.randrange((1 << k) - (1 << 20))
+    for first in [rng.randrange((1 << k) - (1 << 20)) for _ in range(3)] + [(1 << 32) - (1 << 19) + 5]:
         g = Z.zxp_eval(ctx, s, first, 1 << 20)
         o = oracle.ps_sum(blob, first, 1 << 20, nthreads=NCPU)
         assert same_raw(g, o), first
@@ -421,7 +421,12 @@ def test_maximum_k_ranges(ctx, seed, n_node, n_pair, odd, density):
     blob = ps.pack()
     s = Z.zxp_scalar_from_tables(blob)
     N = 1 << 62
+    # (ranges across 2^32 and 2^45: flips of variables 32 and 45 inside a
+    # slice, whose quadratic bit the walk takes from the state itself; with
+    # 64-term slices the crossing falls in a slice's first unaligned steps
+    # or inside its aligned blocks of 16)
     for first, count in [(0, 1 << 16), (N // 2 - 4096, 12289), (N - (1 << 15) - 3, (1 << 15) + 3),
+                         ((1 << 32) - 5003, 10007), ((1 << 32) - 5051, 10007), ((1 << 45) - 827, 4099),
                          (N - 1, 1), (N, 0)]:
         g = Z.zxp_eval(ctx, s, first, count)
         o = oracle.ps_sum(blob, first, count, nthreads=NCPU)

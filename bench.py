@@ -371,9 +371,9 @@ def run_reference(args, world, rank):
 
 
 def inner_launches(k_inner: int) -> int:
-    """Launches that build an inner table (inner.cu): the term kernel with
-    the low 10 bits, then passes of at most 10 bits."""
-    return 1 + (max(k_inner - 10, 0) + 9) // 10
+    """Launches that build an inner table of 32-byte entries (inner.cu):
+    the term kernel with the low 11 bits, then passes of at most 11 bits."""
+    return 1 + (max(k_inner - 11, 0) + 10) // 11
 
 
 def inner_roofline(inner_bits: int, k_inner: int, seconds: float, prof):

@@ -187,7 +187,7 @@ typedef struct zxp_split_opts_s {
     uint32_t max_inner;       /* inner parameters at most (22) */
     uint32_t max_index_bits;  /* inner parameters + crossing forms, <= 26 (24) */
     uint32_t max_cut;         /* crossing non-Clifford forms (3) */
-    uint32_t low_free;        /* lowest outer parameters free of the cut, >= 4 (10) */
+    uint32_t low_free;        /* lowest outer parameters free of the cut, >= 4 (8) */
     uint32_t tries;           /* randomized attempts (24) */
     uint64_t seed;            /* (0: a fixed seed) */
     uint32_t reserved[4];
@@ -204,8 +204,10 @@ typedef struct zxp_split_opts_s {
  * Walsh-Hadamard transform of the inner rows' product, read at the cut's
  * parities: one table of 2^inner_bits entries, computed on the device when
  * the scalar is first evaluated there (zxp_inner_sum).  The GPU then walks
- * 2^(k - k_inner) terms instead of 2^k.  *out has the same value as s (a
- * version-2 scalar when the split lowers the term count, else a copy).
+ * 2^(k - k_inner) terms instead of 2^k.  Of the splits found, the one of
+ * least estimated device time is taken (each more inner parameter halves the
+ * walk and doubles the table).  *out has the same value as s (a version-2
+ * scalar when the split lowers the term count, else a copy).
  * Errors: ZXP_EINVAL (s already split, bad options), ZXP_ENOMEM. */
 int zxp_scalar_split(const zxp_scalar *s, const zxp_split_opts *opts, zxp_scalar **out);
 

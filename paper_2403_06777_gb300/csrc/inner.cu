@@ -3,7 +3,7 @@
 // g the product of the scalar's inner and crossing rows.  Exact in Z[w]
 // modulo 2^64 (or 2^128: the same kernels on 64-byte entries), in two
 // kernels:
-//   1. inner_terms_low: a block evaluates 2^10 consecutive entries
+//   1. inner_terms_low: a block evaluates 2^11 consecutive entries
 //      u = (x_I, q) of g from the inner plan, as the sum kernel evaluates one
 //      term (form bits by XOR of flip rows, the phase exponent from the
 //      coefficient planes and the quadratic bit, the node count, the table
@@ -11,9 +11,9 @@
 //      the folded ones, zero when a zero form is set): the state of the
 //      block's high bits once, that of an entry's low bits from the plan's
 //      table of them, and the quadratic bit's cross part as the parity of
-//      (A x_high) & x_low.  It transforms the low 10 bits and writes the tile
+//      (A x_high) & x_low.  It transforms the low 11 bits and writes the tile
 //      once;
-//   2. wht_pass: each further pass transforms up to 10 more bits of tiles of
+//   2. wht_pass: each further pass transforms up to T more bits of tiles of
 //      2^T entries (2^nb rows of those bits times 2^(T - nb) consecutive
 //      low indices; T = 11, or 10 for 64-byte entries), read and written
 //      once, two tiles per SM so that one block's loads overlap the other's
@@ -34,10 +34,9 @@
 namespace zxp {
 namespace {
 
-constexpr int kLowThreads = 256;
 constexpr uint32_t kTileLog2 = kInnerLowBits;   // the plan tabulates these low bits
 constexpr uint32_t kTile = 1u << kTileLog2;
-constexpr uint32_t kPassBits = 10;              // tile-index bits one pass transforms at most
+constexpr int kLowThreads = (int)kTile / 4;      // four entries a thread
 
 // An entry as 16-byte planes: zw64 in two (c0 c1 | c2 c3), zw128 in four
 // (one coefficient each, low word first).
@@ -66,8 +65,12 @@ template <class Z>
 __host__ __device__ constexpr uint32_t pass_log2() { return Planes<Z>::N == 2 ? 11u : 10u; }
 template <class Z>
 __host__ __device__ constexpr size_t pass_smem() { return (size_t)Planes<Z>::N << pass_log2<Z>() << 4; }
+// tile-index bits one pass transforms at most: all of a tile's (one column
+// of 2^11 rows for 32-byte entries)
+template <class Z>
+constexpr uint32_t pass_bits() { return pass_log2<Z>(); }
 
-static_assert(kTileLog2 == 10, "the low kernel's rounds cover 10 bits");
+static_assert(kTileLog2 == 11, "the low kernel's rounds: five pairs of bits, then bit 10");
 
 // shared-memory slot of tile entry e: bits 3 and 4 of e flip slot bits
 // (0, 1) and (1, 2), a linear map, so slot(e ^ d) = slot(e) ^ slot(d)
@@ -191,7 +194,7 @@ __device__ __forceinline__ Z term_value(const KernelParams& p, const int nwn, co
     return ld_entry(table + idx);
 }
 
-// The first 2^bits entries of g in tiles of 2^10, the low `low_bits` bits
+// The first 2^bits entries of g in tiles of 2^11, the low `low_bits` bits
 // transformed.  Thread t evaluates entries 4t .. 4t + 3, the layout of the
 // first round.
 template <int NW, class Z>
@@ -239,12 +242,16 @@ inner_terms_low(const __grid_constant__ KernelParams p, const int nwn, const int
     }
     radix4(v, round_mask(0, low_bits));
     uint32_t pr = 0;
+    // rounds at bits (q, q + 1) for q = 2, 4, 6, 8; bit 10 alone in the
+    // layout of bits (9, 10)
 #pragma unroll
     for (uint32_t q = 2; q < kTileLog2; q += 2) {
         if (q < low_bits) {   // (the same for the whole block)
-            exchange(sm, kTile, v, t, q - 2, q);
-            pr = q;
-            radix4(v, round_mask(q, low_bits));
+            const bool top = q + 1 >= kTileLog2;
+            const uint32_t qr = top ? kTileLog2 - 2 : q;
+            exchange(sm, kTile, v, t, pr, qr);
+            pr = qr;
+            radix4(v, top ? 2u : round_mask(q, low_bits));
         }
     }
 #pragma unroll
@@ -256,7 +263,7 @@ inner_terms_low(const __grid_constant__ KernelParams p, const int nwn, const int
 
 // One later pass over bits [lo, lo + NB) of an array of 2^total entries: a
 // block holds the 2^NB entries of those bits for 2^C consecutive low indices
-// l (tile index e = row << C | col, C = 11 - NB <= 10 <= lo).  Rounds at bits
+// l (tile index e = row << C | col, C = T - NB <= 10 <= lo).  Rounds at bits
 // C, C + 2, ... of the tile index; for odd NB the last round takes the top
 // two bits and transforms only the top one.
 template <class Z, uint32_t NB>
@@ -338,10 +345,11 @@ cudaError_t table_launch(const Plan& inner, uint32_t k_inner, const Z* itab, con
     default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
-    // the remaining inner bits in passes of at most kPassBits, split evenly
-    // (every pass starts at lo >= 10, so its tile's 2^C columns fit below it)
+    // the remaining inner bits in passes of at most pass_bits, split evenly
+    // (every pass starts at lo = 11 or above, so its tile's 2^C <= 2^10
+    // columns fit below it)
     const uint32_t rem = k_inner - low;
-    const uint32_t passes = (rem + kPassBits - 1) / kPassBits;
+    const uint32_t passes = (rem + pass_bits<Z>() - 1) / pass_bits<Z>();
     for (uint32_t lo = low, left = rem, p = passes; left; p--) {
         const uint32_t nb = (left + p - 1) / p;
         switch (nb) {
@@ -354,7 +362,11 @@ cudaError_t table_launch(const Plan& inner, uint32_t k_inner, const Z* itab, con
         case 7: e = launch_pass<Z, 7>(ftab, lo, bits, stream); break;
         case 8: e = launch_pass<Z, 8>(ftab, lo, bits, stream); break;
         case 9: e = launch_pass<Z, 9>(ftab, lo, bits, stream); break;
-        default: e = launch_pass<Z, 10>(ftab, lo, bits, stream); break;
+        case 10: e = launch_pass<Z, 10>(ftab, lo, bits, stream); break;
+        default:
+            if constexpr (pass_bits<Z>() >= 11) e = launch_pass<Z, 11>(ftab, lo, bits, stream);
+            else return cudaErrorInvalidValue;
+            break;
         }
         if (e != cudaSuccess) return e;
         lo += nb;

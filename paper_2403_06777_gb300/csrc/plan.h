@@ -172,7 +172,7 @@ struct Plan {
     uint32_t k_inner = 0, inner_bits = 0;
     std::vector<uint32_t> zqcol;
     std::shared_ptr<const Plan> inner;
-    // The inner plan's state for the low min(inner_bits, 10) bits of u: per
+    // The inner plan's state for the low min(inner_bits, 11) bits of u: per
     // value e, the XOR of their flip rows (inner nw words) and the quadratic
     // bit of e (one more word); a block of the inner table combines it with
     // its high bits' state.  (The inner plan's table already includes its
@@ -180,8 +180,8 @@ struct Plan {
     std::vector<uint32_t> inner_low;
 };
 
-// Low bits of u tabulated for the inner table (a block's 2^10 entries).
-constexpr uint32_t kInnerLowBits = 10;
+// Low bits of u tabulated for the inner table (a block's 2^11 entries).
+constexpr uint32_t kInnerLowBits = 11;
 
 // Largest inner table index (inner parameters + crossing forms).
 constexpr uint32_t kMaxInnerBits = 26;

@@ -25,13 +25,14 @@ struct SplitOptions {
     uint32_t max_inner = 22;       // inner parameters
     uint32_t max_index_bits = 24;  // inner parameters + crossing forms (table of 2^bits entries)
     uint32_t max_cut = 3;          // crossing non-Clifford forms
-    uint32_t low_free = 10;        // lowest outer parameters no cut form may involve (>= 4)
+    uint32_t low_free = 8;         // lowest outer parameters no cut form may involve (>= 4)
     int tries = 24;                // randomized change-of-variables / partition attempts
     uint64_t seed = 0x5917d;
 };
 
-// *out is a version-2 scalar with the same value when the split lowers the
-// number of outer parameters, else a copy of `in`.  `in` must have
+// *out is a version-2 scalar with the same value when some split lowers the
+// number of outer parameters (the one of least estimated device time among
+// those found), else a copy of `in`.  `in` must have
 // k_inner == 0.  Returns ZXP_OK or ZXP_EINVAL.
 int split_scalar(const PS& in, const SplitOptions& opt, PS* out);
 

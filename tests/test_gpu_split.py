@@ -91,8 +91,9 @@ def test_inner_table_recomputed(ctx):
 
 def test_large_workload_split_sampled_terms(ctx):
     # n = 50, 2000 gates, t = 80: the compiled scalar is split by default;
-    # sampled outer terms (each the sum of 2^k_inner inner terms) and a
-    # ragged range equal the oracle
+    # sampled outer terms (each the sum of 2^k_inner inner terms, from inner
+    # table entries all over the table: every 32 MB chunk it is built in) and
+    # ragged ranges equal the oracle
     w = zi.workload_large(0)
     s = Z.zxp_compile(w.gates, w.n, w.out_bits)
     info = s.info
@@ -100,7 +101,7 @@ def test_large_workload_split_sampled_terms(ctx):
     blob = Z.zxp_scalar_to_tables(s)
     n = 1 << info["k"]
     rng = zi.SplitMix64(80)
-    samples = [(0, 1), (n - 1, 1)] + [(rng.below(n - 4), 1 + rng.below(3)) for _ in range(4)]
+    samples = [(0, 1), (n - 1, 1)] + [(rng.below(n - 4), 1 + rng.below(3)) for _ in range(12)]
     for first, count in samples:
         g = Z.zxp_eval(ctx, s, first, count)
         o = oracle.ps_sum(blob, first, count, nthreads=NCPU)

@@ -18,8 +18,9 @@
 //     assignments that leave every such form unchanged (their kernel),
 //     lightest first, so that the inner sum is constant while the Gray-code
 //     walk flips only them.
-// Several random tie-breaks are tried; the least estimated device time wins
-// (split_cost), over the prefixes of each greedy order.
+// Several random tie-breaks and every limit on the crossing forms are
+// tried; the least estimated device time wins (split_cost), over the
+// prefixes of each greedy order.
 #include "split.h"
 
 #include <string.h>
@@ -175,13 +176,13 @@ std::vector<uint64_t> cut_forms(const Graph& g, uint64_t I, uint64_t O, uint32_t
 
 // Estimated device time (ps) of one full sum after a split into n_inner
 // inner parameters (an inner table of 2^bits entries) and k_o outer ones,
-// from rates measured on GB300: the inner table 16.5 ps per entry for the
+// from rates measured on GB300: the inner table 20.5 ps per entry for the
 // term kernel (the low 11 bits transformed) and 19.3 ps per entry for each
 // further pass of up to 11 bits; the walk 0.374 ps per outer term plus a
 // 15 ps fold per run of 2^low_free terms between cut-parity changes.
 double split_cost(uint32_t n_inner, uint32_t bits, uint32_t k_o, uint32_t low_free) {
     const uint32_t passes = (n_inner > 11 ? n_inner - 11 + 10 : 0) / 11;
-    const double inner = (16.5 + 19.3 * passes) * (double)(1ull << bits);
+    const double inner = (20.5 + 19.3 * passes) * (double)(1ull << bits);
     const double walk = (0.374 + 15.0 / (double)(1ull << low_free)) * (double)(1ull << k_o);
     return inner + walk;
 }
@@ -392,11 +393,17 @@ int split_scalar(const PS& in, const SplitOptions& opt, PS* out) {
     uint64_t rng = opt.seed ^ ((uint64_t)in.k << 32) ^ (in.lin.size() * 0x9E37ull) ^ in.node.size();
     Graph best_g;
     Choice best;
+    // (every limit on the crossing forms up to max_cut: a greedy order under
+    // a looser limit can take a coordinate that brings crossing forms and
+    // miss a partition with fewer index bits)
     for (int t = 0; t < std::max(1, opt.tries); t++) {
         Graph g = to_graph(in, rng);
         for (int r = 0; r < 4; r++) {
-            Choice c = partition(g, opt, rng);
-            if (c.better(best)) { best = c; best_g = g; }
+            SplitOptions o = opt;
+            for (o.max_cut = 0; o.max_cut <= opt.max_cut; o.max_cut++) {
+                Choice c = partition(g, o, rng);
+                if (c.better(best)) { best = c; best_g = g; }
+            }
         }
     }
     if (!best.ok || best.k_o >= in.k) return ZXP_OK;

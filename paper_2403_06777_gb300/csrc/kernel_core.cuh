@@ -490,27 +490,37 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
             zw64 fz = zw_zero();
             if (outer) fz = ldg_zw(p.ftab + zq);
             // (lane-private counters have no folded bits, so the entry of
-            // phase J is w^J times that of phase 0: for each node count the
-            // eight counts combine into the integer element
-            // (c0 - c4) + (c1 - c5) w + (c2 - c6) w^2 + (c3 - c7) w^3 (w^4 = -1)
-            // and one product with the phase-0 entry)
+            // phase J and node count M is w^J u^M, u = w^2 (1 + sqrt2) =
+            // w + w^2 + w^3: for each M the eight counts combine into the
+            // integer element d_M = (c0 - c4) + (c1 - c5) w + (c2 - c6) w^2 +
+            // (c3 - c7) w^3 (w^4 = -1), and sum_M d_M u^M is evaluated by
+            // Horner's rule, a multiplication by u being seven additions of
+            // coefficients.  In 32-bit integers: a run holds at most 2^18
+            // terms (one slice) and each of at most eight steps at most
+            // triples the coefficients, below 2^31.  One product with the
+            // inner-table entry at the run's cut parities follows.)
             auto flush = [&]() {
                 if constexpr (LANE) {
-                    zw64 sum = zw_zero();
-                    for (uint32_t Mi = 0; Mi < ts; Mi++) {
+                    uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+                    for (uint32_t Mi = ts; Mi-- > 0;) {
                         uint32_t c[8];
+                        unsigned char* ptr = reinterpret_cast<unsigned char*>(lctr(Mi));
 #pragma unroll
                         for (uint32_t J = 0; J < 8; J++) {
-                            uint32_t* const ptr = lctr((J << tsh) + Mi);
-                            c[J] = *ptr;
-                            *ptr = 0u;
+                            c[J] = *reinterpret_cast<uint32_t*>(ptr);
+                            *reinterpret_cast<uint32_t*>(ptr) = 0u;
+                            ptr += rb << tsh;
                         }
-                        const zw64 d = zw_make((uint64_t)(int64_t)(int32_t)(c[0] - c[4]),
-                                               (uint64_t)(int64_t)(int32_t)(c[1] - c[5]),
-                                               (uint64_t)(int64_t)(int32_t)(c[2] - c[6]),
-                                               (uint64_t)(int64_t)(int32_t)(c[3] - c[7]));
-                        sum = zw_add(sum, zw_mul(d, lds_zw(sT + Mi)));
+                        // (s0 + s1 w + s2 w^2 + s3 w^3) u + d_M
+                        const uint32_t x = s1 + s2;
+                        const uint32_t n0 = 0u - (x + s3), n1 = s0 - s2 - s3, n2 = s0 + s1 - s3, n3 = s0 + x;
+                        s0 = n0 + (c[0] - c[4]);
+                        s1 = n1 + (c[1] - c[5]);
+                        s2 = n2 + (c[2] - c[6]);
+                        s3 = n3 + (c[3] - c[7]);
                     }
+                    const zw64 sum = zw_make((uint64_t)(int64_t)(int32_t)s0, (uint64_t)(int64_t)(int32_t)s1,
+                                             (uint64_t)(int64_t)(int32_t)s2, (uint64_t)(int64_t)(int32_t)s3);
                     acc = zw_add(acc, zw_mul(sum, fz));
                 }
             };

@@ -178,12 +178,12 @@ std::vector<uint64_t> cut_forms(const Graph& g, uint64_t I, uint64_t O, uint32_t
 // inner parameters (an inner table of 2^bits entries) and k_o outer ones,
 // from rates measured on GB300: the inner table 20.5 ps per entry for the
 // term kernel (the low 11 bits transformed) and 19.3 ps per entry for each
-// further pass of up to 11 bits; the walk 0.374 ps per outer term plus a
-// 15 ps fold per run of 2^low_free terms between cut-parity changes.
+// further pass of up to 11 bits; the walk 0.374 ps per outer term plus an
+// 11 ps fold per run of 2^low_free terms between cut-parity changes.
 double split_cost(uint32_t n_inner, uint32_t bits, uint32_t k_o, uint32_t low_free) {
     const uint32_t passes = (n_inner > 11 ? n_inner - 11 + 10 : 0) / 11;
     const double inner = (20.5 + 19.3 * passes) * (double)(1ull << bits);
-    const double walk = (0.374 + 15.0 / (double)(1ull << low_free)) * (double)(1ull << k_o);
+    const double walk = (0.374 + 11.0 / (double)(1ull << low_free)) * (double)(1ull << k_o);
     return inner + walk;
 }
 

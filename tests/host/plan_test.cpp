@@ -273,6 +273,16 @@ int main(int argc, char** argv) {
         const Model m(pl);
         printf("scalar %s k %u lookup %d lane %d two %d\n", argv[a], m.k, pl.lut_ok ? 1 : 0, pl.lut_lane ? 1 : 0,
                pl.lut_two ? 1 : 0);
+        if (pl.lut_lane) {
+            // the lane-private walk folds a run's counts by Horner's rule in
+            // u = w + w^2 + w^3: the phase-0 entries must be u^M
+            CHECK(pl.kp.xshift == 0);
+            zw64 um = zw_one();
+            for (uint32_t M = 0; M < pl.kp.tab_stride; M++) {
+                for (int c = 0; c < 4; c++) CHECK(pl.table[M].c[c] == um.c[c]);
+                um = zw_mul(um, zw_make(0, 1, 1, 1));
+            }
+        }
         if (pl.k_inner) {
             // the walk's rules: variables 0-3 never change the cut parities
             CHECK(pl.kp.zq_lo >= 4 && (!pl.lut_ok || pl.lut_lane));

@@ -89,9 +89,11 @@ class ClockSampler:
 
 
 # the sources that decide a profiled kernel's code and the tables it reads
+# from a scalar (the scalar itself is pinned by the digest of its table
+# bytes, scalar_sha256)
 KERNEL_SOURCES = ("sum_kernel.cuh", "kernel_core.cuh", "kernel.cu", "kernel_count.cu", "zring.h",
-                  "plan.h", "plan.cpp", "split.cpp")
-INNER_SOURCES = ("inner.cu", "zring.h", "plan.h", "plan.cpp", "split.cpp")
+                  "plan.h", "plan.cpp")
+INNER_SOURCES = ("inner.cu", "zring.h", "plan.h", "plan.cpp")
 
 
 def kernel_source_sha(sources=KERNEL_SOURCES) -> str:
@@ -103,9 +105,17 @@ def kernel_source_sha(sources=KERNEL_SOURCES) -> str:
     return h.hexdigest()
 
 
-def profile_fields(kernel_src_sha: str, name: str = "sum_kernel_medium.txt"):
+def tables_sha(*blobs: bytes) -> str:
+    """Digest of the table bytes of the scalars a profile ran on."""
+    h = hashlib.sha256()
+    for b in blobs:
+        h.update(b)
+    return h.hexdigest()
+
+
+def profile_fields(kernel_src_sha: str, name: str = "sum_kernel_medium.txt", scalar_sha: str | None = None):
     """Fields of a committed ncu summary, if it was taken on the current
-    kernel sources (else None)."""
+    kernel sources and (scalar_sha) on the same scalar (else None)."""
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
@@ -115,6 +125,8 @@ def profile_fields(kernel_src_sha: str, name: str = "sum_kernel_medium.txt"):
             k, v = line.split(":", 1)
             fields[k.strip()] = v.strip()
     if fields.get("kernel_source_sha256") != kernel_src_sha:
+        return None
+    if scalar_sha is not None and fields.get("scalar_sha256") != scalar_sha:
         return None
     return fields
 
@@ -742,13 +754,16 @@ def main():
                   "e2e": {"amplitudes_per_s": 1 / e2e_m, "us_per_request": e2e_m * 1e6,
                           "h2d_bytes_per_step": im["upload_bytes"], "d2h_bytes_per_step": 40,
                           "requests_in_flight": 2},
-                  "roofline": roofline_from_profile(profile_fields(kernel_source_sha(), "sum_kernel_medium.txt"),
+                  "roofline": roofline_from_profile(profile_fields(kernel_source_sha(), "sum_kernel_medium.txt",
+                                                                  tables_sha(blob_m)),
                                                     nm, ms_m / 1e3, peak_m, "profiles/sum_kernel_medium.txt")}
 
     # ---- the k = 36 stand-in with compiled statistics, drawn and relabelled ---
     synth = None
     if rank == 0 and not os.environ.get("ZXP_BENCH_SKIP_LARGE"):
         raw, re = synth36_scalars(Z, zi)
+        sprof = profile_fields(kernel_source_sha(), "sum_kernel_synthetic36.txt",
+                               tables_sha(Z.zxp_scalar_to_tables(raw), Z.zxp_scalar_to_tables(re)))
         synth = {"workload": "synthetic k=36 tables with compiled k 34-40 statistics " + json.dumps(SYNTH36)}
         for tag, sc, n in (("drawn_order", raw, 1 << 34), ("relabelled", re, 1 << 36)):
             Z.zxp_eval_device(ctx, sc, 0, 1 << 24, out.data_ptr())
@@ -761,9 +776,7 @@ def main():
             ms = a.elapsed_time(b)
             synth[tag] = {"kernel_variant": sc.info["kernel_variant"], "terms": n, "ms": ms,
                           "terms_per_s": n / (ms / 1e3),
-                          "instructions_per_term": profile_number(
-                              profile_fields(kernel_source_sha(), "sum_kernel_synthetic36.txt"),
-                              "instructions_per_term_" + tag)}
+                          "instructions_per_term": profile_number(sprof, "instructions_per_term_" + tag)}
         # relabelling keeps the sum: the full sum of both orders
         synth["same_full_sum"] = Z.zxp_zomega_canon(Z.zxp_eval(ctx, raw)) == Z.zxp_zomega_canon(Z.zxp_eval(ctx, re))
         assert synth["same_full_sum"]
@@ -788,7 +801,8 @@ def main():
         unsplit = {"workload": f"{wl.name} seed=0 without the split: one exact amplitude, one launch",
                    "k": il["k"], "terms": nl, "ms": msl, "terms_per_s": nl / (msl / 1e3),
                    "kernel_variant": il["kernel_variant"],
-                   "roofline": roofline_from_profile(profile_fields(kernel_source_sha(), "sum_kernel_large37.txt"),
+                   "roofline": roofline_from_profile(profile_fields(kernel_source_sha(), "sum_kernel_large37.txt",
+                                                                   tables_sha(Z.zxp_scalar_to_tables(sl))),
                                                      nl, msl / 1e3, peak_l, "profiles/sum_kernel_large37.txt"),
                    "clocks": clkl.summary()}
 
@@ -857,7 +871,7 @@ def main():
 
     peak, sms, mhz = issue_peak(torch, local, clocks.get("sm_max_mhz"))
     sha = kernel_source_sha()
-    prof = profile_fields(sha, "sum_kernel_large80.txt")
+    prof = profile_fields(sha, "sum_kernel_large80.txt", tables_sha(blob))
     roof = roofline_from_profile(prof, walked, walk_s, peak, "profiles/sum_kernel_large80.txt")
     roof["sms"] = sms
     roof["sm_max_mhz"] = mhz
@@ -868,7 +882,7 @@ def main():
                                      "basis": "integer microbenchmark (zxp_int_peak kind 4): logic and "
                                               "multiply-add chains in turn on a full grid"}
     launches_per_step = (inner_launches(ki) + 1) if ki else 1
-    iprof = profile_fields(kernel_source_sha(INNER_SOURCES), "inner_table_large80.txt")
+    iprof = profile_fields(kernel_source_sha(INNER_SOURCES), "inner_table_large80.txt", tables_sha(blob))
 
     line = {
         "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world,

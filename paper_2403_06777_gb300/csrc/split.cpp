@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "plan.h"
 #include "zxp.h"
 
 namespace zxp {
@@ -178,12 +179,13 @@ std::vector<uint64_t> cut_forms(const Graph& g, uint64_t I, uint64_t O, uint32_t
 // inner parameters (an inner table of 2^bits entries) and k_o outer ones,
 // from rates measured on GB300: the inner table 20.5 ps per entry for the
 // term kernel (the low 11 bits transformed) and 19.3 ps per entry for each
-// further pass of up to 11 bits; the walk 0.374 ps per outer term plus an
-// 11 ps fold per run of 2^low_free terms between cut-parity changes.
-double split_cost(uint32_t n_inner, uint32_t bits, uint32_t k_o, uint32_t low_free) {
+// further pass of up to 11 bits; the walk 0.374 ps per outer term with the
+// block lookup (0.94 without it) plus an 11 ps fold per run of 2^low_free
+// terms between cut-parity changes.
+double split_cost(uint32_t n_inner, uint32_t bits, uint32_t k_o, uint32_t low_free, bool lookup = true) {
     const uint32_t passes = (n_inner > 11 ? n_inner - 11 + 10 : 0) / 11;
     const double inner = (20.5 + 19.3 * passes) * (double)(1ull << bits);
-    const double walk = (0.374 + 11.0 / (double)(1ull << low_free)) * (double)(1ull << k_o);
+    const double walk = ((lookup ? 0.374 : 0.94) + 11.0 / (double)(1ull << low_free)) * (double)(1ull << k_o);
     return inner + walk;
 }
 
@@ -384,34 +386,14 @@ std::vector<uint64_t> outer_columns(const Graph& g, uint64_t I, uint64_t& rng) {
     return cols;
 }
 
-}  // namespace
-
-int split_scalar(const PS& in, const SplitOptions& opt, PS* out) {
-    if (!out || in.k_inner != 0 || in.k > 62) return ZXP_EINVAL;
-    *out = in;
-    if (in.k < opt.min_k || in.k < opt.low_free + 1 || opt.low_free < 4) return ZXP_OK;
-    uint64_t rng = opt.seed ^ ((uint64_t)in.k << 32) ^ (in.lin.size() * 0x9E37ull) ^ in.node.size();
-    Graph best_g;
-    Choice best;
-    // (every limit on the crossing forms up to max_cut: a greedy order under
-    // a looser limit can take a coordinate that brings crossing forms and
-    // miss a partition with fewer index bits)
-    for (int t = 0; t < std::max(1, opt.tries); t++) {
-        Graph g = to_graph(in, rng);
-        for (int r = 0; r < 4; r++) {
-            SplitOptions o = opt;
-            for (o.max_cut = 0; o.max_cut <= opt.max_cut; o.max_cut++) {
-                Choice c = partition(g, o, rng);
-                if (c.better(best)) { best = c; best_g = g; }
-            }
-        }
-    }
-    if (!best.ok || best.k_o >= in.k) return ZXP_OK;
-    const Graph& g = best_g;
-    const uint32_t k = in.k, ko = best.k_o;
-    const std::vector<uint64_t> cols = outer_columns(g, best.I, rng);
+// The scalar in the variables of graph g with inner coordinates I: outer
+// parameters first (outer_columns), then the inner ones.
+PS make_split(const Graph& g, uint64_t I, uint64_t& rng) {
+    const uint32_t k = g.ps.k;
+    const uint32_t ko = k - (uint32_t)popc(I);
+    const std::vector<uint64_t> cols = outer_columns(g, I, rng);
     std::vector<uint32_t> ipos;
-    for (uint32_t i = 0; i < k; i++) if ((best.I >> i) & 1) ipos.push_back(i);
+    for (uint32_t i = 0; i < k; i++) if ((I >> i) & 1) ipos.push_back(i);
     auto remap = [&](uint64_t m) {
         uint64_t r = 0;
         for (uint32_t j = 0; j < ko; j++) r |= (uint64_t)par(m & cols[j]) << j;
@@ -424,7 +406,62 @@ int split_scalar(const PS& in, const SplitOptions& opt, PS* out) {
     for (auto& r : ps.node) r.mask = remap(r.mask);
     for (auto& r : ps.pair) { r.ma = remap(r.ma); r.mb = remap(r.mb); }
     ps.k_inner = k - ko;
-    *out = std::move(ps);
+    return ps;
+}
+
+}  // namespace
+
+int split_scalar(const PS& in, const SplitOptions& opt, PS* out) {
+    if (!out || in.k_inner != 0 || in.k > 62) return ZXP_EINVAL;
+    *out = in;
+    if (in.k < opt.min_k || in.k < opt.low_free + 1 || opt.low_free < 4) return ZXP_OK;
+    uint64_t rng = opt.seed ^ ((uint64_t)in.k << 32) ^ (in.lin.size() * 0x9E37ull) ^ in.node.size();
+    // the partitions of least estimated cost (with the block lookup's walk
+    // rate), distinct ones, and the graph each was found in
+    constexpr size_t kCands = 6;
+    std::vector<std::pair<Choice, Graph>> cands;
+    // (every limit on the crossing forms up to max_cut: a greedy order under
+    // a looser limit can take a coordinate that brings crossing forms and
+    // miss a partition with fewer index bits)
+    for (int t = 0; t < std::max(1, opt.tries); t++) {
+        Graph g = to_graph(in, rng);
+        for (int r = 0; r < 4; r++) {
+            SplitOptions o = opt;
+            for (o.max_cut = 0; o.max_cut <= opt.max_cut; o.max_cut++) {
+                Choice c = partition(g, o, rng);
+                if (!c.ok || c.k_o >= in.k) continue;
+                if (cands.size() == kCands && !c.better(cands.back().first)) continue;
+                // (the same partition again, under another crossing limit)
+                bool dup = false;
+                for (auto& e : cands) dup = dup || (e.first.I == c.I && e.first.cost == c.cost);
+                if (dup) continue;
+                auto at = std::find_if(cands.begin(), cands.end(), [&](const std::pair<Choice, Graph>& e) {
+                    return c.better(e.first);
+                });
+                cands.insert(at, std::make_pair(c, g));
+                if (cands.size() > kCands) cands.pop_back();
+            }
+        }
+    }
+    // each candidate as the scalar it gives: whether its plan takes the
+    // block lookup (the outer basis decides; another random basis is drawn
+    // when it does not) sets the walk rate of the estimate
+    double best_cost = 0;
+    bool found = false;
+    for (auto& e : cands) {
+        for (int b = 0; b < 3; b++) {
+            PS ps = make_split(e.second, e.first.I, rng);
+            Plan pl;
+            if (build_plan(ps, &pl) != ZXP_OK) break;
+            const double cost = split_cost(ps.k_inner, pl.inner_bits, ps.k - ps.k_inner, pl.kp.zq_lo, pl.lut_ok);
+            if (!found || cost < best_cost) {
+                best_cost = cost;
+                found = true;
+                *out = std::move(ps);
+            }
+            if (pl.lut_ok) break;
+        }
+    }
     return ZXP_OK;
 }
 

@@ -36,7 +36,6 @@ namespace {
 
 constexpr uint32_t kTileLog2 = kInnerLowBits;   // the plan tabulates these low bits
 constexpr uint32_t kTile = 1u << kTileLog2;
-constexpr int kLowThreads = (int)kTile / 4;      // four entries a thread
 
 // An entry as 16-byte planes: zw64 in two (c0 c1 | c2 c3), zw128 in four
 // (one coefficient each, low word first).
@@ -72,17 +71,30 @@ constexpr uint32_t pass_bits() { return pass_log2<Z>(); }
 
 static_assert(kTileLog2 == 11, "the low kernel's rounds: five pairs of bits, then bit 10");
 
-// shared-memory slot of tile entry e: bits 3 and 4 of e flip slot bits
-// (0, 1) and (1, 2), a linear map, so slot(e ^ d) = slot(e) ^ slot(d)
+// Radix of the rounds: a thread holds 2^RB entries that differ in RB bits of
+// the tile index, RB = 3 for 32-byte entries (eight a thread, three bits a
+// round), 2 for 64-byte ones (four a thread: eight would take 128 registers
+// for the values alone).
+template <class Z>
+__host__ __device__ constexpr uint32_t radix_bits() { return Planes<Z>::N == 2 ? 3u : 2u; }
+
+// shared-memory slot of tile entry e, a linear map that keeps e's tile and
+// gives the eight threads of every quarter-warp eight distinct 16-byte bank
+// groups of a 128-byte row in every layout the rounds use (checked for all
+// layouts on the host): RB = 3: bits 3-5 of e flip slot bits 0-2; RB = 2:
+// bits 3 and 4 of e flip slot bits (0, 1) and (1, 2)
+template <uint32_t RB>
 __device__ __forceinline__ uint32_t slot(uint32_t e) {
+    if constexpr (RB == 3) return e ^ ((e >> 3) & 7u);
     return e ^ ((0x5630u >> (((e >> 3) & 3u) << 2)) & 7u);
 }
 
 // tile index of the j-th entry that thread t holds in the round of bits
-// (p, p + 1): j in those bits, t's bits around them
+// [p, p + RB): j in those bits, t's bits around them
+template <uint32_t RB>
 __device__ __forceinline__ uint32_t spread(uint32_t t, uint32_t p, uint32_t j) {
     const uint32_t low = (1u << p) - 1u;
-    return (t & low) | (j << p) | ((t & ~low) << 2);
+    return (t & low) | (j << p) | ((t & ~low) << RB);
 }
 
 template <class Z>
@@ -95,44 +107,56 @@ __device__ __forceinline__ void stage(Z& a, Z& b) {
     }
 }
 
-// both stages of a round on the four entries held: bit p (entry pairs that
-// differ in bit 0 of j) when m & 1, bit p + 1 (bit 1 of j) when m & 2
-template <class Z>
-__device__ __forceinline__ void radix4(Z (&v)[4], uint32_t m) {
-    if (m & 1u) {
-        stage(v[0], v[1]);
-        stage(v[2], v[3]);
-    }
-    if (m & 2u) {
-        stage(v[0], v[2]);
-        stage(v[1], v[3]);
+// the butterfly stages of a round on the 2^RB entries held: bit b of the
+// round (entry pairs that differ in bit b of j) when bit b of m is set
+template <uint32_t RB, class Z>
+__device__ __forceinline__ void radix(Z (&v)[1u << RB], uint32_t m) {
+#pragma unroll
+    for (uint32_t b = 0; b < RB; b++) {
+        if ((m >> b) & 1u) {
+#pragma unroll
+            for (uint32_t j = 0; j < (1u << RB); j++)
+                if (!((j >> b) & 1u)) stage(v[j], v[j | (1u << b)]);
+        }
     }
 }
 
 // from the layout of round bits pf to that of round bits pt (plane k of
 // the tile at sm + k * ps)
-template <class Z>
-__device__ __forceinline__ void exchange(ulonglong2* sm, uint32_t ps, Z (&v)[4], uint32_t t, uint32_t pf,
+template <uint32_t RB, class Z>
+__device__ __forceinline__ void exchange(ulonglong2* sm, uint32_t ps, Z (&v)[1u << RB], uint32_t t, uint32_t pf,
                                          uint32_t pt) {
 #pragma unroll
-    for (uint32_t j = 0; j < 4; j++) {
-        const uint32_t a = slot(spread(t, pf, j));
+    for (uint32_t j = 0; j < (1u << RB); j++) {
+        const uint32_t a = slot<RB>(spread<RB>(t, pf, j));
 #pragma unroll
         for (int k = 0; k < Planes<Z>::N; k++) sm[k * ps + a] = Planes<Z>::get(v[j], k);
     }
     __syncthreads();
 #pragma unroll
-    for (uint32_t j = 0; j < 4; j++) {
-        const uint32_t a = slot(spread(t, pt, j));
+    for (uint32_t j = 0; j < (1u << RB); j++) {
+        const uint32_t a = slot<RB>(spread<RB>(t, pt, j));
 #pragma unroll
         for (int k = 0; k < Planes<Z>::N; k++) Planes<Z>::set(v[j], k, sm[k * ps + a]);
     }
     __syncthreads();
 }
 
-// stages of the round at bits (p, p + 1) among the first `bits` bits
-__device__ __forceinline__ uint32_t round_mask(uint32_t p, uint32_t bits) {
-    return (p < bits ? 1u : 0u) | (p + 1u < bits ? 2u : 0u);
+// the round at tile bits [q, q + RB) of a T-bit tile index, of which the
+// first `bits` are transformed: its layout p (T - RB when the bits run past
+// the tile's top, the lower ones already done) and the stages to take
+template <uint32_t RB>
+__device__ __forceinline__ uint32_t round_at(uint32_t q, uint32_t T) {
+    return q + RB > T ? T - RB : q;
+}
+template <uint32_t RB>
+__device__ __forceinline__ uint32_t round_stages(uint32_t q, uint32_t T, uint32_t bits) {
+    const uint32_t p = round_at<RB>(q, T);
+    uint32_t m = 0;
+#pragma unroll
+    for (uint32_t b = 0; b < RB; b++)
+        if (p + b >= q && p + b < bits) m |= 1u << b;
+    return m;
 }
 
 // entries of the table (16-byte aligned: the table starts on 256)
@@ -194,11 +218,18 @@ __device__ __forceinline__ Z term_value(const KernelParams& p, const int nwn, co
     return ld_entry(table + idx);
 }
 
+// threads of a term-kernel block (2^RB entries a thread) and the blocks an
+// SM should hold
+template <class Z>
+__host__ __device__ constexpr int low_threads() { return (int)(kTile >> radix_bits<Z>()); }
+template <class Z>
+__host__ __device__ constexpr int low_min_blocks() { return Planes<Z>::N == 2 ? 2 : 1; }
+
 // The first 2^bits entries of g in tiles of 2^11, the low `low_bits` bits
-// transformed.  Thread t evaluates entries 4t .. 4t + 3, the layout of the
-// first round.
+// transformed.  Thread t evaluates entries 2^RB t .. 2^RB t + 2^RB - 1, the
+// layout of the first round.
 template <int NW, class Z>
-__global__ void __launch_bounds__(kLowThreads)
+__global__ void __launch_bounds__(low_threads<Z>(), low_min_blocks<Z>())
 inner_terms_low(const __grid_constant__ KernelParams p, const int nwn, const int general,
                 const Z* __restrict__ table, const Z* __restrict__ pv,
                 const uint32_t* __restrict__ frows, const uint64_t* __restrict__ adj,
@@ -233,30 +264,30 @@ inner_terms_low(const __grid_constant__ KernelParams p, const int nwn, const int
     // (every quadratic pair of the high bits was counted from both ends)
     const uint32_t qb = (qb2 >> 1) & 1u;
     const uint32_t ab = (uint32_t)AB;
-    Z v[4];
+    constexpr uint32_t RB = radix_bits<Z>(), E = 1u << RB;
+    Z v[E];
 #pragma unroll
-    for (uint32_t j = 0; j < 4; j++) {
-        const uint32_t e = spread(t, 0, j);
+    for (uint32_t j = 0; j < E; j++) {
+        const uint32_t e = spread<RB>(t, 0, j);
         v[j] = e < n ? term_value<NW, Z>(p, nwn, general, table, pv, LB, qb, ab, low, e)
                      : zw_zero<typename zw_word<Z>::type>();
     }
-    radix4(v, round_mask(0, low_bits));
+    radix<RB>(v, round_stages<RB>(0, kTileLog2, low_bits));
     uint32_t pr = 0;
-    // rounds at bits (q, q + 1) for q = 2, 4, 6, 8; bit 10 alone in the
-    // layout of bits (9, 10)
+    // rounds at bits [q, q + RB) for q = RB, 2 RB, ...; the last one's top
+    // bits alone in the layout of the tile's top RB bits
 #pragma unroll
-    for (uint32_t q = 2; q < kTileLog2; q += 2) {
+    for (uint32_t q = RB; q < kTileLog2; q += RB) {
         if (q < low_bits) {   // (the same for the whole block)
-            const bool top = q + 1 >= kTileLog2;
-            const uint32_t qr = top ? kTileLog2 - 2 : q;
-            exchange(sm, kTile, v, t, pr, qr);
+            const uint32_t qr = round_at<RB>(q, kTileLog2);
+            exchange<RB>(sm, kTile, v, t, pr, qr);
             pr = qr;
-            radix4(v, top ? 2u : round_mask(q, low_bits));
+            radix<RB>(v, round_stages<RB>(q, kTileLog2, low_bits));
         }
     }
 #pragma unroll
-    for (uint32_t j = 0; j < 4; j++) {
-        const uint32_t e = spread(t, pr, j);
+    for (uint32_t j = 0; j < E; j++) {
+        const uint32_t e = spread<RB>(t, pr, j);
         if (e < n) st_entry(out + (base | e), v[j]);
     }
 }
@@ -264,37 +295,37 @@ inner_terms_low(const __grid_constant__ KernelParams p, const int nwn, const int
 // One later pass over bits [lo, lo + NB) of an array of 2^total entries: a
 // block holds the 2^NB entries of those bits for 2^C consecutive low indices
 // l (tile index e = row << C | col, C = T - NB <= 10 <= lo).  Rounds at bits
-// C, C + 2, ... of the tile index; for odd NB the last round takes the top
-// two bits and transforms only the top one.
+// C, C + RB, ... of the tile index; when NB is not a multiple of RB the last
+// round takes the tile's top RB bits and transforms only those not done.
 template <class Z, uint32_t NB>
-__global__ void __launch_bounds__(1u << (pass_log2<Z>() - 2), 2)
+__global__ void __launch_bounds__(1u << (pass_log2<Z>() - radix_bits<Z>()), 2)
 wht_pass(Z* __restrict__ F, const uint32_t lo) {
-    constexpr uint32_t T = pass_log2<Z>(), C = T - NB, NR = (NB + 1) / 2, CM = (1u << C) - 1u;
+    constexpr uint32_t RB = radix_bits<Z>(), E = 1u << RB;
+    constexpr uint32_t T = pass_log2<Z>(), C = T - NB, NR = (NB + RB - 1) / RB, CM = (1u << C) - 1u;
     extern __shared__ ulonglong2 sm[];
     const uint32_t gl = lo - C;   // log2 of the tiles side by side in the low bits
     const uint64_t o = (uint64_t)blockIdx.x >> gl;
     const uint64_t l0 = (uint64_t)(blockIdx.x & ((1u << gl) - 1u)) << C;
     Z* const b = F + ((o << (lo + NB)) | l0);
     const uint32_t t = threadIdx.x;
-    constexpr uint32_t P0 = NB >= 2 ? C : T - 2;
-    Z v[4];
+    const uint32_t P0 = round_at<RB>(C, T);
+    Z v[E];
 #pragma unroll
-    for (uint32_t j = 0; j < 4; j++) {
-        const uint32_t e = spread(t, P0, j);
+    for (uint32_t j = 0; j < E; j++) {
+        const uint32_t e = spread<RB>(t, P0, j);
         v[j] = ld_entry(b + ((uint64_t)(e >> C) << lo) + (e & CM));
     }
     uint32_t pr = P0;
 #pragma unroll
     for (uint32_t r = 0; r < NR; r++) {
-        const bool pair = 2 * r + 1 < NB;
-        const uint32_t q = pair ? C + 2 * r : T - 2;
-        if (r) exchange(sm, 1u << T, v, t, pr, q);
-        pr = q;
-        radix4(v, pair ? 3u : 2u);
+        const uint32_t q = C + RB * r, qr = round_at<RB>(q, T);
+        if (r) exchange<RB>(sm, 1u << T, v, t, pr, qr);
+        pr = qr;
+        radix<RB>(v, round_stages<RB>(q, T, T));
     }
 #pragma unroll
-    for (uint32_t j = 0; j < 4; j++) {
-        const uint32_t e = spread(t, pr, j);
+    for (uint32_t j = 0; j < E; j++) {
+        const uint32_t e = spread<RB>(t, pr, j);
         st_entry(b + ((uint64_t)(e >> C) << lo) + (e & CM), v[j]);
     }
 }
@@ -305,7 +336,8 @@ cudaError_t launch_pass(Z* ftab, uint32_t lo, uint32_t bits, cudaStream_t stream
     cudaError_t e = cudaFuncSetAttribute(wht_pass<Z, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)pass_smem<Z>());
     if (e != cudaSuccess) return e;
-    wht_pass<Z, NB><<<(unsigned)((1ull << bits) >> T), 1u << (T - 2), pass_smem<Z>(), stream>>>(ftab, lo);
+    wht_pass<Z, NB><<<(unsigned)((1ull << bits) >> T), 1u << (T - radix_bits<Z>()), pass_smem<Z>(), stream>>>(
+        ftab, lo);
     return cudaGetLastError();
 }
 
@@ -320,7 +352,7 @@ cudaError_t launch_low(const Plan& in, uint32_t low_bits, const Z* itab, const Z
     // (the 128-bit table holds (J, M) values only: every entry takes the
     // general path)
     const int general = (in.general || Planes<Z>::N == 4) ? 1 : 0;
-    inner_terms_low<NW, Z><<<(unsigned)(1ull << (bits - tb)), kLowThreads, smem, stream>>>(
+    inner_terms_low<NW, Z><<<(unsigned)(1ull << (bits - tb)), low_threads<Z>(), smem, stream>>>(
         in.kp, in.nwn, general, itab, ipv, ifr, iadj, ilow, bits, low_bits, ftab);
     return cudaGetLastError();
 }

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "kernel.h"
 #include "plan.h"
 
@@ -704,6 +706,280 @@ __device__ __forceinline__ void walk_lut(const KernelParams& p, const Smem& sm, 
     if (!fold_each && final_fold && !outer) fold(clear_on_exit);
 }
 
+// The lane-private block lookup (LANE) over a range [first, first + count)
+// whose start, length and slice span are multiples of 256, two states a
+// thread.  The Gray indices of such a range are whole aligned blocks of
+// 256: the set of assignments whose bits 8 and up are the Gray code of one
+// of the blocks' numbers, with any bits 0-7.  The same set is walked as the
+// Gray code over every variable but 7 (compressed index c = t / 2 over the
+// blocks, variable v(i) = i for i < 7, i + 1 above) with variable 7 clear
+// (state A) and set (state B): both take every flip together, so the flip
+// rows, the loop and, variable 7 being below every cut parity (zq_lo >= 8),
+// the counters, the cut parities and the folds are shared, while each state
+// keeps its own form bits, A x, lookup slot and phase.  The sum of the range
+// is the same; the order of the terms within it is not.
+template <int NWN, int NWL, bool TWO, bool OUTER>
+__device__ __forceinline__ void walk_lut_pair(const KernelParams& p, const Smem& sm, uint64_t first,
+                                              uint64_t count, uint64_t span, uint64_t nslices,
+                                              uint64_t s_begin, uint64_t stride, bool fold_each,
+                                              bool clear_on_exit, bool final_fold, zw64& acc) {
+    constexpr int NW = NWN + NWL;
+    constexpr uint32_t RW = row_words(NWN, NWL);
+    constexpr uint32_t SW = seek_stride(NW);
+    const zw64* __restrict__ sT = sm.sT;
+    const uint64_t* __restrict__ sADJ = sm.sADJ;
+    const uint32_t* __restrict__ sADJw = reinterpret_cast<const uint32_t*>(sm.sADJ);
+    const uint32_t* __restrict__ sF = sm.sF;
+    const uint32_t* __restrict__ sS = sm.sS;
+    const uint64_t* __restrict__ sL = sm.sL;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t ts = p.tab_stride;
+    const uint32_t no = p.lut_no, nn = p.lut_nn, lsh = p.lut_shift;
+    const uint32_t mo = (1u << no) - 1u, mn = (1u << nn) - 1u;
+    const uint32_t na = TWO ? p.lut_na : no + nn, ma = (1u << na) - 1u;
+    const uint64_t* __restrict__ sLB = sL + (1u << na);
+    const uint64_t* __restrict__ qlut = TWO ? sLB + (1u << (no + nn - na)) : sL + (1u << (no + nn));
+    constexpr uint32_t tsh = kLaneRowShift, cm = (8u << tsh) - 1u;
+    uint32_t* const lbase = sm.sH + warp * ((uint32_t)kLaneCounters * 32u);
+    unsigned char* const wlb = reinterpret_cast<unsigned char*>(lbase + lane);
+    const uint32_t rb = p.lane_row_bytes;
+    auto lctr = [&](uint32_t idx) { return reinterpret_cast<uint32_t*>(wlb + idx * rb); };
+
+    // a lane's counters summed over the 32 lanes (as walk_lut's fold)
+    auto fold = [&](bool clear) {
+        __syncwarp();
+        const uint32_t tm = (1u << tsh) - 1u;
+        for (uint32_t i = lane; i <= cm; i += 32) {
+            if ((i & tm) >= ts) continue;
+            uint4* row = reinterpret_cast<uint4*>(lbase + i * 32u);
+            uint32_t c = 0;
+#pragma unroll
+            for (uint32_t j = 0; j < 8; j++) {
+                const uint4 v = row[(j + lane) & 7u];
+                c += v.x + v.y + v.z + v.w;
+            }
+            if (c) acc = zw_madd32(acc, lds_zw(sT + (i >> tsh) * ts + (i & tm)), c);
+            if (clear) {
+#pragma unroll
+                for (uint32_t j = 0; j < 8; j++) row[(j + lane) & 7u] = make_uint4(0, 0, 0, 0);
+            }
+        }
+        __syncwarp();
+    };
+
+    struct State {
+        uint32_t L[NW];
+        uint32_t a, us, Jl;
+    };
+    auto node_count = [](const State& w) {
+        uint32_t M = 0;
+#pragma unroll
+        for (int v = 0; v < NWN; v++) M += __popc(w.L[v]);
+        return M;
+    };
+    auto step = [&](State& w, const uint32_t* f, uint32_t du) {
+        uint32_t d0 = 0, x1 = 0;
+#pragma unroll
+        for (int v = 0; v < NWL; v++) {
+            d0 += __popc(w.L[NWN + v] & f[NW + v]);
+            x1 ^= w.L[NWN + v] & f[NW + NWL + v];
+        }
+        w.Jl += f[NW + 2 * NWL] - 2u * d0 - 4u * (uint32_t)__popc(x1);
+        w.us ^= du;
+#pragma unroll
+        for (int v = 0; v < NW; v++) w.L[v] ^= f[v];
+    };
+    auto lookup = [&](const State& w, uint32_t& lo, uint32_t& hi) {
+        if constexpr (TWO) {
+            const uint2 e1 = *reinterpret_cast<const uint2*>(sL + (w.us & ma));
+            const uint2 e2 = *reinterpret_cast<const uint2*>(sLB + (w.us >> na));
+            const uint2 eq = *reinterpret_cast<const uint2*>(qlut + (w.a & 7u));
+            lo = e1.x + e2.x + eq.x;
+            hi = e1.y + e2.y + eq.y;
+        } else {
+            const uint64_t e = sL[w.us] + qlut[w.a & 7u];
+            lo = (uint32_t)e;
+            hi = (uint32_t)(e >> 32);
+        }
+    };
+    auto block8 = [&](State& w) {
+        uint32_t lo, hi;
+        lookup(w, lo, hi);
+        const uint32_t b0 = TWO ? (((w.Jl << tsh) & (7u << tsh)) | node_count(w))
+                                : ((w.Jl & 7u) << tsh) + node_count(w);
+        const uint32_t bx = b0 * 0x01010101u, mk = cm * 0x01010101u;
+        const uint32_t w0 = (lo + bx) & mk, w1 = (hi + bx) & mk;
+        atomicAdd(lctr(b0), 1u);
+        atomicAdd(lctr(__byte_perm(w0, 0u, 0x4440u)), 1u);
+        atomicAdd(lctr(__byte_perm(w0, 0u, 0x4441u)), 1u);
+        atomicAdd(lctr(__byte_perm(w0, 0u, 0x4442u)), 1u);
+        atomicAdd(lctr(w0 >> 24), 1u);
+        atomicAdd(lctr(__byte_perm(w1, 0u, 0x4440u)), 1u);
+        atomicAdd(lctr(__byte_perm(w1, 0u, 0x4441u)), 1u);
+        atomicAdd(lctr(__byte_perm(w1, 0u, 0x4442u)), 1u);
+#pragma unroll
+        for (int v = 0; v < NW; v++) w.L[v] ^= p.R[2][v];
+        w.Jl += hi >> 24;
+        w.a ^= (uint32_t)p.A4[2];
+        w.us ^= p.U4[2];
+    };
+    auto flip3 = [&](State& w) {
+        w.Jl += (w.a >> 1) & 4u;
+        w.a ^= (uint32_t)p.A4[3];
+        step(w, p.R[3], p.U4[3]);
+    };
+    auto load_row = [&](int i, uint32_t (&fr)[RW]) {
+#pragma unroll
+        for (uint32_t w4 = 0; w4 < RW; w4 += 4) {
+            const uint4 t4 = *reinterpret_cast<const uint4*>(sF + i * RW + w4);
+            fr[w4] = t4.x; fr[w4 + 1] = t4.y; fr[w4 + 2] = t4.z; fr[w4 + 3] = t4.w;
+        }
+    };
+    // state of compressed index c: the Gray code of c with a clear bit put
+    // in at variable 7
+    auto expand = [](uint64_t c) {
+        const uint64_t g = c ^ (c >> 1);
+        return (g & 127u) | ((g >> 7) << 8);
+    };
+
+    const uint64_t end = first + count;
+    for (uint64_t s0 = s_begin; s0 < nslices; s0 += stride) {
+        const uint64_t s = s0 + lane;
+        if (s < nslices) {
+            const uint64_t t = first + s * span;
+            const uint64_t tend = (end - t < span) ? end : t + span;
+            const uint64_t c0 = t >> 1, x = expand(c0);
+            // state A at x (as walk_lut's seek)
+            State A;
+#pragma unroll
+            for (int v = 0; v < NW; v++) A.L[v] = p.INV[v];
+            uint64_t a64 = 0;
+            uint32_t q = 0;
+            const uint32_t nnib = (p.k + 3) >> 2;
+            for (uint32_t b = 0; b < nnib; b++) {
+                const uint32_t v = (uint32_t)(x >> (4 * b)) & 15u;
+                const uint32_t* e = sS + (b * 16u + v) * SW;
+                uint32_t ev[SW];
+#pragma unroll
+                for (uint32_t w4 = 0; w4 < SW; w4 += 4) {
+                    const uint4 t4 = *reinterpret_cast<const uint4*>(e + w4);
+                    ev[w4] = t4.x; ev[w4 + 1] = t4.y; ev[w4 + 2] = t4.z; ev[w4 + 3] = t4.w;
+                }
+                q ^= ev[NW + 2] ^ ((uint32_t)__popc(v & (uint32_t)(a64 >> (4 * b))) & 1u);
+                a64 ^= ((uint64_t)ev[NW + 1] << 32) | ev[NW];
+#pragma unroll
+                for (int v2 = 0; v2 < NW; v2++) A.L[v2] ^= ev[v2];
+            }
+            A.a = (uint32_t)a64;
+            {
+                uint32_t P0 = 0, P1 = 0, X2 = 0;
+#pragma unroll
+                for (int v = 0; v < NWN; v++) X2 ^= A.L[v] & p.CB[v];
+#pragma unroll
+                for (int v = 0; v < NWL; v++) {
+                    const uint32_t u = A.L[NWN + v];
+                    P0 += __popc(u & p.C0[v]);
+                    P1 += __popc(u & p.C1[v]);
+                    X2 ^= u & p.C2[v];
+                }
+                A.Jl = P0 + 2u * P1 + 4u * ((uint32_t)__popc(X2) + q);
+            }
+            {
+                uint32_t u = (A.L[NWN] >> lsh) & mo;
+                if (NWN) u |= (A.L[0] & mn) << no;
+                A.us = TWO ? (lut_slot(u & ma) | (lut_slot(u >> na) << na)) : lut_slot(u);
+            }
+            // state B: A with variable 7 flipped
+            State B = A;
+            {
+                uint32_t fr[RW];
+                load_row(7, fr);
+                B.Jl += B.a >> 7 << 2;
+                B.a ^= sADJw[2 * 7];
+                step(B, fr, fr[NW + 2 * NWL] >> 8);
+            }
+            // the cut parities (variable 7 is below zq_lo: the same for B)
+            uint32_t zq = 0;
+            if (OUTER)
+                for (uint64_t m = x >> p.zq_lo; m; m &= m - 1)
+                    zq ^= __ldg(p.zqcol + p.zq_lo + (uint32_t)__ffsll((long long)m) - 1u);
+            zw64 fz = zw_zero();
+            if (OUTER) fz = ldg_zw(p.ftab + zq);
+            // the fold of the counts since the last change of the cut
+            // parities, both states' (walk_lut's flush)
+            auto flush = [&]() {
+                uint32_t s0_ = 0, s1 = 0, s2 = 0, s3 = 0;
+                for (uint32_t Mi = ts; Mi-- > 0;) {
+                    uint32_t c[8];
+                    unsigned char* ptr = reinterpret_cast<unsigned char*>(lctr(Mi));
+#pragma unroll
+                    for (uint32_t J = 0; J < 8; J++) {
+                        c[J] = *reinterpret_cast<uint32_t*>(ptr);
+                        *reinterpret_cast<uint32_t*>(ptr) = 0u;
+                        ptr += rb << tsh;
+                    }
+                    const uint32_t xs = s1 + s2;
+                    const uint32_t n0 = 0u - (xs + s3), n1 = s0_ - s2 - s3, n2 = s0_ + s1 - s3, n3 = s0_ + xs;
+                    s0_ = n0 + (c[0] - c[4]);
+                    s1 = n1 + (c[1] - c[5]);
+                    s2 = n2 + (c[2] - c[6]);
+                    s3 = n3 + (c[3] - c[7]);
+                }
+                const zw64 sum = zw_make((uint64_t)(int64_t)(int32_t)s0_, (uint64_t)(int64_t)(int32_t)s1,
+                                         (uint64_t)(int64_t)(int32_t)s2, (uint64_t)(int64_t)(int32_t)s3);
+                acc = zw_add(acc, zw_mul(sum, fz));
+            };
+            // blocks of 16 compressed steps (the slice's [c0, tend / 2) holds
+            // a multiple of 128 of them): variables 0-2 by two lookups each,
+            // variable 3 between them, then variable v(ctz(c + 16))
+            uint32_t nb = (uint32_t)(((tend >> 1) - c0) >> 4);
+            uint32_t cl = (uint32_t)c0, ch = (uint32_t)(c0 >> 32);
+            for (;;) {
+                cl += 16u;
+                if (cl == 0u) ch++;
+                const bool more = --nb != 0u;   // c + 16 < end / 2 <= 2^(k-1): ctz < k - 1
+                const int ic = !more ? 0 : (cl ? __ffs(cl) - 1 : 31 + __ffs(ch));
+                const int i = ic < 7 ? ic : ic + 1;
+                uint32_t fr[RW];
+                load_row(i, fr);
+                const uint32_t adj = sADJw[2 * i];
+                block8(A);
+                block8(B);
+                flip3(A);
+                flip3(B);
+                block8(A);
+                block8(B);
+                if (!more) break;
+                if (OUTER && (uint32_t)i >= p.zq_lo) {
+                    const uint32_t dz = __ldg(p.zqcol + i);
+                    if (dz) {
+                        flush();
+                        zq ^= dz;
+                        fz = ldg_zw(p.ftab + zq);
+                    }
+                }
+                // (bits above 2: only J mod 8 is used; a flip of a variable
+                // >= 32 takes its bit of A x from the state before it)
+                if (i < 32) {
+                    A.Jl += A.a >> i << 2;
+                    B.Jl += B.a >> i << 2;
+                } else {
+                    const uint64_t xa = expand((((uint64_t)ch << 32) | cl) - 1u);
+                    A.Jl += ((uint32_t)__popcll(sADJ[i] & xa) & 1u) << 2;
+                    B.Jl += ((uint32_t)__popcll(sADJ[i] & (xa | 128u)) & 1u) << 2;
+                }
+                A.a ^= adj;
+                B.a ^= adj;
+                step(A, fr, fr[NW + 2 * NWL] >> 8);
+                step(B, fr, fr[NW + 2 * NWL] >> 8);
+            }
+            if (OUTER) flush();
+        }
+        if (fold_each && !OUTER) fold(true);
+    }
+    if (!fold_each && final_fold && !OUTER) fold(clear_on_exit);
+}
+
 // final_fold false (counting variants with warp-shared counters, one slice
 // per thread): the counters are left for the caller to fold (see
 // fold_block_counters).
@@ -715,6 +991,13 @@ __device__ __forceinline__ void walk(const KernelParams& p, const Smem& sm, uint
                                      uint64_t s_begin, uint64_t stride, bool fold_each,
                                      bool clear_on_exit, bool final_fold, Z& acc) {
     if constexpr (HIST >= 4) {
+        if constexpr (HIST >= 5 && std::is_same<Z, zw64>::value) {
+            if (p.pair_walk) {   // (the same for the whole launch)
+                walk_lut_pair<NWN, NWL, HIST == 6, OUTER>(p, sm, first, count, span, nslices, s_begin, stride,
+                                                          fold_each, clear_on_exit, final_fold, acc);
+                return;
+            }
+        }
         walk_lut<NWN, NWL, XTRA, HIST >= 5, HIST == 6, OUTER>(p, sm, first, count, span, nslices, s_begin,
                                                               stride, fold_each, clear_on_exit, final_fold, acc);
         return;

@@ -104,6 +104,11 @@ struct KernelParams {
     // (zxp_test_table_timeout).  The copies themselves are unchanged, so they
     // have landed long before the wait gives up.
     uint32_t extra_tx;
+    // Lane-private block lookup over a range whose start, length and slices
+    // are multiples of 256 (variable 7 below every cut parity): set at
+    // launch, every thread walks each slice as two states that differ in
+    // variable 7, along one Gray code of the other variables.
+    uint32_t pair_walk;
 };
 
 // each wait suspends the thread for a bounded time (about 4 us measured on a

@@ -461,3 +461,27 @@ def test_block_lookup_smallest_k(ctx):
             assert same_raw(g, o), (i, first, count)
         n9 += s.info["kernel_variant"] == 9
     assert n9 >= 5
+
+
+@pytest.mark.parametrize("seed,args,variant", [
+    (7000, dict(n_lin=6, n_quad=8, n_node=5, odd_nodes_only=True, density=0.05), 11),
+    (7003, dict(n_lin=28, n_quad=4, n_node=5, odd_nodes_only=True, density=0.3), 13),
+])
+def test_block_lookup_two_states_a_thread(ctx, seed, args, variant):
+    """Lane-private block lookup over whole aligned blocks of 256 Gray
+    indices with slices of 256 terms or more: each thread walks a slice as
+    two states that differ in variable 7, along one Gray code of the other
+    variables (another order of the same terms).  A 2^25-term range equals
+    the oracle, and the whole 2^27-term sum taken that way equals the same
+    sum split at an unaligned index (one state a thread there)."""
+    ps = zi.synthetic_ps(seed, 27, **args)
+    blob = ps.pack()
+    s = Z.zxp_scalar_from_tables(blob)
+    assert s.info["kernel_variant"] == variant
+    first, count = 1 << 26, 1 << 25
+    assert same_raw(Z.zxp_eval(ctx, s, first, count), oracle.ps_sum(blob, first, count, nthreads=NCPU))
+    n = 1 << 27
+    whole = Z.zxp_eval(ctx, s)
+    cut = n - 1000
+    parts = Z.zxp_zomega_add(Z.zxp_eval(ctx, s, 0, cut), Z.zxp_eval(ctx, s, cut, n - cut))
+    assert Z.zxp_zomega_canon(parts) == Z.zxp_zomega_canon(whole)

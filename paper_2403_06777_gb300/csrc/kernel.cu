@@ -83,9 +83,9 @@ cudaError_t sum_launch(const Plan& pl, const zw64* dtable, const zw64* dpv, cons
     kp.zqcol = dzq;
     kp.ftab = dftab;
     kp.extra_tx = test_extra_tx();
-    // two states a thread (kernel_core.cuh, walk_lut_pair): the lane-private
-    // block lookup over whole aligned blocks of 256 Gray indices, variable 7
-    // below every cut parity
+    // four states a thread (kernel_core.cuh, walk_lut_pair): the lane-private
+    // block lookup over whole aligned blocks of 256 Gray indices, variables 6
+    // and 7 below every cut parity
     kp.pair_walk = (hist_mode(pl) >= 5 && pl.kp.k >= 8 && (!pl.k_inner || pl.kp.zq_lo >= 8) &&
                     count && !(first & 255u) && !(count & 255u) && !(span & 255u))
                        ? 1u
@@ -141,7 +141,7 @@ void sum_shape(const Plan& pl, int sm_count, int max_grid_cap, uint64_t count, u
     uint64_t al = hist_mode(pl) >= 4 ? 16 : 8;
     if (pl.k_inner && pl.kp.zq_lo < 64) al = std::max<uint64_t>(al, 1ull << std::min<uint32_t>(pl.kp.zq_lo, 16));
     // (lane-private block lookup: slices of whole blocks of 256, which the
-    // walk takes two states at a time)
+    // walk takes four states at a time)
     if (hist_mode(pl) >= 5 && sp >= 256) al = std::max<uint64_t>(al, 256);
     sp = (sp + al - 1) & ~(al - 1);
     if (sp < 64) sp = 64;

@@ -105,9 +105,9 @@ struct KernelParams {
     // have landed long before the wait gives up.
     uint32_t extra_tx;
     // Lane-private block lookup over a range whose start, length and slices
-    // are multiples of 256 (variable 7 below every cut parity): set at
-    // launch, every thread walks each slice as two states that differ in
-    // variable 7, along one Gray code of the other variables.
+    // are multiples of 256 (variables 6 and 7 below every cut parity): set
+    // at launch, every thread walks each slice as four states that differ in
+    // variables 6 and 7, along one Gray code of the other variables.
     uint32_t pair_walk;
 };
 

@@ -467,11 +467,11 @@ def test_block_lookup_smallest_k(ctx):
     (7000, dict(n_lin=6, n_quad=8, n_node=5, odd_nodes_only=True, density=0.05), 11),
     (7003, dict(n_lin=28, n_quad=4, n_node=5, odd_nodes_only=True, density=0.3), 13),
 ])
-def test_block_lookup_two_states_a_thread(ctx, seed, args, variant):
+def test_block_lookup_four_states_a_thread(ctx, seed, args, variant):
     """Lane-private block lookup over whole aligned blocks of 256 Gray
     indices with slices of 256 terms or more: each thread walks a slice as
-    two states that differ in variable 7, along one Gray code of the other
-    variables (another order of the same terms).  A 2^25-term range equals
+    four states that differ in variables 6 and 7, along one Gray code of the
+    other variables (another order of the same terms).  A 2^25-term range equals
     the oracle, and the whole 2^27-term sum taken that way equals the same
     sum split at an unaligned index (one state a thread there)."""
     ps = zi.synthetic_ps(seed, 27, **args)

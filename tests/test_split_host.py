@@ -47,3 +47,16 @@ def test_large_workloads_split_for_the_block_lookup(seed):
     assert info["inner_bits"] <= 24 and info["k"] <= 34, info
     if seed == 0:
         assert (info["k"], info["k_inner"], info["inner_bits"]) == (30, 21, 22), info
+
+
+@pytest.mark.parametrize("max_inner,max_bits", [(10, 12), (16, 18), (22, 24)])
+def test_split_honours_its_limits(max_inner, max_bits):
+    """Whatever the cost estimates prefer, the kept split stays within the
+    limits asked for: inner parameters and index bits (inner parameters and
+    crossing forms)."""
+    w = zi.workload_large(0)
+    base = Z.zxp_compile(w.gates, w.n, w.out_bits, split=False)
+    sp = Z.zxp_scalar_split(base, max_inner=max_inner, max_index_bits=max_bits)
+    info = sp.info
+    assert 0 < info["k_inner"] <= max_inner and info["inner_bits"] <= max_bits, info
+    assert info["k"] + info["k_inner"] == base.info["k"]
